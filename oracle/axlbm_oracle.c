@@ -1,0 +1,447 @@
+/*
+ * axlbm_oracle.c -- plain, slow FP64 CPU oracle for the improved axisymmetric
+ * lattice Boltzmann scheme of Li, He, Tang and Tao (arXiv:1003.0282).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or calls
+ * this file; only the test-suite, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no code, header, table or helper with the CUDA
+ * library: the lattice tables below are re-declared here on purpose.
+ *
+ * What it computes (one time step, t -> t+1, for every node):
+ *   1. macroscopic variables from the pre-collision distributions
+ *        u_theta = sum g / rho0                       (Sec. III C, after Eq. 54)
+ *        T       = sum h                              (temperature extension)
+ *        u_r     = (sum e_r f + F_ext,r/2) / (sum f + mu0/r^2)   (Eq. 16 with the
+ *                  half-force terms of Eq. 15 for the inertial and body forces)
+ *        u_z     = (sum e_z f + F_ext,z/2) / sum f   (Eq. 16)
+ *        rho     = sum f / (1 + u_r/(2r))            (Eq. 17)
+ *   2. equilibrium (Eq. 6), force F_r = -2 mu0 u_r / r^2 + rho0 u_theta^2 / r,
+ *      F_z = a(t) + rho0 g beta (T - T_ref)           (Eq. 12, Sec. III C)
+ *      source S_a = [3 (e_a - u).F / rho - u_r / r] f^eq_a            (Eq. 12)
+ *   3. BGK collision with the radius-dependent rate                   (Eq. 13)
+ *        f*_a = f_a - w_a (f_a - f^eq_a) + (1 - w_a/2) S_a,
+ *        w_a  = (1 + tau e_ar / r) / (tau + 1/2)
+ *   4. D2Q4 azimuthal distribution                              (Eqs. 53-54)
+ *        g*_a = g_a - wg_a (g_a - g^eq_a) + S^g_a,
+ *        g^eq_a = rho0 u_theta / 4 (1 + 2 e_a.u),
+ *        S^g_a = -(1/r)(2 u_r + nu / r) g^eq_a,
+ *        wg_a = (1 + tau_g e_ar / r)/(tau_g + 1/2), tau_g = 2 tau / 3, nu = tau_g / 2
+ *      and the temperature distribution built the same way (not in the paper):
+ *        h*_a = h_a - wh_a (h_a - h^eq_a) - (u_r / r) h^eq_a,
+ *        h^eq_a = T / 4 (1 + 2 e_a.u), wh_a = (1 + tau_T e_ar / r)/(tau_T + 1/2)
+ *   5. push streaming into a second lattice, with the boundary rules below.
+ *
+ * tau here is the paper's tau (mu = tau rho c_s^2, omega = 1/(tau + 1/2),
+ * Eq. 8 and the line after Eq. 36); the caller passes the standard relaxation
+ * time tau_s = tau + 1/2 and the oracle subtracts the half.
+ *
+ * Grid: node (j, k) sits at r = r0 + j + 1/2, z = k + 1/2.  The inner face is
+ * r = r0 (the axis when r0 = 0), the outer face r = r0 + nr, the axial faces
+ * z = 0 and z = nz.  Boundary rules, applied to a population that leaves a
+ * fluid node towards a site outside the fluid:
+ *   - a site beyond a periodic face is the wrapped fluid node;
+ *   - a site beyond a solid face returns the population to its own node with
+ *     reversed velocity (half-way bounce-back).  For g the returned value is
+ *     -g* + rho0 u_w / 2 with u_w = Omega r at the crossing point (moving wall
+ *     or lid, anti-bounce-back); for h it is -h* + T_w / 2 on a Dirichlet face
+ *     and h* on an adiabatic face;
+ *   - a site beyond a mirror face (the axis, Sec. IV A "specular reflection";
+ *     a free surface) is the mirror image of a fluid node: the population
+ *     arrives there with its velocity mirrored; g changes sign across the axis
+ *     (u_theta is odd in r), h and f do not.
+ * A site outside in both r and z is solid if either face makes it solid.  On
+ * the mixed top face (a crystal disk r < r_split on a free surface) the rule is
+ * taken where the link crosses the face.
+ *
+ * Layout of every field: [population][k][j], j fastest, FP64.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 2
+
+/* inner face */
+#define ORC_AXIS 0
+#define ORC_INNER_WALL 1
+/* axial faces */
+#define ORC_PERIODIC 0
+#define ORC_WALL 1
+#define ORC_FREE 2
+#define ORC_MIXED 3 /* wall for r < r_split, free surface beyond (top only) */
+/* face ids */
+#define F_IN 0
+#define F_OUT 1
+#define F_LO 2
+#define F_HI 3
+
+typedef struct {
+    int32_t nr, nz;
+    int32_t inner;              /* ORC_AXIS or ORC_INNER_WALL */
+    int32_t z_lo, z_hi;         /* ORC_PERIODIC / ORC_WALL / ORC_FREE / ORC_MIXED */
+    int32_t swirl, temperature; /* 0 or 1 */
+    int32_t t_dirichlet[4];     /* per face: 1 = fixed T, 0 = adiabatic */
+    int32_t pad;
+    double r0;                  /* radius of the inner face */
+    double tau_s;               /* standard relaxation time = tau + 1/2 */
+    double tau_t_s;             /* same for the temperature distribution */
+    double rho0;
+    double az0, omega_t;        /* axial body force a(t) = az0 cos(omega_t t) */
+    double gbeta, t_ref;        /* Boussinesq: F_z += rho0 g beta (T - T_ref) */
+    double r_split;             /* ORC_MIXED: wall part for r < r_split */
+    double omega_w[4];          /* per face: angular velocity of the wall */
+    double t_w[4];              /* per face: wall temperature when Dirichlet */
+} orc_params;
+
+/* D2Q9, components (r, z): rest, four axis links, four diagonals (Eq. 6). */
+static const int CR[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CZ[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double WT[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+/* D2Q4 (Eq. 53). */
+static const int QR[4] = {1, 0, -1, 0};
+static const int QZ[4] = {0, 1, 0, -1};
+
+static int find9(int cr, int cz) {
+    for (int a = 0; a < 9; ++a)
+        if (CR[a] == cr && CZ[a] == cz) return a;
+    return -1;
+}
+static int find4(int cr, int cz) {
+    for (int a = 0; a < 4; ++a)
+        if (QR[a] == cr && QZ[a] == cz) return a;
+    return -1;
+}
+
+static double node_r(const orc_params* p, int j) { return p->r0 + j + 0.5; }
+
+int orc_validate(const orc_params* p) {
+    if (p->nr < 1 || p->nz < 1) return ORC_EINVAL;
+    if (!(p->tau_s > 0.5) || !(p->rho0 > 0.0)) return ORC_EINVAL;
+    if (p->inner == ORC_AXIS && p->r0 != 0.0) return ORC_EINVAL;
+    if (p->inner == ORC_INNER_WALL && !(p->r0 >= 0.0)) return ORC_EINVAL;
+    if (p->z_lo == ORC_MIXED) return ORC_EINVAL;
+    if ((p->z_lo == ORC_PERIODIC) != (p->z_hi == ORC_PERIODIC)) return ORC_EINVAL;
+    if (p->temperature && !(p->tau_t_s > 0.5)) return ORC_EINVAL;
+    return ORC_OK;
+}
+
+/* Moments of one node, Eqs. 15-17 with the half-force terms.  out[0..4] =
+ * rho, u_r, u_z, u_theta, T.  Returns sum f (used by the mass budget). */
+static double cell_moments(const orc_params* p, double r, double a_t, const double* f,
+                           const double* g, const double* h, double* out) {
+    const double tau = p->tau_s - 0.5;
+    const double mu0 = p->rho0 * tau / 3.0;
+    double s0 = 0.0, sr = 0.0, sz = 0.0;
+    for (int a = 0; a < 9; ++a) {
+        s0 += f[a];
+        sr += CR[a] * f[a];
+        sz += CZ[a] * f[a];
+    }
+    double uth = 0.0, temp = 0.0;
+    if (p->swirl) {
+        for (int a = 0; a < 4; ++a) uth += g[a];
+        uth /= p->rho0;
+    }
+    if (p->temperature) {
+        for (int a = 0; a < 4; ++a) temp += h[a];
+    }
+    const double fext_r = p->rho0 * uth * uth / r;
+    double fext_z = a_t;
+    if (p->temperature) fext_z += p->rho0 * p->gbeta * (temp - p->t_ref);
+    const double ur = (sr + 0.5 * fext_r) / (s0 + mu0 / (r * r));
+    const double uz = (sz + 0.5 * fext_z) / s0;
+    const double rho = s0 / (1.0 + 0.5 * ur / r);
+    out[0] = rho;
+    out[1] = ur;
+    out[2] = uz;
+    out[3] = uth;
+    out[4] = temp;
+    return s0;
+}
+
+/* Collision of one node at radius r and time-level force a_t.  fin/gin/hin are
+ * the pre-collision populations, fout/gout/hout receive the post-collision
+ * ones, mom (optional) the moments rho, u_r, u_z, u_theta, T. */
+void orc_collide_cell(const orc_params* p, double r, double a_t, const double* fin,
+                      const double* gin, const double* hin, double* fout, double* gout,
+                      double* hout, double* mom) {
+    double m[5];
+    cell_moments(p, r, a_t, fin, gin, hin, m);
+    const double rho = m[0], ur = m[1], uz = m[2], uth = m[3], temp = m[4];
+    const double tau = p->tau_s - 0.5;
+    const double mu0 = p->rho0 * tau / 3.0;
+
+    /* force of Eq. 12 plus the inertial force and the body forces */
+    const double fr = -2.0 * mu0 * ur / (r * r) + p->rho0 * uth * uth / r;
+    double fz = a_t;
+    if (p->temperature) fz += p->rho0 * p->gbeta * (temp - p->t_ref);
+
+    const double usq = ur * ur + uz * uz;
+    for (int a = 0; a < 9; ++a) {
+        const double eu = CR[a] * ur + CZ[a] * uz;
+        const double feq = WT[a] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+        const double src = (3.0 * ((CR[a] - ur) * fr + (CZ[a] - uz) * fz) / rho - ur / r) * feq;
+        const double om = (1.0 + tau * CR[a] / r) / (tau + 0.5);
+        fout[a] = fin[a] - om * (fin[a] - feq) + (1.0 - 0.5 * om) * src;
+    }
+    if (p->swirl) {
+        const double taug = 2.0 * tau / 3.0;
+        const double nu = taug / 2.0;
+        for (int a = 0; a < 4; ++a) {
+            const double eu = QR[a] * ur + QZ[a] * uz;
+            const double geq = p->rho0 * uth / 4.0 * (1.0 + 2.0 * eu);
+            const double sg = -(1.0 / r) * (2.0 * ur + nu / r) * geq;
+            const double om = (1.0 + taug * QR[a] / r) / (taug + 0.5);
+            gout[a] = gin[a] - om * (gin[a] - geq) + sg;
+        }
+    }
+    if (p->temperature) {
+        const double taut = p->tau_t_s - 0.5;
+        for (int a = 0; a < 4; ++a) {
+            const double eu = QR[a] * ur + QZ[a] * uz;
+            const double heq = temp / 4.0 * (1.0 + 2.0 * eu);
+            const double sh = -(ur / r) * heq;
+            const double om = (1.0 + taut * QR[a] / r) / (taut + 0.5);
+            hout[a] = hin[a] - om * (hin[a] - heq) + sh;
+        }
+    }
+    if (mom) memcpy(mom, m, sizeof m);
+}
+
+/* ---- boundary classification of a lattice site ---------------------------------- */
+
+typedef struct {
+    int solid;  /* 1: beyond a solid face */
+    int face;   /* solid face id */
+    int j, k;   /* fluid node (possibly wrapped / mirror image) */
+    int fr, fz; /* 1: reached through a mirror in r / in z */
+} orc_site;
+
+/* Kind of the top face where a link crosses it at radius rc.  On a mixed top
+ * the part r < r_split is a wall (the crystal disk), the rest a free surface.
+ * Classifying by the crossing point (not by the site beyond the face) keeps the
+ * two diagonals that cross at one corner point under one rule, so streaming
+ * stays a one-to-one map of populations. */
+static int top_kind_at(const orc_params* p, double rc) {
+    if (p->z_hi != ORC_MIXED) return p->z_hi;
+    return rc < p->r_split ? ORC_WALL : ORC_FREE;
+}
+
+/* Where the population leaving fluid node (j, k) with velocity (cr, cz) lands. */
+static orc_site classify(const orc_params* p, int j, int k, int cr, int cz) {
+    orc_site s;
+    s.solid = 0;
+    s.face = -1;
+    s.j = j + cr;
+    s.k = k + cz;
+    s.fr = 0;
+    s.fz = 0;
+    if (s.k < 0 || s.k >= p->nz) {
+        const int face = s.k < 0 ? F_LO : F_HI;
+        const int kind = s.k < 0 ? p->z_lo : top_kind_at(p, node_r(p, j) + 0.5 * cr);
+        if (kind == ORC_PERIODIC) {
+            s.k = ((s.k % p->nz) + p->nz) % p->nz;
+        } else if (kind == ORC_WALL) {
+            s.solid = 1;
+            s.face = face;
+            return s;
+        } else { /* free surface: mirror in z */
+            s.k = s.k < 0 ? -1 - s.k : 2 * p->nz - 1 - s.k;
+            s.fz = 1;
+        }
+    }
+    if (s.j < 0) {
+        if (p->inner == ORC_AXIS) {
+            s.j = -1 - s.j;
+            s.fr = 1;
+        } else {
+            s.solid = 1;
+            s.face = F_IN;
+        }
+    } else if (s.j >= p->nr) {
+        s.solid = 1;
+        s.face = F_OUT;
+    }
+    return s;
+}
+
+/* azimuthal wall velocity where a D2Q4 link from column j crosses face `face` */
+static double wall_uth(const orc_params* p, int face, int j) {
+    switch (face) {
+        case F_IN: return p->omega_w[F_IN] * p->r0;
+        case F_OUT: return p->omega_w[F_OUT] * (p->r0 + p->nr);
+        default: return p->omega_w[face] * node_r(p, j);
+    }
+}
+
+/* Streaming of the post-collision lattice (fp, gp, hp) into (fn, gn, hn). */
+void orc_stream(const orc_params* p, const double* fp, const double* gp, const double* hp,
+                double* fn, double* gn, double* hn) {
+    const int nr = p->nr, nz = p->nz;
+    const size_t n = (size_t)nr * nz;
+    for (int k = 0; k < nz; ++k) {
+        for (int j = 0; j < nr; ++j) {
+            const size_t x = (size_t)k * nr + j;
+            for (int a = 0; a < 9; ++a) {
+                const double v = fp[a * n + x];
+                orc_site s = classify(p, j, k, CR[a], CZ[a]);
+                if (s.solid) {
+                    fn[find9(-CR[a], -CZ[a]) * n + x] = v;
+                } else {
+                    const int b = find9(s.fr ? -CR[a] : CR[a], s.fz ? -CZ[a] : CZ[a]);
+                    fn[b * n + (size_t)s.k * nr + s.j] = v;
+                }
+            }
+            if (p->swirl) {
+                for (int a = 0; a < 4; ++a) {
+                    const double v = gp[a * n + x];
+                    orc_site s = classify(p, j, k, QR[a], QZ[a]);
+                    if (s.solid) {
+                        gn[find4(-QR[a], -QZ[a]) * n + x] =
+                            -v + 0.5 * p->rho0 * wall_uth(p, s.face, j);
+                    } else {
+                        const int b = find4(s.fr ? -QR[a] : QR[a], s.fz ? -QZ[a] : QZ[a]);
+                        gn[b * n + (size_t)s.k * nr + s.j] = s.fr ? -v : v;
+                    }
+                }
+            }
+            if (p->temperature) {
+                for (int a = 0; a < 4; ++a) {
+                    const double v = hp[a * n + x];
+                    orc_site s = classify(p, j, k, QR[a], QZ[a]);
+                    if (s.solid) {
+                        const double out =
+                            p->t_dirichlet[s.face] ? -v + 0.5 * p->t_w[s.face] : v;
+                        hn[find4(-QR[a], -QZ[a]) * n + x] = out;
+                    } else {
+                        const int b = find4(s.fr ? -QR[a] : QR[a], s.fz ? -QZ[a] : QZ[a]);
+                        hn[b * n + (size_t)s.k * nr + s.j] = v;
+                    }
+                }
+            }
+        }
+    }
+}
+
+static double force_at(const orc_params* p, int64_t t) {
+    return p->az0 * cos(p->omega_t * (double)t);
+}
+
+/* n time steps starting at time t0; f, g, h are updated in place. */
+int orc_step(const orc_params* p, int64_t t0, int64_t nsteps, double* f, double* g, double* h) {
+    if (orc_validate(p) != ORC_OK) return ORC_EINVAL;
+    const size_t n = (size_t)p->nr * p->nz;
+    double* fp = (double*)calloc(9 * n, sizeof(double));
+    double* gp = (double*)calloc(4 * n, sizeof(double));
+    double* hp = (double*)calloc(4 * n, sizeof(double));
+    if (!fp || !gp || !hp) {
+        free(fp);
+        free(gp);
+        free(hp);
+        return ORC_ENOMEM;
+    }
+    double fi[9], fo[9], gi[4], go[4], hi[4], ho[4];
+    for (int64_t s = 0; s < nsteps; ++s) {
+        const double a_t = force_at(p, t0 + s);
+        for (int k = 0; k < p->nz; ++k) {
+            for (int j = 0; j < p->nr; ++j) {
+                const size_t x = (size_t)k * p->nr + j;
+                for (int a = 0; a < 9; ++a) fi[a] = f[a * n + x];
+                for (int a = 0; a < 4; ++a) {
+                    gi[a] = p->swirl ? g[a * n + x] : 0.0;
+                    hi[a] = p->temperature ? h[a * n + x] : 0.0;
+                }
+                orc_collide_cell(p, node_r(p, j), a_t, fi, gi, hi, fo, go, ho, NULL);
+                for (int a = 0; a < 9; ++a) fp[a * n + x] = fo[a];
+                for (int a = 0; a < 4; ++a) {
+                    if (p->swirl) gp[a * n + x] = go[a];
+                    if (p->temperature) hp[a * n + x] = ho[a];
+                }
+            }
+        }
+        orc_stream(p, fp, gp, hp, f, g, h);
+    }
+    free(fp);
+    free(gp);
+    free(hp);
+    return ORC_OK;
+}
+
+/* Macroscopic fields at time t: out is [5][nz][nr] (rho, u_r, u_z, u_theta, T). */
+int orc_moments(const orc_params* p, int64_t t, const double* f, const double* g,
+                const double* h, double* out) {
+    if (orc_validate(p) != ORC_OK) return ORC_EINVAL;
+    const size_t n = (size_t)p->nr * p->nz;
+    const double a_t = force_at(p, t);
+    double fi[9], gi[4] = {0, 0, 0, 0}, hi[4] = {0, 0, 0, 0}, m[5];
+    for (int k = 0; k < p->nz; ++k) {
+        for (int j = 0; j < p->nr; ++j) {
+            const size_t x = (size_t)k * p->nr + j;
+            for (int a = 0; a < 9; ++a) fi[a] = f[a * n + x];
+            for (int a = 0; a < 4; ++a) {
+                if (p->swirl) gi[a] = g[a * n + x];
+                if (p->temperature) hi[a] = h[a * n + x];
+            }
+            cell_moments(p, node_r(p, j), a_t, fi, gi, hi, m);
+            for (int q = 0; q < 5; ++q) out[q * n + x] = m[q];
+        }
+    }
+    return ORC_OK;
+}
+
+/* Equilibrium initialisation from macroscopic fields fields[5][nz][nr]
+ * (rho, u_r, u_z, u_theta, T): f = f^eq (Eq. 6), g = g^eq, h = h^eq (Eq. 54). */
+int orc_equilibrium(const orc_params* p, const double* fields, double* f, double* g,
+                    double* h) {
+    if (orc_validate(p) != ORC_OK) return ORC_EINVAL;
+    const size_t n = (size_t)p->nr * p->nz;
+    for (size_t x = 0; x < n; ++x) {
+        const double rho = fields[x], ur = fields[n + x], uz = fields[2 * n + x];
+        const double uth = fields[3 * n + x], temp = fields[4 * n + x];
+        const double usq = ur * ur + uz * uz;
+        for (int a = 0; a < 9; ++a) {
+            const double eu = CR[a] * ur + CZ[a] * uz;
+            f[a * n + x] = WT[a] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+        }
+        for (int a = 0; a < 4; ++a) {
+            const double eu = QR[a] * ur + QZ[a] * uz;
+            if (p->swirl) g[a * n + x] = p->rho0 * uth / 4.0 * (1.0 + 2.0 * eu);
+            if (p->temperature) h[a * n + x] = temp / 4.0 * (1.0 + 2.0 * eu);
+        }
+    }
+    return ORC_OK;
+}
+
+/* Check quantities at time t: mass = sum of all f (row-major order), budget =
+ * sum of rho u_r / r (the mass the next collision removes), speed[nz][nr] =
+ * sqrt(u_r^2 + u_z^2) for the convergence test of Eq. 57. */
+int orc_stats(const orc_params* p, int64_t t, const double* f, const double* g,
+              const double* h, double* mass, double* budget, double* speed) {
+    if (orc_validate(p) != ORC_OK) return ORC_EINVAL;
+    const size_t n = (size_t)p->nr * p->nz;
+    const double a_t = force_at(p, t);
+    double fi[9], gi[4] = {0, 0, 0, 0}, hi[4] = {0, 0, 0, 0}, m[5];
+    double msum = 0.0, bsum = 0.0;
+    for (int k = 0; k < p->nz; ++k) {
+        for (int j = 0; j < p->nr; ++j) {
+            const size_t x = (size_t)k * p->nr + j;
+            for (int a = 0; a < 9; ++a) fi[a] = f[a * n + x];
+            for (int a = 0; a < 4; ++a) {
+                if (p->swirl) gi[a] = g[a * n + x];
+                if (p->temperature) hi[a] = h[a * n + x];
+            }
+            msum += cell_moments(p, node_r(p, j), a_t, fi, gi, hi, m);
+            bsum += m[0] * m[1] / node_r(p, j);
+            if (speed) speed[x] = sqrt(m[1] * m[1] + m[2] * m[2]);
+        }
+    }
+    *mass = msum;
+    *budget = bsum;
+    return ORC_OK;
+}
+
+int orc_abi_version(void) { return 1; }

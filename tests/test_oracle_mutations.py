@@ -1,0 +1,74 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a temporary copy of the oracle's C source (a
+dropped term, a flipped sign, a wrong factor, a missed mirror), builds it with
+gcc, and runs the pin tests against it in a subprocess.  The case passes when
+at least one pin fails.  Nothing here touches the GPU or the CUDA library.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "axlbm_oracle.c")
+
+MUTATIONS = {
+    "half force dropped from u_z (Eq. 15)":
+        ("const double uz = (sz + 0.5 * fext_z) / s0;", "const double uz = sz / s0;"),
+    "sign of the radial rate term (Eq. 13)":
+        ("(1.0 + tau * CR[a] / r) / (tau + 0.5)", "(1.0 - tau * CR[a] / r) / (tau + 0.5)"),
+    "mu/r^2 dropped from the u_r denominator (Eq. 16)":
+        ("/ (s0 + mu0 / (r * r));", "/ s0;"),
+    "sign in the density (Eq. 17)":
+        ("s0 / (1.0 + 0.5 * ur / r)", "s0 / (1.0 - 0.5 * ur / r)"),
+    "sign of u_r/r in the source (Eq. 12)":
+        ("- ur / r) * feq;", "+ ur / r) * feq;"),
+    "factor 2 in F_r (Eq. 12)":
+        ("const double fr = -2.0 * mu0", "const double fr = -1.0 * mu0"),
+    "inertial force dropped (Sec. III C)":
+        ("+ p->rho0 * uth * uth / r;\n    double fz", ";\n    double fz"),
+    "second-order equilibrium coefficient (Eq. 6)":
+        ("4.5 * eu * eu - 1.5 * usq);\n        const double src",
+         "3.0 * eu * eu - 1.5 * usq);\n        const double src"),
+    "trapezoidal factor of the source (Eq. 13)":
+        ("(1.0 - 0.5 * om) * src;", "src;"),
+    "nu/r term of S^g dropped (Eq. 54)":
+        ("(2.0 * ur + nu / r) * geq", "(2.0 * ur) * geq"),
+    "tau_g = tau instead of 2 tau / 3":
+        ("const double taug = 2.0 * tau / 3.0;", "const double taug = tau;"),
+    "g not odd across the axis":
+        ("= s.fr ? -v : v;", "= v;"),
+    "moving-wall term doubled":
+        ("-v + 0.5 * p->rho0 * wall_uth", "-v + 1.0 * p->rho0 * wall_uth"),
+    "temperature source dropped":
+        ("const double sh = -(ur / r) * heq;", "const double sh = 0.0 * heq;"),
+    "temperature rate without the radial term":
+        ("(1.0 + taut * QR[a] / r) / (taut + 0.5)", "1.0 / (taut + 0.5)"),
+    "axis reflection without the r flip":
+        ("find9(s.fr ? -CR[a] : CR[a], s.fz ? -CZ[a] : CZ[a])", "find9(CR[a], s.fz ? -CZ[a] : CZ[a])"),
+    "mixed top classified by node instead of crossing point":
+        ("top_kind_at(p, node_r(p, j) + 0.5 * cr)", "top_kind_at(p, node_r(p, j))"),
+    "u_theta not divided by rho0":
+        ("        uth /= p->rho0;\n", ""),
+    "sign of the buoyancy force":
+        ("fz += p->rho0 * p->gbeta * (temp - p->t_ref);", "fz -= p->rho0 * p->gbeta * (temp - p->t_ref);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor not found: {name}"
+    mutated = tmp_path / "oracle_mutant.c"
+    mutated.write_text(src.replace(old, new, 1))
+    lib = tmp_path / "liboracle_mutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(lib), str(mutated), "-lm"],
+                   check=True)
+    env = dict(os.environ, AXLBM_ORACLE_LIB=str(lib))
+    res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                          os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert res.returncode != 0, f"no pin caught: {name}\n{res.stdout[-2000:]}"
