@@ -1,0 +1,278 @@
+"""Throughput benchmark of the axisymmetric lattice Boltzmann hot path.
+
+One benchmark step = one axlbm_step call of --inner lattice time steps over
+the whole workload (bulk collide-and-stream, boundary ring, and the check
+step with its FP64 reductions that ends every call).  The metric is MLUPS:
+million lattice-node updates per second, whole job.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Default workload: a Hagen-Poiseuille pipe of 4096 x 8192 nodes (D2Q9, FP32
+arithmetic, FP32 deviation storage), 2.4 GB of populations -- far larger than
+the 129 MB L2, so no cache flush is needed between steps.  Multi-GPU runs are
+independent replicas of the same pipe (one domain does not shard), so the
+scaling is weak.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# DRAM traffic of the bulk kernel from the ncu capture summarised in profiles/:
+# (dram__bytes_read.sum + dram__bytes_write.sum) / algorithmic bytes of the
+# captured launch, keyed by kernel and the SHA-256 prefix of the kernel source
+# at capture time.  Reported as null once the source has changed.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--inner", type=int, default=50, help="lattice time steps per benchmark step")
+    p.add_argument("--nr", type=int, default=4096)
+    p.add_argument("--nz", type=int, default=8192)
+    p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("ops_impl.cuh", "lattice.cuh"):
+        with open(os.path.join(ROOT, "paper_1003_0282_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+        return False
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, v in enumerate(flags) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(pb_full, inner: int, budget_s: float = 12.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    a 256 x 512 section of the same pipe, advanced until ~budget_s of CPU time."""
+    import oracle
+    from paper_1003_0282_gb300 import inputs as I
+
+    sample = I.hagen_poiseuille(nr=256, nz=512, tau=pb_full.tau, umax=0.01)
+    st = oracle.rest_state(sample)
+    oracle.step(st, 2)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        oracle.step(st, inner)
+        steps += inner
+    dt = time.perf_counter() - t0
+    return {"value": sample.cells * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, pipe section 256x512 nodes, {steps} lattice steps, {dt:.1f} s, single thread"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores, one bounded
+    sample of the workload per benchmark step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1003_0282_gb300 import inputs as I
+
+    pb = I.large_pipe(nr=args.nr, nz=args.nz)
+    sample = I.hagen_poiseuille(nr=128, nz=128, tau=pb.tau, umax=0.01)
+    st = oracle.rest_state(sample)
+    inner = max(1, min(args.inner, 10))
+    for _ in range(args.warmup):
+        oracle.step(st, inner)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step(st, inner)
+    dt = time.perf_counter() - t0
+    value = sample.cells * inner * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"pipe {args.nr}x{args.nz} D2Q9 (bounded sample 128x128, {inner} lattice steps per step)",
+                   "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"pipe section 128x128 nodes x {inner} lattice steps per benchmark step"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    from paper_1003_0282_gb300 import axlbm as B
+    from paper_1003_0282_gb300 import inputs as I
+
+    pb = I.large_pipe(nr=args.nr, nz=args.nz)
+    fields = torch.tensor(I.random_fields(pb.nr, pb.nz, seed=1000 + rank, du=1e-3, duth=0.0), dtype=torch.float32,
+                          device="cuda")
+    dom = B.Domain(pb, args.precision)
+    dom.set_fields(fields)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        dom.step(args.inner)
+    barrier()
+    B.axlbm_kernel_timing(dom.handle, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            dom.step(args.inner)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    bulk_n, bulk_ms, bulk_bytes, all_launches = B.axlbm_kernel_times(dom.handle)
+    B.axlbm_kernel_timing(dom.handle, False)
+    res, mass, _ = dom.residual()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    updates = pb.cells * args.inner * args.steps * world
+    value = updates / (ms / 1e3) / 1e6
+
+    # end to end through the C ABI with pinned host buffers: fields in, moments out
+    host_in = torch.empty((5, pb.nz, pb.nr), dtype=torch.float64, pin_memory=True)
+    host_in.copy_(torch.from_numpy(I.random_fields(pb.nr, pb.nz, seed=2000 + rank, du=1e-3, duth=0.0)))
+    host_out = torch.empty((3, pb.nz, pb.nr), dtype=torch.float32, pin_memory=True)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        B.axlbm_set_fields(dom.handle, host_in.data_ptr(), B.F64, 0)
+        dom.step(args.inner)
+        B.axlbm_moments(dom.handle, B.RHO | B.UR | B.UZ, host_out.data_ptr(), B.F32, 0)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = pb.cells * args.inner * args.e2e_steps * world / e2e_s / 1e6
+    dom.close()
+
+    if rank == 0:
+        peak, peak_kind = peaks()
+        achieved = bulk_bytes / (bulk_ms / 1e3) / 1e9 if bulk_ms > 0 else 0.0
+        sha = kernel_source_sha()
+        key = f"k_bulk {args.precision} d2q9"
+        tr = NCU_TRAFFIC.get(key)
+        traffic = None
+        if tr and tr["src_sha"] == sha:
+            traffic = tr["dram_per_alg_byte"] * bulk_bytes / max(bulk_n, 1)
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": f"pipe {pb.nr}x{pb.nz} D2Q9 (Hagen-Poiseuille force, axis + bounce-back wall, "
+                                   f"periodic z)", "precision": args.precision, "nodes": pb.cells,
+                       "lattice_steps_per_step": args.inner,
+                       "cache": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "k_bulk (even + odd AA steps)", "launches": bulk_n,
+                         "avg_launch_ms": bulk_ms / max(bulk_n, 1),
+                         "alg_bytes_per_launch": bulk_bytes / max(bulk_n, 1)},
+            "e2e": {"value": e2e_value, "unit": "MLUPS",
+                    "h2d_bytes_per_step": 5 * 8 * pb.cells, "d2h_bytes_per_step": 3 * 4 * pb.cells},
+            "gpu_launches": all_launches,
+            "clocks": clk.summary(),
+            "check": {"residual": res, "mass": mass},
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(pb, args.inner)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

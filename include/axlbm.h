@@ -1,0 +1,221 @@
+/*
+ * axlbm.h -- C ABI of the GB300 axisymmetric lattice Boltzmann library.
+ *
+ * The library advances the improved axisymmetric lattice Boltzmann scheme of
+ * Li, He, Tang and Tao (arXiv:1003.0282) on the (r, z) half-plane:
+ *   - D2Q9 distribution f with the BGK update of Eq. 13, the radius-dependent
+ *     rate w_a = (1 + tau e_ar / r) / (tau + 1/2) and the gradient-free source
+ *     S_a of Eq. 12; macroscopic variables from Eqs. 16-17 (Sec. III A);
+ *   - optional D2Q4 azimuthal-velocity distribution g of Eqs. 53-54 with the
+ *     inertial force rho0 u_theta^2 / r added to F_r (Sec. III C);
+ *   - optional D2Q4 temperature distribution h (not in the paper: built like
+ *     g, h^eq = T/4 (1 + 2 e.u), source -(u_r/r) h^eq, Boussinesq force
+ *     rho0 g beta (T - T_ref) added to F_z);
+ *   - the axis by specular reflection (Sec. IV A), half-way bounce-back walls,
+ *     lids turning about the axis (anti-bounce-back for g), free surfaces and
+ *     periodic ends.
+ *
+ * Conventions used by every call:
+ *   - Lattice units: dx = dt = 1, c_s^2 = 1/3 (Eq. 6).
+ *   - Node (j, k), 0 <= j < nr, 0 <= k < nz, sits at r = r0 + j + 1/2,
+ *     z = k + 1/2.  The inner face is r = r0 (the axis when r0 = 0), the outer
+ *     face r = r0 + nr, the axial faces z = 0 ("lo") and z = nz ("hi").
+ *   - tau arguments are the standard BGK relaxation time tau_s; the paper's
+ *     tau (mu = tau rho c_s^2, Eq. 8) is tau_s - 1/2.
+ *   - Host-facing arrays are dense, C order, [field or population][k][j]
+ *     with j fastest.  D2Q9 order (r, z components): 0 (0,0), 1 (1,0),
+ *     2 (0,1), 3 (-1,0), 4 (0,-1), 5 (1,1), 6 (-1,1), 7 (-1,-1), 8 (1,-1).
+ *     D2Q4 order: 0 (1,0), 1 (0,1), 2 (-1,0), 3 (0,-1).  Macroscopic fields:
+ *     0 rho, 1 u_r, 2 u_z, 3 u_theta, 4 T.
+ *   - Errors: every call returns a status and never aborts or prints.  The
+ *     text of the last error on a handle is kept on it (axlbm_last_error).
+ *     A CUDA error inside a call returns AXLBM_ECUDA.
+ *   - Streams: work is queued on the stream given to axlbm_create (0 = the
+ *     legacy default stream).  Calls that return data to the host synchronise
+ *     that stream; the others are asynchronous.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef AXLBM_H
+#define AXLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define AXLBM_API __attribute__((visibility("default")))
+#else
+#define AXLBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AXLBM_ABI_VERSION 1
+
+typedef enum {
+    AXLBM_OK = 0,
+    AXLBM_EINVAL = 1,       /* bad argument or inconsistent problem description */
+    AXLBM_ENOMEM = 2,       /* device allocation failed or caller memory too small */
+    AXLBM_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    AXLBM_ENONFINITE = 4,   /* the last check found a NaN or Inf in rho or u */
+    AXLBM_ETIMEOUT = 5,     /* a bounded device wait gave up */
+    AXLBM_EUNSUPPORTED = 6  /* valid request this build does not provide */
+} axlbm_status;
+
+/* Storage of the distributions.  Collision arithmetic is FP64 for AXLBM_FP64
+ * and FP32 otherwise.  Every mode stores the deviation of each population
+ * from its rest value (f_a - w_a rho0, g_a, h_a - T_ref/4); the 16-bit modes
+ * halve the bytes moved per cell. */
+typedef enum {
+    AXLBM_FP64 = 0,
+    AXLBM_FP32 = 1,
+    AXLBM_FP16_DEV = 2,
+    AXLBM_BF16_DEV = 3
+} axlbm_precision;
+
+enum { AXLBM_INNER_AXIS = 0, AXLBM_INNER_WALL = 1 };
+enum {
+    AXLBM_Z_PERIODIC = 0, /* both axial faces periodic, or neither */
+    AXLBM_Z_WALL = 1,     /* half-way bounce-back; g sees the wall speed Omega r */
+    AXLBM_Z_FREE = 2,     /* free surface: mirror in z (zero normal gradient) */
+    AXLBM_Z_MIXED = 3     /* "hi" only: wall where the link crosses at r < r_split
+                             (crystal disk), free surface beyond */
+};
+enum { AXLBM_FACE_INNER = 0, AXLBM_FACE_OUTER = 1, AXLBM_FACE_LO = 2, AXLBM_FACE_HI = 3 };
+
+/* field mask bits for axlbm_moments */
+enum { AXLBM_RHO = 1, AXLBM_UR = 2, AXLBM_UZ = 4, AXLBM_UTH = 8, AXLBM_T = 16 };
+/* element types of caller arrays */
+enum { AXLBM_F64 = 0, AXLBM_F32 = 1 };
+
+typedef struct {
+    int32_t nr, nz;           /* nodes in r and z, each >= 1 */
+    int32_t precision;        /* axlbm_precision */
+    int32_t with_swirl;       /* 1: carry g (Eqs. 53-54) */
+    int32_t with_temperature; /* 1: carry h */
+    int32_t reserved;         /* must be 0 */
+    double r0;                /* radius of the inner face; 0 with the axis */
+} axlbm_grid;
+
+typedef struct {
+    double rho0;          /* reference density (incompressible limit, Sec. III A) */
+    double az0, omega_t;  /* axial body force density a(t) = az0 cos(omega_t t) */
+    double gbeta, t_ref;  /* Boussinesq: F_z += rho0 gbeta (T - t_ref) */
+    double tau_t;         /* temperature relaxation time (standard); kappa = (tau_t - 1/2)/2 */
+    double t_init;        /* uniform temperature of the initial state */
+} axlbm_forcing;
+
+typedef struct {
+    int32_t inner;          /* AXLBM_INNER_AXIS (needs r0 == 0) or AXLBM_INNER_WALL */
+    int32_t z_lo, z_hi;     /* AXLBM_Z_*; z_lo may not be AXLBM_Z_MIXED */
+    int32_t t_dirichlet[4]; /* per face (AXLBM_FACE_*): 1 fixed temperature, 0 adiabatic */
+    int32_t reserved;       /* must be 0 */
+    double r_split;         /* AXLBM_Z_MIXED: wall part of the top face is r < r_split */
+    double omega[4];        /* per face: angular velocity; u_theta,wall = omega * r */
+    double t_wall[4];       /* per face: temperature where t_dirichlet is 1 */
+} axlbm_boundary;
+
+typedef struct axlbm_handle axlbm_handle;
+
+/* ABI version of the loaded library (AXLBM_ABI_VERSION at build time). */
+AXLBM_API int32_t axlbm_abi_version(void);
+
+/* Static description of a status code. */
+AXLBM_API const char* axlbm_status_string(axlbm_status status);
+
+/* Device bytes a handle for `grid` needs (populations, check buffers and
+ * reduction scratch), for callers that provide the memory themselves.
+ * Returns AXLBM_EINVAL for an invalid grid. */
+AXLBM_API axlbm_status axlbm_state_bytes(const axlbm_grid* grid, size_t* bytes);
+
+/* Create a domain at rest: f = f^eq(rho0, 0), g = 0, h = h^eq(t_init, 0),
+ * time 0.  tau is the standard relaxation time of f (> 1/2).
+ *   cuda_stream: a cudaStream_t (may be NULL for the legacy stream); every
+ *     kernel of this handle runs on it.
+ *   state_mem / state_bytes: caller-owned device memory of at least
+ *     axlbm_state_bytes() bytes, 256-byte aligned, that the handle uses for
+ *     all its device state and never frees; or NULL / 0 to let the library
+ *     allocate (and later free) it.  The caller keeps caller-owned memory
+ *     alive until axlbm_destroy returns.
+ *   out: receives the handle; unchanged on failure.
+ * Validates the description: AXLBM_EINVAL on an invalid grid, tau <= 1/2,
+ * rho0 <= 0, an axis with r0 != 0, one periodic axial face without the
+ * other, a mixed bottom face, or tau_t <= 1/2 with temperature.  The call
+ * writes the initial state and synchronises the stream before it returns. */
+AXLBM_API axlbm_status axlbm_create(const axlbm_grid* grid, double tau, const axlbm_forcing* forcing,
+                          const axlbm_boundary* boundary, void* cuda_stream, void* state_mem,
+                          size_t state_bytes, axlbm_handle** out);
+
+/* Advance n >= 0 time steps (t -> t + n), asynchronously on the handle's
+ * stream.  The forcing a(t) is taken at the pre-collision time of each step.
+ * The last step of every call with n >= 1 is a check step: it records the
+ * Eq. 57 residual max |sqrt(u_r^2+u_z^2)^(t+1) - sqrt(u_r^2+u_z^2)^t| between
+ * the last two time levels, the mass sum f and the budget sum rho u_r / r of
+ * that step's pre-collision state (FP64 reductions), read by axlbm_residual.
+ * When n == 1 and the previous step was not a check step the residual is
+ * reported as +Inf. */
+AXLBM_API axlbm_status axlbm_step(axlbm_handle* h, int64_t n);
+
+/* Macroscopic fields at the current time (Eqs. 16-17, u_theta = sum g / rho0,
+ * T = sum h).  field_mask selects fields (AXLBM_RHO | ...); `out` receives
+ * the selected fields in mask-bit order, each [nz][nr], as out_dtype
+ * (AXLBM_F64 / AXLBM_F32), caller-owned, on the device when out_on_device is
+ * 1 (queued asynchronously) and on the host otherwise (synchronises).
+ * Requesting u_theta without swirl or T without temperature is AXLBM_EINVAL. */
+AXLBM_API axlbm_status axlbm_moments(axlbm_handle* h, uint32_t field_mask, void* out, int32_t out_dtype,
+                           int32_t out_on_device);
+
+/* Results of the last check step: residual of Eq. 57, mass, budget (each may
+ * be NULL).  Synchronises the stream.  Returns AXLBM_ENONFINITE (with the
+ * values still written) when the check saw a NaN or Inf, and AXLBM_EINVAL
+ * before the first step. */
+AXLBM_API axlbm_status axlbm_residual(axlbm_handle* h, double* residual, double* mass, double* budget);
+
+/* Reset the state to the equilibria of given macroscopic fields
+ * [5][nz][nr] (rho, u_r, u_z, u_theta, T) of element type in_dtype, on the
+ * device (on_device = 1, read asynchronously) or the host (copied before the
+ * call returns).  Fields of disabled distributions are ignored.  Time is
+ * kept.  This is the warm-start entry point. */
+AXLBM_API axlbm_status axlbm_set_fields(axlbm_handle* h, const void* fields, int32_t in_dtype,
+                              int32_t on_device);
+
+/* Copy the populations at the current time to host FP64 arrays f [9][nz][nr],
+ * g [4][nz][nr], t_pop [4][nz][nr] (g / t_pop may be NULL; must be NULL when
+ * the distribution is disabled).  Synchronises. */
+AXLBM_API axlbm_status axlbm_get_populations(axlbm_handle* h, double* f, double* g, double* t_pop);
+
+/* Replace the populations with host FP64 arrays (layout as above) and set the
+ * time to `time`.  Synchronises.  Used for tests and checkpoint / resume. */
+AXLBM_API axlbm_status axlbm_set_populations(axlbm_handle* h, const double* f, const double* g,
+                                   const double* t_pop, int64_t time);
+
+/* Current time level. */
+AXLBM_API axlbm_status axlbm_time(const axlbm_handle* h, int64_t* time);
+
+/* Device timing of the bulk update kernel (the kernel that moves almost all
+ * bytes), for throughput and roofline reporting.  enable = 1 clears the
+ * totals and starts recording a CUDA event pair around every bulk-kernel
+ * launch on the handle's stream; enable = 0 stops recording (totals kept). */
+AXLBM_API axlbm_status axlbm_kernel_timing(axlbm_handle* h, int32_t enable);
+
+/* Totals since timing was enabled (synchronises the stream): number of
+ * bulk-kernel launches, their summed device time in milliseconds, the
+ * algorithmic bytes they moved (each updated node reads and writes every
+ * stored population once; check steps add the |u| plane), and the number of
+ * all library kernel launches on the stream.  Any pointer may be NULL. */
+AXLBM_API axlbm_status axlbm_kernel_times(axlbm_handle* h, int64_t* bulk_launches, double* bulk_ms,
+                                          double* bulk_bytes, int64_t* all_launches);
+
+/* Free the handle and library-owned memory (after synchronising its stream). */
+AXLBM_API axlbm_status axlbm_destroy(axlbm_handle* h);
+
+/* Text of the last error on `h`, or of the last failed axlbm_create when h is
+ * NULL.  Never NULL; valid until the next call on the same handle. */
+AXLBM_API const char* axlbm_last_error(const axlbm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AXLBM_H */

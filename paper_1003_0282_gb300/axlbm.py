@@ -1,0 +1,283 @@
+"""Thin ctypes binding of ``libaxlbm`` (include/axlbm.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  The functions keep the C names; :class:`Domain` bundles a handle
+with PyTorch-owned device memory and the caller's CUDA stream.  Importing this
+module loads the library and raises ``RuntimeError`` if it is missing; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import inputs as _inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libaxlbm.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED = range(7)
+FP64, FP32, FP16_DEV, BF16_DEV = range(4)
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP16_DEV, "bf16": BF16_DEV}
+INNER_AXIS, INNER_WALL = 0, 1
+Z_PERIODIC, Z_WALL, Z_FREE, Z_MIXED = range(4)
+RHO, UR, UZ, UTH, T = 1, 2, 4, 8, 16
+F64, F32 = 0, 1
+_ZKIND = {"periodic": Z_PERIODIC, "wall": Z_WALL, "free": Z_FREE, "mixed": Z_MIXED}
+_INNER = {"axis": INNER_AXIS, "wall": INNER_WALL}
+
+
+class axlbm_grid(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int32), ("nz", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("with_swirl", ctypes.c_int32), ("with_temperature", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("r0", ctypes.c_double)]
+
+
+class axlbm_forcing(ctypes.Structure):
+    _fields_ = [("rho0", ctypes.c_double), ("az0", ctypes.c_double), ("omega_t", ctypes.c_double),
+                ("gbeta", ctypes.c_double), ("t_ref", ctypes.c_double), ("tau_t", ctypes.c_double),
+                ("t_init", ctypes.c_double)]
+
+
+class axlbm_boundary(ctypes.Structure):
+    _fields_ = [("inner", ctypes.c_int32), ("z_lo", ctypes.c_int32), ("z_hi", ctypes.c_int32),
+                ("t_dirichlet", ctypes.c_int32 * 4), ("reserved", ctypes.c_int32),
+                ("r_split", ctypes.c_double), ("omega", ctypes.c_double * 4),
+                ("t_wall", ctypes.c_double * 4)]
+
+
+class AxlbmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"axlbm status {status}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libaxlbm; raises RuntimeError when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libaxlbm is not built ({LIB_PATH} missing); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        H = ctypes.c_void_p
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.axlbm_abi_version.restype = ctypes.c_int32
+        L.axlbm_abi_version.argtypes = []
+        L.axlbm_status_string.restype = ctypes.c_char_p
+        L.axlbm_status_string.argtypes = [ctypes.c_int]
+        L.axlbm_state_bytes.argtypes = [ctypes.POINTER(axlbm_grid), ctypes.POINTER(ctypes.c_size_t)]
+        L.axlbm_create.argtypes = [ctypes.POINTER(axlbm_grid), ctypes.c_double, ctypes.POINTER(axlbm_forcing),
+                                   ctypes.POINTER(axlbm_boundary), ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_size_t, ctypes.POINTER(H)]
+        L.axlbm_step.argtypes = [H, ctypes.c_int64]
+        L.axlbm_moments.argtypes = [H, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
+        L.axlbm_residual.argtypes = [H, dp, dp, dp]
+        L.axlbm_set_fields.argtypes = [H, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
+        L.axlbm_get_populations.argtypes = [H, dp, dp, dp]
+        L.axlbm_set_populations.argtypes = [H, dp, dp, dp, ctypes.c_int64]
+        L.axlbm_time.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
+        L.axlbm_destroy.argtypes = [H]
+        L.axlbm_kernel_timing.argtypes = [H, ctypes.c_int32]
+        L.axlbm_kernel_times.argtypes = [H, ctypes.POINTER(ctypes.c_int64), dp, dp, ctypes.POINTER(ctypes.c_int64)]
+        L.axlbm_last_error.restype = ctypes.c_char_p
+        L.axlbm_last_error.argtypes = [H]
+        for name in ("axlbm_state_bytes", "axlbm_create", "axlbm_step", "axlbm_moments", "axlbm_residual",
+                     "axlbm_set_fields", "axlbm_get_populations", "axlbm_set_populations", "axlbm_time",
+                     "axlbm_destroy", "axlbm_kernel_timing", "axlbm_kernel_times"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int, handle=None) -> int:
+    if status != OK:
+        msg = lib().axlbm_last_error(handle).decode(errors="replace")
+        raise AxlbmError(status, msg or lib().axlbm_status_string(status).decode())
+    return status
+
+
+def _dptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ----------------------------------------------------------------------------- C-named wrappers
+
+
+def axlbm_abi_version() -> int:
+    return int(lib().axlbm_abi_version())
+
+
+def axlbm_state_bytes(grid: axlbm_grid) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().axlbm_state_bytes(ctypes.byref(grid), ctypes.byref(n)))
+    return int(n.value)
+
+
+def axlbm_create(grid: axlbm_grid, tau: float, forcing: axlbm_forcing, boundary: axlbm_boundary,
+                 stream: int = 0, state_mem: int = 0, state_bytes: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().axlbm_create(ctypes.byref(grid), float(tau), ctypes.byref(forcing), ctypes.byref(boundary),
+                              ctypes.c_void_p(stream or None), ctypes.c_void_p(state_mem or None),
+                              ctypes.c_size_t(state_bytes), ctypes.byref(h)))
+    return h
+
+
+def axlbm_step(h, n: int) -> None:
+    _check(lib().axlbm_step(h, int(n)), h)
+
+
+def axlbm_moments(h, mask: int, out_ptr: int, out_dtype: int, out_on_device: int) -> None:
+    _check(lib().axlbm_moments(h, int(mask), ctypes.c_void_p(out_ptr), int(out_dtype), int(out_on_device)), h)
+
+
+def axlbm_residual(h, allow_nonfinite: bool = False):
+    r, m, b = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    st = lib().axlbm_residual(h, ctypes.byref(r), ctypes.byref(m), ctypes.byref(b))
+    if not (allow_nonfinite and st == ENONFINITE):
+        _check(st, h)
+    return r.value, m.value, b.value
+
+
+def axlbm_set_fields(h, ptr: int, in_dtype: int, on_device: int) -> None:
+    _check(lib().axlbm_set_fields(h, ctypes.c_void_p(ptr), int(in_dtype), int(on_device)), h)
+
+
+def axlbm_get_populations(h, f: np.ndarray, g: Optional[np.ndarray], t_pop: Optional[np.ndarray]) -> None:
+    _check(lib().axlbm_get_populations(h, _dptr(f), _dptr(g), _dptr(t_pop)), h)
+
+
+def axlbm_set_populations(h, f: np.ndarray, g: Optional[np.ndarray], t_pop: Optional[np.ndarray],
+                          time: int) -> None:
+    _check(lib().axlbm_set_populations(h, _dptr(f), _dptr(g), _dptr(t_pop), int(time)), h)
+
+
+def axlbm_time(h) -> int:
+    t = ctypes.c_int64()
+    _check(lib().axlbm_time(h, ctypes.byref(t)), h)
+    return int(t.value)
+
+
+def axlbm_kernel_timing(h, enable: bool) -> None:
+    _check(lib().axlbm_kernel_timing(h, int(bool(enable))), h)
+
+
+def axlbm_kernel_times(h):
+    """(bulk launches, bulk device ms, bulk algorithmic bytes, all launches)."""
+    nb, na = ctypes.c_int64(), ctypes.c_int64()
+    ms, by = ctypes.c_double(), ctypes.c_double()
+    _check(lib().axlbm_kernel_times(h, ctypes.byref(nb), ctypes.byref(ms), ctypes.byref(by), ctypes.byref(na)), h)
+    return int(nb.value), ms.value, by.value, int(na.value)
+
+
+def axlbm_destroy(h) -> None:
+    _check(lib().axlbm_destroy(h))
+
+
+# ----------------------------------------------------------------------------- structs from a Problem
+
+
+def structs(pb: "_inputs.Problem", precision: str = "fp32"):
+    """(grid, tau, forcing, boundary) for a Problem."""
+    g = axlbm_grid(nr=pb.nr, nz=pb.nz, precision=PRECISIONS[precision], with_swirl=int(bool(pb.swirl)),
+                   with_temperature=int(bool(pb.temperature)), reserved=0, r0=float(pb.r0))
+    f = axlbm_forcing(rho0=pb.rho0, az0=pb.az0, omega_t=pb.omega_t, gbeta=pb.gbeta, t_ref=pb.t_ref,
+                      tau_t=pb.tau_t, t_init=pb.t_ref)
+    b = axlbm_boundary()
+    b.inner = _INNER[pb.inner]
+    b.z_lo, b.z_hi = _ZKIND[pb.z_lo], _ZKIND[pb.z_hi]
+    b.reserved = 0
+    b.r_split = float(pb.r_split)
+    for i, face in enumerate(_inputs.FACES):
+        b.t_dirichlet[i] = int(pb.t_dirichlet(face))
+        b.omega[i] = pb.omega_of(face)
+        b.t_wall[i] = pb.t_value(face)
+    return g, float(pb.tau), f, b
+
+
+class Domain:
+    """One axisymmetric domain on the current CUDA device.
+
+    Device memory comes from PyTorch (a uint8 tensor handed to the library as
+    caller-owned state memory) and work runs on the current PyTorch stream.
+    """
+
+    def __init__(self, pb: "_inputs.Problem", precision: str = "fp32", stream=None):
+        import torch
+
+        self.pb = pb
+        self.precision = precision
+        self.grid, self.tau, self.forcing, self.boundary = structs(pb, precision)
+        nbytes = axlbm_state_bytes(self.grid)
+        self._mem = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = axlbm_create(self.grid, self.tau, self.forcing, self.boundary,
+                                   stream=self.stream.cuda_stream, state_mem=self._mem.data_ptr(),
+                                   state_bytes=nbytes)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None:
+            axlbm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- stepping
+    def step(self, n: int) -> None:
+        axlbm_step(self.handle, n)
+
+    @property
+    def time(self) -> int:
+        return axlbm_time(self.handle)
+
+    def residual(self, allow_nonfinite: bool = False):
+        """(residual of Eq. 57, mass, budget) of the last check step."""
+        return axlbm_residual(self.handle, allow_nonfinite)
+
+    # -- data movement
+    def moments(self, mask: int = RHO | UR | UZ, dtype=np.float64) -> np.ndarray:
+        """Selected fields on the host, shape [nfields][nz][nr]."""
+        nf = bin(mask).count("1")
+        out = np.empty((nf, self.pb.nz, self.pb.nr), dtype=dtype)
+        axlbm_moments(self.handle, mask, out.ctypes.data, F64 if dtype == np.float64 else F32, 0)
+        return out
+
+    def moments_device(self, mask: int, out) -> None:
+        """Selected fields into a CUDA tensor (float32 or float64), asynchronously."""
+        import torch
+
+        axlbm_moments(self.handle, mask, out.data_ptr(), F32 if out.dtype == torch.float32 else F64, 1)
+
+    def set_fields(self, fields) -> None:
+        """Equilibrium reset from fields [5][nz][nr] (numpy on the host or a CUDA tensor)."""
+        if isinstance(fields, np.ndarray):
+            a = np.ascontiguousarray(fields, dtype=np.float64)
+            axlbm_set_fields(self.handle, a.ctypes.data, F64, 0)
+        else:
+            import torch
+
+            axlbm_set_fields(self.handle, fields.data_ptr(), F32 if fields.dtype == torch.float32 else F64, 1)
+
+    def get_populations(self):
+        shape = (self.pb.nz, self.pb.nr)
+        f = np.empty((9,) + shape)
+        g = np.empty((4,) + shape) if self.pb.swirl else None
+        h = np.empty((4,) + shape) if self.pb.temperature else None
+        axlbm_get_populations(self.handle, f, g, h)
+        return f, g, h
+
+    def set_populations(self, f, g=None, h=None, time: int = 0) -> None:
+        cast = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+        axlbm_set_populations(self.handle, cast(f), cast(g), cast(h), time)

@@ -1,0 +1,112 @@
+// internal.h -- structures shared by the host API and the kernel instantiations.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/axlbm.h"
+
+namespace axl {
+
+// Problem geometry and boundary description as the kernels see it.
+struct Geom {
+    int nr, nz;
+    long long pitch;  // elements per row (multiple of 128 bytes)
+    long long plane;  // elements per population plane (nz * pitch)
+    double r0;
+    int inner, z_lo, z_hi;
+    double r_split;
+};
+
+// Per-step forcing state on the device.  Kernels of a step with AA parity p
+// read a_z[p]; the last kernel of the step writes a_z[1 - p] for the next
+// time level and advances t (one thread), so graphs of many steps need no
+// host updates.
+struct Clock {
+    double a_z[2];
+    long long t;
+    long long pad;
+};
+
+// Coefficients in the arithmetic type R.
+template <class R>
+struct Coef {
+    R rho0, inv_rho0;
+    R c0, c1;       // f: omega_a = c0 + c1 e_ar / r            (Eq. 13)
+    R mu0;          // rho0 * tau / 3                           (Eq. 16, mu -> mu0)
+    R g0, g1, nu;   // g: omega = g0 + g1 e_r / r, nu = tau_g/2  (Eqs. 53-54)
+    R h0, h1;       // temperature: omega = h0 + h1 e_r / r
+    R gbeta, t_ref;
+    R omega_w[4];   // wall angular velocities per face
+    R t_w[4];       // wall temperatures per face
+    int t_dir[4];   // 1: Dirichlet face
+};
+
+struct Layout {
+    int nplanes;      // 9 (+4 g) (+4 h)
+    int g_plane;      // first g plane (or -1)
+    int h_plane;      // first h plane (or -1)
+    size_t elem;      // bytes per stored value
+    long long pitch, plane;
+    size_t pop_bytes, speed_bytes, part_bytes;
+    size_t off_speed, off_part, off_result, off_clock, total;
+    int bx, by, gx, gy;   // bulk launch
+    int nframe, frame_blocks;
+    int nparts;           // reduction slots
+};
+
+}  // namespace axl
+
+struct axlbm_handle {
+    axlbm_grid grid;
+    double tau;
+    axlbm_forcing forcing;
+    axlbm_boundary bc;
+    cudaStream_t stream;
+    char* mem;
+    bool owns_mem;
+    axl::Layout L;
+    axl::Geom G;
+    int parity;         // AA layout parity: 0 natural, 1 after an even step
+    int64_t t;          // time level
+    bool speed_valid;   // the speed buffer holds |u| of time t - 1 (last step was a check step)
+    bool have_check;    // a check step has run
+    bool last_residual_valid;  // the last check step compared two consecutive levels
+    // bulk-kernel timing
+    bool timing;
+    std::vector<cudaEvent_t> ev;     // event pairs of launches not yet folded into the totals
+    std::vector<double> ev_bytes;    // algorithmic bytes of those launches
+    size_t ev_used;
+    int64_t bulk_launches, all_launches;
+    double bulk_ms, bulk_bytes;
+    std::string err;
+};
+
+namespace axl {
+
+// Precision-specific launchers (one set per storage type, see ops_impl.cuh).
+struct Ops {
+    // one time step; bulk_before / bulk_after (may be null) are recorded on the
+    // stream around the bulk kernel; returns the number of kernels launched in *nlaunch
+    cudaError_t (*step)(axlbm_handle* h, int check, int residual, cudaEvent_t bulk_before,
+                        cudaEvent_t bulk_after, int* nlaunch);
+    cudaError_t (*moments)(axlbm_handle* h, void* out_dev, unsigned mask, int out_f32);
+    cudaError_t (*init_fields)(axlbm_handle* h, const void* fields_dev, int in_f32);
+    cudaError_t (*gather)(axlbm_handle* h, double* out_dev);
+    cudaError_t (*scatter)(axlbm_handle* h, const double* in_dev);
+    cudaError_t (*finalize)(axlbm_handle* h, int parity);
+};
+
+// Fixed-order reduction of per-block check partials [n][4] (max, sum, sum,
+// sum) into result[4] on `stream` (reduce.cu).
+cudaError_t launch_finalize(const double* partials, int n, double* result, cudaStream_t stream);
+
+extern const Ops ops_fp64;
+extern const Ops ops_fp32;
+extern const Ops ops_fp16;
+extern const Ops ops_bf16;
+
+}  // namespace axl
