@@ -441,3 +441,15 @@ def test_oracle_rejects_inconsistent_problems(orc):
     assert not orc.validate(I.Problem(nr=4, nz=4, tau=0.8, r0=2.0, inner="axis"))
     assert not orc.validate(I.Problem(nr=4, nz=4, tau=0.8, z_lo="periodic", z_hi="wall"))
     assert not orc.validate(I.Problem(nr=0, nz=4, tau=0.8))
+
+
+def test_equilibrium_reproduces_its_fields(orc):
+    """Eqs. 6 and 54: sum f^eq = rho, sum e f^eq = rho u, sum g^eq = rho0 u_theta,
+    sum h^eq = T.  Far from the axis and without forces the moments of Eqs.
+    16-17 must therefore return the fields the equilibrium was built from."""
+    pb = I.Problem(nr=9, nz=7, tau=0.8, r0=1e12, inner="wall", swirl=True, temperature=True, rho0=1.2)
+    fields = I.random_fields(9, 7, seed=4, rho0=1.2)
+    st = orc.equilibrium(pb, fields)
+    got = orc.moments(st)
+    for q in range(5):
+        assert np.max(np.abs(got[q] - fields[q])) <= 1e-12 * max(1.0, np.max(np.abs(fields[q]))), q
