@@ -207,6 +207,31 @@ AXLBM_API axlbm_status axlbm_kernel_timing(axlbm_handle* h, int32_t enable);
 AXLBM_API axlbm_status axlbm_kernel_times(axlbm_handle* h, int64_t* bulk_launches, double* bulk_ms,
                                           double* bulk_bytes, int64_t* all_launches);
 
+/* Check-step statistics that allocate nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc, such as
+ * code running inside another framework's memory pool or a real-time loop
+ * that forbids allocations after start-up.  It computes what a check step of
+ * axlbm_step records -- out[0] = max |s - speed_prev| (the Eq. 57 residual;
+ * 0 when speed_prev is NULL), out[1] = sum f (mass), out[2] = sum
+ * rho u_r / r (budget), out[3] = number of nodes with a non-finite rho or u
+ * -- for one time level given by the caller, where s = sqrt(u_r^2 + u_z^2)
+ * from Eqs. 16-17 at force a_z.
+ *   f, g, t_pop: device, FP64 populations [9|4|4][nz][nr] (g / t_pop exactly
+ *     when the grid enables them); the grid's precision field is ignored.
+ *   speed_prev: device [nz][nr] speeds of the previous level, or NULL.
+ *   speed_out: device [nz][nr] receives s, or NULL.
+ *   out: device double[4].  Work is queued on cuda_stream (asynchronous).
+ * Its block partials live in a fixed 512 KiB device array that every GPU
+ * loading this library holds until the process exits; calls with more than
+ * 4,194,304 nodes return AXLBM_EINVAL.  The first call on a device looks up
+ * that array's address (make it before any stream capture).  Calls share the
+ * array: calls that overlap on the GPU race.  Errors are read with
+ * axlbm_last_error(NULL). */
+AXLBM_API axlbm_status axlbm_check_static(const axlbm_grid* grid, double tau, const axlbm_forcing* forcing,
+                                          const double* f, const double* g, const double* t_pop, double a_z,
+                                          const double* speed_prev, double* speed_out, double* out,
+                                          void* cuda_stream);
+
 /* Free the handle and library-owned memory (after synchronising its stream). */
 AXLBM_API axlbm_status axlbm_destroy(axlbm_handle* h);
 

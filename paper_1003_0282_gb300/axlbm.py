@@ -85,11 +85,15 @@ def lib() -> ctypes.CDLL:
         L.axlbm_destroy.argtypes = [H]
         L.axlbm_kernel_timing.argtypes = [H, ctypes.c_int32]
         L.axlbm_kernel_times.argtypes = [H, ctypes.POINTER(ctypes.c_int64), dp, dp, ctypes.POINTER(ctypes.c_int64)]
+        L.axlbm_check_static.argtypes = [ctypes.POINTER(axlbm_grid), ctypes.c_double,
+                                         ctypes.POINTER(axlbm_forcing), ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p]
         L.axlbm_last_error.restype = ctypes.c_char_p
         L.axlbm_last_error.argtypes = [H]
         for name in ("axlbm_state_bytes", "axlbm_create", "axlbm_step", "axlbm_moments", "axlbm_residual",
                      "axlbm_set_fields", "axlbm_get_populations", "axlbm_set_populations", "axlbm_time",
-                     "axlbm_destroy", "axlbm_kernel_timing", "axlbm_kernel_times"):
+                     "axlbm_destroy", "axlbm_kernel_timing", "axlbm_kernel_times", "axlbm_check_static"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -176,6 +180,16 @@ def axlbm_kernel_times(h):
     ms, by = ctypes.c_double(), ctypes.c_double()
     _check(lib().axlbm_kernel_times(h, ctypes.byref(nb), ctypes.byref(ms), ctypes.byref(by), ctypes.byref(na)), h)
     return int(nb.value), ms.value, by.value, int(na.value)
+
+
+def axlbm_check_static(grid: axlbm_grid, tau: float, forcing: axlbm_forcing, f_ptr: int, g_ptr: int,
+                       t_ptr: int, a_z: float, speed_prev_ptr: int, speed_out_ptr: int, out_ptr: int,
+                       stream: int = 0) -> None:
+    """Check-step statistics over caller device buffers, without allocating."""
+    vp = lambda p: ctypes.c_void_p(p or None)
+    _check(lib().axlbm_check_static(ctypes.byref(grid), float(tau), ctypes.byref(forcing), vp(f_ptr), vp(g_ptr),
+                                    vp(t_ptr), float(a_z), vp(speed_prev_ptr), vp(speed_out_ptr), vp(out_ptr),
+                                    vp(stream)))
 
 
 def axlbm_destroy(h) -> None:

@@ -164,6 +164,11 @@ double bulk_bytes_of(const axlbm_handle* h, int check, int residual) {
 
 }  // namespace
 
+namespace axl {
+// Error text of a call that has no handle, read back by axlbm_last_error(NULL).
+void set_handleless_error(const char* msg) { g_create_error = msg; }
+}  // namespace axl
+
 extern "C" {
 
 int32_t axlbm_abi_version(void) { return AXLBM_ABI_VERSION; }

@@ -104,6 +104,9 @@ struct Ops {
 // sum) into result[4] on `stream` (reduce.cu).
 cudaError_t launch_finalize(const double* partials, int n, double* result, cudaStream_t stream);
 
+// Error text of a call that has no handle (axlbm_last_error(NULL)).
+void set_handleless_error(const char* msg);
+
 extern const Ops ops_fp64;
 extern const Ops ops_fp32;
 extern const Ops ops_fp16;
