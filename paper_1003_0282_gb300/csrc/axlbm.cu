@@ -66,17 +66,12 @@ Layout make_layout(const axlbm_grid* g) {
     L.pop_bytes = align_up((size_t)L.nplanes * (size_t)L.plane * L.elem, 256);
     const size_t rbytes = g->precision == AXLBM_FP64 ? 8 : 4;
     L.speed_bytes = align_up((size_t)L.plane * rbytes, 256);
-    // bulk launch: 256 threads, rows of up to 128 nodes
-    L.bx = g->nr >= 128 ? 128 : (int)align_up((size_t)g->nr, 32);
-    if (L.bx > 256) L.bx = 256;
-    L.by = 256 / L.bx;
-    L.gx = (g->nr + L.bx - 1) / L.bx;
-    long long gy = (g->nz + L.by - 1) / L.by;
-    if (gy > 65535) gy = 65535;
-    L.gy = (int)gy;
+    // bulk tiles of kTileK x kTileJ nodes, persistent CTAs
+    L.tiles_j = (g->nr + axl::kTileJ - 1) / axl::kTileJ;
+    L.tiles_k = (g->nz + axl::kTileK - 1) / axl::kTileK;
     L.nframe = g->nz == 1 ? g->nr : 2 * g->nr + (g->nz - 2) * (g->nr > 1 ? 2 : 1);
     L.frame_blocks = (L.nframe + 255) / 256;
-    L.nparts = L.gx * L.gy + L.frame_blocks;
+    L.nparts = axl::kMaxBulkBlocks + L.frame_blocks;
     L.part_bytes = align_up((size_t)L.nparts * 4 * sizeof(double), 256);
     L.off_speed = L.pop_bytes;
     L.off_part = L.off_speed + L.speed_bytes;
@@ -100,6 +95,7 @@ void write_clock(axlbm_handle* h, axl::Clock* host) {
     host->a_z[0] = host->a_z[1] = 0.0;
     host->a_z[h->parity] = h->forcing.az0 * cos(h->forcing.omega_t * (double)h->t);
     host->t = h->t;
+    host->err = 0;
     host->pad = 0;
 }
 
@@ -246,6 +242,14 @@ axlbm_status axlbm_create(const axlbm_grid* grid, double tau, const axlbm_forcin
     h->have_check = false;
     h->last_residual_valid = false;
     h->timing = false;
+    h->check_parts = 0;
+    h->bulk_grid[0][0] = h->bulk_grid[0][1] = h->bulk_grid[1][0] = h->bulk_grid[1][1] = 0;
+    {
+        int dev = 0;
+        h->num_sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (h->num_sms < 1) h->num_sms = 1;
+    }
     h->ev_used = 0;
     h->bulk_launches = h->all_launches = 0;
     h->bulk_ms = h->bulk_bytes = 0.0;
@@ -266,6 +270,10 @@ axlbm_status axlbm_create(const axlbm_grid* grid, double tau, const axlbm_forcin
     cudaError_t e = cudaMemsetAsync(h->mem, 0, L.total, h->stream);
     axlbm_status st = AXLBM_OK;
     if (e != cudaSuccess) st = cuda_fail(h, e, "memset");
+    if (st == AXLBM_OK) {
+        e = ops_for(grid->precision)->prepare(h);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "TMA descriptor");
+    }
     if (st == AXLBM_OK) st = upload_clock(h);
     if (st == AXLBM_OK) {
         // rest state: rho0, zero velocity, uniform t_init
@@ -371,9 +379,12 @@ axlbm_status axlbm_residual(axlbm_handle* h, double* residual, double* mass, dou
     if (!h) return fail(nullptr, AXLBM_EINVAL, "handle is NULL");
     if (!h->have_check) return fail(h, AXLBM_EINVAL, "no check step has run yet");
     double r[4];
+    axl::Clock clk;
     cudaError_t e = cudaMemcpyAsync(r, h->mem + h->L.off_result, sizeof r, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&clk, h->mem + h->L.off_clock, sizeof clk, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "residual read");
+    if (clk.err) return fail(h, AXLBM_ETIMEOUT, "a bounded wait for a TMA copy gave up; the state is not valid");
     if (residual) *residual = h->last_residual_valid ? r[0] : INFINITY;
     if (mass) *mass = r[1];
     if (budget) *budget = r[2];

@@ -1,6 +1,7 @@
 // internal.h -- structures shared by the host API and the kernel instantiations.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -10,6 +11,12 @@
 #include "../../include/axlbm.h"
 
 namespace axl {
+
+// Bulk-kernel tiling: tiles of kTileK rows x kTileJ nodes, at most
+// kMaxBulkBlocks persistent CTAs (each leaves one check partial).
+constexpr int kTileJ = 128;
+constexpr int kTileK = 4;
+constexpr int kMaxBulkBlocks = 4096;
 
 // Problem geometry and boundary description as the kernels see it.
 struct Geom {
@@ -28,7 +35,8 @@ struct Geom {
 struct Clock {
     double a_z[2];
     long long t;
-    long long pad;
+    unsigned int err;  // bit 0: a bounded wait in a kernel gave up
+    unsigned int pad;
 };
 
 // Coefficients in the arithmetic type R.
@@ -53,14 +61,15 @@ struct Layout {
     long long pitch, plane;
     size_t pop_bytes, speed_bytes, part_bytes;
     size_t off_speed, off_part, off_result, off_clock, total;
-    int bx, by, gx, gy;   // bulk launch
+    int tiles_j, tiles_k;  // bulk tiles
     int nframe, frame_blocks;
-    int nparts;           // reduction slots
+    int nparts;           // reduction slots (bulk blocks of any launch + frame blocks)
 };
 
 }  // namespace axl
 
 struct axlbm_handle {
+    CUtensorMap tmap;  // TMA view of the population planes (x = row, y = k, z = plane)
     axlbm_grid grid;
     double tau;
     axlbm_forcing forcing;
@@ -75,6 +84,9 @@ struct axlbm_handle {
     bool speed_valid;   // the speed buffer holds |u| of time t - 1 (last step was a check step)
     bool have_check;    // a check step has run
     bool last_residual_valid;  // the last check step compared two consecutive levels
+    int num_sms;
+    int bulk_grid[2][2];  // persistent grid per (parity, check), from the occupancy API
+    int check_parts;      // partials written by the last check step
     // bulk-kernel timing
     bool timing;
     std::vector<cudaEvent_t> ev;     // event pairs of launches not yet folded into the totals
@@ -98,6 +110,7 @@ struct Ops {
     cudaError_t (*gather)(axlbm_handle* h, double* out_dev);
     cudaError_t (*scatter)(axlbm_handle* h, const double* in_dev);
     cudaError_t (*finalize)(axlbm_handle* h, int parity);
+    cudaError_t (*prepare)(axlbm_handle* h);  // encode the TMA descriptor
 };
 
 // Fixed-order reduction of per-block check partials [n][4] (max, sum, sum,

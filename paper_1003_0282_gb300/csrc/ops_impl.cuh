@@ -27,8 +27,12 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 #include "internal.h"
 #include "lattice.cuh"
+#include "pair.cuh"
+#include "tma.cuh"
 
 namespace axl {
 
@@ -47,75 +51,110 @@ struct KArgs {
     int g_plane, h_plane;
     int nframe;
     int residual;  // 1: compare |u| with the stored previous level
+    int tiles_j, tiles_k;  // bulk tiles (kTileJ x kTileK nodes) along r and z
+    unsigned int* err;     // device error word (bit 0: a bounded wait gave up)
 };
 
 // ---------------------------------------------------------------------------- collision
 
+// One collision of the improved scheme (Eqs. 12-17, Eq. 13's BGK update with
+// the radius-dependent rate, Eqs. 53-54 for g, the same form for h), written
+// to share work between populations:
+//   f^eq_a - w_a rho0 = w_a P_a,  P_a = A + B (e_a.u) + Cq (e_a.u)^2,
+//     A = drho - 1.5 rho u^2, B = 3 rho, Cq = 4.5 rho                 (Eq. 6)
+//   S_a = F_a f^eq_a,  F_a = base + e_ar 3F_r/rho + e_az 3F_z/rho,
+//     base = -3 (u.F)/rho - u_r/r                                       (Eq. 12)
+//   d'_a = (1 - om_a) d_a + om_a w_a P_a + (1 - om_a/2) w_a F_a (rho0 + P_a),
+// where d_a = f_a - w_a rho0 is the stored deviation and om_a depends only on
+// the sign of e_ar at a given radius.  R is double, float, or a pair of
+// floats (two nodes at the same radius); Sc is its scalar type.
 template <class R, bool SW, bool TH>
 struct Cell {
+    using Sc = typename ScalarOf<R>::type;
     R d[9];  // f_a - w_a rho0
     R g[4];  // g_a
     R h[4];  // h_a - T_ref / 4
-    R rho, ur, uz, s0;
+    R rho, ur, uz, s0, ds0;
 
-    // One BGK collision (Eqs. 12-17, 53-54) at inverse radius inv_r with the
-    // axial body force az of this time level.
-    __device__ __forceinline__ void collide(R inv_r, const Coef<R>& C, R az) {
-        const R half = R(0.5);
-        R ds0 = d[0];
-#pragma unroll
-        for (int a = 1; a < 9; ++a) ds0 += d[a];
+    __device__ __forceinline__ void collide(Sc inv_r, const Coef<Sc>& C, Sc az) {
+        const Sc W0 = Sc(4.0 / 9.0), W1 = Sc(1.0 / 9.0), W2 = Sc(1.0 / 36.0);
+        const Sc half = Sc(0.5), one = Sc(1);
+        // rates by the sign of e_r (Eq. 13) and their combinations
+        const Sc om0 = C.c0, omp = C.c0 + C.c1 * inv_r, omm = C.c0 - C.c1 * inv_r;
+        const Sc inv_r2 = inv_r * inv_r;
+
+        // moments (Eqs. 14-17 with the half-force terms)
+        ds0 = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
         const R sr = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
         const R sz = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
-        s0 = C.rho0 + ds0;
-        R uth = R(0), dtemp = R(0);
-        if (SW) uth = ((g[0] + g[1]) + (g[2] + g[3])) * C.inv_rho0;
+        s0 = ds0 + R(C.rho0);
+        R gsum = R(Sc(0)), dtemp = R(Sc(0));
+        if (SW) gsum = (g[0] + g[1]) + (g[2] + g[3]);
         if (TH) dtemp = (h[0] + h[1]) + (h[2] + h[3]);  // T - T_ref
-        const R fext_r = SW ? C.rho0 * uth * uth * inv_r : R(0);
-        const R fext_z = TH ? az + C.rho0 * C.gbeta * dtemp : az;
-        const R inv_r2 = inv_r * inv_r;
-        ur = (sr + half * fext_r) / (s0 + C.mu0 * inv_r2);
-        uz = (sz + half * fext_z) / s0;
-        const R urr = ur * inv_r;
-        const R den = R(1) + half * urr;
-        rho = s0 / den;
-        const R drho = (ds0 - half * C.rho0 * urr) / den;
-        const R fr = fext_r - R(2) * C.mu0 * ur * inv_r2;
+        const R uth = gsum * R(C.inv_rho0);
+        const R fext_r = SW ? (uth * uth) * R(C.rho0 * inv_r) : R(Sc(0));
+        const R fext_z = TH ? fmaR(dtemp, R(C.rho0 * C.gbeta), R(az)) : R(az);
+        const R inv_s0 = rcp(s0);
+        ur = fmaR(fext_r, R(half), sr) * rcp(s0 + R(C.mu0 * inv_r2));
+        uz = fmaR(fext_z, R(half), sz) * inv_s0;
+        const R urr = ur * R(inv_r);
+        const R den = fmaR(urr, R(half), R(one));
+        const R inv_den = rcp(den);
+        rho = s0 * inv_den;
+        const R drho = fmaR(urr, R(-half * C.rho0), ds0) * inv_den;
+        const R fr = fmaR(ur, R(Sc(-2) * C.mu0 * inv_r2), fext_r);
         const R fz = fext_z;
-        const R inv_rho = R(1) / rho;
-        const R usq = R(1.5) * (ur * ur + uz * uz);
-        const R base = -R(3) * (ur * fr + uz * fz) * inv_rho - urr;
-        const R fr3 = R(3) * fr * inv_rho, fz3 = R(3) * fz * inv_rho;
+        const R inv_rho = den * inv_s0;
+
+        // equilibrium polynomials P_a
+        const R ur2 = ur * ur, uz2 = uz * uz;
+        const R A = fmaR(rho * R(Sc(-1.5)), ur2 + uz2, drho);
+        const R B = rho * R(Sc(3)), Cq = rho * R(Sc(4.5));
+        const R Bur = B * ur, Buz = B * uz, Cur2 = Cq * ur2, Cuz2 = Cq * uz2;
+        const R Cx = (Cq + Cq) * (ur * uz);
+        const R Ps = A + Cur2, Pz = A + Cuz2, Q = Ps + Cuz2;
+        const R Qp = Q + Cx, Qm = Q - Cx, Bs = Bur + Buz, Bd = Bur - Buz;
+        const R P[9] = {A, Ps + Bur, Pz + Buz, Ps - Bur, Pz - Buz, Qp + Bs, Qm - Bd, Qp - Bs, Qm + Bd};
+        // source factors F_a
+        const R fr3 = fr * inv_rho * R(Sc(3)), fz3 = fz * inv_rho * R(Sc(3));
+        const R base = fmaR((ur * fr + uz * fz) * R(Sc(-3)), inv_rho, R(Sc(0)) - urr);
+        const R F1 = base + fr3, F3 = base - fr3;
+        const R F[9] = {base, F1, base + fz3, F3, base - fz3, F1 + fz3, F3 + fz3, F3 - fz3, F1 - fz3};
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            const int ex = cr9(a), ez = cz9(a);
-            const R w = R(w9(a));
-            const R eu = R(ex) * ur + R(ez) * uz;
-            const R feq_d = w * (drho + rho * (R(3) * eu + R(4.5) * eu * eu - usq));
-            const R src = (base + R(ex) * fr3 + R(ez) * fz3) * (w * C.rho0 + feq_d);
-            const R om = ex == 0 ? C.c0 : (ex > 0 ? C.c0 + C.c1 * inv_r : C.c0 - C.c1 * inv_r);
-            d[a] = d[a] - om * (d[a] - feq_d) + (R(1) - half * om) * src;
+            const int ex = cr9(a);
+            const Sc om = ex == 0 ? om0 : (ex > 0 ? omp : omm);
+            const Sc w = a == 0 ? W0 : (a <= 4 ? W1 : W2);
+            const R kwF = F[a] * R((one - half * om) * w);
+            const R t = fmaR(kwF, P[a] + R(C.rho0), P[a] * R(om * w));
+            d[a] = fmaR(R(one - om), d[a], t);
         }
         if (SW) {
-            const R sg = -inv_r * (R(2) * ur + C.nu * inv_r);
-            const R g4 = C.rho0 * uth * R(0.25);
+            // g' = (1 - om_g) g + (om_g + S^g / g^eq) g^eq                 (Eqs. 53-54)
+            const R g4 = gsum * R(Sc(0.25));
+            const R g2r = (g4 + g4) * ur, g2z = (g4 + g4) * uz;
+            const R geq[4] = {g4 + g2r, g4 + g2z, g4 - g2r, g4 - g2z};
+            const R sg = fmaR(ur, R(Sc(-2) * inv_r), R(-C.nu * inv_r2));
+            const Sc gp = C.g0 + C.g1 * inv_r, gm = C.g0 - C.g1 * inv_r;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int ex = cr4(q), ez = cz4(q);
-                const R geq = g4 * (R(1) + R(2) * (R(ex) * ur + R(ez) * uz));
-                const R om = ex == 0 ? C.g0 : (ex > 0 ? C.g0 + C.g1 * inv_r : C.g0 - C.g1 * inv_r);
-                g[q] = g[q] - om * (g[q] - geq) + sg * geq;
+                const int ex = cr4(q);
+                const Sc om = ex == 0 ? C.g0 : (ex > 0 ? gp : gm);
+                g[q] = fmaR(R(one - om), g[q], (sg + R(om)) * geq[q]);
             }
         }
         if (TH) {
-            const R temp4 = (dtemp + C.t_ref) * R(0.25);
-            const R tref4 = C.t_ref * R(0.25);
+            // h' = (1 - om_h) h + (om_h - u_r/r) h^eq - om_h T_ref/4 (stored deviations)
+            const R h4 = (dtemp + R(C.t_ref)) * R(Sc(0.25));
+            const R h2r = (h4 + h4) * ur, h2z = (h4 + h4) * uz;
+            const R heq[4] = {h4 + h2r, h4 + h2z, h4 - h2r, h4 - h2z};
+            const Sc hp = C.h0 + C.h1 * inv_r, hm = C.h0 - C.h1 * inv_r;
+            const Sc tref4 = C.t_ref * Sc(0.25);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int ex = cr4(q), ez = cz4(q);
-                const R heq = temp4 * (R(1) + R(2) * (R(ex) * ur + R(ez) * uz));
-                const R om = ex == 0 ? C.h0 : (ex > 0 ? C.h0 + C.h1 * inv_r : C.h0 - C.h1 * inv_r);
-                h[q] = h[q] - om * (h[q] - (heq - tref4)) - urr * heq;
+                const int ex = cr4(q);
+                const Sc om = ex == 0 ? C.h0 : (ex > 0 ? hp : hm);
+                h[q] = fmaR(R(one - om), h[q], fmaR(R(om) - urr, heq[q], R(-om * tref4)));
             }
         }
     }
@@ -360,78 +399,322 @@ __device__ __forceinline__ R inv_radius(const Geom& G, int j) {
 
 // ---------------------------------------------------------------------------- kernels
 
-// Bulk update: every node in even steps, interior nodes in odd steps.
-template <class S, class R, bool SW, bool TH, int PAR, bool CHK>
-__global__ void __launch_bounds__(kThreads) k_bulk(const KArgs<S, R> A) {
-    const Geom& G = A.G;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const R az = R(A.clock->a_z[PAR]);
-    Red red{0.0, 0.0, 0.0, 0.0};
-    for (int k = blockIdx.y * blockDim.y + threadIdx.y; k < G.nz; k += gridDim.y * blockDim.y) {
-        bool act = j < G.nr;
-        if (PAR == 1) act = act && j > 0 && j < G.nr - 1 && k > 0 && k < G.nz - 1;
-        if (!act) continue;
-        const long long x = (long long)k * G.pitch + j;
-        Cell<R, SW, TH> c;
-        if (PAR == 0) {
-#pragma unroll
-            for (int a = 0; a < 9; ++a) c.d[a] = Codec<S>::load(A.pop + a * G.plane + x);
-            if (SW) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) c.g[q] = Codec<S>::load(A.pop + (A.g_plane + q) * G.plane + x);
-            }
-            if (TH) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) c.h[q] = Codec<S>::load(A.pop + (A.h_plane + q) * G.plane + x);
-            }
-        } else {
-#pragma unroll
-            for (int a = 0; a < 9; ++a)
-                c.d[a] = Codec<S>::load(A.pop + opp9(a) * G.plane + x - cz9(a) * G.pitch - cr9(a));
-            if (SW) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    c.g[q] = Codec<S>::load(A.pop + (A.g_plane + opp4(q)) * G.plane + x - cz4(q) * G.pitch - cr4(q));
-            }
-            if (TH) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    c.h[q] = Codec<S>::load(A.pop + (A.h_plane + opp4(q)) * G.plane + x - cz4(q) * G.pitch - cr4(q));
-            }
-        }
-        const R inv_r = inv_radius<R>(G, j);
-        c.collide(inv_r, A.C, az);
-        if (PAR == 0) {
-#pragma unroll
-            for (int a = 0; a < 9; ++a) Codec<S>::store(A.pop + opp9(a) * G.plane + x, c.d[a]);
-            if (SW) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) Codec<S>::store(A.pop + (A.g_plane + opp4(q)) * G.plane + x, c.g[q]);
-            }
-            if (TH) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) Codec<S>::store(A.pop + (A.h_plane + opp4(q)) * G.plane + x, c.h[q]);
-            }
-        } else {
-#pragma unroll
-            for (int a = 0; a < 9; ++a)
-                Codec<S>::store(A.pop + a * G.plane + x + cz9(a) * G.pitch + cr9(a), c.d[a]);
-            if (SW) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    Codec<S>::store(A.pop + (A.g_plane + q) * G.plane + x + cz4(q) * G.pitch + cr4(q), c.g[q]);
-            }
-            if (TH) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    Codec<S>::store(A.pop + (A.h_plane + q) * G.plane + x + cz4(q) * G.pitch + cr4(q), c.h[q]);
-            }
-        }
-        if (CHK) check_cell(A, j, k, inv_r, c, red);
+// ---------------------------------------------------------------------------- bulk kernel
+
+// Tiles of kTileK rows x kTileJ nodes; each population plane of a tile is
+// staged in shared memory by one TMA box that starts kHalo<S> elements before
+// the tile (so its x coordinate is 16-byte aligned) and is kBoxW<S> wide.
+constexpr int kBulkThreads = 256;
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz: only a broken copy can take this long
+template <class S>
+constexpr int kHalo = 16 / (int)sizeof(S);
+template <class S>
+constexpr int kBoxW = kTileJ + 2 * kHalo<S>;
+
+template <bool SW, bool TH>
+__host__ __device__ constexpr int nplanes() { return 9 + (SW ? 4 : 0) + (TH ? 4 : 0); }
+
+template <class S, bool SW, bool TH>
+__host__ __device__ constexpr int stage_elems() { return nplanes<SW, TH>() * kTileK * kBoxW<S>; }
+
+// Pipeline depth: three stages when they fit in ~200 KB, else two.
+template <class S, bool SW, bool TH>
+__host__ __device__ constexpr int nstages() { return 3 * stage_elems<S, SW, TH>() * (int)sizeof(S) <= 200 * 1024 ? 3 : 2; }
+
+// Dynamic shared memory of the bulk kernel: the stages plus 128 bytes to
+// align their base to 128 bytes.
+template <class S, bool SW, bool TH>
+__host__ __device__ constexpr size_t bulk_smem_bytes() {
+    return (size_t)nstages<S, SW, TH>() * stage_elems<S, SW, TH>() * sizeof(S) + 128;
+}
+
+// Velocity of stored plane p (f planes, then g, then h).
+template <bool SW>
+__device__ __forceinline__ constexpr int plane_cr(int p) { return p < 9 ? cr9(p) : cr4((p - 9) & 3); }
+template <bool SW>
+__device__ __forceinline__ constexpr int plane_cz(int p) { return p < 9 ? cz9(p) : cz4((p - 9) & 3); }
+
+// Access to the nodes held in one arithmetic value: one for float / double,
+// two for a pair (lane 0 = .x, lane 1 = .y).
+template <class R>
+struct Lanes {
+    static constexpr int n = 1;
+    template <class S>
+    __device__ static __forceinline__ R load(const S* p, int /*lane_stride*/) { return Codec<S>::load(p); }
+    __device__ static __forceinline__ R get(R v, int) { return v; }
+};
+template <>
+struct Lanes<F2> {
+    static constexpr int n = 2;
+    template <class S>
+    __device__ static __forceinline__ F2 load(const S* p, int lane_stride) {
+        return F2(Codec<S>::load(p), Codec<S>::load(p + lane_stride));
     }
-    if (CHK) block_reduce_store(red, A.partials + 4ll * (A.part_offset + blockIdx.y * gridDim.x + blockIdx.x));
-    if (PAR == 0 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
-        advance_clock(A.clock, PAR, A.az0, A.omega_t);
+    __device__ static __forceinline__ float get(F2 v, int l) { return l ? v.v.y : v.v.x; }
+};
+
+// Per-thread check accumulators in the arithmetic type (FP32 in FP32 mode:
+// the mass is kept as the deviation sum, so FP32 partial sums lose nothing
+// that matters), folded to FP64 per warp and per block.
+template <class R>
+struct RedR {
+    R rmax, dmass, budget;
+    int bad, count;
+};
+
+template <class R>
+__device__ __forceinline__ void block_reduce_store_r(RedR<R> v, double rho0, double* out) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        v.rmax = max(v.rmax, __shfl_down_sync(0xffffffffu, v.rmax, off));
+        v.dmass += __shfl_down_sync(0xffffffffu, v.dmass, off);
+        v.budget += __shfl_down_sync(0xffffffffu, v.budget, off);
+        v.bad += __shfl_down_sync(0xffffffffu, v.bad, off);
+        v.count += __shfl_down_sync(0xffffffffu, v.count, off);
+    }
+    Red w{(double)v.rmax, (double)v.count * rho0 + (double)v.dmass, (double)v.budget, (double)v.bad};
+    __shared__ double sh[4][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        sh[0][warp] = w.rmax;
+        sh[1][warp] = w.mass;
+        sh[2][warp] = w.budget;
+        sh[3][warp] = w.bad;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        Red x{0.0, 0.0, 0.0, 0.0};
+        if (lane < nwarps) x = Red{sh[0][lane], sh[1][lane], sh[2][lane], sh[3][lane]};
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            x.rmax = fmax(x.rmax, __shfl_down_sync(0xffffffffu, x.rmax, off));
+            x.mass += __shfl_down_sync(0xffffffffu, x.mass, off);
+            x.budget += __shfl_down_sync(0xffffffffu, x.budget, off);
+            x.bad += __shfl_down_sync(0xffffffffu, x.bad, off);
+        }
+        if (lane == 0) {
+            out[0] = x.rmax;
+            out[1] = x.mass;
+            out[2] = x.budget;
+            out[3] = x.bad;
+        }
+    }
+}
+
+// Tile visited at position i: odd steps walk the tiles backwards, so they
+// start on the rows the even step wrote last (still in L2).
+template <int PAR>
+__device__ __forceinline__ int tile_at(int i, int ntiles) { return PAR ? ntiles - 1 - i : i; }
+
+// Issue the TMA boxes of every plane of `tile` into stage buffer `dst`.
+template <class S, bool SW, bool TH, int PAR>
+__device__ __forceinline__ void issue_tile(const CUtensorMap* map, S* dst, uint64_t* bar, int tile, int tiles_j) {
+    constexpr int P = nplanes<SW, TH>();
+    constexpr uint32_t bytes = (uint32_t)(P * kTileK * kBoxW<S> * sizeof(S));
+    const int j0 = (tile % tiles_j) * kTileJ, k0 = (tile / tiles_j) * kTileK;
+    mbar_arrive_expect_tx(bar, bytes);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        // odd step: node (j, k) needs plane p at (j + e_pr, k + e_pz)
+        const int dy = PAR ? plane_cz<SW>(p) : 0;
+        tma_load_3d(dst + p * kTileK * kBoxW<S>, map, bar, j0 - kHalo<S>, k0 + dy, p);
+    }
+}
+
+// Bulk update (persistent, warp-specialised): every node in even steps,
+// interior nodes in odd steps.  Even: plane a of a node is its own population
+// a, written back to plane opp(a) of the node.  Odd: population a comes from
+// plane opp(a) of the node x - e_a and goes to plane a of x + e_a.
+//
+// Warp kConsumerWarps is the producer: one lane issues the TMA boxes of the
+// CTA's tiles into a ring of NS stages, refilling a stage once its "empty"
+// barrier shows that every consumer warp has finished with it.  Consumer
+// warps wait on the stage's "full" barrier, update their nodes from shared
+// memory, store to global memory, and release the stage per warp.  Every
+// wait is bounded; a wait that gives up raises the CTA's abort flag, the
+// producer lets the copies it issued land, and the error word is set.
+constexpr int kConsumerWarps = kBulkThreads / 32;
+
+template <class S, class R, bool SW, bool TH, int PAR, bool CHK>
+__global__ void __launch_bounds__(kBulkThreads + 32, (SW || TH || CHK) ? 2 : 3)
+k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
+    constexpr int NS = nstages<S, SW, TH>();
+    constexpr int STAGE = stage_elems<S, SW, TH>();
+    constexpr int HB = kHalo<S>, BW = kBoxW<S>;
+    constexpr int HP = SW ? 13 : 9;  // first h plane
+    using RC = typename std::conditional<std::is_same<R, float>::value, F2, R>::type;  // per-thread arithmetic
+    using Sc = R;
+    static_assert(kTileK == 4 && kBulkThreads == 2 * kTileJ, "pairing assumes 4-row tiles and 2 threads per column");
+    constexpr int kRowsPerThread = kTileK * kTileJ / kBulkThreads;  // 2: rows rr0 and rr0 + 2
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    S* sm = reinterpret_cast<S*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    __shared__ __align__(8) uint64_t full[NS];
+    __shared__ __align__(8) uint64_t empty[NS];
+    __shared__ volatile int abort_flag;
+
+    const Geom& G = A.G;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int ntiles = A.tiles_j * A.tiles_k;
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
+        abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    RedR<R> red{R(0), R(0), R(0), 0, 0};
+    if (warp == kConsumerWarps) {
+        // ---------------- producer
+        if (lane == 0) {
+            prefetch_tensormap(&map);
+            int last_par[NS];
+            for (int s = 0; s < NS; ++s) last_par[s] = -1;
+            int it = 0;
+            for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++it) {
+                const int s = it % NS;
+                if (it >= NS && !mbar_wait_bounded(&empty[s], (uint32_t)(((it / NS) - 1) & 1), kWaitCycles)) {
+                    abort_flag = 1;
+                    break;
+                }
+                if (abort_flag) break;
+                issue_tile<S, SW, TH, PAR>(&map, sm + s * STAGE, &full[s], tile_at<PAR>(i, ntiles), A.tiles_j);
+                last_par[s] = (it / NS) & 1;
+            }
+            if (abort_flag) {
+                // let every copy this CTA issued land before the CTA exits
+                for (int s = 0; s < NS; ++s)
+                    if (last_par[s] >= 0) mbar_wait_bounded(&full[s], (uint32_t)last_par[s], kWaitCycles);
+            }
+        }
+    } else {
+        // ---------------- consumers
+        // FP32 arithmetic: each thread updates the two nodes of its column in
+        // rows rr and rr + 2 as one pair (same radius); FP64: one node at a time.
+        constexpr int NL = Lanes<RC>::n;
+        const Sc az = Sc(A.clock->a_z[PAR]);
+        const int jj = tid % kTileJ;
+        int it = 0;
+        for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++it) {
+            const int s = it % NS;
+            const int tile = tile_at<PAR>(i, ntiles);
+            const int j0 = (tile % A.tiles_j) * kTileJ, k0 = (tile / A.tiles_j) * kTileK;
+            const int j = j0 + jj;
+            // the previous level's |u| of this thread's nodes, loaded before the
+            // wait so its latency overlaps the wait and the collision
+            // (this thread's nodes are rows rr0 + 2m, m < kRowsPerThread, of column jj)
+            R sp_old[kRowsPerThread];
+            if (CHK) {
+#pragma unroll
+                for (int m = 0; m < kRowsPerThread; ++m) {
+                    const int k = k0 + tid / kTileJ + 2 * m;
+                    sp_old[m] = (A.residual && j < G.nr && k < G.nz) ? A.speed[(long long)k * G.pitch + j] : R(0);
+                }
+            }
+            if (!mbar_wait_bounded(&full[s], (uint32_t)((it / NS) & 1), kWaitCycles) || abort_flag) {
+                abort_flag = 1;
+                break;
+            }
+            const S* st = sm + s * STAGE;
+            const Sc inv_r = rcp(Sc(G.r0 + (double)j + 0.5));
+#pragma unroll
+            for (int rr = tid / kTileJ; rr < kTileK / NL; rr += kBulkThreads / kTileJ) {
+                bool act[NL];
+                int kk[NL];
+                bool any = false;
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    kk[l] = k0 + rr + l * (kTileK / NL);
+                    act[l] = j < G.nr && kk[l] < G.nz;
+                    if (PAR == 1) act[l] = act[l] && j > 0 && j < G.nr - 1 && kk[l] > 0 && kk[l] < G.nz - 1;
+                    any = any || act[l];
+                }
+                if (!any) continue;
+                Cell<RC, SW, TH> c;
+                const S* row = st + rr * BW + HB + jj;
+                constexpr int LROW = (kTileK / NL) * BW;  // shared-memory distance between the lanes' rows
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    const int p = PAR ? opp9(a) : a;
+                    c.d[a] = Lanes<RC>::template load<S>(row + p * kTileK * BW + (PAR ? cr9(p) : 0), LROW);
+                }
+                if (SW) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int p = PAR ? opp4(q) : q;
+                        c.g[q] = Lanes<RC>::template load<S>(row + (9 + p) * kTileK * BW + (PAR ? cr4(p) : 0), LROW);
+                    }
+                }
+                if (TH) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int p = PAR ? opp4(q) : q;
+                        c.h[q] = Lanes<RC>::template load<S>(row + (HP + p) * kTileK * BW + (PAR ? cr4(p) : 0), LROW);
+                    }
+                }
+                c.collide(inv_r, A.C, az);
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    if (!act[l]) continue;
+                    const long long x = (long long)kk[l] * G.pitch + j;
+                    if (PAR == 0) {
+#pragma unroll
+                        for (int a = 0; a < 9; ++a) Codec<S>::store(A.pop + opp9(a) * G.plane + x, Lanes<RC>::get(c.d[a], l));
+                        if (SW) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                Codec<S>::store(A.pop + (9 + opp4(q)) * G.plane + x, Lanes<RC>::get(c.g[q], l));
+                        }
+                        if (TH) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                Codec<S>::store(A.pop + (HP + opp4(q)) * G.plane + x, Lanes<RC>::get(c.h[q], l));
+                        }
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < 9; ++a)
+                            Codec<S>::store(A.pop + a * G.plane + x + cz9(a) * G.pitch + cr9(a), Lanes<RC>::get(c.d[a], l));
+                        if (SW) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                Codec<S>::store(A.pop + (9 + q) * G.plane + x + cz4(q) * G.pitch + cr4(q),
+                                                Lanes<RC>::get(c.g[q], l));
+                        }
+                        if (TH) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                Codec<S>::store(A.pop + (HP + q) * G.plane + x + cz4(q) * G.pitch + cr4(q),
+                                                Lanes<RC>::get(c.h[q], l));
+                        }
+                    }
+                    if (CHK) {
+                        const R vur = Lanes<RC>::get(c.ur, l), vuz = Lanes<RC>::get(c.uz, l);
+                        const R vrho = Lanes<RC>::get(c.rho, l);
+                        const R sp = sqrt(vur * vur + vuz * vuz);
+                        if (A.residual) red.rmax = max(red.rmax, (R)fabs(sp - sp_old[(rr - tid / kTileJ) / 2 + l]));
+                        A.speed[x] = sp;
+                        red.dmass += Lanes<RC>::get(c.ds0, l);
+                        red.budget += vrho * vur * inv_r;
+                        red.bad += (isfinite(vrho) && isfinite(vur) && isfinite(vuz)) ? 0 : 1;
+                        red.count += 1;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with stage s
+        }
+    }
+    __syncthreads();
+    if (abort_flag) {
+        if (tid == 0) atomicOr(A.err, 1u);
+        return;
+    }
+    if (CHK) block_reduce_store_r(red, (double)A.C.rho0, A.partials + 4ll * (A.part_offset + blockIdx.x));
+    if (PAR == 0 && blockIdx.x == 0 && tid == 0) advance_clock(A.clock, PAR, A.az0, A.omega_t);
 }
 
 // Coordinates of the i-th node of the outer ring (bottom row, top row, then
@@ -615,7 +898,69 @@ KArgs<S, R> make_args(axlbm_handle* h) {
     A.h_plane = h->L.h_plane < 0 ? 0 : h->L.h_plane;
     A.nframe = h->L.nframe;
     A.residual = 0;
+    A.tiles_j = h->L.tiles_j;
+    A.tiles_k = h->L.tiles_k;
+    A.err = &A.clock->err;
     return A;
+}
+
+// Launch the persistent bulk kernel: one CTA per (SM x resident CTAs), capped
+// by the number of tiles; returns the number of CTAs launched in *blocks.
+template <class S, class R, bool SW, bool TH, int PAR, bool CHK>
+cudaError_t launch_bulk(axlbm_handle* h, const KArgs<S, R>& A, int* blocks) {
+    auto kern = k_bulk<S, R, SW, TH, PAR, CHK>;
+    constexpr size_t smem = bulk_smem_bytes<S, SW, TH>();
+    int& grid = h->bulk_grid[PAR][CHK ? 1 : 0];
+    if (grid == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBulkThreads + 32, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        const long long tiles = (long long)A.tiles_j * A.tiles_k;
+        long long g = (long long)h->num_sms * per_sm;
+        if (g > tiles) g = tiles;
+        if (g > kMaxBulkBlocks) g = kMaxBulkBlocks;
+        grid = (int)g;
+    }
+    kern<<<grid, kBulkThreads + 32, smem, h->stream>>>(h->tmap, A);
+    *blocks = grid;
+    return cudaGetLastError();
+}
+
+template <class S>
+constexpr CUtensorMapDataType tma_type() {
+    return sizeof(S) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                          : (sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                            : (std::is_same<S, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                              : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16));
+}
+
+// TMA descriptor of the population planes: x = node along r (pitch elements),
+// y = row k, z = plane; box kBoxW x kTileK x 1.
+template <class S>
+cudaError_t prepare_impl(axlbm_handle* h) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<Encode>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)h->L.pitch, (cuuint64_t)h->G.nz, (cuuint64_t)h->L.nplanes};
+    const cuuint64_t strides[2] = {(cuuint64_t)h->L.pitch * sizeof(S), (cuuint64_t)h->L.plane * sizeof(S)};
+    const cuuint32_t box[3] = {(cuuint32_t)kBoxW<S>, (cuuint32_t)kTileK, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = encode(&h->tmap, tma_type<S>(), 3, h->mem, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 template <class S, class R, bool SW, bool TH>
@@ -623,32 +968,30 @@ cudaError_t step_sw(axlbm_handle* h, int check, int residual, cudaEvent_t ev0, c
     KArgs<S, R> A = make_args<S, R>(h);
     A.residual = residual;
     const Layout& L = h->L;
-    const dim3 blk(L.bx, L.by), grd(L.gx, L.gy);
     *nlaunch = 0;
+    int blocks = 0;
+    cudaError_t e = cudaSuccess;
+    if (ev0) cudaEventRecord(ev0, h->stream);
     if (h->parity == 0) {
-        if (ev0) cudaEventRecord(ev0, h->stream);
-        if (check) k_bulk<S, R, SW, TH, 0, true><<<grd, blk, 0, h->stream>>>(A);
-        else k_bulk<S, R, SW, TH, 0, false><<<grd, blk, 0, h->stream>>>(A);
+        e = check ? launch_bulk<S, R, SW, TH, 0, true>(h, A, &blocks) : launch_bulk<S, R, SW, TH, 0, false>(h, A, &blocks);
         if (ev1) cudaEventRecord(ev1, h->stream);
         *nlaunch = 1;
+        if (check) h->check_parts = blocks;
     } else {
-        const bool interior = h->G.nr > 2 && h->G.nz > 2;
-        if (ev0) cudaEventRecord(ev0, h->stream);
-        if (interior) {
-            if (check) k_bulk<S, R, SW, TH, 1, true><<<grd, blk, 0, h->stream>>>(A);
-            else k_bulk<S, R, SW, TH, 1, false><<<grd, blk, 0, h->stream>>>(A);
+        if (h->G.nr > 2 && h->G.nz > 2) {
+            e = check ? launch_bulk<S, R, SW, TH, 1, true>(h, A, &blocks) : launch_bulk<S, R, SW, TH, 1, false>(h, A, &blocks);
             *nlaunch += 1;
-        } else if (check) {
-            // no interior: the bulk slots of the partials must still be neutral
-            cudaMemsetAsync(A.partials, 0, sizeof(double) * 4 * L.gx * L.gy, h->stream);
         }
         if (ev1) cudaEventRecord(ev1, h->stream);
-        A.part_offset = L.gx * L.gy;
+        if (e != cudaSuccess) return e;
+        A.part_offset = blocks;  // the frame blocks follow the bulk blocks
         if (check) k_frame<S, R, SW, TH, true><<<L.frame_blocks, kThreads, 0, h->stream>>>(A);
         else k_frame<S, R, SW, TH, false><<<L.frame_blocks, kThreads, 0, h->stream>>>(A);
         *nlaunch += 1;
+        if (check) h->check_parts = blocks + L.frame_blocks;
+        e = cudaGetLastError();
     }
-    return cudaGetLastError();
+    return e;
 }
 
 template <class S, class R>
@@ -724,12 +1067,11 @@ cudaError_t scatter_impl(axlbm_handle* h, const double* in) {
     AXL_DISPATCH_SWTH(scatter_sw, h, in);
 }
 
-// Reduce the partials of the check step that just ran with AA parity `parity`.
-inline cudaError_t finalize_impl(axlbm_handle* h, int parity) {
+// Reduce the partials of the check step that just ran.
+inline cudaError_t finalize_impl(axlbm_handle* h, int /*parity*/) {
     const double* parts = reinterpret_cast<const double*>(h->mem + h->L.off_part);
     double* res = reinterpret_cast<double*>(h->mem + h->L.off_result);
-    const int n = parity == 0 ? h->L.gx * h->L.gy : h->L.nparts;
-    return launch_finalize(parts, n, res, h->stream);
+    return launch_finalize(parts, h->check_parts, res, h->stream);
 }
 
 template <class S, class R>
@@ -741,6 +1083,7 @@ Ops make_ops() {
     o.gather = &gather_impl<S, R>;
     o.scatter = &scatter_impl<S, R>;
     o.finalize = &finalize_impl;
+    o.prepare = &prepare_impl<S>;
     return o;
 }
 
