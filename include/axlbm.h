@@ -232,6 +232,84 @@ AXLBM_API axlbm_status axlbm_check_static(const axlbm_grid* grid, double tau, co
                                           const double* speed_prev, double* speed_out, double* out,
                                           void* cuda_stream);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent domains of uneven size advanced together: every step is
+ * one persistent launch over a packed tile list of all domains (plus one
+ * launch for all domains' boundary rings in odd steps).  Each domain follows
+ * exactly the single-domain update above (its own grid, tau, forcing and
+ * boundary); only the storage precision is common.  Domains must all carry
+ * the swirl distribution g; temperature may differ between domains.
+ * Supported storage: AXLBM_FP32 and AXLBM_FP16_DEV. */
+typedef struct axlbm_batch axlbm_batch;
+
+typedef struct {
+    axlbm_grid grid;          /* precision field ignored (the batch's applies) */
+    double tau;               /* standard relaxation time of f */
+    axlbm_forcing forcing;
+    axlbm_boundary boundary;
+} axlbm_domain;
+
+/* Device bytes of a batch of n domains (populations, check buffers, tile
+ * lists, descriptors) for callers that provide the memory themselves. */
+AXLBM_API axlbm_status axlbm_batch_state_bytes(const axlbm_domain* domains, int32_t n, int32_t precision,
+                                               size_t* bytes);
+
+/* Create a batch at rest (every domain as axlbm_create leaves it), time 0.
+ * Validates every domain as axlbm_create does (AXLBM_EINVAL naming the
+ * first bad domain in axlbm_batch_last_error), packs the domains, and picks
+ * the bulk tile shape by timing the candidates on this batch (the result is
+ * cached per GPU, precision and population mix for the process).  Memory
+ * and stream conventions as axlbm_create.  Synchronises. */
+AXLBM_API axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t precision,
+                                          void* cuda_stream, void* state_mem, size_t state_bytes,
+                                          axlbm_batch** out);
+
+/* Advance every domain n >= 0 steps (asynchronous).  As axlbm_step, the last
+ * step of every call is a check step recording each domain's Eq. 57
+ * residual, mass and budget. */
+AXLBM_API axlbm_status axlbm_batch_step(axlbm_batch* b, int64_t n);
+
+/* Per-domain results of the last check step into out[3 * d + 0..2] =
+ * residual (Eq. 57), mass, budget (host, n * 3 doubles).  Synchronises.
+ * AXLBM_ENONFINITE (values still written) if any domain saw a NaN or Inf. */
+AXLBM_API axlbm_status axlbm_batch_residuals(axlbm_batch* b, double* out);
+
+/* Macroscopic fields of domain d, as axlbm_moments. */
+AXLBM_API axlbm_status axlbm_batch_moments(axlbm_batch* b, int32_t d, uint32_t field_mask, void* out,
+                                           int32_t out_dtype, int32_t out_on_device);
+
+/* Equilibrium reset of domain d from fields [5][nz][nr], as axlbm_set_fields.
+ * Needs the batch at an even time level (AXLBM_EINVAL otherwise): the other
+ * domains' populations are left in the layout of that level. */
+AXLBM_API axlbm_status axlbm_batch_set_fields(axlbm_batch* b, int32_t d, const void* fields, int32_t in_dtype,
+                                              int32_t on_device);
+
+/* Populations of domain d at the current level (host FP64, layout as
+ * axlbm_get_populations).  Synchronises. */
+AXLBM_API axlbm_status axlbm_batch_get_populations(axlbm_batch* b, int32_t d, double* f, double* g,
+                                                   double* t_pop);
+
+/* Replace domain d's populations (host FP64).  Even time level only, as
+ * axlbm_batch_set_fields.  Synchronises. */
+AXLBM_API axlbm_status axlbm_batch_set_populations(axlbm_batch* b, int32_t d, const double* f, const double* g,
+                                                   const double* t_pop);
+
+/* Time level of the batch, and the bulk tile shape (rows x nodes) in use. */
+AXLBM_API axlbm_status axlbm_batch_time(const axlbm_batch* b, int64_t* time);
+AXLBM_API axlbm_status axlbm_batch_tile_shape(const axlbm_batch* b, int32_t* rows, int32_t* nodes);
+
+/* Bulk-kernel timing of the batch, as axlbm_kernel_timing / axlbm_kernel_times. */
+AXLBM_API axlbm_status axlbm_batch_kernel_timing(axlbm_batch* b, int32_t enable);
+AXLBM_API axlbm_status axlbm_batch_kernel_times(axlbm_batch* b, int64_t* bulk_launches, double* bulk_ms,
+                                                double* bulk_bytes, int64_t* all_launches);
+
+/* Free the batch (after synchronising its stream). */
+AXLBM_API axlbm_status axlbm_batch_destroy(axlbm_batch* b);
+
+/* Text of the last error on b, or of the last failed batch call without a
+ * batch when b is NULL. */
+AXLBM_API const char* axlbm_batch_last_error(const axlbm_batch* b);
+
 /* Free the handle and library-owned memory (after synchronising its stream). */
 AXLBM_API axlbm_status axlbm_destroy(axlbm_handle* h);
 

@@ -49,6 +49,11 @@ class axlbm_boundary(ctypes.Structure):
                 ("t_wall", ctypes.c_double * 4)]
 
 
+class axlbm_domain(ctypes.Structure):
+    _fields_ = [("grid", axlbm_grid), ("tau", ctypes.c_double), ("forcing", axlbm_forcing),
+                ("boundary", axlbm_boundary)]
+
+
 class AxlbmError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"axlbm status {status}: {message}")
@@ -91,6 +96,29 @@ def lib() -> ctypes.CDLL:
                                          ctypes.c_void_p, ctypes.c_void_p]
         L.axlbm_last_error.restype = ctypes.c_char_p
         L.axlbm_last_error.argtypes = [H]
+        DP = ctypes.POINTER(axlbm_domain)
+        L.axlbm_batch_state_bytes.argtypes = [DP, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+        L.axlbm_batch_create.argtypes = [DP, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_size_t, ctypes.POINTER(H)]
+        L.axlbm_batch_step.argtypes = [H, ctypes.c_int64]
+        L.axlbm_batch_residuals.argtypes = [H, dp]
+        L.axlbm_batch_moments.argtypes = [H, ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.c_int32]
+        L.axlbm_batch_set_fields.argtypes = [H, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
+        L.axlbm_batch_get_populations.argtypes = [H, ctypes.c_int32, dp, dp, dp]
+        L.axlbm_batch_set_populations.argtypes = [H, ctypes.c_int32, dp, dp, dp]
+        L.axlbm_batch_time.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
+        L.axlbm_batch_tile_shape.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+        L.axlbm_batch_kernel_timing.argtypes = [H, ctypes.c_int32]
+        L.axlbm_batch_kernel_times.argtypes = [H, ctypes.POINTER(ctypes.c_int64), dp, dp, ctypes.POINTER(ctypes.c_int64)]
+        L.axlbm_batch_destroy.argtypes = [H]
+        L.axlbm_batch_last_error.restype = ctypes.c_char_p
+        L.axlbm_batch_last_error.argtypes = [H]
+        for name in ("axlbm_batch_state_bytes", "axlbm_batch_create", "axlbm_batch_step", "axlbm_batch_residuals",
+                     "axlbm_batch_moments", "axlbm_batch_set_fields", "axlbm_batch_get_populations",
+                     "axlbm_batch_set_populations", "axlbm_batch_time", "axlbm_batch_tile_shape",
+                     "axlbm_batch_kernel_timing", "axlbm_batch_kernel_times", "axlbm_batch_destroy"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("axlbm_state_bytes", "axlbm_create", "axlbm_step", "axlbm_moments", "axlbm_residual",
                      "axlbm_set_fields", "axlbm_get_populations", "axlbm_set_populations", "axlbm_time",
                      "axlbm_destroy", "axlbm_kernel_timing", "axlbm_kernel_times", "axlbm_check_static"):
@@ -295,3 +323,163 @@ class Domain:
     def set_populations(self, f, g=None, h=None, time: int = 0) -> None:
         cast = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
         axlbm_set_populations(self.handle, cast(f), cast(g), cast(h), time)
+
+
+# ----------------------------------------------------------------------------- batches
+
+
+def _bcheck(status: int, batch=None) -> int:
+    if status != OK:
+        msg = lib().axlbm_batch_last_error(batch).decode(errors="replace")
+        raise AxlbmError(status, msg or lib().axlbm_status_string(status).decode())
+    return status
+
+
+def domain_array(problems):
+    """ctypes array of axlbm_domain for a list of Problems."""
+    arr = (axlbm_domain * len(problems))()
+    for i, pb in enumerate(problems):
+        g, tau, f, b = structs(pb, "fp32")
+        arr[i].grid, arr[i].tau, arr[i].forcing, arr[i].boundary = g, tau, f, b
+    return arr
+
+
+def axlbm_batch_state_bytes(domains, precision: int) -> int:
+    n = ctypes.c_size_t()
+    _bcheck(lib().axlbm_batch_state_bytes(domains, len(domains), int(precision), ctypes.byref(n)))
+    return int(n.value)
+
+
+def axlbm_batch_create(domains, precision: int, stream: int = 0, state_mem: int = 0, state_bytes: int = 0):
+    h = ctypes.c_void_p()
+    _bcheck(lib().axlbm_batch_create(domains, len(domains), int(precision), ctypes.c_void_p(stream or None),
+                                     ctypes.c_void_p(state_mem or None), ctypes.c_size_t(state_bytes),
+                                     ctypes.byref(h)))
+    return h
+
+
+def axlbm_batch_step(b, n: int) -> None:
+    _bcheck(lib().axlbm_batch_step(b, int(n)), b)
+
+
+def axlbm_batch_residuals(b, n_domains: int, allow_nonfinite: bool = False) -> np.ndarray:
+    out = np.empty((n_domains, 3))
+    st = lib().axlbm_batch_residuals(b, _dptr(out))
+    if not (allow_nonfinite and st == ENONFINITE):
+        _bcheck(st, b)
+    return out
+
+
+def axlbm_batch_moments(b, d: int, mask: int, out_ptr: int, out_dtype: int, out_on_device: int) -> None:
+    _bcheck(lib().axlbm_batch_moments(b, int(d), int(mask), ctypes.c_void_p(out_ptr), int(out_dtype),
+                                      int(out_on_device)), b)
+
+
+def axlbm_batch_set_fields(b, d: int, ptr: int, in_dtype: int, on_device: int) -> None:
+    _bcheck(lib().axlbm_batch_set_fields(b, int(d), ctypes.c_void_p(ptr), int(in_dtype), int(on_device)), b)
+
+
+def axlbm_batch_get_populations(b, d: int, f, g, t_pop) -> None:
+    _bcheck(lib().axlbm_batch_get_populations(b, int(d), _dptr(f), _dptr(g), _dptr(t_pop)), b)
+
+
+def axlbm_batch_set_populations(b, d: int, f, g, t_pop) -> None:
+    _bcheck(lib().axlbm_batch_set_populations(b, int(d), _dptr(f), _dptr(g), _dptr(t_pop)), b)
+
+
+def axlbm_batch_time(b) -> int:
+    t = ctypes.c_int64()
+    _bcheck(lib().axlbm_batch_time(b, ctypes.byref(t)), b)
+    return int(t.value)
+
+
+def axlbm_batch_tile_shape(b):
+    r, c = ctypes.c_int32(), ctypes.c_int32()
+    _bcheck(lib().axlbm_batch_tile_shape(b, ctypes.byref(r), ctypes.byref(c)), b)
+    return int(r.value), int(c.value)
+
+
+def axlbm_batch_kernel_timing(b, enable: bool) -> None:
+    _bcheck(lib().axlbm_batch_kernel_timing(b, int(bool(enable))), b)
+
+
+def axlbm_batch_kernel_times(b):
+    nb, na = ctypes.c_int64(), ctypes.c_int64()
+    ms, by = ctypes.c_double(), ctypes.c_double()
+    _bcheck(lib().axlbm_batch_kernel_times(b, ctypes.byref(nb), ctypes.byref(ms), ctypes.byref(by),
+                                           ctypes.byref(na)), b)
+    return int(nb.value), ms.value, by.value, int(na.value)
+
+
+def axlbm_batch_destroy(b) -> None:
+    _bcheck(lib().axlbm_batch_destroy(b))
+
+
+class Batch:
+    """Many domains advanced together, on PyTorch-owned device memory and stream."""
+
+    def __init__(self, problems, precision: str = "fp32", stream=None):
+        import torch
+
+        self.problems = list(problems)
+        self.domains = domain_array(self.problems)
+        self.precision = PRECISIONS[precision]
+        nbytes = axlbm_batch_state_bytes(self.domains, self.precision)
+        self._mem = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = axlbm_batch_create(self.domains, self.precision, stream=self.stream.cuda_stream,
+                                         state_mem=self._mem.data_ptr(), state_bytes=nbytes)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None:
+            axlbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int) -> None:
+        axlbm_batch_step(self.handle, n)
+
+    @property
+    def time(self) -> int:
+        return axlbm_batch_time(self.handle)
+
+    @property
+    def tile_shape(self):
+        return axlbm_batch_tile_shape(self.handle)
+
+    def residuals(self, allow_nonfinite: bool = False) -> np.ndarray:
+        """[n][3]: residual (Eq. 57), mass, budget of each domain's last check step."""
+        return axlbm_batch_residuals(self.handle, len(self.problems), allow_nonfinite)
+
+    def moments(self, d: int, mask: int = RHO | UR | UZ, dtype=np.float64) -> np.ndarray:
+        pb = self.problems[d]
+        out = np.empty((bin(mask).count("1"), pb.nz, pb.nr), dtype=dtype)
+        axlbm_batch_moments(self.handle, d, mask, out.ctypes.data, F64 if dtype == np.float64 else F32, 0)
+        return out
+
+    def set_fields(self, d: int, fields) -> None:
+        if isinstance(fields, np.ndarray):
+            a = np.ascontiguousarray(fields, dtype=np.float64)
+            axlbm_batch_set_fields(self.handle, d, a.ctypes.data, F64, 0)
+        else:
+            import torch
+
+            axlbm_batch_set_fields(self.handle, d, fields.data_ptr(),
+                                   F32 if fields.dtype == torch.float32 else F64, 1)
+
+    def get_populations(self, d: int):
+        pb = self.problems[d]
+        shape = (pb.nz, pb.nr)
+        f, g = np.empty((9,) + shape), np.empty((4,) + shape)
+        h = np.empty((4,) + shape) if pb.temperature else None
+        axlbm_batch_get_populations(self.handle, d, f, g, h)
+        return f, g, h
+
+    def set_populations(self, d: int, f, g, h=None) -> None:
+        cast = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+        axlbm_batch_set_populations(self.handle, d, cast(f), cast(g), cast(h))

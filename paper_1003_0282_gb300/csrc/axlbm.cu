@@ -161,6 +161,32 @@ double bulk_bytes_of(const axlbm_handle* h, int check, int residual) {
 }  // namespace
 
 namespace axl {
+
+// Checks of one problem description shared by axlbm_create and the batch.
+bool validate_problem(const axlbm_grid* grid, double tau, const axlbm_forcing* forcing, const axlbm_boundary* bc,
+                      std::string* why) {
+    if (!grid_ok(grid, why)) return false;
+    auto no = [&](const char* m) { *why = m; return false; };
+    if (!forcing || !bc) return no("forcing and boundary must not be NULL");
+    if (!(tau > 0.5) || !isfinite(tau)) return no("tau must be > 1/2");
+    if (!(forcing->rho0 > 0.0) || !isfinite(forcing->rho0)) return no("rho0 must be > 0");
+    if (grid->with_temperature && !(forcing->tau_t > 0.5)) return no("tau_t must be > 1/2");
+    if (bc->inner != AXLBM_INNER_AXIS && bc->inner != AXLBM_INNER_WALL) return no("bad inner face kind");
+    if (bc->inner == AXLBM_INNER_AXIS && grid->r0 != 0.0) return no("the axis needs r0 == 0");
+    if (bc->z_lo < 0 || bc->z_lo > 2 || bc->z_hi < 0 || bc->z_hi > 3)
+        return no("bad axial face kind (the bottom face cannot be mixed)");
+    if ((bc->z_lo == AXLBM_Z_PERIODIC) != (bc->z_hi == AXLBM_Z_PERIODIC)) return no("periodic needs both axial faces periodic");
+    if (bc->reserved != 0) return no("boundary.reserved must be 0");
+    for (int f = 0; f < 4; ++f) {
+        if (bc->t_dirichlet[f] != 0 && bc->t_dirichlet[f] != 1) return no("t_dirichlet must be 0 or 1");
+        if (!isfinite(bc->omega[f]) || !isfinite(bc->t_wall[f])) return no("wall values must be finite");
+    }
+    if (!isfinite(forcing->az0) || !isfinite(forcing->omega_t) || !isfinite(forcing->gbeta) || !isfinite(forcing->t_ref) ||
+        !isfinite(forcing->t_init) || !isfinite(bc->r_split))
+        return no("forcing values must be finite");
+    return true;
+}
+
 // Error text of a call that has no handle, read back by axlbm_last_error(NULL).
 void set_handleless_error(const char* msg) { g_create_error = msg; }
 }  // namespace axl
@@ -194,25 +220,7 @@ axlbm_status axlbm_create(const axlbm_grid* grid, double tau, const axlbm_forcin
                           size_t state_bytes, axlbm_handle** out) {
     std::string why;
     if (!out) return fail(nullptr, AXLBM_EINVAL, "out is NULL");
-    if (!grid_ok(grid, &why)) return fail(nullptr, AXLBM_EINVAL, why);
-    if (!forcing || !bc) return fail(nullptr, AXLBM_EINVAL, "forcing and boundary must not be NULL");
-    if (!(tau > 0.5) || !isfinite(tau)) return fail(nullptr, AXLBM_EINVAL, "tau must be > 1/2");
-    if (!(forcing->rho0 > 0.0) || !isfinite(forcing->rho0)) return fail(nullptr, AXLBM_EINVAL, "rho0 must be > 0");
-    if (grid->with_temperature && !(forcing->tau_t > 0.5)) return fail(nullptr, AXLBM_EINVAL, "tau_t must be > 1/2");
-    if (bc->inner != AXLBM_INNER_AXIS && bc->inner != AXLBM_INNER_WALL) return fail(nullptr, AXLBM_EINVAL, "bad inner face kind");
-    if (bc->inner == AXLBM_INNER_AXIS && grid->r0 != 0.0) return fail(nullptr, AXLBM_EINVAL, "the axis needs r0 == 0");
-    if (bc->z_lo < 0 || bc->z_lo > 2 || bc->z_hi < 0 || bc->z_hi > 3)
-        return fail(nullptr, AXLBM_EINVAL, "bad axial face kind (the bottom face cannot be mixed)");
-    if ((bc->z_lo == AXLBM_Z_PERIODIC) != (bc->z_hi == AXLBM_Z_PERIODIC))
-        return fail(nullptr, AXLBM_EINVAL, "periodic needs both axial faces periodic");
-    if (bc->reserved != 0) return fail(nullptr, AXLBM_EINVAL, "boundary.reserved must be 0");
-    for (int f = 0; f < 4; ++f) {
-        if (bc->t_dirichlet[f] != 0 && bc->t_dirichlet[f] != 1) return fail(nullptr, AXLBM_EINVAL, "t_dirichlet must be 0 or 1");
-        if (!isfinite(bc->omega[f]) || !isfinite(bc->t_wall[f])) return fail(nullptr, AXLBM_EINVAL, "wall values must be finite");
-    }
-    if (!isfinite(forcing->az0) || !isfinite(forcing->omega_t) || !isfinite(forcing->gbeta) || !isfinite(forcing->t_ref) ||
-        !isfinite(forcing->t_init))
-        return fail(nullptr, AXLBM_EINVAL, "forcing values must be finite");
+    if (!axl::validate_problem(grid, tau, forcing, bc, &why)) return fail(nullptr, AXLBM_EINVAL, why);
 
     Layout L = make_layout(grid);
     if (state_mem && state_bytes < L.total) return fail(nullptr, AXLBM_ENOMEM, "state_mem smaller than axlbm_state_bytes()");
@@ -236,6 +244,8 @@ axlbm_status axlbm_create(const axlbm_grid* grid, double tau, const axlbm_forcin
     h->G.z_lo = bc->z_lo;
     h->G.z_hi = bc->z_hi;
     h->G.r_split = bc->r_split;
+    h->G.col0 = 0;
+    h->G.row0 = 0;
     h->parity = 0;
     h->t = 0;
     h->speed_valid = false;

@@ -1,0 +1,663 @@
+// batch.cu -- host side of the batch C ABI (include/axlbm.h, "batches").
+//
+// Packing: domains are sorted by height and placed left to right in shelves
+// of a common-pitch array (columns aligned to 32 elements), so one TMA
+// descriptor covers every domain and a tile never spans two domains.
+// Tiles (bulk kernel) are listed row-major over that array, so concurrently
+// running CTAs sweep neighbouring domains' rows together (shared rows of the
+// TMA boxes then hit L2).  Tile shape: the candidates are timed on the batch
+// at creation and the fastest kept (cached per GPU, precision, mix).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "batch.cuh"
+#include "batch_internal.h"
+
+using axl::BatchLayout;
+using axl::BatchOps;
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+const BatchOps* batch_ops_for(int precision) {
+    switch (precision) {
+        case AXLBM_FP32: return &axl::batch_ops_fp32;
+        case AXLBM_FP16_DEV: return &axl::batch_ops_fp16;
+        default: return nullptr;
+    }
+}
+
+size_t al(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
+
+axlbm_status bfail(axlbm_batch* b, axlbm_status st, const std::string& msg) {
+    if (b) b->err = msg; else g_batch_error = msg;
+    return st;
+}
+
+axlbm_status bcuda(axlbm_batch* b, cudaError_t e, const char* where) {
+    return bfail(b, AXLBM_ECUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+// Shelf packing and every offset of the device layout.  col0/row0 receive each
+// domain's position; tiles[s] the tile lists per candidate shape.
+struct Plan {
+    BatchLayout L;
+    std::vector<int> col0, row0;
+    std::vector<int> tiles[axl::kBatchShapes];      // 4 ints per tile
+    std::vector<int> tstart[axl::kBatchShapes], tindex[axl::kBatchShapes];
+    std::vector<int> ring, rstart;                  // 2 ints per ring node
+    int thmax;
+};
+
+bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::string* why) {
+    if (!dom || n < 1 || n > 65535) { *why = "need 1..65535 domains"; return false; }
+    if (!batch_ops_for(precision)) { *why = "batch storage must be AXLBM_FP32 or AXLBM_FP16_DEV"; return false; }
+    P->thmax = 0;
+    for (int d = 0; d < n; ++d) {
+        std::string w;
+        if (!axl::validate_problem(&dom[d].grid, dom[d].tau, &dom[d].forcing, &dom[d].boundary, &w)) {
+            *why = "domain " + std::to_string(d) + ": " + w;
+            return false;
+        }
+        if (!dom[d].grid.with_swirl) { *why = "domain " + std::to_string(d) + ": batches need with_swirl = 1"; return false; }
+        if ((long long)dom[d].grid.nr * dom[d].grid.nz > (1ll << 28)) { *why = "domain too large for a batch"; return false; }
+        P->thmax |= dom[d].grid.with_temperature;
+    }
+    BatchLayout& L = P->L;
+    L.elem = precision == AXLBM_FP32 ? 4 : 2;
+    L.nplanes = P->thmax ? 17 : 13;
+    // shelf packing, tallest first
+    std::vector<int> order(n);
+    long long area = 0;
+    int maxw = 0;
+    for (int d = 0; d < n; ++d) {
+        order[d] = d;
+        const int w = (dom[d].grid.nr + 31) / 32 * 32;
+        area += (long long)w * dom[d].grid.nz;
+        maxw = std::max(maxw, w);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dom[a].grid.nz > dom[b].grid.nz; });
+    long long width = (long long)(sqrt((double)area) * 1.1);
+    width = (width + 31) / 32 * 32;
+    if (width < maxw) width = maxw;
+    if (width > 16384) width = std::max<long long>(16384, maxw);
+    P->col0.assign(n, 0);
+    P->row0.assign(n, 0);
+    long long row = 0, col = 0, shelf_h = 0;
+    for (int d : order) {
+        const int w = (dom[d].grid.nr + 31) / 32 * 32;
+        if (col + w > width) {
+            row += shelf_h;
+            col = 0;
+            shelf_h = 0;
+        }
+        P->col0[d] = (int)col;
+        P->row0[d] = (int)row;
+        col += w;
+        shelf_h = std::max<long long>(shelf_h, dom[d].grid.nz);
+    }
+    L.rows = row + shelf_h;
+    L.pitch = width;
+    L.plane = L.pitch * L.rows;
+    if (L.rows > (1ll << 30) || L.pitch * L.rows * L.nplanes > (1ll << 38)) { *why = "batch too large"; return false; }
+    // tiles per candidate shape, row-major over the array
+    for (int s = 0; s < axl::kBatchShapes; ++s) {
+        const int TK = axl::kShapeTK[s], TJ = axl::kShapeTJ[s];
+        struct T { int d, j0, k0; };
+        std::vector<T> list;
+        for (int d = 0; d < n; ++d)
+            for (int k = 0; k < dom[d].grid.nz; k += TK)
+                for (int j = 0; j < dom[d].grid.nr; j += TJ) list.push_back({d, P->col0[d] + j, P->row0[d] + k});
+        std::stable_sort(list.begin(), list.end(), [](const T& a, const T& b) {
+            return a.k0 != b.k0 ? a.k0 < b.k0 : a.j0 < b.j0;
+        });
+        P->tiles[s].clear();
+        std::vector<std::vector<int>> per(n);
+        for (size_t i = 0; i < list.size(); ++i) {
+            P->tiles[s].insert(P->tiles[s].end(), {list[i].d, list[i].j0, list[i].k0, 0});
+            per[list[i].d].push_back((int)i);
+        }
+        P->tstart[s].assign(1, 0);
+        P->tindex[s].clear();
+        for (int d = 0; d < n; ++d) {
+            P->tindex[s].insert(P->tindex[s].end(), per[d].begin(), per[d].end());
+            P->tstart[s].push_back((int)P->tindex[s].size());
+        }
+        L.shape[s].ntiles = (int)list.size();
+    }
+    // outer rings, domain by domain
+    P->ring.clear();
+    P->rstart.assign(1, 0);
+    for (int d = 0; d < n; ++d) {
+        const int nr = dom[d].grid.nr, nz = dom[d].grid.nz;
+        const int nf = nz == 1 ? nr : 2 * nr + (nz - 2) * (nr > 1 ? 2 : 1);
+        for (int i = 0; i < nf; ++i) P->ring.insert(P->ring.end(), {d, i});
+        P->rstart.push_back((int)(P->ring.size() / 2));
+    }
+    L.nring = (int)(P->ring.size() / 2);
+    // offsets
+    int maxtiles = 0;
+    for (int s = 0; s < axl::kBatchShapes; ++s) maxtiles = std::max(maxtiles, L.shape[s].ntiles);
+    size_t off = al((size_t)L.nplanes * L.plane * L.elem);
+    L.off_speed = off;
+    off += al((size_t)L.plane * 4);
+    L.off_tilepart = off;
+    off += al((size_t)maxtiles * 32);
+    L.off_ringpart = off;
+    off += al((size_t)L.nring * 32);
+    L.off_result = off;
+    off += al((size_t)n * 32);
+    L.off_az = off;
+    off += al((size_t)n * 16);
+    L.off_clock = off;
+    off += 256;
+    L.off_doms = off;
+    off += al((size_t)n * sizeof(axl::DomDesc));
+    L.off_ring = off;
+    off += al((size_t)L.nring * 8);
+    L.off_rstart = off;
+    off += al((size_t)(n + 1) * 4);
+    for (int s = 0; s < axl::kBatchShapes; ++s) {
+        L.shape[s].off_tiles = off;
+        off += al((size_t)L.shape[s].ntiles * 16);
+        L.shape[s].off_tstart = off;
+        off += al((size_t)(n + 1) * 4);
+        L.shape[s].off_tindex = off;
+        off += al((size_t)L.shape[s].ntiles * 4);
+    }
+    L.total = off;
+    return true;
+}
+
+std::mutex g_tune_lock;
+std::map<std::string, int> g_tune_cache;
+
+axlbm_status upload(axlbm_batch* b, size_t off, const void* src, size_t bytes) {
+    if (!bytes) return AXLBM_OK;
+    cudaError_t e = cudaMemcpyAsync(b->mem + off, src, bytes, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? AXLBM_OK : bcuda(b, e, "upload");
+}
+
+// Every domain at rest (deviation storage: f and g deviations are zero; h
+// holds (t_init - t_ref)/4), time t = 0.
+axlbm_status reset_rest(axlbm_batch* b) {
+    const BatchLayout& L = b->L;
+    cudaError_t e = cudaMemsetAsync(b->mem, 0, L.off_clock + 256, b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "memset");
+    std::vector<double> az(2 * b->n, 0.0);
+    for (int d = 0; d < b->n; ++d) az[2 * d] = b->desc[d].forcing.az0;  // a(0) = az0 cos(0)
+    axlbm_status st = upload(b, L.off_az, az.data(), az.size() * sizeof(double));
+    if (st != AXLBM_OK) return st;
+    for (int d = 0; d < b->n; ++d) {
+        const axlbm_domain& D = b->desc[d];
+        if (!D.grid.with_temperature || D.forcing.t_init == D.forcing.t_ref) continue;
+        const long long nn = (long long)D.grid.nr * D.grid.nz;
+        std::vector<double> f(5 * nn, 0.0);
+        for (long long i = 0; i < nn; ++i) {
+            f[i] = D.forcing.rho0;
+            f[4 * nn + i] = D.forcing.t_init;
+        }
+        double* dev = nullptr;
+        e = cudaMalloc(&dev, f.size() * sizeof(double));
+        if (e != cudaSuccess) return bcuda(b, e, "init staging");
+        e = cudaMemcpyAsync(dev, f.data(), f.size() * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = batch_ops_for(b->precision)->init(b, d, dev, 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        cudaFree(dev);
+        if (e != cudaSuccess) return bcuda(b, e, "initial state");
+    }
+    b->parity = 0;
+    b->t = 0;
+    b->speed_valid = b->have_check = b->last_residual_valid = false;
+    return AXLBM_OK;
+}
+
+double batch_bulk_bytes(const axlbm_batch* b, int check, int residual) {
+    double bytes = 0.0;
+    for (int d = 0; d < b->n; ++d) {
+        const axlbm_domain& D = b->desc[d];
+        const double nodes = b->parity == 0 ? (double)D.grid.nr * D.grid.nz
+                                            : (D.grid.nr > 2 && D.grid.nz > 2 ? (double)(D.grid.nr - 2) * (D.grid.nz - 2) : 0.0);
+        double per = 2.0 * (13 + (D.grid.with_temperature ? 4 : 0)) * (double)b->L.elem;
+        if (check) per += 4.0 * (residual ? 2.0 : 1.0);
+        bytes += nodes * per;
+    }
+    return bytes;
+}
+
+constexpr size_t kBatchEventPairs = 1024;
+
+axlbm_status batch_fold_timing(axlbm_batch* b) {
+    if (b->ev_used == 0) return AXLBM_OK;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "timing");
+    for (size_t i = 0; i < b->ev_used; ++i) {
+        float ms = 0.0f;
+        e = cudaEventElapsedTime(&ms, b->ev[2 * i], b->ev[2 * i + 1]);
+        if (e != cudaSuccess) return bcuda(b, e, "timing");
+        b->bulk_ms += ms;
+        b->bulk_bytes += b->ev_bytes[i];
+    }
+    b->ev_used = 0;
+    b->ev_bytes.clear();
+    return AXLBM_OK;
+}
+
+axlbm_status batch_timing_slot(axlbm_batch* b, cudaEvent_t* ev0, cudaEvent_t* ev1) {
+    if (b->ev.empty()) {
+        b->ev.resize(2 * kBatchEventPairs, nullptr);
+        for (auto& e : b->ev) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return bcuda(b, r, "event create");
+        }
+    }
+    if (b->ev_used == kBatchEventPairs) {
+        axlbm_status st = batch_fold_timing(b);
+        if (st != AXLBM_OK) return st;
+    }
+    *ev0 = b->ev[2 * b->ev_used];
+    *ev1 = b->ev[2 * b->ev_used + 1];
+    ++b->ev_used;
+    return AXLBM_OK;
+}
+
+axlbm_status batch_step_n(axlbm_batch* b, int64_t n) {
+    const BatchOps* ops = batch_ops_for(b->precision);
+    for (int64_t s = 0; s < n; ++s) {
+        const bool last = s == n - 1, before_last = s == n - 2;
+        const int check = (last || before_last) ? 1 : 0;
+        const int residual = (last && (n >= 2 || b->speed_valid)) ? 1 : 0;
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        if (b->timing) {
+            axlbm_status st = batch_timing_slot(b, &ev0, &ev1);
+            if (st != AXLBM_OK) return st;
+            b->ev_bytes.push_back(batch_bulk_bytes(b, check, residual));
+        }
+        int nl = 0;
+        cudaError_t e = ops->step(b, check, residual, ev0, ev1, &nl);
+        if (e == cudaSuccess && last) {
+            e = ops->fold(b, b->parity == 1);
+            ++nl;
+        }
+        if (e != cudaSuccess) return bcuda(b, e, "batch step launch");
+        if (b->timing) {
+            b->all_launches += nl;
+            b->bulk_launches += 1;
+        }
+        if (last) {
+            b->have_check = true;
+            b->speed_valid = true;
+            b->last_residual_valid = residual != 0;
+            b->last_check_parity = b->parity;
+        } else {
+            b->speed_valid = check != 0;
+        }
+        b->parity ^= 1;
+        b->t += 1;
+    }
+    return AXLBM_OK;
+}
+
+// Time the candidate tile shapes on this batch and keep the fastest.
+axlbm_status tune(axlbm_batch* b) {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        return bfail(b, AXLBM_ECUDA, "device query");
+    const std::string key = std::string(prop.name) + "|" + std::to_string(b->precision) + "|" + std::to_string(b->thmax);
+    {
+        std::lock_guard<std::mutex> g(g_tune_lock);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            b->shape = it->second;
+            return AXLBM_OK;
+        }
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return bfail(b, AXLBM_ECUDA, "event create");
+    float best = 1e30f;
+    int best_shape = 0;
+    axlbm_status st = AXLBM_OK;
+    for (int s = 0; s < axl::kBatchShapes && st == AXLBM_OK; ++s) {
+        b->shape = s;
+        st = batch_step_n(b, 2);  // warm-up: occupancy query, caches
+        if (st != AXLBM_OK) break;
+        cudaEventRecord(e0, b->stream);
+        st = batch_step_n(b, 8);
+        cudaEventRecord(e1, b->stream);
+        if (st != AXLBM_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = bfail(b, AXLBM_ECUDA, "tuning");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_shape = s;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != AXLBM_OK) return st;
+    b->shape = best_shape;
+    std::lock_guard<std::mutex> g(g_tune_lock);
+    g_tune_cache[key] = best_shape;
+    return AXLBM_OK;
+}
+
+bool domain_ok(const axlbm_batch* b, int d) { return b && d >= 0 && d < b->n; }
+
+}  // namespace
+
+extern "C" {
+
+axlbm_status axlbm_batch_state_bytes(const axlbm_domain* domains, int32_t n, int32_t precision, size_t* bytes) {
+    Plan P;
+    std::string why;
+    if (!bytes) return bfail(nullptr, AXLBM_EINVAL, "bytes is NULL");
+    if (!plan_batch(domains, n, precision, &P, &why)) return bfail(nullptr, AXLBM_EINVAL, why);
+    *bytes = P.L.total;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t precision, void* cuda_stream,
+                                void* state_mem, size_t state_bytes, axlbm_batch** out) {
+    if (!out) return bfail(nullptr, AXLBM_EINVAL, "out is NULL");
+    Plan P;
+    std::string why;
+    if (!plan_batch(domains, n, precision, &P, &why)) return bfail(nullptr, AXLBM_EINVAL, why);
+    if (state_mem && state_bytes < P.L.total) return bfail(nullptr, AXLBM_ENOMEM, "state_mem smaller than axlbm_batch_state_bytes()");
+    if (state_mem && (reinterpret_cast<uintptr_t>(state_mem) & 255u))
+        return bfail(nullptr, AXLBM_EINVAL, "state_mem must be 256-byte aligned");
+    axlbm_batch* b = new (std::nothrow) axlbm_batch();
+    if (!b) return bfail(nullptr, AXLBM_ENOMEM, "host allocation failed");
+    b->n = n;
+    b->precision = precision;
+    b->thmax = P.thmax;
+    b->desc.assign(domains, domains + n);
+    b->col0 = P.col0;
+    b->row0 = P.row0;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->L = P.L;
+    b->shape = 0;
+    memset(b->grid, 0, sizeof b->grid);
+    b->timing = false;
+    b->ev_used = 0;
+    b->bulk_launches = b->all_launches = 0;
+    b->bulk_ms = b->bulk_bytes = 0.0;
+    b->last_check_parity = 0;
+    {
+        int dev = 0;
+        b->num_sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (b->num_sms < 1) b->num_sms = 1;
+    }
+    if (state_mem) {
+        b->mem = static_cast<char*>(state_mem);
+        b->owns_mem = false;
+    } else {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, P.L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return bfail(nullptr, AXLBM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        b->mem = static_cast<char*>(p);
+        b->owns_mem = true;
+    }
+    axlbm_status st = AXLBM_OK;
+    // descriptors and lists
+    std::vector<axl::DomDesc> dd(n);
+    for (int d = 0; d < n; ++d) {
+        const axlbm_domain& D = domains[d];
+        axl::DomDesc& x = dd[d];
+        memset(&x, 0, sizeof x);
+        x.nr = D.grid.nr;
+        x.nz = D.grid.nz;
+        x.col0 = P.col0[d];
+        x.row0 = P.row0[d];
+        x.inner = D.boundary.inner;
+        x.z_lo = D.boundary.z_lo;
+        x.z_hi = D.boundary.z_hi;
+        x.swirl = D.grid.with_swirl;
+        x.temperature = D.grid.with_temperature;
+        x.r0 = D.grid.r0;
+        x.r_split = D.boundary.r_split;
+        x.az0 = D.forcing.az0;
+        x.omega_t = D.forcing.omega_t;
+        x.cf = axl::make_coef<float>(D.tau, D.forcing, D.boundary);
+        x.cd = axl::make_coef<double>(D.tau, D.forcing, D.boundary);
+    }
+    const BatchLayout& L = b->L;
+    if (st == AXLBM_OK) st = upload(b, L.off_doms, dd.data(), dd.size() * sizeof(axl::DomDesc));
+    if (st == AXLBM_OK) st = upload(b, L.off_ring, P.ring.data(), P.ring.size() * sizeof(int));
+    if (st == AXLBM_OK) st = upload(b, L.off_rstart, P.rstart.data(), P.rstart.size() * sizeof(int));
+    for (int s = 0; s < axl::kBatchShapes && st == AXLBM_OK; ++s) {
+        st = upload(b, L.shape[s].off_tiles, P.tiles[s].data(), P.tiles[s].size() * sizeof(int));
+        if (st == AXLBM_OK) st = upload(b, L.shape[s].off_tstart, P.tstart[s].data(), P.tstart[s].size() * sizeof(int));
+        if (st == AXLBM_OK) st = upload(b, L.shape[s].off_tindex, P.tindex[s].data(), P.tindex[s].size() * sizeof(int));
+        if (st == AXLBM_OK) {
+            cudaError_t e = batch_ops_for(precision)->encode(b, s);
+            if (e != cudaSuccess) st = bcuda(b, e, "TMA descriptor");
+        }
+    }
+    if (st == AXLBM_OK) st = reset_rest(b);
+    if (st == AXLBM_OK) st = tune(b);
+    if (st == AXLBM_OK) st = reset_rest(b);
+    if (st == AXLBM_OK) {
+        cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) st = bcuda(b, e, "create");
+    }
+    if (st != AXLBM_OK) {
+        g_batch_error = b->err;
+        if (b->owns_mem) cudaFree(b->mem);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_step(axlbm_batch* b, int64_t n) {
+    if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
+    if (n < 0) return bfail(b, AXLBM_EINVAL, "n must be >= 0");
+    return batch_step_n(b, n);
+}
+
+axlbm_status axlbm_batch_residuals(axlbm_batch* b, double* out) {
+    if (!b || !out) return bfail(b, AXLBM_EINVAL, "batch and out are required");
+    if (!b->have_check) return bfail(b, AXLBM_EINVAL, "no check step has run yet");
+    std::vector<double> r(4 * (size_t)b->n);
+    axl::Clock clk;
+    cudaError_t e = cudaMemcpyAsync(r.data(), b->mem + b->L.off_result, r.size() * sizeof(double),
+                                    cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&clk, b->mem + b->L.off_clock, sizeof clk, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "residual read");
+    if (clk.err) return bfail(b, AXLBM_ETIMEOUT, "a bounded wait for a TMA copy gave up; the state is not valid");
+    bool bad = false;
+    for (int d = 0; d < b->n; ++d) {
+        out[3 * d + 0] = b->last_residual_valid ? r[4 * d] : INFINITY;
+        out[3 * d + 1] = r[4 * d + 1];
+        out[3 * d + 2] = r[4 * d + 2];
+        bad = bad || r[4 * d + 3] != 0.0;
+    }
+    if (bad) return bfail(b, AXLBM_ENONFINITE, "non-finite density or velocity in the last check step");
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_moments(axlbm_batch* b, int32_t d, uint32_t mask, void* out, int32_t out_dtype,
+                                 int32_t out_on_device) {
+    if (!domain_ok(b, d)) return bfail(b, AXLBM_EINVAL, "bad batch or domain index");
+    const axlbm_domain& D = b->desc[d];
+    if (!out || mask == 0 || (mask & ~31u)) return bfail(b, AXLBM_EINVAL, "bad output or field mask");
+    if ((mask & AXLBM_T) && !D.grid.with_temperature) return bfail(b, AXLBM_EINVAL, "T needs with_temperature");
+    if (out_dtype != AXLBM_F64 && out_dtype != AXLBM_F32) return bfail(b, AXLBM_EINVAL, "bad out_dtype");
+    int nf = 0;
+    for (int f = 0; f < 5; ++f) nf += (mask >> f) & 1;
+    const size_t bytes = (size_t)nf * D.grid.nr * D.grid.nz * (out_dtype == AXLBM_F32 ? 4 : 8);
+    const BatchOps* ops = batch_ops_for(b->precision);
+    if (out_on_device) {
+        cudaError_t e = ops->moments(b, d, out, mask, out_dtype == AXLBM_F32);
+        return e == cudaSuccess ? AXLBM_OK : bcuda(b, e, "moments");
+    }
+    void* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, AXLBM_ENOMEM, "staging buffer");
+    }
+    e = ops->moments(b, d, tmp, mask, out_dtype == AXLBM_F32);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(tmp);
+    return e == cudaSuccess ? AXLBM_OK : bcuda(b, e, "moments");
+}
+
+axlbm_status axlbm_batch_set_fields(axlbm_batch* b, int32_t d, const void* fields, int32_t in_dtype,
+                                    int32_t on_device) {
+    if (!domain_ok(b, d) || !fields || (in_dtype != AXLBM_F64 && in_dtype != AXLBM_F32))
+        return bfail(b, AXLBM_EINVAL, "bad batch, domain index or fields");
+    if (b->parity != 0) return bfail(b, AXLBM_EINVAL, "set_fields needs an even time level");
+    const axlbm_domain& D = b->desc[d];
+    const size_t bytes = (size_t)5 * D.grid.nr * D.grid.nz * (in_dtype == AXLBM_F32 ? 4 : 8);
+    const BatchOps* ops = batch_ops_for(b->precision);
+    cudaError_t e;
+    if (on_device) {
+        e = ops->init(b, d, fields, in_dtype == AXLBM_F32);
+    } else {
+        void* tmp = nullptr;
+        e = cudaMalloc(&tmp, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(b, AXLBM_ENOMEM, "staging buffer");
+        }
+        e = cudaMemcpyAsync(tmp, fields, bytes, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = ops->init(b, d, tmp, in_dtype == AXLBM_F32);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        cudaFree(tmp);
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "set_fields");
+    b->speed_valid = false;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_get_populations(axlbm_batch* b, int32_t d, double* f, double* g, double* tp) {
+    if (!domain_ok(b, d) || !f) return bfail(b, AXLBM_EINVAL, "bad batch, domain index or arrays");
+    const axlbm_domain& D = b->desc[d];
+    if (tp && !D.grid.with_temperature) return bfail(b, AXLBM_EINVAL, "t_pop needs with_temperature");
+    const size_t nn = (size_t)D.grid.nr * D.grid.nz;
+    const size_t nq = 13 + (D.grid.with_temperature ? 4 : 0);
+    double* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, sizeof(double) * nq * nn);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, AXLBM_ENOMEM, "staging buffer");
+    }
+    std::vector<double> host(nq * nn);
+    e = batch_ops_for(b->precision)->gather(b, d, tmp);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host.data(), tmp, sizeof(double) * nq * nn, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return bcuda(b, e, "get_populations");
+    memcpy(f, host.data(), sizeof(double) * 9 * nn);
+    if (g) memcpy(g, host.data() + 9 * nn, sizeof(double) * 4 * nn);
+    if (tp) memcpy(tp, host.data() + 13 * nn, sizeof(double) * 4 * nn);
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_set_populations(axlbm_batch* b, int32_t d, const double* f, const double* g,
+                                         const double* tp) {
+    if (!domain_ok(b, d) || !f || !g) return bfail(b, AXLBM_EINVAL, "bad batch, domain index or arrays");
+    const axlbm_domain& D = b->desc[d];
+    if (D.grid.with_temperature && !tp) return bfail(b, AXLBM_EINVAL, "t_pop is required with temperature");
+    if (b->parity != 0) return bfail(b, AXLBM_EINVAL, "set_populations needs an even time level");
+    const size_t nn = (size_t)D.grid.nr * D.grid.nz;
+    const size_t nq = 13 + (D.grid.with_temperature ? 4 : 0);
+    std::vector<double> host(nq * nn);
+    memcpy(host.data(), f, sizeof(double) * 9 * nn);
+    memcpy(host.data() + 9 * nn, g, sizeof(double) * 4 * nn);
+    if (D.grid.with_temperature) memcpy(host.data() + 13 * nn, tp, sizeof(double) * 4 * nn);
+    double* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, sizeof(double) * nq * nn);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, AXLBM_ENOMEM, "staging buffer");
+    }
+    e = cudaMemcpyAsync(tmp, host.data(), sizeof(double) * nq * nn, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = batch_ops_for(b->precision)->scatter(b, d, tmp);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return bcuda(b, e, "set_populations");
+    b->speed_valid = false;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_time(const axlbm_batch* b, int64_t* t) {
+    if (!b || !t) return AXLBM_EINVAL;
+    *t = b->t;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_tile_shape(const axlbm_batch* b, int32_t* rows, int32_t* nodes) {
+    if (!b) return AXLBM_EINVAL;
+    if (rows) *rows = axl::kShapeTK[b->shape];
+    if (nodes) *nodes = axl::kShapeTJ[b->shape];
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_kernel_timing(axlbm_batch* b, int32_t enable) {
+    if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
+    if (enable) {
+        axlbm_status st = batch_fold_timing(b);
+        if (st != AXLBM_OK) return st;
+        b->bulk_launches = b->all_launches = 0;
+        b->bulk_ms = b->bulk_bytes = 0.0;
+    }
+    b->timing = enable != 0;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_kernel_times(axlbm_batch* b, int64_t* bulk_launches, double* bulk_ms, double* bulk_bytes,
+                                      int64_t* all_launches) {
+    if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
+    axlbm_status st = batch_fold_timing(b);
+    if (st != AXLBM_OK) return st;
+    if (bulk_launches) *bulk_launches = b->bulk_launches;
+    if (bulk_ms) *bulk_ms = b->bulk_ms;
+    if (bulk_bytes) *bulk_bytes = b->bulk_bytes;
+    if (all_launches) *all_launches = b->all_launches;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_destroy(axlbm_batch* b) {
+    if (!b) return AXLBM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    for (auto ev : b->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (b->owns_mem) {
+        cudaError_t e2 = cudaFree(b->mem);
+        if (e == cudaSuccess) e = e2;
+    }
+    delete b;
+    return e == cudaSuccess ? AXLBM_OK : AXLBM_ECUDA;
+}
+
+const char* axlbm_batch_last_error(const axlbm_batch* b) {
+    if (!b) return g_batch_error.c_str();
+    return b->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// batch_internal.h -- state of a batch and its per-precision launchers.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace axl {
+
+// Candidate bulk tile shapes (rows x nodes), 512 nodes each.
+constexpr int kBatchShapes = 2;
+constexpr int kShapeTK[kBatchShapes] = {4, 8};
+constexpr int kShapeTJ[kBatchShapes] = {128, 64};
+
+struct BatchTiles {
+    int ntiles;
+    size_t off_tiles;   // int4 [ntiles]
+    size_t off_tstart;  // int [ndom + 1]
+    size_t off_tindex;  // int [ntiles]
+};
+
+struct BatchLayout {
+    size_t elem;
+    int nplanes;
+    long long pitch, rows, plane;
+    int nring;
+    size_t off_speed, off_tilepart, off_ringpart, off_result, off_az, off_clock, off_doms, off_ring, off_rstart;
+    BatchTiles shape[kBatchShapes];
+    size_t total;
+};
+
+}  // namespace axl
+
+struct axlbm_batch {
+    CUtensorMap tmap[axl::kBatchShapes];
+    int n;
+    int precision;
+    int thmax;  // some domain carries temperature
+    std::vector<axlbm_domain> desc;
+    std::vector<int> col0, row0;
+    cudaStream_t stream;
+    char* mem;
+    bool owns_mem;
+    axl::BatchLayout L;
+    int shape;                        // tile shape in use
+    int grid[axl::kBatchShapes][2][2];  // persistent grid per (shape, parity, check)
+    int num_sms;
+    int parity;
+    int64_t t;
+    bool speed_valid, have_check, last_residual_valid;
+    int last_check_parity;
+    // timing
+    bool timing;
+    std::vector<cudaEvent_t> ev;
+    std::vector<double> ev_bytes;
+    size_t ev_used;
+    int64_t bulk_launches, all_launches;
+    double bulk_ms, bulk_bytes;
+    std::string err;
+};
+
+namespace axl {
+
+struct BatchOps {
+    cudaError_t (*encode)(axlbm_batch* b, int shape);  // TMA descriptor of a tile shape
+    // one step of every domain; bulk kernel bracketed by ev0/ev1 (may be null)
+    cudaError_t (*step)(axlbm_batch* b, int check, int residual, cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch);
+    cudaError_t (*fold)(axlbm_batch* b, int with_ring);
+    cudaError_t (*moments)(axlbm_batch* b, int d, void* out, unsigned mask, int out_f32);
+    cudaError_t (*init)(axlbm_batch* b, int d, const void* fields, int in_f32);
+    cudaError_t (*gather)(axlbm_batch* b, int d, double* out);
+    cudaError_t (*scatter)(axlbm_batch* b, int d, const double* in);
+};
+
+extern const BatchOps batch_ops_fp32;
+extern const BatchOps batch_ops_fp16;
+
+}  // namespace axl

@@ -22,10 +22,11 @@ constexpr int kMaxBulkBlocks = 4096;
 struct Geom {
     int nr, nz;
     long long pitch;  // elements per row (multiple of 128 bytes)
-    long long plane;  // elements per population plane (nz * pitch)
+    long long plane;  // elements per population plane
     double r0;
     int inner, z_lo, z_hi;
     double r_split;
+    int col0, row0;   // position of node (0, 0) in the array (non-zero for a domain of a batch)
 };
 
 // Per-step forcing state on the device.  Kernels of a step with AA parity p
@@ -116,6 +117,16 @@ struct Ops {
 // Fixed-order reduction of per-block check partials [n][4] (max, sum, sum,
 // sum) into result[4] on `stream` (reduce.cu).
 cudaError_t launch_finalize(const double* partials, int n, double* result, cudaStream_t stream);
+
+// Fixed-order per-domain fold of a batch's tile partials (and ring values
+// after an odd step) into result[d][4] (reduce.cu).
+cudaError_t launch_domain_fold(int ndom, const int* tile_start, const int* tile_index, const double* tile_part,
+                               const int* ring_start, const double* ring_part, int with_ring, double* result,
+                               cudaStream_t stream);
+
+// Checks of one problem description (grid, tau, forcing, boundary).
+bool validate_problem(const axlbm_grid* grid, double tau, const axlbm_forcing* forcing, const axlbm_boundary* bc,
+                      std::string* why);
 
 // Error text of a call that has no handle (axlbm_last_error(NULL)).
 void set_handleless_error(const char* msg);

@@ -45,6 +45,7 @@ struct KArgs {
     double* partials;
     int part_offset;
     Clock* clock;
+    const double* az;  // body force a(t) by AA parity of the current level (the clock's, or a batch domain's)
     double az0, omega_t;
     Geom G;
     Coef<R> C;
@@ -223,7 +224,7 @@ __device__ __forceinline__ R bounce_h(const Coef<R>& C, int face, R v) {
 
 template <class S>
 __device__ __forceinline__ S* slot(S* pop, const Geom& G, int plane, int j, int k) {
-    return pop + (long long)plane * G.plane + (long long)k * G.pitch + j;
+    return pop + (long long)plane * G.plane + (long long)(G.row0 + k) * G.pitch + (G.col0 + j);
 }
 
 // Pull the odd-step populations of node (j, k) with boundary rules.
@@ -377,7 +378,7 @@ template <class S, class R, bool SW, bool TH>
 __device__ __forceinline__ void check_cell(const KArgs<S, R>& A, int j, int k, R inv_r,
                                            const Cell<R, SW, TH>& c, Red& red) {
     const R sp = sqrt(c.ur * c.ur + c.uz * c.uz);
-    R* spp = A.speed + (long long)k * A.G.pitch + j;
+    R* spp = A.speed + (long long)(A.G.row0 + k) * A.G.pitch + (A.G.col0 + j);
     if (A.residual) red.rmax = fmax(red.rmax, (double)fabs(sp - *spp));
     *spp = sp;
     red.mass += (double)c.s0;
@@ -596,7 +597,7 @@ k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
         // FP32 arithmetic: each thread updates the two nodes of its column in
         // rows rr and rr + 2 as one pair (same radius); FP64: one node at a time.
         constexpr int NL = Lanes<RC>::n;
-        const Sc az = Sc(A.clock->a_z[PAR]);
+        const Sc az = Sc(A.az[PAR]);
         const int jj = tid % kTileJ;
         int it = 0;
         for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++it) {
@@ -749,7 +750,7 @@ __global__ void __launch_bounds__(kThreads) k_frame(const KArgs<S, R> A) {
         Cell<R, SW, TH> c;
         pull_odd(A, j, k, c);
         const R inv_r = inv_radius<R>(G, j);
-        c.collide(inv_r, A.C, R(A.clock->a_z[1]));
+        c.collide(inv_r, A.C, R(A.az[1]));
         push_odd(A, j, k, c);
         if (CHK) check_cell(A, j, k, inv_r, c, red);
     }
@@ -773,7 +774,7 @@ __global__ void __launch_bounds__(kThreads) k_moments(const KArgs<S, R> A, int p
         const R inv_r = inv_radius<R>(G, j);
         const R uth = SW ? ((c.g[0] + c.g[1]) + (c.g[2] + c.g[3])) * A.C.inv_rho0 : R(0);
         const R temp = TH ? ((c.h[0] + c.h[1]) + (c.h[2] + c.h[3])) + A.C.t_ref : R(0);
-        c.collide(inv_r, A.C, R(A.clock->a_z[parity]));  // sets rho, ur, uz from the pre-collision state
+        c.collide(inv_r, A.C, R(A.az[parity]));  // sets rho, ur, uz from the pre-collision state
         const R vals[5] = {c.rho, c.ur, c.uz, uth, temp};
         int slotn = 0;
         for (int f = 0; f < 5; ++f) {
@@ -856,10 +857,20 @@ __global__ void __launch_bounds__(kThreads) k_init(const KArgs<S, R> A, const I*
 // ---------------------------------------------------------------------------- launchers
 
 template <class R>
+Coef<R> make_coef(double tau_s, const axlbm_forcing& fo, const axlbm_boundary& bc);
+
+template <class R>
 Coef<R> make_coef(const axlbm_handle* h) {
+    return make_coef<R>(h->tau, h->forcing, h->bc);
+}
+
+// Coefficients of Eqs. 13, 16 and 53-54 in the arithmetic type (tau_s is the
+// standard relaxation time; the paper's tau is tau_s - 1/2).
+template <class R>
+Coef<R> make_coef(double tau_s, const axlbm_forcing& fo, const axlbm_boundary& bc) {
     Coef<R> C;
-    const double tau = h->tau - 0.5;  // the paper's tau
-    const double rho0 = h->forcing.rho0;
+    const double tau = tau_s - 0.5;  // the paper's tau
+    const double rho0 = fo.rho0;
     C.rho0 = R(rho0);
     C.inv_rho0 = R(1.0 / rho0);
     C.c0 = R(1.0 / (tau + 0.5));
@@ -869,15 +880,15 @@ Coef<R> make_coef(const axlbm_handle* h) {
     C.g0 = R(1.0 / (taug + 0.5));
     C.g1 = R(taug / (taug + 0.5));
     C.nu = R(taug / 2.0);
-    const double taut = h->forcing.tau_t - 0.5;
+    const double taut = fo.tau_t - 0.5;
     C.h0 = R(1.0 / (taut + 0.5));
     C.h1 = R(taut / (taut + 0.5));
-    C.gbeta = R(h->forcing.gbeta);
-    C.t_ref = R(h->forcing.t_ref);
+    C.gbeta = R(fo.gbeta);
+    C.t_ref = R(fo.t_ref);
     for (int f = 0; f < 4; ++f) {
-        C.omega_w[f] = R(h->bc.omega[f]);
-        C.t_w[f] = R(h->bc.t_wall[f]);
-        C.t_dir[f] = h->bc.t_dirichlet[f];
+        C.omega_w[f] = R(bc.omega[f]);
+        C.t_w[f] = R(bc.t_wall[f]);
+        C.t_dir[f] = bc.t_dirichlet[f];
     }
     return C;
 }
@@ -890,6 +901,7 @@ KArgs<S, R> make_args(axlbm_handle* h) {
     A.partials = reinterpret_cast<double*>(h->mem + h->L.off_part);
     A.part_offset = 0;
     A.clock = reinterpret_cast<Clock*>(h->mem + h->L.off_clock);
+    A.az = A.clock->a_z;
     A.az0 = h->forcing.az0;
     A.omega_t = h->forcing.omega_t;
     A.G = h->G;
@@ -1009,36 +1021,50 @@ inline int grid_for(long long n) {
     return int(b < 1 ? 1 : b);
 }
 
+// Launchers over an argument block (a single domain, or one domain of a batch).
+template <class S, class R, bool SW, bool TH>
+cudaError_t moments_args(const KArgs<S, R>& A, int parity, void* out, unsigned mask, int out_f32, cudaStream_t st) {
+    const int nb = grid_for((long long)A.G.nr * A.G.nz);
+    if (out_f32) k_moments<S, R, SW, TH, float><<<nb, kThreads, 0, st>>>(A, parity, mask, (float*)out);
+    else k_moments<S, R, SW, TH, double><<<nb, kThreads, 0, st>>>(A, parity, mask, (double*)out);
+    return cudaGetLastError();
+}
+template <class S, class R, bool SW, bool TH>
+cudaError_t init_args(const KArgs<S, R>& A, const void* fields, int in_f32, cudaStream_t st) {
+    const int nb = grid_for((long long)A.G.nr * A.G.nz);
+    if (in_f32) k_init<S, R, SW, TH, float><<<nb, kThreads, 0, st>>>(A, (const float*)fields);
+    else k_init<S, R, SW, TH, double><<<nb, kThreads, 0, st>>>(A, (const double*)fields);
+    return cudaGetLastError();
+}
+template <class S, class R, bool SW, bool TH>
+cudaError_t gather_args(const KArgs<S, R>& A, int parity, double* out, cudaStream_t st) {
+    k_gather<S, R, SW, TH><<<grid_for((long long)A.G.nr * A.G.nz), kThreads, 0, st>>>(A, parity, out);
+    return cudaGetLastError();
+}
+template <class S, class R, bool SW, bool TH>
+cudaError_t scatter_args(const KArgs<S, R>& A, const double* in, cudaStream_t st) {
+    k_scatter<S, R, SW, TH><<<grid_for((long long)A.G.nr * A.G.nz), kThreads, 0, st>>>(A, in);
+    return cudaGetLastError();
+}
+
 template <class S, class R, bool SW, bool TH>
 cudaError_t moments_sw(axlbm_handle* h, void* out, unsigned mask, int out_f32) {
-    KArgs<S, R> A = make_args<S, R>(h);
-    const int nb = grid_for((long long)h->G.nr * h->G.nz);
-    if (out_f32) k_moments<S, R, SW, TH, float><<<nb, kThreads, 0, h->stream>>>(A, h->parity, mask, (float*)out);
-    else k_moments<S, R, SW, TH, double><<<nb, kThreads, 0, h->stream>>>(A, h->parity, mask, (double*)out);
-    return cudaGetLastError();
+    return moments_args<S, R, SW, TH>(make_args<S, R>(h), h->parity, out, mask, out_f32, h->stream);
 }
 
 template <class S, class R, bool SW, bool TH>
 cudaError_t init_sw(axlbm_handle* h, const void* fields, int in_f32) {
-    KArgs<S, R> A = make_args<S, R>(h);
-    const int nb = grid_for((long long)h->G.nr * h->G.nz);
-    if (in_f32) k_init<S, R, SW, TH, float><<<nb, kThreads, 0, h->stream>>>(A, (const float*)fields);
-    else k_init<S, R, SW, TH, double><<<nb, kThreads, 0, h->stream>>>(A, (const double*)fields);
-    return cudaGetLastError();
+    return init_args<S, R, SW, TH>(make_args<S, R>(h), fields, in_f32, h->stream);
 }
 
 template <class S, class R, bool SW, bool TH>
 cudaError_t gather_sw(axlbm_handle* h, double* out) {
-    KArgs<S, R> A = make_args<S, R>(h);
-    k_gather<S, R, SW, TH><<<grid_for((long long)h->G.nr * h->G.nz), kThreads, 0, h->stream>>>(A, h->parity, out);
-    return cudaGetLastError();
+    return gather_args<S, R, SW, TH>(make_args<S, R>(h), h->parity, out, h->stream);
 }
 
 template <class S, class R, bool SW, bool TH>
 cudaError_t scatter_sw(axlbm_handle* h, const double* in) {
-    KArgs<S, R> A = make_args<S, R>(h);
-    k_scatter<S, R, SW, TH><<<grid_for((long long)h->G.nr * h->G.nz), kThreads, 0, h->stream>>>(A, in);
-    return cudaGetLastError();
+    return scatter_args<S, R, SW, TH>(make_args<S, R>(h), in, h->stream);
 }
 
 #define AXL_DISPATCH_SWTH(FN, ...)                                            \

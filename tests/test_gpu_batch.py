@@ -1,0 +1,163 @@
+"""Batched uneven domains in one persistent launch, against the oracle.
+
+Each domain of a batch must follow exactly the single-domain update: the
+tests compare every domain with the FP64 oracle after 1, 2, ... steps, check
+that a batch reproduces single-domain runs bit for bit (each node's update
+depends only on its own inputs, so packing and tile order cannot change it),
+and check the per-domain check-step statistics.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1003_0282_gb300 import inputs as I
+from parity_util import POP_TOL, rel_err, seeded_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1003_0282_gb300 import build
+    build.build()
+    from paper_1003_0282_gb300 import axlbm
+    return axlbm
+
+
+def mixed_batch():
+    """Uneven domains: cavities of several sizes and Reynolds numbers, a
+    Wheeler-type cell with temperature, an annulus, a free-surface cell."""
+    doms = [
+        I.rotating_lid_cavity(nr=70, aspect=1.5, re=300.0),
+        I.rotating_lid_cavity(nr=33, aspect=2.5, re=150.0),
+        I.wheeler_cell(nr=40, re_x=200.0, prandtl=1.0, grashof=2e4),
+        I.rotating_lid_cavity(nr=130, aspect=1.0, re=500.0),
+        dataclasses.replace(I.rotating_lid_cavity(nr=20, aspect=3.0, re=100.0), z_hi="free"),
+        dataclasses.replace(I.rotating_lid_cavity(nr=25, aspect=1.2, re=100.0), inner="wall", r0=6.0,
+                            omega={"inner": 0.002, "hi": 0.004}),
+        I.wheeler_cell(nr=17, re_x=150.0, prandtl=5.0, grashof=1e4),
+    ]
+    return doms
+
+
+@pytest.mark.parametrize("precision", ["fp32"])
+def test_batch_matches_oracle_per_domain(B, precision):
+    doms = mixed_batch()
+    batch = B.Batch(doms, precision)
+    states = []
+    for d, pb in enumerate(doms):
+        st = seeded_state(pb, 100 + d)
+        batch.set_populations(d, st.f, st.g, st.h if pb.temperature else None)
+        states.append(st)
+    worst = 0.0
+    for n in (1, 1, 2, 7, 29):
+        batch.step(n)
+        for d, pb in enumerate(doms):
+            oracle.step(states[d], n)
+            f, g, h = batch.get_populations(d)
+            errs = [rel_err(f, states[d].f), rel_err(g, states[d].g)]
+            if pb.temperature:
+                errs.append(rel_err(h, states[d].h))
+            worst = max(worst, max(errs))
+    assert batch.time == 40
+    batch.close()
+    assert worst <= POP_TOL[precision], worst
+
+
+def test_batch_equals_single_domain_runs_bitwise(B):
+    doms = mixed_batch()
+    batch = B.Batch(doms, "fp32")
+    singles = []
+    for d, pb in enumerate(doms):
+        st = seeded_state(pb, 200 + d)
+        batch.set_populations(d, st.f, st.g, st.h if pb.temperature else None)
+        dom = B.Domain(pb, "fp32")
+        dom.set_populations(st.f, st.g, st.h if pb.temperature else None, time=0)
+        singles.append(dom)
+    batch.step(13)
+    for d, dom in enumerate(singles):
+        dom.step(13)
+        fb, gb, hb = batch.get_populations(d)
+        fs, gs, hs = dom.get_populations()
+        assert np.array_equal(fb, fs) and np.array_equal(gb, gs), d
+        if hb is not None:
+            assert np.array_equal(hb, hs), d
+        rb = batch.moments(d, B.RHO | B.UR | B.UZ | B.UTH)
+        rs = dom.moments(B.RHO | B.UR | B.UZ | B.UTH)
+        assert np.array_equal(rb, rs), d
+        dom.close()
+    batch.close()
+
+
+def test_batch_check_statistics_per_domain(B):
+    doms = mixed_batch()
+    batch = B.Batch(doms, "fp32")
+    refs = []
+    for d, pb in enumerate(doms):
+        st = seeded_state(pb, 300 + d)
+        batch.set_populations(d, st.f, st.g, st.h if pb.temperature else None)
+        refs.append(st)
+    batch.step(11)   # checks the step 10 -> 11: levels 9 and 10
+    res = batch.residuals()
+    for d, pb in enumerate(doms):
+        ref = refs[d]
+        oracle.step(ref, 9)
+        _, _, sp9 = oracle.stats(ref)
+        oracle.step(ref, 1)
+        m10, b10, sp10 = oracle.stats(ref)
+        assert res[d, 0] == pytest.approx(float(np.max(np.abs(sp10 - sp9))), rel=2e-3, abs=1e-9), d
+        assert res[d, 1] == pytest.approx(m10, rel=1e-7), d
+        assert res[d, 2] == pytest.approx(b10, rel=1e-3, abs=1e-9), d
+    batch.step(2)    # an even number of steps: checks ending on an even level use no ring values
+    assert np.all(np.isfinite(batch.residuals()))
+    batch.close()
+
+
+def test_batch_fields_io_and_parity_rule(B):
+    doms = mixed_batch()[:3]
+    batch = B.Batch(doms, "fp32")
+    fields = I.random_fields(doms[2].nr, doms[2].nz, seed=9)
+    batch.set_fields(2, fields)
+    want = oracle.equilibrium(doms[2], fields)
+    f, g, h = batch.get_populations(2)
+    assert rel_err(f, want.f) <= 1e-6 and rel_err(g, want.g) <= 1e-6 and rel_err(h, want.h) <= 1e-6
+    batch.step(1)
+    with pytest.raises(B.AxlbmError) as ei:
+        batch.set_fields(0, I.random_fields(doms[0].nr, doms[0].nz, seed=1))
+    assert ei.value.status == B.EINVAL
+    batch.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_full_sweep_sampled_domains(B, precision):
+    """The uneven sweep (256 rotating-lid cavities with N_r in [64, 256] and
+    64 Wheeler-type 128 x 128 cells, about 17.6 M nodes) in one batch; a few
+    domains are compared whole with the oracle after 6 steps from a seeded
+    state, every domain's mass budget is checked."""
+    doms = I.batch_sweep()
+    batch = B.Batch(doms, precision)
+    picks = [0, 7, 255, 256, 300, 319]
+    small = sorted(picks, key=lambda d: doms[d].cells)[:4]
+    states = {}
+    for d in small:
+        st = seeded_state(doms[d], 500 + d)
+        batch.set_populations(d, st.f, st.g, st.h if doms[d].temperature else None)
+        states[d] = st
+    batch.step(5)
+    r5 = batch.residuals()
+    batch.step(1)
+    r6 = batch.residuals()
+    tol = POP_TOL.get(precision, 5e-3)
+    for d in small:
+        oracle.step(states[d], 6)
+        f, g, _ = batch.get_populations(d)
+        assert rel_err(f, states[d].f) <= tol and rel_err(g, states[d].g) <= max(tol, 1e-4 if precision == "fp16" else tol), d
+    # mass budget M(6) = M(5) - B(5) in every domain (storage rounding only)
+    mtol = 1e-9 if precision == "fp32" else 1e-5
+    assert np.all(np.abs(r6[:, 1] - (r5[:, 1] - r5[:, 2])) <= mtol * np.abs(r5[:, 1]))
+    batch.close()
