@@ -1,17 +1,21 @@
 """Throughput benchmark of the axisymmetric lattice Boltzmann hot path.
 
-One benchmark step = one axlbm_step call of --inner lattice time steps over
-the whole workload (bulk collide-and-stream, boundary ring, and the check
-step with its FP64 reductions that ends every call).  The metric is MLUPS:
+One benchmark step = one solver call of --inner lattice time steps over the
+whole workload (bulk collide-and-stream, boundary rings, and the check step
+with its FP64 reductions that ends every call).  The metric is MLUPS:
 million lattice-node updates per second, whole job.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batch|pipe] [--precision fp32|fp16|...]
 
-Default workload: a Hagen-Poiseuille pipe of 4096 x 8192 nodes (D2Q9, FP32
-arithmetic, FP32 deviation storage), 2.4 GB of populations -- far larger than
-the 129 MB L2, so no cache flush is needed between steps.  Multi-GPU runs are
-independent replicas of the same pipe (one domain does not shard), so the
-scaling is weak.  Prints one JSON line on rank 0.
+Default workload (``batch``): the uneven sweep -- 256 rotating-lid cavities
+(N_r ~ U{64..256}, H/R ~ U[1, 3.5], Re ~ U[500, 3000]) and 64 Wheeler-type
+128 x 128 cells with temperature (Pr 0.05 / 5, Gr 1e4-1e6), 17.0 M nodes, one
+persistent launch per step, FP32 arithmetic and FP32 deviation storage
+(1.5 GB, far larger than the 129 MB L2, so no cache flush is needed).
+``pipe``: one 4096 x 8192 Hagen-Poiseuille pipe (D2Q9 only).  Under torchrun
+every rank advances its own seeded sweep (independent domains, no collective
+on the data path): weak scaling.  Prints one JSON line on rank 0.
 """
 from __future__ import annotations
 
@@ -23,6 +27,8 @@ import statistics
 import subprocess
 import sys
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -41,6 +47,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--inner", type=int, default=50, help="lattice time steps per benchmark step")
+    p.add_argument("--workload", choices=["batch", "pipe"], default="batch")
+    p.add_argument("--scale", type=float, default=1.0, help="batch: shrink every domain (small profiling cases)")
     p.add_argument("--nr", type=int, default=4096)
     p.add_argument("--nz", type=int, default=8192)
     p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
@@ -116,13 +124,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(pb_full, inner: int, budget_s: float = 12.0):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload:
-    a 256 x 512 section of the same pipe, advanced until ~budget_s of CPU time."""
-    import oracle
+def cpu_sample(workload: str):
+    """A bounded piece of the workload for the oracle: one 64 x 96 rotating-lid
+    cavity of the sweep's kind (batch) or a 256 x 512 pipe section (pipe)."""
     from paper_1003_0282_gb300 import inputs as I
+    if workload == "pipe":
+        return I.hagen_poiseuille(nr=256, nz=512, tau=0.8, umax=0.01), "pipe section 256x512"
+    return I.rotating_lid_cavity(nr=64, aspect=1.5, re=1000.0), "rotating-lid cavity 64x96 (Re 1000)"
 
-    sample = I.hagen_poiseuille(nr=256, nz=512, tau=pb_full.tau, umax=0.01)
+
+def cpu_baseline(workload: str, inner: int, budget_s: float = 12.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload,
+    advanced until ~budget_s of CPU time, single-threaded."""
+    import oracle
+
+    sample, what = cpu_sample(workload)
     st = oracle.rest_state(sample)
     oracle.step(st, 2)
     steps, t0 = 0, time.perf_counter()
@@ -131,7 +147,7 @@ def cpu_baseline(pb_full, inner: int, budget_s: float = 12.0):
         steps += inner
     dt = time.perf_counter() - t0
     return {"value": sample.cells * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle, pipe section 256x512 nodes, {steps} lattice steps, {dt:.1f} s, single thread"}
+            "sample": f"FP64 oracle, {what}, {steps} lattice steps, {dt:.1f} s, single thread"}
 
 
 def run_reference(args):
@@ -143,8 +159,7 @@ def run_reference(args):
     import oracle
     from paper_1003_0282_gb300 import inputs as I
 
-    pb = I.large_pipe(nr=args.nr, nz=args.nz)
-    sample = I.hagen_poiseuille(nr=128, nz=128, tau=pb.tau, umax=0.01)
+    sample, what = cpu_sample(args.workload)
     st = oracle.rest_state(sample)
     inner = max(1, min(args.inner, 10))
     for _ in range(args.warmup):
@@ -158,10 +173,10 @@ def run_reference(args):
         "impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"pipe {args.nr}x{args.nz} D2Q9 (bounded sample 128x128, {inner} lattice steps per step)",
+        "config": {"workload": f"{args.workload} (bounded sample: {what}, {inner} lattice steps per step)",
                    "precision": "fp64 oracle"},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"pipe section 128x128 nodes x {inner} lattice steps per benchmark step"},
+                         "sample": f"{what} x {inner} lattice steps per benchmark step"},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -185,11 +200,24 @@ def main():
     from paper_1003_0282_gb300 import axlbm as B
     from paper_1003_0282_gb300 import inputs as I
 
-    pb = I.large_pipe(nr=args.nr, nz=args.nz)
-    fields = torch.tensor(I.random_fields(pb.nr, pb.nz, seed=1000 + rank, du=1e-3, duth=0.0), dtype=torch.float32,
-                          device="cuda")
-    dom = B.Domain(pb, args.precision)
-    dom.set_fields(fields)
+    if args.workload == "pipe":
+        pb = I.large_pipe(nr=args.nr, nz=args.nz)
+        problems = [pb]
+        solver = B.Domain(pb, args.precision)
+        solver.set_fields(torch.tensor(I.random_fields(pb.nr, pb.nz, seed=1000 + rank, du=1e-3, duth=0.0),
+                                       dtype=torch.float32, device="cuda"))
+        timing_on = lambda on: B.axlbm_kernel_timing(solver.handle, on)
+        kernel_times = lambda: B.axlbm_kernel_times(solver.handle)
+        workload = (f"pipe {pb.nr}x{pb.nz} D2Q9 (Hagen-Poiseuille force, axis + bounce-back wall, periodic z)")
+    else:
+        problems = I.batch_sweep(seed=20261202 + rank, scale=args.scale)
+        solver = B.Batch(problems, args.precision)
+        timing_on = lambda on: B.axlbm_batch_kernel_timing(solver.handle, on)
+        kernel_times = lambda: B.axlbm_batch_kernel_times(solver.handle)
+        workload = (f"batched uneven sweep: {sum(not p.temperature for p in problems)} rotating-lid cavities + "
+                    f"{sum(p.temperature for p in problems)} Wheeler-type cells with temperature, one persistent "
+                    f"launch per step" + (f" (radii scaled by {args.scale})" if args.scale != 1.0 else ""))
+    nodes = sum(p.cells for p in problems)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -198,77 +226,90 @@ def main():
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        dom.step(args.inner)
+        solver.step(args.inner)
     barrier()
-    B.axlbm_kernel_timing(dom.handle, True)
+    timing_on(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         barrier()
         ev0.record(stream)
         for _ in range(args.steps):
-            dom.step(args.inner)
+            solver.step(args.inner)
         ev1.record(stream)
         barrier()
     ms = ev0.elapsed_time(ev1)
-    bulk_n, bulk_ms, bulk_bytes, all_launches = B.axlbm_kernel_times(dom.handle)
-    B.axlbm_kernel_timing(dom.handle, False)
-    res, mass, _ = dom.residual()
+    bulk_n, bulk_ms, bulk_bytes, all_launches = kernel_times()
+    timing_on(False)
+    if args.workload == "pipe":
+        res, mass, _ = solver.residual()
+    else:
+        rr = solver.residuals()
+        res, mass = float(rr[:, 0].max()), float(rr[:, 1].sum())
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    updates = pb.cells * args.inner * args.steps * world
+    updates = nodes * args.inner * args.steps * world
     value = updates / (ms / 1e3) / 1e6
 
     # end to end through the C ABI with pinned host buffers: fields in, moments out
-    host_in = torch.empty((5, pb.nz, pb.nr), dtype=torch.float64, pin_memory=True)
-    host_in.copy_(torch.from_numpy(I.random_fields(pb.nr, pb.nz, seed=2000 + rank, du=1e-3, duth=0.0)))
-    host_out = torch.empty((3, pb.nz, pb.nr), dtype=torch.float32, pin_memory=True)
+    fin = np.concatenate([I.random_fields(p.nr, p.nz, seed=2000 + rank + i, du=1e-3, duth=1e-3).ravel()
+                          for i, p in enumerate(problems)])
+    host_in = torch.empty(fin.size, dtype=torch.float32, pin_memory=True)
+    host_in.copy_(torch.from_numpy(fin.astype(np.float32)))
+    host_out = torch.empty(3 * nodes, dtype=torch.float32, pin_memory=True)
+    if solver.time % 2:
+        solver.step(1)  # fields are set at an even level
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        B.axlbm_set_fields(dom.handle, host_in.data_ptr(), B.F64, 0)
-        dom.step(args.inner)
-        B.axlbm_moments(dom.handle, B.RHO | B.UR | B.UZ, host_out.data_ptr(), B.F32, 0)
+        if args.workload == "pipe":
+            B.axlbm_set_fields(solver.handle, host_in.data_ptr(), B.F32, 0)
+            solver.step(args.inner)
+            B.axlbm_moments(solver.handle, B.RHO | B.UR | B.UZ, host_out.data_ptr(), B.F32, 0)
+        else:
+            B.axlbm_batch_set_fields_all(solver.handle, host_in.data_ptr(), B.F32, 0)
+            solver.step(args.inner)
+            B.axlbm_batch_moments_all(solver.handle, B.RHO | B.UR | B.UZ, host_out.data_ptr(), B.F32, 0)
     barrier()
     e2e_s = time.perf_counter() - t0
     if world > 1:
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = pb.cells * args.inner * args.e2e_steps * world / e2e_s / 1e6
-    dom.close()
+    e2e_value = nodes * args.inner * args.e2e_steps * world / e2e_s / 1e6
+    solver.close()
 
     if rank == 0:
         peak, peak_kind = peaks()
         achieved = bulk_bytes / (bulk_ms / 1e3) / 1e9 if bulk_ms > 0 else 0.0
         sha = kernel_source_sha()
-        key = f"k_bulk {args.precision} d2q9"
+        key = f"{args.workload} {args.precision}"
         tr = NCU_TRAFFIC.get(key)
         traffic = None
         if tr and tr["src_sha"] == sha:
             traffic = tr["dram_per_alg_byte"] * bulk_bytes / max(bulk_n, 1)
+        kernel = "k_bulk (even + odd AA steps)" if args.workload == "pipe" else "k_bulk_batch (even + odd AA steps)"
         line = {
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-            "config": {"workload": f"pipe {pb.nr}x{pb.nz} D2Q9 (Hagen-Poiseuille force, axis + bounce-back wall, "
-                                   f"periodic z)", "precision": args.precision, "nodes": pb.cells,
-                       "lattice_steps_per_step": args.inner,
-                       "cache": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+            "config": {"workload": workload, "precision": args.precision, "nodes": nodes,
+                       "domains": len(problems), "lattice_steps_per_step": args.inner,
+                       "cache": "inputs larger than L2 (no flush)", "parallelism": f"independent replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_bulk (even + odd AA steps)", "launches": bulk_n,
+                         "kernel": kernel, "launches": bulk_n,
                          "avg_launch_ms": bulk_ms / max(bulk_n, 1),
                          "alg_bytes_per_launch": bulk_bytes / max(bulk_n, 1)},
             "e2e": {"value": e2e_value, "unit": "MLUPS",
-                    "h2d_bytes_per_step": 5 * 8 * pb.cells, "d2h_bytes_per_step": 3 * 4 * pb.cells},
+                    "h2d_bytes_per_step": 5 * 4 * nodes, "d2h_bytes_per_step": 3 * 4 * nodes},
             "gpu_launches": all_launches,
             "clocks": clk.summary(),
             "check": {"residual": res, "mass": mass},
         }
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(pb, args.inner)
+            line["cpu_baseline"] = cpu_baseline(args.workload, args.inner)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -284,6 +284,16 @@ AXLBM_API axlbm_status axlbm_batch_moments(axlbm_batch* b, int32_t d, uint32_t f
 AXLBM_API axlbm_status axlbm_batch_set_fields(axlbm_batch* b, int32_t d, const void* fields, int32_t in_dtype,
                                               int32_t on_device);
 
+/* Every domain at once: fields of all domains packed one after another in
+ * domain order, each [5][nz][nr] (set) or [nfields][nz][nr] (moments), of
+ * element type dtype, on the device or the host (one staging copy for the
+ * whole batch).  Same rules as the per-domain calls; set_fields_all needs an
+ * even time level. */
+AXLBM_API axlbm_status axlbm_batch_set_fields_all(axlbm_batch* b, const void* fields, int32_t in_dtype,
+                                                  int32_t on_device);
+AXLBM_API axlbm_status axlbm_batch_moments_all(axlbm_batch* b, uint32_t field_mask, void* out, int32_t out_dtype,
+                                               int32_t out_on_device);
+
 /* Populations of domain d at the current level (host FP64, layout as
  * axlbm_get_populations).  Synchronises. */
 AXLBM_API axlbm_status axlbm_batch_get_populations(axlbm_batch* b, int32_t d, double* f, double* g,

@@ -40,7 +40,8 @@ class _Params(ctypes.Structure):
         ("tau_t_s", ctypes.c_double), ("rho0", ctypes.c_double), ("az0", ctypes.c_double),
         ("omega_t", ctypes.c_double), ("gbeta", ctypes.c_double), ("t_ref", ctypes.c_double),
         ("r_split", ctypes.c_double), ("omega_w", ctypes.c_double * 4),
-        ("t_w", ctypes.c_double * 4),
+        ("t_w", ctypes.c_double * 4), ("collision", ctypes.c_int32), ("pad2", ctypes.c_int32),
+        ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
     ]
 
 
@@ -76,6 +77,8 @@ def _load():
         lib.orc_collide_cell.restype = None
         lib.orc_stream.argtypes = [P, dp, dp, dp, dp, dp, dp]
         lib.orc_stream.restype = None
+        lib.orc_mrt_matrix.argtypes = [dp]
+        lib.orc_mrt_matrix.restype = None
         _lib = lib
     return _lib
 
@@ -94,6 +97,8 @@ def params(pb) -> _Params:
     p.r0, p.tau_s, p.tau_t_s, p.rho0 = float(pb.r0), float(pb.tau), float(pb.tau_t), float(pb.rho0)
     p.az0, p.omega_t = float(pb.az0), float(pb.omega_t)
     p.gbeta, p.t_ref, p.r_split = float(pb.gbeta), float(pb.t_ref), float(pb.r_split)
+    p.collision = {"bgk": 0, "mrt": 1}[getattr(pb, "collision", "bgk")]
+    p.s_eps, p.s_q = float(getattr(pb, "s_eps", 0.0)), float(getattr(pb, "s_q", 0.0))
     return p
 
 
@@ -203,3 +208,10 @@ def stream(pb, fp, gp=None, hp=None):
 
 def node_radii(pb) -> np.ndarray:
     return pb.r0 + np.arange(pb.nr) + 0.5
+
+
+def mrt_matrix() -> np.ndarray:
+    """The oracle's MRT moment basis M (9 x 9), rows as in Eq. 38."""
+    out = np.empty(81)
+    _load().orc_mrt_matrix(_ptr(out))
+    return out.reshape(9, 9)

@@ -30,6 +30,10 @@
  *        h*_a = h_a - wh_a (h_a - h^eq_a) - (u_r / r) h^eq_a,
  *        h^eq_a = T / 4 (1 + 2 e_a.u), wh_a = (1 + tau_T e_ar / r)/(tau_T + 1/2)
  *   5. push streaming into a second lattice, with the boundary rules below.
+ * With collision = 1 step 3 is the MRT scheme of Sec. III B instead (Eqs.
+ * 37-51: moment-space relaxation, moment-space source, momentum correction);
+ * f then stands for the shifted distribution f - S/2 and steps 1-2, 4-5 are
+ * unchanged.
  *
  * tau here is the paper's tau (mu = tau rho c_s^2, omega = 1/(tau + 1/2),
  * Eq. 8 and the line after Eq. 36); the caller passes the standard relaxation
@@ -94,6 +98,9 @@ typedef struct {
     double r_split;             /* ORC_MIXED: wall part for r < r_split */
     double omega_w[4];          /* per face: angular velocity of the wall */
     double t_w[4];              /* per face: wall temperature when Dirichlet */
+    int32_t collision;          /* 0: BGK (Eq. 13), 1: MRT (Eqs. 37-51) */
+    int32_t pad2;
+    double s_eps, s_q;          /* MRT rates of epsilon and q (0: defaults, see mrt_rates) */
 } orc_params;
 
 /* D2Q9, components (r, z): rest, four axis links, four diagonals (Eq. 6). */
@@ -126,6 +133,7 @@ int orc_validate(const orc_params* p) {
     if (p->z_lo == ORC_MIXED) return ORC_EINVAL;
     if ((p->z_lo == ORC_PERIODIC) != (p->z_hi == ORC_PERIODIC)) return ORC_EINVAL;
     if (p->temperature && !(p->tau_t_s > 0.5)) return ORC_EINVAL;
+    if (p->collision != 0 && p->collision != 1) return ORC_EINVAL;
     return ORC_OK;
 }
 
@@ -163,6 +171,9 @@ static double cell_moments(const orc_params* p, double r, double a_t, const doub
     return s0;
 }
 
+static void mrt_collide_f(const orc_params* p, double r, const double* fin, double rho, double ur, double uz,
+                          double fr, double fz, double* fout);
+
 /* Collision of one node at radius r and time-level force a_t.  fin/gin/hin are
  * the pre-collision populations, fout/gout/hout receive the post-collision
  * ones, mom (optional) the moments rho, u_r, u_z, u_theta, T. */
@@ -181,12 +192,16 @@ void orc_collide_cell(const orc_params* p, double r, double a_t, const double* f
     if (p->temperature) fz += p->rho0 * p->gbeta * (temp - p->t_ref);
 
     const double usq = ur * ur + uz * uz;
-    for (int a = 0; a < 9; ++a) {
-        const double eu = CR[a] * ur + CZ[a] * uz;
-        const double feq = WT[a] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
-        const double src = (3.0 * ((CR[a] - ur) * fr + (CZ[a] - uz) * fz) / rho - ur / r) * feq;
-        const double om = (1.0 + tau * CR[a] / r) / (tau + 0.5);
-        fout[a] = fin[a] - om * (fin[a] - feq) + (1.0 - 0.5 * om) * src;
+    if (p->collision == 1) {
+        mrt_collide_f(p, r, fin, rho, ur, uz, fr, fz, fout);
+    } else {
+        for (int a = 0; a < 9; ++a) {
+            const double eu = CR[a] * ur + CZ[a] * uz;
+            const double feq = WT[a] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+            const double src = (3.0 * ((CR[a] - ur) * fr + (CZ[a] - uz) * fz) / rho - ur / r) * feq;
+            const double om = (1.0 + tau * CR[a] / r) / (tau + 0.5);
+            fout[a] = fin[a] - om * (fin[a] - feq) + (1.0 - 0.5 * om) * src;
+        }
     }
     if (p->swirl) {
         const double taug = 2.0 * tau / 3.0;
@@ -210,6 +225,95 @@ void orc_collide_cell(const orc_params* p, double r, double a_t, const double* f
         }
     }
     if (mom) memcpy(mom, m, sizeof m);
+}
+
+/* ---- MRT collision (Sec. III B) --------------------------------------------------- */
+
+/* Moment basis of Eq. 38 in the order rho, e, epsilon, j_x, q_x, j_y, q_y,
+ * p_xx, p_xy with (x, y) = (r, z): rows are 1, -4 + 3|e|^2,
+ * 4 - 21|e|^2/2 + 9|e|^4/2, e_x, (-5 + 3|e|^2) e_x, e_y, (-5 + 3|e|^2) e_y,
+ * e_x^2 - e_y^2, e_x e_y -- the orthogonal D2Q9 basis the paper takes from
+ * its Ref. [9]. */
+static void mrt_matrix(double M[9][9]) {
+    for (int a = 0; a < 9; ++a) {
+        const double ex = CR[a], ey = CZ[a], e2 = ex * ex + ey * ey;
+        M[0][a] = 1.0;
+        M[1][a] = -4.0 + 3.0 * e2;
+        M[2][a] = 4.0 - 10.5 * e2 + 4.5 * e2 * e2;
+        M[3][a] = ex;
+        M[4][a] = (-5.0 + 3.0 * e2) * ex;
+        M[5][a] = ey;
+        M[6][a] = (-5.0 + 3.0 * e2) * ey;
+        M[7][a] = ex * ex - ey * ey;
+        M[8][a] = ex * ey;
+    }
+}
+
+/* The rows are orthogonal: M^-1 = M^T diag(1 / |row|^2). */
+static void mrt_inverse(const double M[9][9], double Mi[9][9]) {
+    for (int i = 0; i < 9; ++i) {
+        double n2 = 0.0;
+        for (int a = 0; a < 9; ++a) n2 += M[i][a] * M[i][a];
+        for (int a = 0; a < 9; ++a) Mi[a][i] = M[i][a] / n2;
+    }
+}
+
+/* Relaxation rates Lambda = diag(s_rho, s_e, s_eps, s_j, s_q, s_j, s_q, s_v, s_v):
+ * s_v = 1/(tau + 1/2) from the viscosity, s_e = s_v (bulk = shear viscosity,
+ * Sec. IV B), s_eps and s_q from the parameters (defaults: s_eps = s_v and
+ * s_q such that (1/s_v - 1/2)(1/s_q - 1/2) = 1/4).  The conserved moments'
+ * rates do not change the result; they are set to 1. */
+static void mrt_rates(const orc_params* p, double L[9]) {
+    const double tau = p->tau_s - 0.5;
+    const double sv = 1.0 / (tau + 0.5);
+    const double seps = p->s_eps > 0.0 ? p->s_eps : sv;
+    const double sq = p->s_q > 0.0 ? p->s_q : 1.0 / (0.5 + 0.25 / (1.0 / sv - 0.5));
+    L[0] = 1.0;
+    L[1] = sv;
+    L[2] = seps;
+    L[3] = 1.0;
+    L[4] = sq;
+    L[5] = 1.0;
+    L[6] = sq;
+    L[7] = sv;
+    L[8] = sv;
+}
+
+/* One MRT collision: Eq. 41 in moment space with the source of Eq. 51 taken
+ * as -(u_r/r) m^eq + S' (the sign that matches Eq. 12), then the momentum
+ * correction of Eqs. 49-50, then back to populations. */
+static void mrt_collide_f(const orc_params* p, double r, const double* fin, double rho, double ur, double uz,
+                          double fr, double fz, double* fout) {
+    double M[9][9], Mi[9][9], L[9];
+    mrt_matrix(M);
+    mrt_inverse(M, Mi);
+    mrt_rates(p, L);
+    double m[9];
+    for (int i = 0; i < 9; ++i) {
+        m[i] = 0.0;
+        for (int a = 0; a < 9; ++a) m[i] += M[i][a] * fin[a];
+    }
+    const double usq = ur * ur + uz * uz;
+    const double meq[9] = {rho, rho * (-2.0 + 3.0 * usq), rho * (1.0 - 3.0 * usq), rho * ur, -rho * ur,
+                           rho * uz, -rho * uz, rho * (ur * ur - uz * uz), rho * ur * uz};   /* Eq. 39 */
+    const double uF = ur * fr + uz * fz;
+    const double sp[9] = {0.0, 6.0 * uF, -6.0 * uF, fr, -fr, fz, -fz,
+                          2.0 * (ur * fr - uz * fz), ur * fz + uz * fr};                     /* Eq. 51 */
+    double src[9], mp[9];
+    for (int i = 0; i < 9; ++i) src[i] = -(ur / r) * meq[i] + sp[i];
+    for (int i = 0; i < 9; ++i) mp[i] = m[i] - L[i] * (m[i] - meq[i]) + (1.0 - 0.5 * L[i]) * src[i];  /* Eq. 41 */
+    /* Eqs. 49-50: m^(1) = (m - m^eq) + S/2 */
+    const double sv = L[7], se = L[1];
+    const double gamma = (1.0 - 0.5 * sv) / r;
+    const double e1 = (m[1] - meq[1]) + 0.5 * src[1];
+    const double pxx1 = (m[7] - meq[7]) + 0.5 * src[7];
+    const double pxy1 = (m[8] - meq[8]) + 0.5 * src[8];
+    mp[3] -= gamma * ((se / (6.0 * sv)) * e1 + 0.5 * pxx1);
+    mp[5] -= gamma * pxy1;
+    for (int a = 0; a < 9; ++a) {
+        fout[a] = 0.0;
+        for (int i = 0; i < 9; ++i) fout[a] += Mi[a][i] * mp[i];
+    }
 }
 
 /* ---- boundary classification of a lattice site ---------------------------------- */
@@ -444,4 +548,12 @@ int orc_stats(const orc_params* p, int64_t t, const double* f, const double* g,
     return ORC_OK;
 }
 
-int orc_abi_version(void) { return 1; }
+/* The MRT moment basis (for the tests' checks of Eqs. 38-39). */
+void orc_mrt_matrix(double* out81) {
+    double M[9][9];
+    mrt_matrix(M);
+    for (int i = 0; i < 9; ++i)
+        for (int a = 0; a < 9; ++a) out81[9 * i + a] = M[i][a];
+}
+
+int orc_abi_version(void) { return 2; }

@@ -106,6 +106,8 @@ def lib() -> ctypes.CDLL:
                                           ctypes.c_int32]
         L.axlbm_batch_set_fields.argtypes = [H, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
         L.axlbm_batch_get_populations.argtypes = [H, ctypes.c_int32, dp, dp, dp]
+        L.axlbm_batch_set_fields_all.argtypes = [H, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
+        L.axlbm_batch_moments_all.argtypes = [H, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
         L.axlbm_batch_set_populations.argtypes = [H, ctypes.c_int32, dp, dp, dp]
         L.axlbm_batch_time.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_batch_tile_shape.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
@@ -117,7 +119,8 @@ def lib() -> ctypes.CDLL:
         for name in ("axlbm_batch_state_bytes", "axlbm_batch_create", "axlbm_batch_step", "axlbm_batch_residuals",
                      "axlbm_batch_moments", "axlbm_batch_set_fields", "axlbm_batch_get_populations",
                      "axlbm_batch_set_populations", "axlbm_batch_time", "axlbm_batch_tile_shape",
-                     "axlbm_batch_kernel_timing", "axlbm_batch_kernel_times", "axlbm_batch_destroy"):
+                     "axlbm_batch_kernel_timing", "axlbm_batch_kernel_times", "axlbm_batch_destroy",
+                     "axlbm_batch_set_fields_all", "axlbm_batch_moments_all"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("axlbm_state_bytes", "axlbm_create", "axlbm_step", "axlbm_moments", "axlbm_residual",
                      "axlbm_set_fields", "axlbm_get_populations", "axlbm_set_populations", "axlbm_time",
@@ -379,6 +382,15 @@ def axlbm_batch_set_fields(b, d: int, ptr: int, in_dtype: int, on_device: int) -
     _bcheck(lib().axlbm_batch_set_fields(b, int(d), ctypes.c_void_p(ptr), int(in_dtype), int(on_device)), b)
 
 
+def axlbm_batch_set_fields_all(b, ptr: int, in_dtype: int, on_device: int) -> None:
+    _bcheck(lib().axlbm_batch_set_fields_all(b, ctypes.c_void_p(ptr), int(in_dtype), int(on_device)), b)
+
+
+def axlbm_batch_moments_all(b, mask: int, out_ptr: int, out_dtype: int, out_on_device: int) -> None:
+    _bcheck(lib().axlbm_batch_moments_all(b, int(mask), ctypes.c_void_p(out_ptr), int(out_dtype),
+                                          int(out_on_device)), b)
+
+
 def axlbm_batch_get_populations(b, d: int, f, g, t_pop) -> None:
     _bcheck(lib().axlbm_batch_get_populations(b, int(d), _dptr(f), _dptr(g), _dptr(t_pop)), b)
 
@@ -471,6 +483,27 @@ class Batch:
 
             axlbm_batch_set_fields(self.handle, d, fields.data_ptr(),
                                    F32 if fields.dtype == torch.float32 else F64, 1)
+
+    def set_fields_all(self, fields) -> None:
+        """Fields of every domain, packed in domain order ([5][nz][nr] each); numpy or CUDA tensor."""
+        if isinstance(fields, np.ndarray):
+            a = np.ascontiguousarray(fields, dtype=np.float64)
+            axlbm_batch_set_fields_all(self.handle, a.ctypes.data, F64, 0)
+        else:
+            import torch
+
+            axlbm_batch_set_fields_all(self.handle, fields.data_ptr(), F32 if fields.dtype == torch.float32 else F64,
+                                       0 if fields.device.type == "cpu" else 1)
+
+    def moments_all(self, mask: int, out) -> None:
+        """Selected fields of every domain into a packed buffer (numpy or torch, host or CUDA)."""
+        if isinstance(out, np.ndarray):
+            axlbm_batch_moments_all(self.handle, mask, out.ctypes.data, F64 if out.dtype == np.float64 else F32, 0)
+        else:
+            import torch
+
+            axlbm_batch_moments_all(self.handle, mask, out.data_ptr(), F32 if out.dtype == torch.float32 else F64,
+                                    0 if out.device.type == "cpu" else 1)
 
     def get_populations(self, d: int):
         pb = self.problems[d]

@@ -554,6 +554,76 @@ axlbm_status axlbm_batch_set_fields(axlbm_batch* b, int32_t d, const void* field
     return AXLBM_OK;
 }
 
+axlbm_status axlbm_batch_set_fields_all(axlbm_batch* b, const void* fields, int32_t in_dtype, int32_t on_device) {
+    if (!b || !fields || (in_dtype != AXLBM_F64 && in_dtype != AXLBM_F32))
+        return bfail(b, AXLBM_EINVAL, "bad batch or fields");
+    if (b->parity != 0) return bfail(b, AXLBM_EINVAL, "set_fields needs an even time level");
+    const size_t es = in_dtype == AXLBM_F32 ? 4 : 8;
+    size_t total = 0;
+    for (int d = 0; d < b->n; ++d) total += (size_t)5 * b->desc[d].grid.nr * b->desc[d].grid.nz;
+    const char* src = static_cast<const char*>(fields);
+    void* tmp = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        e = cudaMalloc(&tmp, total * es);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(b, AXLBM_ENOMEM, "staging buffer");
+        }
+        e = cudaMemcpyAsync(tmp, fields, total * es, cudaMemcpyHostToDevice, b->stream);
+        src = static_cast<const char*>(tmp);
+    }
+    const BatchOps* ops = batch_ops_for(b->precision);
+    size_t off = 0;
+    for (int d = 0; d < b->n && e == cudaSuccess; ++d) {
+        e = ops->init(b, d, src + off * es, in_dtype == AXLBM_F32);
+        off += (size_t)5 * b->desc[d].grid.nr * b->desc[d].grid.nz;
+    }
+    if (tmp) {
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        cudaFree(tmp);
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "set_fields_all");
+    b->speed_valid = false;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_moments_all(axlbm_batch* b, uint32_t mask, void* out, int32_t out_dtype, int32_t out_on_device) {
+    if (!b || !out || mask == 0 || (mask & ~31u)) return bfail(b, AXLBM_EINVAL, "bad batch, output or field mask");
+    if (out_dtype != AXLBM_F64 && out_dtype != AXLBM_F32) return bfail(b, AXLBM_EINVAL, "bad out_dtype");
+    if (mask & AXLBM_T)
+        for (int d = 0; d < b->n; ++d)
+            if (!b->desc[d].grid.with_temperature) return bfail(b, AXLBM_EINVAL, "T needs with_temperature in every domain");
+    int nf = 0;
+    for (int f = 0; f < 5; ++f) nf += (mask >> f) & 1;
+    const size_t es = out_dtype == AXLBM_F32 ? 4 : 8;
+    size_t total = 0;
+    for (int d = 0; d < b->n; ++d) total += (size_t)nf * b->desc[d].grid.nr * b->desc[d].grid.nz;
+    char* dst = static_cast<char*>(out);
+    void* tmp = nullptr;
+    if (!out_on_device) {
+        cudaError_t e = cudaMalloc(&tmp, total * es);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(b, AXLBM_ENOMEM, "staging buffer");
+        }
+        dst = static_cast<char*>(tmp);
+    }
+    const BatchOps* ops = batch_ops_for(b->precision);
+    cudaError_t e = cudaSuccess;
+    size_t off = 0;
+    for (int d = 0; d < b->n && e == cudaSuccess; ++d) {
+        e = ops->moments(b, d, dst + off * es, mask, out_dtype == AXLBM_F32);
+        off += (size_t)nf * b->desc[d].grid.nr * b->desc[d].grid.nz;
+    }
+    if (tmp) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, total * es, cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        cudaFree(tmp);
+    }
+    return e == cudaSuccess ? AXLBM_OK : bcuda(b, e, "moments_all");
+}
+
 axlbm_status axlbm_batch_get_populations(axlbm_batch* b, int32_t d, double* f, double* g, double* tp) {
     if (!domain_ok(b, d) || !f) return bfail(b, AXLBM_EINVAL, "bad batch, domain index or arrays");
     const axlbm_domain& D = b->desc[d];

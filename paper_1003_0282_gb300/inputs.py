@@ -55,6 +55,9 @@ class Problem:
     r_split: float = 0.0            # MIXED top: wall for r < r_split
     omega: Dict[str, float] = dataclasses.field(default_factory=dict)     # wall angular velocity per face
     t_wall: Dict[str, float] = dataclasses.field(default_factory=dict)    # Dirichlet temperature per face
+    collision: str = "bgk"          # "bgk" (Eq. 13) or "mrt" (Eqs. 37-51)
+    s_eps: float = 0.0              # MRT rate of epsilon (0: the default)
+    s_q: float = 0.0                # MRT rate of q (0: the default)
     name: str = ""
 
     def omega_of(self, face: str) -> float:

@@ -161,3 +161,26 @@ def test_full_sweep_sampled_domains(B, precision):
     mtol = 1e-9 if precision == "fp32" else 1e-5
     assert np.all(np.abs(r6[:, 1] - (r5[:, 1] - r5[:, 2])) <= mtol * np.abs(r5[:, 1]))
     batch.close()
+
+
+def test_batch_packed_fields_match_per_domain_calls(B):
+    doms = mixed_batch()
+    batch = B.Batch(doms, "fp32")
+    packed = np.concatenate([I.random_fields(pb.nr, pb.nz, seed=40 + d).ravel() for d, pb in enumerate(doms)])
+    batch.set_fields_all(packed)
+    off = 0
+    for d, pb in enumerate(doms):
+        want = oracle.equilibrium(pb, packed[off:off + 5 * pb.cells].reshape(5, pb.nz, pb.nr))
+        f, g, _ = batch.get_populations(d)
+        assert rel_err(f, want.f) <= 1e-6 and rel_err(g, want.g) <= 1e-6, d
+        off += 5 * pb.cells
+    batch.step(3)
+    mask = B.RHO | B.UR | B.UZ | B.UTH
+    allm = np.empty(sum(4 * pb.cells for pb in doms), dtype=np.float32)
+    batch.moments_all(mask, allm)
+    off = 0
+    for d, pb in enumerate(doms):
+        one = batch.moments(d, mask, dtype=np.float32)
+        assert np.array_equal(allm[off:off + 4 * pb.cells].reshape(4, pb.nz, pb.nr), one), d
+        off += 4 * pb.cells
+    batch.close()

@@ -52,6 +52,14 @@ MUTATIONS = {
         ("top_kind_at(p, node_r(p, j) + 0.5 * cr)", "top_kind_at(p, node_r(p, j))"),
     "u_theta not divided by rho0":
         ("        uth /= p->rho0;\n", ""),
+    "MRT: momentum correction of Eq. 49 with the wrong sign":
+        ("mp[3] -= gamma * ((se / (6.0 * sv)) * e1 + 0.5 * pxx1);", "mp[3] += gamma * ((se / (6.0 * sv)) * e1 + 0.5 * pxx1);"),
+    "MRT: correction of Eq. 50 dropped":
+        ("    mp[5] -= gamma * pxy1;\n", ""),
+    "MRT: source sign of Eq. 51 taken as printed (+)":
+        ("src[i] = -(ur / r) * meq[i] + sp[i];", "src[i] = (ur / r) * meq[i] + sp[i];"),
+    "MRT: half-source dropped from m^(1)":
+        ("const double pxy1 = (m[8] - meq[8]) + 0.5 * src[8];", "const double pxy1 = (m[8] - meq[8]);"),
     "sign of the buoyancy force":
         ("fz += p->rho0 * p->gbeta * (temp - p->t_ref);", "fz -= p->rho0 * p->gbeta * (temp - p->t_ref);"),
 }
@@ -69,6 +77,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                    check=True)
     env = dict(os.environ, AXLBM_ORACLE_LIB=str(lib))
     res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                          os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                          os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                          os.path.join(ROOT, "tests", "test_oracle_mrt.py")],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert res.returncode != 0, f"no pin caught: {name}\n{res.stdout[-2000:]}"
