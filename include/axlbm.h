@@ -51,7 +51,7 @@
 extern "C" {
 #endif
 
-#define AXLBM_ABI_VERSION 1
+#define AXLBM_ABI_VERSION 2
 
 typedef enum {
     AXLBM_OK = 0,
@@ -84,6 +84,11 @@ enum {
 };
 enum { AXLBM_FACE_INNER = 0, AXLBM_FACE_OUTER = 1, AXLBM_FACE_LO = 2, AXLBM_FACE_HI = 3 };
 
+/* Collision model of f.  AXLBM_MRT: moment-space relaxation with the source
+ * in moment space and the momentum correction of Sec. III B (Eqs. 41, 49-51);
+ * rates s_v = 1/tau, s_e = s_v, s_eps and s_q from axlbm_forcing. */
+enum { AXLBM_BGK = 0, AXLBM_MRT = 1 };
+
 /* field mask bits for axlbm_moments */
 enum { AXLBM_RHO = 1, AXLBM_UR = 2, AXLBM_UZ = 4, AXLBM_UTH = 8, AXLBM_T = 16 };
 /* element types of caller arrays */
@@ -94,7 +99,7 @@ typedef struct {
     int32_t precision;        /* axlbm_precision */
     int32_t with_swirl;       /* 1: carry g (Eqs. 53-54) */
     int32_t with_temperature; /* 1: carry h */
-    int32_t reserved;         /* must be 0 */
+    int32_t collision;        /* AXLBM_BGK (Eq. 13) or AXLBM_MRT (Eqs. 37-51) for f */
     double r0;                /* radius of the inner face; 0 with the axis */
 } axlbm_grid;
 
@@ -104,6 +109,8 @@ typedef struct {
     double gbeta, t_ref;  /* Boussinesq: F_z += rho0 gbeta (T - t_ref) */
     double tau_t;         /* temperature relaxation time (standard); kappa = (tau_t - 1/2)/2 */
     double t_init;        /* uniform temperature of the initial state */
+    double mrt_s_eps;     /* MRT rate of epsilon; 0 selects s_v */
+    double mrt_s_q;       /* MRT rate of q; 0 selects (1/s_v - 1/2)(1/s_q - 1/2) = 1/4 */
 } axlbm_forcing;
 
 typedef struct {
@@ -141,7 +148,8 @@ AXLBM_API axlbm_status axlbm_state_bytes(const axlbm_grid* grid, size_t* bytes);
  *   out: receives the handle; unchanged on failure.
  * Validates the description: AXLBM_EINVAL on an invalid grid, tau <= 1/2,
  * rho0 <= 0, an axis with r0 != 0, one periodic axial face without the
- * other, a mixed bottom face, or tau_t <= 1/2 with temperature.  The call
+ * other, a mixed bottom face, tau_t <= 1/2 with temperature, an unknown
+ * collision model, or MRT rates outside (0, 2).  The call
  * writes the initial state and synchronises the stream before it returns. */
 AXLBM_API axlbm_status axlbm_create(const axlbm_grid* grid, double tau, const axlbm_forcing* forcing,
                           const axlbm_boundary* boundary, void* cuda_stream, void* state_mem,

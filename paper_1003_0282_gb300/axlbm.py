@@ -26,6 +26,7 @@ INNER_AXIS, INNER_WALL = 0, 1
 Z_PERIODIC, Z_WALL, Z_FREE, Z_MIXED = range(4)
 RHO, UR, UZ, UTH, T = 1, 2, 4, 8, 16
 F64, F32 = 0, 1
+BGK, MRT = 0, 1
 _ZKIND = {"periodic": Z_PERIODIC, "wall": Z_WALL, "free": Z_FREE, "mixed": Z_MIXED}
 _INNER = {"axis": INNER_AXIS, "wall": INNER_WALL}
 
@@ -33,13 +34,13 @@ _INNER = {"axis": INNER_AXIS, "wall": INNER_WALL}
 class axlbm_grid(ctypes.Structure):
     _fields_ = [("nr", ctypes.c_int32), ("nz", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("with_swirl", ctypes.c_int32), ("with_temperature", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("r0", ctypes.c_double)]
+                ("collision", ctypes.c_int32), ("r0", ctypes.c_double)]
 
 
 class axlbm_forcing(ctypes.Structure):
     _fields_ = [("rho0", ctypes.c_double), ("az0", ctypes.c_double), ("omega_t", ctypes.c_double),
                 ("gbeta", ctypes.c_double), ("t_ref", ctypes.c_double), ("tau_t", ctypes.c_double),
-                ("t_init", ctypes.c_double)]
+                ("t_init", ctypes.c_double), ("mrt_s_eps", ctypes.c_double), ("mrt_s_q", ctypes.c_double)]
 
 
 class axlbm_boundary(ctypes.Structure):
@@ -233,9 +234,10 @@ def axlbm_destroy(h) -> None:
 def structs(pb: "_inputs.Problem", precision: str = "fp32"):
     """(grid, tau, forcing, boundary) for a Problem."""
     g = axlbm_grid(nr=pb.nr, nz=pb.nz, precision=PRECISIONS[precision], with_swirl=int(bool(pb.swirl)),
-                   with_temperature=int(bool(pb.temperature)), reserved=0, r0=float(pb.r0))
+                   with_temperature=int(bool(pb.temperature)), collision={"bgk": BGK, "mrt": MRT}[pb.collision],
+                   r0=float(pb.r0))
     f = axlbm_forcing(rho0=pb.rho0, az0=pb.az0, omega_t=pb.omega_t, gbeta=pb.gbeta, t_ref=pb.t_ref,
-                      tau_t=pb.tau_t, t_init=pb.t_ref)
+                      tau_t=pb.tau_t, t_init=pb.t_ref, mrt_s_eps=float(pb.s_eps), mrt_s_q=float(pb.s_q))
     b = axlbm_boundary()
     b.inner = _INNER[pb.inner]
     b.z_lo, b.z_hi = _ZKIND[pb.z_lo], _ZKIND[pb.z_hi]

@@ -48,7 +48,7 @@ bool grid_ok(const axlbm_grid* g, std::string* why) {
         *why = "with_swirl / with_temperature must be 0 or 1";
         return false;
     }
-    if (g->reserved != 0) { *why = "grid.reserved must be 0"; return false; }
+    if (g->collision != AXLBM_BGK && g->collision != AXLBM_MRT) { *why = "unknown collision model"; return false; }
     if (!(g->r0 >= 0.0) || !isfinite(g->r0)) { *why = "r0 must be finite and >= 0"; return false; }
     return true;
 }
@@ -184,6 +184,8 @@ bool validate_problem(const axlbm_grid* grid, double tau, const axlbm_forcing* f
     if (!isfinite(forcing->az0) || !isfinite(forcing->omega_t) || !isfinite(forcing->gbeta) || !isfinite(forcing->t_ref) ||
         !isfinite(forcing->t_init) || !isfinite(bc->r_split))
         return no("forcing values must be finite");
+    if (!(forcing->mrt_s_eps >= 0.0 && forcing->mrt_s_eps < 2.0) || !(forcing->mrt_s_q >= 0.0 && forcing->mrt_s_q < 2.0))
+        return no("MRT rates must lie in (0, 2) (0 selects the default)");
     return true;
 }
 

@@ -439,6 +439,7 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
         x.omega_t = D.forcing.omega_t;
         x.cf = axl::make_coef<float>(D.tau, D.forcing, D.boundary);
         x.cd = axl::make_coef<double>(D.tau, D.forcing, D.boundary);
+        x.cf.mrt = x.cd.mrt = D.grid.collision == AXLBM_MRT;
     }
     const BatchLayout& L = b->L;
     if (st == AXLBM_OK) st = upload(b, L.off_doms, dd.data(), dd.size() * sizeof(axl::DomDesc));

@@ -54,6 +54,7 @@ KArgs<S, R> domain_args(axlbm_batch* b, int d) {
     K.G.col0 = b->col0[d];
     K.G.row0 = b->row0[d];
     K.C = make_coef<R>(D.tau, D.forcing, D.boundary);
+    K.C.mrt = D.grid.collision == AXLBM_MRT;
     K.g_plane = 9;
     K.h_plane = 13;
     K.nframe = 0;

@@ -131,6 +131,7 @@ extern "C" AXLBM_API axlbm_status axlbm_check_static(const axlbm_grid* grid, dou
     C.h1 = taut / (taut + 0.5);
     C.gbeta = forcing->gbeta;
     C.t_ref = forcing->t_ref;
+    C.mrt = 0;  // moments only: the collision model does not enter them
 
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     const int blocks = int((n + kThreads - 1) / kThreads);

@@ -52,6 +52,11 @@ struct Coef {
     R omega_w[4];   // wall angular velocities per face
     R t_w[4];       // wall temperatures per face
     int t_dir[4];   // 1: Dirichlet face
+    // MRT (Sec. III B): rates s_e = s_v, s_eps, s_q and derived factors
+    int mrt;
+    R sv, se, seps, sq;
+    R k_e6;         // s_e / (6 s_v) of Eq. 49
+    R mrt_gam;      // 1 - s_v / 2 (Eq. 49: gamma = mrt_gam / r)
 };
 
 struct Layout {

@@ -117,6 +117,9 @@ struct Cell {
         const R Qp = Q + Cx, Qm = Q - Cx, Bs = Bur + Buz, Bd = Bur - Buz;
         const R P[9] = {A, Ps + Bur, Pz + Buz, Ps - Bur, Pz - Buz, Qp + Bs, Qm - Bd, Qp - Bs, Qm + Bd};
         // source factors F_a
+        if (C.mrt) {
+            collide_mrt(inv_r, C, drho, fr, fz);
+        } else {
         const R fr3 = fr * inv_rho * R(Sc(3)), fz3 = fz * inv_rho * R(Sc(3));
         const R base = fmaR((ur * fr + uz * fz) * R(Sc(-3)), inv_rho, R(Sc(0)) - urr);
         const R F1 = base + fr3, F3 = base - fr3;
@@ -129,6 +132,7 @@ struct Cell {
             const R kwF = F[a] * R((one - half * om) * w);
             const R t = fmaR(kwF, P[a] + R(C.rho0), P[a] * R(om * w));
             d[a] = fmaR(R(one - om), d[a], t);
+        }
         }
         if (SW) {
             // g' = (1 - om_g) g + (om_g + S^g / g^eq) g^eq                 (Eqs. 53-54)
@@ -158,6 +162,87 @@ struct Cell {
                 h[q] = fmaR(R(one - om), h[q], fmaR(R(om) - urr, heq[q], R(-om * tref4)));
             }
         }
+    }
+
+    // MRT collision of f (Sec. III B) on the stored deviations d = f - w rho0,
+    // given the moments (rho, u of Eqs. 16-17 already in the members), drho =
+    // rho - rho0 and the force (fr, fz) of Eq. 12.  Moment basis of Eq. 38
+    // (orthogonal D2Q9: rho, e, eps, j_r, q_r, j_z, q_z, p_rr, p_rz); M w rho0
+    // = rho0 (1, -2, 1, 0, ...).  Eq. 41 with the source -(u_r/r) m^eq + S'
+    // of Eq. 51, the correction of Eqs. 49-50, then M^-1 = M^T diag(1/|row|^2).
+    __device__ __forceinline__ void collide_mrt(Sc inv_r, const Coef<Sc>& C, R drho, R fr, R fz) {
+        const Sc one = Sc(1), half = Sc(0.5);
+        // moments of the deviations
+        const R ax = (d[1] + d[2]) + (d[3] + d[4]);
+        const R dg = (d[5] + d[6]) + (d[7] + d[8]);
+        const R md1 = fmaR(d[0], R(Sc(-4)), (dg + dg) - ax);
+        const R md2 = fmaR(d[0], R(Sc(4)), dg - (ax + ax));
+        const R x13 = d[1] - d[3], x24 = d[2] - d[4];
+        const R dq_r = (d[5] - d[6]) + (d[8] - d[7]);
+        const R dq_z = (d[5] + d[6]) - (d[7] + d[8]);
+        const R md4 = fmaR(x13, R(Sc(-2)), dq_r);
+        const R md6 = fmaR(x24, R(Sc(-2)), dq_z);
+        const R md7 = (d[1] + d[3]) - (d[2] + d[4]);
+        const R md8 = (d[5] + d[7]) - (d[6] + d[8]);
+        // equilibria (Eq. 39) and source (Eq. 51)
+        const R ru = rho * ur, rz = rho * uz;
+        const R u2 = ur * ur + uz * uz;
+        const R r3u2 = rho * u2 * R(Sc(3));
+        const R pxx_eq = rho * (ur * ur - uz * uz), pxy_eq = ru * uz;
+        const R uF = ur * fr + uz * fz;
+        const R mu = R(Sc(0)) - ur * R(inv_r);  // -u_r / r
+        const R e_eq = fmaR(rho, R(Sc(-2)), r3u2), eps_eq = rho - r3u2;
+        const R S0 = mu * rho;
+        const R S1 = fmaR(mu, e_eq, uF * R(Sc(6)));
+        const R S2 = fmaR(mu, eps_eq, uF * R(Sc(-6)));
+        const R S3 = fmaR(mu, ru, fr);
+        const R S4 = (R(Sc(0)) - fr) - mu * ru;
+        const R S5 = fmaR(mu, rz, fz);
+        const R S6 = (R(Sc(0)) - fz) - mu * rz;
+        const R S7 = fmaR(mu, pxx_eq, (ur * fr - uz * fz) * R(Sc(2)));
+        const R S8 = fmaR(mu, pxy_eq, ur * fz + uz * fr);
+        // non-equilibrium parts m - m^eq
+        const R ne1 = md1 + (drho + drho) - r3u2;
+        const R ne2 = (md2 - drho) + r3u2;
+        const R ne4 = md4 + ru;
+        const R ne6 = md6 + rz;
+        const R ne7 = md7 - pxx_eq;
+        const R ne8 = md8 - pxy_eq;
+        // relaxation (Eq. 41); conserved moments with unit rate
+        const R p0 = fmaR(S0, R(half), drho);                                      // rho + S0/2 - rho0
+        const R p1 = fmaR(ne1, R(one - C.se), fmaR(S1, R(one - half * C.se), r3u2 - (drho + drho)));
+        const R p2 = fmaR(ne2, R(one - C.seps), fmaR(S2, R(one - half * C.seps), drho - r3u2));
+        const R p3 = fmaR(S3, R(half), ru);
+        const R p4 = fmaR(ne4, R(one - C.sq), fmaR(S4, R(one - half * C.sq), R(Sc(0)) - ru));
+        const R p5 = fmaR(S5, R(half), rz);
+        const R p6 = fmaR(ne6, R(one - C.sq), fmaR(S6, R(one - half * C.sq), R(Sc(0)) - rz));
+        const R p7 = fmaR(ne7, R(one - C.sv), fmaR(S7, R(one - half * C.sv), pxx_eq));
+        const R p8 = fmaR(ne8, R(one - C.sv), fmaR(S8, R(one - half * C.sv), pxy_eq));
+        // momentum correction (Eqs. 49-50), m^(1) = (m - m^eq) + S/2, gamma = (1 - s_v/2)/r
+        const Sc gam = C.mrt_gam * inv_r;
+        const R e1 = fmaR(S1, R(half), ne1);
+        const R pxx1 = fmaR(S7, R(half), ne7);
+        const R pxy1 = fmaR(S8, R(half), ne8);
+        const R q3 = p3 - R(gam) * fmaR(e1, R(C.k_e6), pxx1 * R(half));
+        const R q5 = fmaR(pxy1, R(-gam), p5);
+        // back to populations: d_a = sum_i M[i][a] p_i / |row i|^2
+        const R a0 = p0 * R(Sc(1.0 / 9.0)), a1 = p1 * R(Sc(1.0 / 36.0)), a2 = p2 * R(Sc(1.0 / 36.0));
+        const R a3 = q3 * R(Sc(1.0 / 6.0)), a4 = p4 * R(Sc(1.0 / 12.0)), a5 = q5 * R(Sc(1.0 / 6.0));
+        const R a6 = p6 * R(Sc(1.0 / 12.0)), a7 = p7 * R(Sc(0.25)), a8 = p8 * R(Sc(0.25));
+        const R c0 = fmaR(a2 - a1, R(Sc(4)), a0);           // rest
+        const R cx = (a0 - a1) - (a2 + a2);                   // axis links, common part
+        const R cd = (a0 + (a1 + a1)) + a2;                   // diagonals, common part
+        const R jr = fmaR(a4, R(Sc(-2)), a3), jz = fmaR(a6, R(Sc(-2)), a5);
+        const R dr = a3 + a4, dz = a5 + a6;
+        d[0] = c0;
+        d[1] = (cx + jr) + a7;
+        d[2] = (cx + jz) - a7;
+        d[3] = (cx - jr) + a7;
+        d[4] = (cx - jz) - a7;
+        d[5] = ((cd + dr) + dz) + a8;
+        d[6] = ((cd - dr) + dz) - a8;
+        d[7] = ((cd - dr) - dz) + a8;
+        d[8] = ((cd + dr) - dz) - a8;
     }
 };
 
@@ -861,7 +946,9 @@ Coef<R> make_coef(double tau_s, const axlbm_forcing& fo, const axlbm_boundary& b
 
 template <class R>
 Coef<R> make_coef(const axlbm_handle* h) {
-    return make_coef<R>(h->tau, h->forcing, h->bc);
+    Coef<R> C = make_coef<R>(h->tau, h->forcing, h->bc);
+    C.mrt = h->grid.collision == AXLBM_MRT;
+    return C;
 }
 
 // Coefficients of Eqs. 13, 16 and 53-54 in the arithmetic type (tau_s is the
@@ -890,6 +977,18 @@ Coef<R> make_coef(double tau_s, const axlbm_forcing& fo, const axlbm_boundary& b
         C.t_w[f] = R(bc.t_wall[f]);
         C.t_dir[f] = bc.t_dirichlet[f];
     }
+    // MRT rates (used when the caller sets C.mrt): s_v from the viscosity,
+    // s_e = s_v, s_eps and s_q given or defaulted
+    const double sv = 1.0 / (tau + 0.5);
+    const double seps = fo.mrt_s_eps > 0.0 ? fo.mrt_s_eps : sv;
+    const double sq = fo.mrt_s_q > 0.0 ? fo.mrt_s_q : 1.0 / (0.5 + 0.25 / (1.0 / sv - 0.5));
+    C.mrt = 0;
+    C.sv = R(sv);
+    C.se = R(sv);
+    C.seps = R(seps);
+    C.sq = R(sq);
+    C.k_e6 = R(1.0 / 6.0);  // s_e / (6 s_v) with s_e = s_v
+    C.mrt_gam = R(1.0 - 0.5 * sv);
     return C;
 }
 

@@ -123,3 +123,69 @@ def test_mrt_womersley_paper_case(orc):
         orc.step(st, 9 * period + n * period // 16 - st.t)
         xis.append(A.xi(orc.moments(st)[2, 0], A.womersley(r, st.t, radius, pb.az0, 1.0, pb.omega_t, mu)))
     assert np.mean(xis) <= 0.005  # paper: 0.33 %
+
+
+def test_mrt_equilibrium_state_is_rate_independent(orc):
+    """A state with no non-equilibrium part, f = M^-1 (m^eq - S/2) (so that the
+    unshifted f of Eq. 37 is at equilibrium), has m^(1) = 0: the correction of
+    Eqs. 49-50 vanishes and Eq. 41 gives M^-1 (m^eq + S/2) for every choice of
+    rates, at any radius."""
+    M = textbook_basis()
+    rng = np.random.default_rng(6)
+    for _ in range(10):
+        tau_s = float(rng.uniform(0.55, 1.2))
+        rho, ur, uz, r = float(rng.uniform(0.95, 1.05)), float(rng.uniform(-0.03, 0.03)), \
+            float(rng.uniform(-0.03, 0.03)), float(rng.uniform(0.5, 10.0))
+        mu0 = (tau_s - 0.5) / 3.0
+        fr, fz = -2.0 * mu0 * ur / r ** 2, 0.0
+        meq = rho * np.array([1, -2 + 3 * (ur ** 2 + uz ** 2), 1 - 3 * (ur ** 2 + uz ** 2), ur, -ur, uz, -uz,
+                              ur ** 2 - uz ** 2, ur * uz])
+        uF = ur * fr + uz * fz
+        S = -(ur / r) * meq + np.array([0, 6 * uF, -6 * uF, fr, -fr, fz, -fz, 2 * (ur * fr - uz * fz),
+                                        ur * fz + uz * fr])
+        f = np.linalg.solve(M, meq - 0.5 * S)
+        want = np.linalg.solve(M, meq + 0.5 * S)
+        for s_eps, s_q in ((1.1, 1.3), (1.6, 0.7), (0.0, 0.0)):
+            pb = I.Problem(nr=4, nz=4, tau=tau_s, collision="mrt", s_eps=s_eps, s_q=s_q)
+            fo, _, _, mom = orc.collide_cell(pb, r, 0.0, f)
+            assert mom[1] == pytest.approx(ur, rel=1e-12, abs=1e-16) and mom[2] == pytest.approx(uz, rel=1e-12, abs=1e-16)
+            assert np.max(np.abs(fo - want)) <= 1e-14
+
+
+def test_mrt_momentum_correction_recovers_the_axisymmetric_viscous_terms(orc):
+    """Chapman-Enskog check of Eqs. 45-50: give a node the first-order
+    non-equilibrium moments of a chosen velocity gradient (Eq. 45), with rho
+    and j consistent with Eqs. 14-15.  One collision must then change the
+    momentum by the source plus exactly the terms the correction exists for:
+    dj_r = S_3 + mu (2 du_r/dr) / r  (Eq. 47),  dj_z = S_5 + mu (du_z/dr + du_r/dz) / r
+    (Eq. 48), mu = (1/s_v - 1/2) rho / 3."""
+    M = textbook_basis()
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        tau_s = float(rng.uniform(0.55, 1.2))
+        sv = 1.0 / tau_s
+        rho, ur, uz = float(rng.uniform(0.97, 1.03)), float(rng.uniform(-0.02, 0.02)), float(rng.uniform(-0.02, 0.02))
+        r = float(rng.uniform(0.5, 8.0))
+        a, b, c, d = rng.uniform(-1e-3, 1e-3, 4)  # du_r/dr, du_z/dz, du_z/dr, du_r/dz
+        mu0 = (tau_s - 0.5) / 3.0
+        fr, fz = -2.0 * mu0 * ur / r ** 2, 0.0
+        u2 = ur ** 2 + uz ** 2
+        meq = rho * np.array([1, -2 + 3 * u2, 1 - 3 * u2, ur, -ur, uz, -uz, ur ** 2 - uz ** 2, ur * uz])
+        uF = ur * fr + uz * fz
+        S = -(ur / r) * meq + np.array([0, 6 * uF, -6 * uF, fr, -fr, fz, -fz, 2 * (ur * fr - uz * fz),
+                                        ur * fz + uz * fr])
+        m1 = np.zeros(9)
+        m1[1] = -2 * rho * (a + b) / sv                 # Eq. 45 with s_e = s_v
+        m1[7] = -(2 * rho / 3) * (a - b) / sv
+        m1[8] = -(rho / 3) * (c + d) / sv
+        m1[2], m1[4], m1[6] = rng.uniform(-1e-4, 1e-4, 3)  # other non-hydrodynamic parts: arbitrary
+        mbar = meq + m1 - 0.5 * S
+        f = np.linalg.solve(M, mbar)
+        pb = I.Problem(nr=4, nz=4, tau=tau_s, collision="mrt", s_eps=1.2, s_q=1.5)
+        fo, _, _, mom = orc.collide_cell(pb, r, 0.0, f)
+        assert mom[1] == pytest.approx(ur, rel=1e-12, abs=1e-16)
+        mu = (1 / sv - 0.5) * rho / 3
+        djr = E9[:, 0] @ (fo - f)
+        djz = E9[:, 1] @ (fo - f)
+        assert djr == pytest.approx(S[3] + mu * 2 * a / r, rel=1e-9, abs=1e-17)
+        assert djz == pytest.approx(S[5] + mu * (c + d) / r, rel=1e-9, abs=1e-17)
