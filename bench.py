@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--shard", choices=["weak", "strong"], default="weak",
+                   help="batch under torchrun: a sweep per rank (weak) or one sweep split over the ranks (strong)")
     return p.parse_args()
 
 
@@ -69,7 +71,7 @@ def peaks():
 def kernel_source_sha():
     import hashlib
     h = hashlib.sha256()
-    for name in ("ops_impl.cuh", "lattice.cuh"):
+    for name in ("ops_impl.cuh", "lattice.cuh", "pair.cuh", "tma.cuh", "batch.cuh", "batch.cu"):
         with open(os.path.join(ROOT, "paper_1003_0282_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -199,6 +201,7 @@ def main():
 
     from paper_1003_0282_gb300 import axlbm as B
     from paper_1003_0282_gb300 import inputs as I
+    from paper_1003_0282_gb300 import shard as S
 
     if args.workload == "pipe":
         pb = I.large_pipe(nr=args.nr, nz=args.nz)
@@ -210,7 +213,7 @@ def main():
         kernel_times = lambda: B.axlbm_kernel_times(solver.handle)
         workload = (f"pipe {pb.nr}x{pb.nz} D2Q9 (Hagen-Poiseuille force, axis + bounce-back wall, periodic z)")
     else:
-        problems = I.batch_sweep(seed=20261202 + rank, scale=args.scale)
+        problems = S.rank_problems(I.batch_sweep, world, rank, args.shard, scale=args.scale)
         solver = B.Batch(problems, args.precision)
         timing_on = lambda on: B.axlbm_batch_kernel_timing(solver.handle, on)
         kernel_times = lambda: B.axlbm_batch_kernel_times(solver.handle)
@@ -245,11 +248,11 @@ def main():
     else:
         rr = solver.residuals()
         res, mass = float(rr[:, 0].max()), float(rr[:, 1].sum())
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    updates = nodes * args.inner * args.steps * world
+    ms = S.max_over_ranks(ms)
+    res = S.max_over_ranks(res)
+    mass = S.sum_over_ranks(mass)
+    all_nodes = int(round(S.sum_over_ranks(nodes)))
+    updates = all_nodes * args.inner * args.steps
     value = updates / (ms / 1e3) / 1e6
 
     # end to end through the C ABI with pinned host buffers: fields in, moments out
@@ -273,11 +276,8 @@ def main():
             B.axlbm_batch_moments_all(solver.handle, B.RHO | B.UR | B.UZ, host_out.data_ptr(), B.F32, 0)
     barrier()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = nodes * args.inner * args.e2e_steps * world / e2e_s / 1e6
+    e2e_s = S.max_over_ranks(e2e_s)
+    e2e_value = all_nodes * args.inner * args.e2e_steps / e2e_s / 1e6
     solver.close()
 
     if rank == 0:
@@ -292,18 +292,21 @@ def main():
         kernel = "k_bulk (even + odd AA steps)" if args.workload == "pipe" else "k_bulk_batch (even + odd AA steps)"
         line = {
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": args.shard if (world > 1 and args.workload == "batch") else "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-            "config": {"workload": workload, "precision": args.precision, "nodes": nodes,
+            "config": {"workload": workload, "precision": args.precision, "nodes": all_nodes,
                        "domains": len(problems), "lattice_steps_per_step": args.inner,
-                       "cache": "inputs larger than L2 (no flush)", "parallelism": f"independent replicas x{world}"},
+                       "cache": "inputs larger than L2 (no flush)",
+                       "parallelism": (f"independent domains on {world} ranks ({args.shard})" if world > 1
+                                       else "one GPU")},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": kernel, "launches": bulk_n,
                          "avg_launch_ms": bulk_ms / max(bulk_n, 1),
                          "alg_bytes_per_launch": bulk_bytes / max(bulk_n, 1)},
             "e2e": {"value": e2e_value, "unit": "MLUPS",
-                    "h2d_bytes_per_step": 5 * 4 * nodes, "d2h_bytes_per_step": 3 * 4 * nodes},
+                    "h2d_bytes_per_step": 5 * 4 * all_nodes, "d2h_bytes_per_step": 3 * 4 * all_nodes},
             "gpu_launches": all_launches,
             "clocks": clk.summary(),
             "check": {"residual": res, "mass": mass},

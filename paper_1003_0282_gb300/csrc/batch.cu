@@ -1,12 +1,16 @@
 // batch.cu -- host side of the batch C ABI (include/axlbm.h, "batches").
 //
-// Packing: domains are sorted by height and placed left to right in shelves
-// of a common-pitch array (columns aligned to 32 elements), so one TMA
-// descriptor covers every domain and a tile never spans two domains.
-// Tiles (bulk kernel) are listed row-major over that array, so concurrently
-// running CTAs sweep neighbouring domains' rows together (shared rows of the
-// TMA boxes then hit L2).  Tile shape: the candidates are timed on the batch
-// at creation and the fastest kept (cached per GPU, precision, mix).
+// Packing: domains are sorted by temperature flag and height and placed left
+// to right in shelves of a common-pitch array, side by side without gaps,
+// each shelf starting on a row that is a multiple of kRowAlign, so one TMA
+// descriptor covers every domain.  The bulk tiles form a regular grid over
+// the occupied part of the array: a tile may straddle several domains of a
+// shelf (up to kSlots: every domain is given at least kMinCols columns), so
+// only the shelves' ragged ends are loaded without being updated.  Tiles are
+// listed row-major, so concurrently running CTAs sweep neighbouring rows
+// together (shared rows of the TMA boxes then hit L2).  Tile shape: the
+// candidates are timed on the batch at creation and the fastest kept (cached
+// per GPU, precision, mix).
 #include <math.h>
 #include <string.h>
 
@@ -46,12 +50,17 @@ axlbm_status bcuda(axlbm_batch* b, cudaError_t e, const char* where) {
     return bfail(b, AXLBM_ECUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
 }
 
+// Narrowest column span a domain is given: a window of the widest tile
+// then meets at most kSlots domains.
+constexpr int kMaxTJ = 128;
+constexpr int kMinCols = (kMaxTJ - 1) / (axl::kSlots - 1) + 1;
+
 // Shelf packing and every offset of the device layout.  col0/row0 receive each
 // domain's position; tiles[s] the tile lists per candidate shape.
 struct Plan {
     BatchLayout L;
     std::vector<int> col0, row0;
-    std::vector<int> tiles[axl::kBatchShapes];      // 4 ints per tile
+    std::vector<axl::TileRec> tiles[axl::kBatchShapes];
     std::vector<int> tstart[axl::kBatchShapes], tindex[axl::kBatchShapes];
     std::vector<int> ring, rstart;                  // 2 ints per ring node
     int thmax;
@@ -71,59 +80,101 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
         if ((long long)dom[d].grid.nr * dom[d].grid.nz > (1ll << 28)) { *why = "domain too large for a batch"; return false; }
         P->thmax |= dom[d].grid.with_temperature;
     }
+    for (int s = 0; s < axl::kBatchShapes; ++s)
+        if (axl::kShapeTJ[s] > kMaxTJ || axl::kShapeTK[s] > axl::kRowAlign || axl::kRowAlign % axl::kShapeTK[s]) {
+            *why = "internal: tile shape table";
+            return false;
+        }
     BatchLayout& L = P->L;
     L.elem = precision == AXLBM_FP32 ? 4 : 2;
     L.nplanes = P->thmax ? 17 : 13;
-    // shelf packing, tallest first
+    auto span = [&](int d) { return std::max(dom[d].grid.nr, kMinCols); };
+    auto up = [](long long v, long long a) { return (v + a - 1) / a * a; };
+    // shelves: domains without temperature first, tallest first
     std::vector<int> order(n);
     long long area = 0;
     int maxw = 0;
     for (int d = 0; d < n; ++d) {
         order[d] = d;
-        const int w = (dom[d].grid.nr + 31) / 32 * 32;
-        area += (long long)w * dom[d].grid.nz;
-        maxw = std::max(maxw, w);
+        area += (long long)span(d) * dom[d].grid.nz;
+        maxw = std::max(maxw, span(d));
     }
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dom[a].grid.nz > dom[b].grid.nz; });
-    long long width = (long long)(sqrt((double)area) * 1.1);
-    width = (width + 31) / 32 * 32;
-    if (width < maxw) width = maxw;
-    if (width > 16384) width = std::max<long long>(16384, maxw);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (dom[a].grid.with_temperature != dom[b].grid.with_temperature)
+            return dom[a].grid.with_temperature < dom[b].grid.with_temperature;
+        return dom[a].grid.nz > dom[b].grid.nz;
+    });
+    long long width = up((long long)(sqrt((double)area) * 1.1), kMaxTJ);
+    width = std::max<long long>(width, up(maxw, kMaxTJ));
+    if (width > 16384) width = std::max<long long>(16384, up(maxw, kMaxTJ));
     P->col0.assign(n, 0);
     P->row0.assign(n, 0);
-    long long row = 0, col = 0, shelf_h = 0;
-    for (int d : order) {
-        const int w = (dom[d].grid.nr + 31) / 32 * 32;
-        if (col + w > width) {
-            row += shelf_h;
-            col = 0;
-            shelf_h = 0;
+    struct Shelf { long long row, height; int first, last; };  // order[first .. last)
+    std::vector<Shelf> shelves;
+    {
+        long long row = 0, col = 0, sh = 0;
+        int first = 0, prev_th = -1;
+        for (int i = 0; i < n; ++i) {
+            const int d = order[i];
+            const int th = dom[d].grid.with_temperature;
+            if (i > first && (col + span(d) > width || th != prev_th)) {
+                shelves.push_back({row, up(sh, axl::kRowAlign), first, i});
+                row += up(sh, axl::kRowAlign);
+                col = 0;
+                sh = 0;
+                first = i;
+            }
+            P->col0[d] = (int)col;
+            P->row0[d] = (int)row;
+            col += span(d);
+            sh = std::max<long long>(sh, dom[d].grid.nz);
+            prev_th = th;
         }
-        P->col0[d] = (int)col;
-        P->row0[d] = (int)row;
-        col += w;
-        shelf_h = std::max<long long>(shelf_h, dom[d].grid.nz);
+        shelves.push_back({row, up(sh, axl::kRowAlign), first, n});
+        L.rows = row + up(sh, axl::kRowAlign);
     }
-    L.rows = row + shelf_h;
     L.pitch = width;
     L.plane = L.pitch * L.rows;
     if (L.rows > (1ll << 30) || L.pitch * L.rows * L.nplanes > (1ll << 38)) { *why = "batch too large"; return false; }
-    // tiles per candidate shape, row-major over the array
+    // tiles per candidate shape: the grid cells of each shelf's row bands that
+    // hold at least one node, row-major; (tile, slot) entries per domain
     for (int s = 0; s < axl::kBatchShapes; ++s) {
         const int TK = axl::kShapeTK[s], TJ = axl::kShapeTJ[s];
-        struct T { int d, j0, k0; };
-        std::vector<T> list;
-        for (int d = 0; d < n; ++d)
-            for (int k = 0; k < dom[d].grid.nz; k += TK)
-                for (int j = 0; j < dom[d].grid.nr; j += TJ) list.push_back({d, P->col0[d] + j, P->row0[d] + k});
-        std::stable_sort(list.begin(), list.end(), [](const T& a, const T& b) {
-            return a.k0 != b.k0 ? a.k0 < b.k0 : a.j0 < b.j0;
-        });
-        P->tiles[s].clear();
+        std::vector<axl::TileRec>& T = P->tiles[s];
+        T.clear();
         std::vector<std::vector<int>> per(n);
-        for (size_t i = 0; i < list.size(); ++i) {
-            P->tiles[s].insert(P->tiles[s].end(), {list[i].d, list[i].j0, list[i].k0, 0});
-            per[list[i].d].push_back((int)i);
+        for (const Shelf& sf : shelves) {
+            const int th = dom[order[sf.first]].grid.with_temperature;
+            for (long long k0 = sf.row; k0 < sf.row + sf.height; k0 += TK) {
+                int lo = sf.first;  // first domain of the shelf not left of the window
+                for (long long j0 = 0; j0 < width; j0 += TJ) {
+                    while (lo < sf.last && P->col0[order[lo]] + span(order[lo]) <= j0) ++lo;
+                    axl::TileRec r;
+                    memset(&r, 0, sizeof r);
+                    r.k0 = (int)k0;
+                    r.j0 = (int)j0;
+                    r.th = th;
+                    bool live = false;
+                    int q = 0;
+                    for (int i = lo; i < sf.last && P->col0[order[i]] < j0 + TJ; ++i, ++q) {
+                        const int d = order[i];
+                        if (q == axl::kSlots) {
+                            *why = "internal: a tile meets more than kSlots domains";
+                            return false;
+                        }
+                        r.start[q] = (int)std::max<long long>(P->col0[d] - j0, 0);
+                        r.dom[q] = d;
+                        const bool rows = k0 < P->row0[d] + dom[d].grid.nz;
+                        const bool cols = P->col0[d] + dom[d].grid.nr > j0;
+                        if (rows && cols) {
+                            live = true;
+                            per[d].push_back((int)T.size() * axl::kSlots + q);
+                        }
+                    }
+                    r.nseg = q;
+                    if (live) T.push_back(r);
+                }
+            }
         }
         P->tstart[s].assign(1, 0);
         P->tindex[s].clear();
@@ -131,7 +182,9 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
             P->tindex[s].insert(P->tindex[s].end(), per[d].begin(), per[d].end());
             P->tstart[s].push_back((int)P->tindex[s].size());
         }
-        L.shape[s].ntiles = (int)list.size();
+        L.shape[s].ntiles = (int)T.size();
+        L.shape[s].nentries = (int)P->tindex[s].size();
+        if (T.empty()) { *why = "internal: no tiles"; return false; }
     }
     // outer rings, domain by domain
     P->ring.clear();
@@ -150,7 +203,7 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
     L.off_speed = off;
     off += al((size_t)L.plane * 4);
     L.off_tilepart = off;
-    off += al((size_t)maxtiles * 32);
+    off += al((size_t)maxtiles * axl::kSlots * 32);
     L.off_ringpart = off;
     off += al((size_t)L.nring * 32);
     L.off_result = off;
@@ -161,17 +214,19 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
     off += 256;
     L.off_doms = off;
     off += al((size_t)n * sizeof(axl::DomDesc));
+    L.off_slots = off;
+    off += al((size_t)n * sizeof(axl::SlotDesc));
     L.off_ring = off;
     off += al((size_t)L.nring * 8);
     L.off_rstart = off;
     off += al((size_t)(n + 1) * 4);
     for (int s = 0; s < axl::kBatchShapes; ++s) {
         L.shape[s].off_tiles = off;
-        off += al((size_t)L.shape[s].ntiles * 16);
+        off += al((size_t)L.shape[s].ntiles * sizeof(axl::TileRec));
         L.shape[s].off_tstart = off;
         off += al((size_t)(n + 1) * 4);
         L.shape[s].off_tindex = off;
-        off += al((size_t)L.shape[s].ntiles * 4);
+        off += al((size_t)L.shape[s].nentries * 4);
     }
     L.total = off;
     return true;
@@ -420,6 +475,7 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
     axlbm_status st = AXLBM_OK;
     // descriptors and lists
     std::vector<axl::DomDesc> dd(n);
+    std::vector<axl::SlotDesc> sd(n);
     for (int d = 0; d < n; ++d) {
         const axlbm_domain& D = domains[d];
         axl::DomDesc& x = dd[d];
@@ -440,13 +496,24 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
         x.cf = axl::make_coef<float>(D.tau, D.forcing, D.boundary);
         x.cd = axl::make_coef<double>(D.tau, D.forcing, D.boundary);
         x.cf.mrt = x.cd.mrt = D.grid.collision == AXLBM_MRT;
+        axl::SlotDesc& y = sd[d];
+        memset(&y, 0, sizeof y);
+        y.nr = x.nr;
+        y.nz = x.nz;
+        y.col0 = x.col0;
+        y.row0 = x.row0;
+        y.temperature = x.temperature;
+        y.r0 = x.r0;
+        y.rho0 = D.forcing.rho0;
+        y.c = x.cf;
     }
     const BatchLayout& L = b->L;
     if (st == AXLBM_OK) st = upload(b, L.off_doms, dd.data(), dd.size() * sizeof(axl::DomDesc));
+    if (st == AXLBM_OK) st = upload(b, L.off_slots, sd.data(), sd.size() * sizeof(axl::SlotDesc));
     if (st == AXLBM_OK) st = upload(b, L.off_ring, P.ring.data(), P.ring.size() * sizeof(int));
     if (st == AXLBM_OK) st = upload(b, L.off_rstart, P.rstart.data(), P.rstart.size() * sizeof(int));
     for (int s = 0; s < axl::kBatchShapes && st == AXLBM_OK; ++s) {
-        st = upload(b, L.shape[s].off_tiles, P.tiles[s].data(), P.tiles[s].size() * sizeof(int));
+        st = upload(b, L.shape[s].off_tiles, P.tiles[s].data(), P.tiles[s].size() * sizeof(axl::TileRec));
         if (st == AXLBM_OK) st = upload(b, L.shape[s].off_tstart, P.tstart[s].data(), P.tstart[s].size() * sizeof(int));
         if (st == AXLBM_OK) st = upload(b, L.shape[s].off_tindex, P.tindex[s].data(), P.tindex[s].size() * sizeof(int));
         if (st == AXLBM_OK) {

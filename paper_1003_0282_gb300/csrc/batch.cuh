@@ -1,22 +1,26 @@
 // batch.cuh -- kernels of the batched solver: many uneven domains advanced by
 // one persistent launch per step.
 //
-// The domains are packed side by side into one pitched array (the atlas):
+// The domains are packed into one pitched array (the atlas) in shelves:
 // domain d occupies columns [col0, col0 + nr) of rows [row0, row0 + nz) of
-// every population plane.  A tile list (domain, first column, first row)
-// covers every domain; the persistent bulk kernel walks it with the same TMA
-// pipeline as the single-domain kernel, reading each tile's domain
-// descriptor (geometry, boundary kinds, coefficients).  Domains never write
-// outside their own rectangle: even steps write the node's own slots, odd
-// steps move interior populations inside the domain, and the ring kernel
-// folds every boundary rule back into the domain.
+// every population plane; the domains of a shelf sit side by side without
+// gaps and every shelf starts on a row that is a multiple of kRowAlign.  The
+// bulk tiles are a regular grid over the atlas, so a tile may straddle up to
+// kSlots domains of one shelf (each lane finds its domain by its column).
+// Domains never write outside their own rectangle: even steps write the
+// node's own slots, odd steps move interior populations inside the domain,
+// and the ring kernels fold every boundary rule back into the domain.
 #pragma once
 
 #include "ops_impl.cuh"
 
 namespace axl {
 
-// Per-domain description the kernels read (coefficients in both arithmetic types).
+constexpr int kSlots = 4;     // domains a tile may meet
+constexpr int kRowAlign = 8;  // shelf rows start on multiples of this (>= every tile height)
+
+// Per-domain description the ring and per-domain kernels read (coefficients
+// in both arithmetic types).
 struct DomDesc {
     int nr, nz, col0, row0;
     int inner, z_lo, z_hi, swirl;
@@ -25,6 +29,34 @@ struct DomDesc {
     double az0, omega_t;
     Coef<float> cf;
     Coef<double> cd;
+};
+
+// What the bulk kernel reads of a domain; one copy per tile slot is staged in
+// shared memory by a bulk copy next to the tile's data (16-byte multiple).
+struct __align__(16) SlotDesc {
+    int nr, nz, col0, row0;
+    int temperature, pad0, pad1, pad2;
+    double r0, rho0;
+    CoefCore<float> c;
+};
+static_assert(sizeof(SlotDesc) % 16 == 0, "bulk copies move 16-byte multiples");
+
+// One bulk tile: rows [k0, k0 + TK) and columns [j0, j0 + TJ) of the atlas;
+// slot q covers tile columns [start[q], start[q + 1]) and belongs to domain
+// dom[q] (slots in column order, start[0] = 0).  th: the tile's shelf holds
+// domains with temperature.
+struct TileRec {
+    int k0, j0, nseg, th;
+    int start[kSlots];
+    int dom[kSlots];
+};
+static_assert(sizeof(TileRec) == 48, "tile records are three 16-byte words");
+
+// The tile record plus each slot's force a(t), as the producer leaves them in
+// shared memory for the consumers.
+struct TileMeta {
+    TileRec r;
+    float az[kSlots];
 };
 
 template <class R>
@@ -55,51 +87,87 @@ struct BatchArgs {
     S* pop;
     long long pitch, plane;  // atlas row pitch and plane size (elements)
     const DomDesc* doms;
+    const SlotDesc* slots;   // [ndom]
     int ndom;
-    const int4* tiles;       // {domain, first column, first row, 0}, atlas coordinates
+    const TileRec* tiles;
     int ntiles;
     const int2* ring;        // {domain, index in the domain's outer ring}
     int nring;
     double* dom_az;          // [ndom][2]: a(t) of each domain by AA parity
     Clock* clock;            // time level and error word
     R* speed;                // |u| plane, atlas-shaped
-    double* tile_part;       // [ntiles][4] check partials
+    double* tile_part;       // [ntiles][kSlots][4] check partials per tile slot
     double* ring_part;       // [nring][4] check values of ring nodes
     int residual;
 };
 
-// Block-wide (consumer warps only) reduction of one tile's check values into
-// out[4]; uses named barrier 1 over kBulkThreads threads.
+// Global -> shared bulk copy completing on an mbarrier (16-byte aligned
+// addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Per-slot reduction of one tile's check values (consumer warps only).  The
+// lanes of one slot form a contiguous run of each warp (slots are column
+// ranges), so a segmented scan leaves each run's total in its last lane; the
+// runs' totals are summed over the warps in a fixed order.  Uses named
+// barrier 1 over kBulkThreads threads.
 template <class R>
-__device__ __forceinline__ void consumer_reduce_store(RedR<R> v, double rho0, double* out, double (*sh)[kBulkThreads / 32]) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        v.rmax = max(v.rmax, __shfl_down_sync(0xffffffffu, v.rmax, off));
-        v.dmass += __shfl_down_sync(0xffffffffu, v.dmass, off);
-        v.budget += __shfl_down_sync(0xffffffffu, v.budget, off);
-        v.bad += __shfl_down_sync(0xffffffffu, v.bad, off);
-        v.count += __shfl_down_sync(0xffffffffu, v.count, off);
-    }
+__device__ __forceinline__ void slot_reduce_store(RedR<R> v, int q, const TileRec& tr, const SlotDesc* sl,
+                                                  double* out, double (*sh)[4][kBulkThreads / 32]) {
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        sh[0][warp] = (double)v.rmax;
-        sh[1][warp] = (double)v.count * rho0 + (double)v.dmass;
-        sh[2][warp] = (double)v.budget;
-        sh[3][warp] = (double)v.bad;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const R rm = __shfl_up_sync(full, v.rmax, off);
+        const R dm = __shfl_up_sync(full, v.dmass, off);
+        const R bu = __shfl_up_sync(full, v.budget, off);
+        const int bd = __shfl_up_sync(full, v.bad, off);
+        const int ct = __shfl_up_sync(full, v.count, off);
+        const int qo = __shfl_up_sync(full, q, off);
+        if (lane >= off && qo == q) {
+            v.rmax = max(v.rmax, rm);
+            v.dmass += dm;
+            v.budget += bu;
+            v.bad += bd;
+            v.count += ct;
+        }
+    }
+    const int qn = __shfl_down_sync(full, q, 1);
+#pragma unroll
+    for (int u = 0; u < kSlots; ++u) {
+        const unsigned m = __ballot_sync(full, q == u);
+        if (lane == u && m == 0u) {
+            sh[u][0][warp] = 0.0;
+            sh[u][1][warp] = 0.0;
+            sh[u][2][warp] = 0.0;
+            sh[u][3][warp] = 0.0;
+        }
+    }
+    if (lane == 31 || qn != q) {
+        sh[q][0][warp] = (double)v.rmax;
+        sh[q][1][warp] = (double)v.count * sl[q].rho0 + (double)v.dmass;
+        sh[q][2][warp] = (double)v.budget;
+        sh[q][3][warp] = (double)v.bad;
     }
     asm volatile("bar.sync 1, %0;" ::"r"(kBulkThreads) : "memory");
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < tr.nseg) {
+        const int u = threadIdx.x;
         double r[4] = {0.0, 0.0, 0.0, 0.0};
         for (int w = 0; w < kBulkThreads / 32; ++w) {
-            r[0] = fmax(r[0], sh[0][w]);
-            r[1] += sh[1][w];
-            r[2] += sh[2][w];
-            r[3] += sh[3][w];
+            r[0] = fmax(r[0], sh[u][0][w]);
+            r[1] += sh[u][1][w];
+            r[2] += sh[u][2][w];
+            r[3] += sh[u][3][w];
         }
-        out[0] = r[0];
-        out[1] = r[1];
-        out[2] = r[2];
-        out[3] = r[3];
+        out[4 * u + 0] = r[0];
+        out[4 * u + 1] = r[1];
+        out[4 * u + 2] = r[2];
+        out[4 * u + 3] = r[3];
     }
     asm volatile("bar.sync 1, %0;" ::"r"(kBulkThreads) : "memory");
 }
@@ -118,41 +186,52 @@ __host__ __device__ constexpr int batch_nstages() {
     return 3 * batch_stage_elems<S, SW, TH, TK, TJ>() * (int)sizeof(S) <= 200 * 1024 ? 3 : 2;
 }
 
+// Dynamic shared memory: the stages (128-byte aligned), then the slot
+// descriptors and the tile records of every stage.
+template <class S, bool SW, bool TH, int TK, int TJ>
+__host__ __device__ constexpr size_t batch_stage_bytes() {
+    return (size_t)batch_nstages<S, SW, TH, TK, TJ>() * batch_stage_elems<S, SW, TH, TK, TJ>() * sizeof(S);
+}
 template <class S, bool SW, bool TH, int TK, int TJ>
 __host__ __device__ constexpr size_t batch_smem_bytes() {
-    return (size_t)batch_nstages<S, SW, TH, TK, TJ>() * batch_stage_elems<S, SW, TH, TK, TJ>() * sizeof(S) + 128;
+    return batch_stage_bytes<S, SW, TH, TK, TJ>() +
+           (size_t)batch_nstages<S, SW, TH, TK, TJ>() * (kSlots * sizeof(SlotDesc) + sizeof(TileMeta)) + 128;
 }
 
-// Issue the boxes of the planes a tile's domain uses (f, g, then h if it has
-// temperature) into a stage.
+// Issue the boxes of the planes the tile's shelf uses (f, g, then h if it
+// has temperature) into a stage.
 template <class S, bool SW, bool TH, int PAR, int TK, int TJ>
-__device__ __forceinline__ void batch_issue(const CUtensorMap* map, S* dst, uint64_t* bar, int4 t, bool dom_th) {
+__device__ __forceinline__ void batch_issue(const CUtensorMap* map, S* dst, uint64_t* bar, int j0, int k0, bool th) {
     constexpr int BW = batch_box_w<S, TK, TJ>(), HB = 16 / (int)sizeof(S);
-    const int P = 9 + (SW ? 4 : 0) + ((TH && dom_th) ? 4 : 0);
-    mbar_arrive_expect_tx(bar, (uint32_t)(P * TK * BW * sizeof(S)));
+    const int P = 9 + (SW ? 4 : 0) + ((TH && th) ? 4 : 0);
     for (int p = 0; p < P; ++p) {
         const int dy = PAR ? plane_cz<SW>(p) : 0;
-        tma_load_3d(dst + p * TK * BW, map, bar, t.y - HB, t.z + dy, p);
+        tma_load_3d(dst + p * TK * BW, map, bar, j0 - HB, k0 + dy, p);
     }
+}
+
+template <class S, bool SW, bool TH, int TK, int TJ>
+__device__ __forceinline__ uint32_t batch_tile_bytes(bool th) {
+    constexpr int BW = batch_box_w<S, TK, TJ>();
+    const int P = 9 + (SW ? 4 : 0) + ((TH && th) ? 4 : 0);
+    return (uint32_t)(P * TK * BW * sizeof(S));
 }
 
 // Update one node pair (or one node) of a tile from its stage.
 template <class S, class R, class RC, bool SW, bool THD, int PAR, bool CHK, int TK, int TJ>
-__device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const DomDesc& D, const Coef<R>& C, const S* st,
-                                            int4 t, int jj, int rr, R inv_r, R az, const R* sp_old,
-                                            RedR<R>& red) {
+__device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const SlotDesc& D, const S* st, int k0, int j0,
+                                            int jj, int rr, R inv_r, R az, const R* sp_old, RedR<R>& red) {
     constexpr int NL = Lanes<RC>::n;
     constexpr int BW = batch_box_w<S, TK, TJ>(), HB = 16 / (int)sizeof(S);
     constexpr int HP = SW ? 13 : 9;
-    const int jl = t.y - D.col0 + jj;  // local column
+    const int jl = j0 + jj - D.col0;  // local column (>= 0: the slot starts at or before this column)
     bool act[NL];
-    int kl[NL];
     bool any = false;
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-        kl[l] = t.z - D.row0 + rr + l * (TK / NL);
-        act[l] = jl < D.nr && kl[l] < D.nz;
-        if (PAR == 1) act[l] = act[l] && jl > 0 && jl < D.nr - 1 && kl[l] > 0 && kl[l] < D.nz - 1;
+        const int kl = k0 - D.row0 + rr + l * (TK / NL);
+        act[l] = jl < D.nr && kl < D.nz;
+        if (PAR == 1) act[l] = act[l] && jl > 0 && jl < D.nr - 1 && kl > 0 && kl < D.nz - 1;
         any = any || act[l];
     }
     if (!any) return;
@@ -178,12 +257,12 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const DomD
             c.h[q] = Lanes<RC>::template load<S>(row + (HP + p) * TK * BW + (PAR ? cr4(p) : 0), LROW);
         }
     }
-    c.collide(inv_r, C, az);
+    c.collide(inv_r, D.c, az);
     const long long pl = A.plane;
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
         if (!act[l]) continue;
-        const long long x = (long long)(t.z + rr + l * (TK / NL)) * A.pitch + (t.y + jj);
+        const long long x = (long long)(k0 + rr + l * (TK / NL)) * A.pitch + (j0 + jj);
         if (PAR == 0) {
 #pragma unroll
             for (int a = 0; a < 9; ++a) Codec<S>::store(A.pop + opp9(a) * pl + x, Lanes<RC>::get(c.d[a], l));
@@ -224,21 +303,29 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const DomD
 }
 
 // Persistent, warp-specialised bulk update of every domain of the batch
-// (even step: every node; odd step: interior nodes).  SW: every domain
-// carries g; TH: domains may carry h (per-domain flag).
+// (even step: every node; odd step: interior nodes).  The producer lane
+// stages, per tile, the population boxes (TMA), each slot's domain
+// descriptor (bulk copy) and the tile record with the slots' a(t) (plain
+// shared stores), all completing on the stage's full barrier.  SW: every
+// domain carries g; TH: shelves may carry h (per-tile flag).
 template <class S, class R, bool SW, bool TH, int PAR, bool CHK, int TK, int TJ>
 __global__ void __launch_bounds__(kBulkThreads + 32, 2)
 k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
     constexpr int NS = batch_nstages<S, SW, TH, TK, TJ>();
     constexpr int STAGE = batch_stage_elems<S, SW, TH, TK, TJ>();
     using RC = typename std::conditional<std::is_same<R, float>::value, F2, R>::type;
+    static_assert(std::is_same<R, float>::value, "batch arithmetic is FP32");
     static_assert(TK * TJ == 2 * kBulkThreads, "two nodes of one column per consumer thread");
+    static_assert(TK <= kRowAlign && kRowAlign % TK == 0, "a tile row band stays inside one shelf");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    S* sm = reinterpret_cast<S*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    S* sm = reinterpret_cast<S*>(base);
+    SlotDesc* slots = reinterpret_cast<SlotDesc*>(base + batch_stage_bytes<S, SW, TH, TK, TJ>());
+    TileMeta* meta = reinterpret_cast<TileMeta*>(slots + NS * kSlots);
     __shared__ __align__(8) uint64_t full[NS];
     __shared__ __align__(8) uint64_t empty[NS];
     __shared__ volatile int abort_flag;
-    __shared__ double red_sh[4][kBulkThreads / 32];
+    __shared__ double red_sh[kSlots][4][kBulkThreads / 32];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = A.ntiles;
@@ -265,8 +352,32 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
                     break;
                 }
                 if (abort_flag) break;
-                const int4 t = A.tiles[batch_tile_at<PAR>(i, ntiles)];
-                batch_issue<S, SW, TH, PAR, TK, TJ>(&map, sm + s * STAGE, &full[s], t, A.doms[t.x].temperature != 0);
+                const int4* src = reinterpret_cast<const int4*>(A.tiles + batch_tile_at<PAR>(i, ntiles));
+                const int4 w0 = src[0], w1 = src[1], w2 = src[2];
+                TileMeta& M = meta[s];
+                M.r.k0 = w0.x;
+                M.r.j0 = w0.y;
+                M.r.nseg = w0.z;
+                M.r.th = w0.w;
+                M.r.start[0] = w1.x;
+                M.r.start[1] = w1.y;
+                M.r.start[2] = w1.z;
+                M.r.start[3] = w1.w;
+                M.r.dom[0] = w2.x;
+                M.r.dom[1] = w2.y;
+                M.r.dom[2] = w2.z;
+                M.r.dom[3] = w2.w;
+                const int dom[kSlots] = {w2.x, w2.y, w2.z, w2.w};
+#pragma unroll
+                for (int q = 0; q < kSlots; ++q)
+                    if (q < w0.z) M.az[q] = (float)A.dom_az[2 * dom[q] + PAR];
+                // the plain stores above are released by the arrive below
+                mbar_arrive_expect_tx(&full[s], batch_tile_bytes<S, SW, TH, TK, TJ>(w0.w != 0) +
+                                                    (uint32_t)(w0.z * sizeof(SlotDesc)));
+#pragma unroll
+                for (int q = 0; q < kSlots; ++q)
+                    if (q < w0.z) bulk_copy_g2s(&slots[s * kSlots + q], A.slots + dom[q], sizeof(SlotDesc), &full[s]);
+                batch_issue<S, SW, TH, PAR, TK, TJ>(&map, sm + s * STAGE, &full[s], w0.y, w0.x, w0.w != 0);
                 last_par[s] = (it / NS) & 1;
             }
             if (abort_flag) {
@@ -281,18 +392,6 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
         for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++it) {
             const int s = it % NS;
             const int tile = batch_tile_at<PAR>(i, ntiles);
-            const int4 t = A.tiles[tile];
-            const DomDesc& D = A.doms[t.x];
-            R sp_old[2];
-            if (CHK) {
-#pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    const int jl = t.y - D.col0 + jj, kl = t.z - D.row0 + rr0 + m * (TK / 2);
-                    sp_old[m] = (A.residual && jl < D.nr && kl < D.nz)
-                                    ? A.speed[(long long)(t.z + rr0 + m * (TK / 2)) * A.pitch + t.y + jj]
-                                    : R(0);
-                }
-            }
             bool fail = !mbar_wait_bounded(&full[s], (uint32_t)((it / NS) & 1), kWaitCycles) || abort_flag;
             // check steps synchronise the consumers per tile: decide together
             if (CHK) fail = bar_red_or(1, kBulkThreads, fail);
@@ -300,20 +399,34 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
                 abort_flag = 1;
                 break;
             }
+            const TileMeta& M = meta[s];
+            const int k0 = M.r.k0, j0 = M.r.j0, nseg = M.r.nseg;
+            int q = 0;
+#pragma unroll
+            for (int u = 1; u < kSlots; ++u) q += (u < nseg && jj >= M.r.start[u]) ? 1 : 0;
+            const SlotDesc& D = slots[s * kSlots + q];
+            const R az = R(M.az[q]);
+            const int jl = j0 + jj - D.col0;
+            const R inv_r = rcp(R(D.r0 + (double)jl + 0.5));
+            R sp_old[2] = {R(0), R(0)};
+            if (CHK && A.residual) {
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const int kl = k0 - D.row0 + rr0 + m * (TK / 2);
+                    if (jl < D.nr && kl < D.nz) sp_old[m] = A.speed[(long long)(k0 + rr0 + m * (TK / 2)) * A.pitch + j0 + jj];
+                }
+            }
             const S* st = sm + s * STAGE;
-            const Coef<R>& C = dom_coef<R>(D);
-            const R inv_r = rcp(R(D.r0 + (double)(t.y - D.col0 + jj) + 0.5));
-            const R az = R(A.dom_az[2 * t.x + PAR]);
             RedR<R> red{R(0), R(0), R(0), 0, 0};
-            const bool dth = TH && D.temperature;
+            const bool dth = TH && M.r.th;
 #pragma unroll
             for (int rr = rr0; rr < TK / Lanes<RC>::n; rr += kBulkThreads / TJ) {
-                if (dth) batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ>(A, D, C, st, t, jj, rr, inv_r, az, sp_old, red);
-                else batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ>(A, D, C, st, t, jj, rr, inv_r, az, sp_old, red);
+                if (dth) batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ>(A, D, st, k0, j0, jj, rr, inv_r, az, sp_old, red);
+                else batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ>(A, D, st, k0, j0, jj, rr, inv_r, az, sp_old, red);
             }
+            if (CHK) slot_reduce_store(red, q, M.r, slots + s * kSlots, A.tile_part + 4ll * kSlots * tile, red_sh);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
-            if (CHK) consumer_reduce_store(red, (double)D.cd.rho0, A.tile_part + 4ll * tile, red_sh);
         }
     }
     __syncthreads();
@@ -331,56 +444,43 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
     }
 }
 
-// Odd-step update of every domain's outer ring (boundary rules), one node per thread.
-template <class S, class R, bool SW, bool TH, bool CHK>
-__global__ void __launch_bounds__(kThreads) k_ring_batch(const BatchArgs<S, R> A) {
+// Odd-step update of the outer rings (boundary rules), one node per thread,
+// for the domains whose temperature flag equals THD; the other entries are
+// left to the launch of the other class.  Keeping one cell type per kernel
+// makes each class's arithmetic the same instruction sequence as the
+// single-domain ring kernel.  The launch with `advance` set moves every
+// domain's force and the time level to the next step.
+template <class S, class R, bool SW, bool THD, bool CHK>
+__global__ void __launch_bounds__(kThreads) k_ring_batch(const BatchArgs<S, R> A, int advance) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < A.nring) {
         const int2 e = A.ring[i];
         const DomDesc& D = A.doms[e.x];
-        KArgs<S, R> K;
-        K.pop = A.pop;
-        K.G = dom_geom(D, A.pitch, A.plane);
-        K.C = dom_coef<R>(D);
-        K.g_plane = 9;
-        K.h_plane = SW ? 13 : 9;
-        int j, k;
-        frame_coord(K.G, e.y, j, k);
-        const R inv_r = R(1) / R(D.r0 + (double)j + 0.5);
-        const R az = R(A.dom_az[2 * e.x + 1]);
-        Red red{0.0, 0.0, 0.0, 0.0};
-        if (TH && D.temperature) {
-            Cell<R, SW, TH> c;
-            pull_odd(K, j, k, c);
-            c.collide(inv_r, K.C, az);
-            push_odd(K, j, k, c);
+        if ((D.temperature != 0) == THD) {
+            KArgs<S, R> K;
+            K.pop = A.pop;
+            K.G = dom_geom(D, A.pitch, A.plane);
+            K.C = dom_coef<R>(D);
+            K.g_plane = 9;
+            K.h_plane = SW ? 13 : 9;
+            K.speed = A.speed;
+            K.residual = A.residual;
+            int j, k;
+            frame_coord(K.G, e.y, j, k);
+            Red red{0.0, 0.0, 0.0, 0.0};
+            ring_node<S, R, SW, THD, CHK>(K, j, k, R(A.dom_az[2 * e.x + 1]), red);
             if (CHK) {
-                K.speed = A.speed;
-                K.residual = A.residual;
-                check_cell(K, j, k, inv_r, c, red);
+                double* o = A.ring_part + 4ll * i;
+                o[0] = red.rmax;
+                o[1] = red.mass;
+                o[2] = red.budget;
+                o[3] = red.bad;
             }
-        } else {
-            Cell<R, SW, false> c;
-            pull_odd(K, j, k, c);
-            c.collide(inv_r, K.C, az);
-            push_odd(K, j, k, c);
-            if (CHK) {
-                K.speed = A.speed;
-                K.residual = A.residual;
-                check_cell(K, j, k, inv_r, c, red);
-            }
-        }
-        if (CHK) {
-            double* o = A.ring_part + 4ll * i;
-            o[0] = red.rmax;
-            o[1] = red.mass;
-            o[2] = red.budget;
-            o[3] = red.bad;
         }
     }
-    // the ring kernel is the last kernel of an odd step: move every domain's
-    // force to the next level (other blocks read only the odd slot)
-    if (blockIdx.x == 0) {
+    // the ring kernels end an odd step: move every domain's force to the next
+    // level (other blocks read only the odd slot)
+    if (advance && blockIdx.x == 0) {
         const long long t1 = A.clock->t + 1;
         for (int d = threadIdx.x; d < A.ndom; d += blockDim.x)
             A.dom_az[2 * d] = A.doms[d].az0 * cos(A.doms[d].omega_t * (double)t1);

@@ -15,9 +15,10 @@ constexpr int kShapeTJ[kBatchShapes] = {128, 64};
 
 struct BatchTiles {
     int ntiles;
-    size_t off_tiles;   // int4 [ntiles]
+    int nentries;       // (tile, slot) pairs that hold a domain's nodes
+    size_t off_tiles;   // TileRec [ntiles]
     size_t off_tstart;  // int [ndom + 1]
-    size_t off_tindex;  // int [ntiles]
+    size_t off_tindex;  // int [nentries]: tile * kSlots + slot, grouped by domain
 };
 
 struct BatchLayout {
@@ -25,7 +26,8 @@ struct BatchLayout {
     int nplanes;
     long long pitch, rows, plane;
     int nring;
-    size_t off_speed, off_tilepart, off_ringpart, off_result, off_az, off_clock, off_doms, off_ring, off_rstart;
+    size_t off_speed, off_tilepart, off_ringpart, off_result, off_az, off_clock, off_doms, off_slots, off_ring,
+        off_rstart;
     BatchTiles shape[kBatchShapes];
     size_t total;
 };

@@ -14,8 +14,9 @@ BatchArgs<S, R> batch_args(axlbm_batch* b) {
     A.pitch = L.pitch;
     A.plane = L.plane;
     A.doms = reinterpret_cast<const DomDesc*>(b->mem + L.off_doms);
+    A.slots = reinterpret_cast<const SlotDesc*>(b->mem + L.off_slots);
     A.ndom = b->n;
-    A.tiles = reinterpret_cast<const int4*>(b->mem + L.shape[b->shape].off_tiles);
+    A.tiles = reinterpret_cast<const TileRec*>(b->mem + L.shape[b->shape].off_tiles);
     A.ntiles = L.shape[b->shape].ntiles;
     A.ring = reinterpret_cast<const int2*>(b->mem + L.off_ring);
     A.nring = L.nring;
@@ -106,9 +107,14 @@ cudaError_t batch_step_th(axlbm_batch* b, int check, int residual, cudaEvent_t e
     if (ev1) cudaEventRecord(ev1, b->stream);
     if (e != cudaSuccess) return e;
     const int blocks = (A.nring + kThreads - 1) / kThreads;
-    if (check) k_ring_batch<S, R, true, TH, true><<<blocks, kThreads, 0, b->stream>>>(A);
-    else k_ring_batch<S, R, true, TH, false><<<blocks, kThreads, 0, b->stream>>>(A);
+    if (check) k_ring_batch<S, R, true, false, true><<<blocks, kThreads, 0, b->stream>>>(A, TH ? 0 : 1);
+    else k_ring_batch<S, R, true, false, false><<<blocks, kThreads, 0, b->stream>>>(A, TH ? 0 : 1);
     *nl = 2;
+    if (TH) {
+        if (check) k_ring_batch<S, R, true, true, true><<<blocks, kThreads, 0, b->stream>>>(A, 1);
+        else k_ring_batch<S, R, true, true, false><<<blocks, kThreads, 0, b->stream>>>(A, 1);
+        *nl = 3;
+    }
     return cudaGetLastError();
 }
 

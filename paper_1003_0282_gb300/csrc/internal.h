@@ -40,23 +40,29 @@ struct Clock {
     unsigned int pad;
 };
 
-// Coefficients in the arithmetic type R.
+// Collision coefficients in the arithmetic type R: everything the collision
+// of a node reads (the boundary rules add the wall data of Coef below).
 template <class R>
-struct Coef {
+struct CoefCore {
     R rho0, inv_rho0;
     R c0, c1;       // f: omega_a = c0 + c1 e_ar / r            (Eq. 13)
     R mu0;          // rho0 * tau / 3                           (Eq. 16, mu -> mu0)
     R g0, g1, nu;   // g: omega = g0 + g1 e_r / r, nu = tau_g/2  (Eqs. 53-54)
     R h0, h1;       // temperature: omega = h0 + h1 e_r / r
     R gbeta, t_ref;
-    R omega_w[4];   // wall angular velocities per face
-    R t_w[4];       // wall temperatures per face
-    int t_dir[4];   // 1: Dirichlet face
     // MRT (Sec. III B): rates s_e = s_v, s_eps, s_q and derived factors
     int mrt;
     R sv, se, seps, sq;
     R k_e6;         // s_e / (6 s_v) of Eq. 49
     R mrt_gam;      // 1 - s_v / 2 (Eq. 49: gamma = mrt_gam / r)
+};
+
+// Collision coefficients plus the wall data of the boundary rules.
+template <class R>
+struct Coef : CoefCore<R> {
+    R omega_w[4];   // wall angular velocities per face
+    R t_w[4];       // wall temperatures per face
+    int t_dir[4];   // 1: Dirichlet face
 };
 
 struct Layout {

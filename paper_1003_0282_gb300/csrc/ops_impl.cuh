@@ -77,7 +77,7 @@ struct Cell {
     R h[4];  // h_a - T_ref / 4
     R rho, ur, uz, s0, ds0;
 
-    __device__ __forceinline__ void collide(Sc inv_r, const Coef<Sc>& C, Sc az) {
+    __device__ __forceinline__ void collide(Sc inv_r, const CoefCore<Sc>& C, Sc az) {
         const Sc W0 = Sc(4.0 / 9.0), W1 = Sc(1.0 / 9.0), W2 = Sc(1.0 / 36.0);
         const Sc half = Sc(0.5), one = Sc(1);
         // rates by the sign of e_r (Eq. 13) and their combinations
@@ -170,7 +170,7 @@ struct Cell {
     // (orthogonal D2Q9: rho, e, eps, j_r, q_r, j_z, q_z, p_rr, p_rz); M w rho0
     // = rho0 (1, -2, 1, 0, ...).  Eq. 41 with the source -(u_r/r) m^eq + S'
     // of Eq. 51, the correction of Eqs. 49-50, then M^-1 = M^T diag(1/|row|^2).
-    __device__ __forceinline__ void collide_mrt(Sc inv_r, const Coef<Sc>& C, R drho, R fr, R fz) {
+    __device__ __forceinline__ void collide_mrt(Sc inv_r, const CoefCore<Sc>& C, R drho, R fr, R fz) {
         const Sc one = Sc(1), half = Sc(0.5);
         // moments of the deviations
         const R ax = (d[1] + d[2]) + (d[3] + d[4]);
@@ -823,6 +823,20 @@ __device__ __forceinline__ void frame_coord(const Geom& G, int i, int& j, int& k
     j = (i % cols) == 0 ? 0 : G.nr - 1;
 }
 
+// Odd-step update of one outer-ring node (j, k): pull with the boundary
+// rules, collide, push, check values.  Kept out of line so that the
+// single-domain and batch ring kernels run one compiled instruction sequence
+// (a domain gets the same bits whichever of the two updates it).
+template <class S, class R, bool SW, bool TH, bool CHK>
+__device__ __noinline__ void ring_node(const KArgs<S, R>& A, int j, int k, R az, Red& red) {
+    Cell<R, SW, TH> c;
+    pull_odd(A, j, k, c);
+    const R inv_r = inv_radius<R>(A.G, j);
+    c.collide(inv_r, A.C, az);
+    push_odd(A, j, k, c);
+    if (CHK) check_cell(A, j, k, inv_r, c, red);
+}
+
 // Odd-step update of the outer ring with the boundary rules.
 template <class S, class R, bool SW, bool TH, bool CHK>
 __global__ void __launch_bounds__(kThreads) k_frame(const KArgs<S, R> A) {
@@ -832,12 +846,7 @@ __global__ void __launch_bounds__(kThreads) k_frame(const KArgs<S, R> A) {
     if (i < A.nframe) {
         int j, k;
         frame_coord(G, i, j, k);
-        Cell<R, SW, TH> c;
-        pull_odd(A, j, k, c);
-        const R inv_r = inv_radius<R>(G, j);
-        c.collide(inv_r, A.C, R(A.az[1]));
-        push_odd(A, j, k, c);
-        if (CHK) check_cell(A, j, k, inv_r, c, red);
+        ring_node<S, R, SW, TH, CHK>(A, j, k, R(A.az[1]), red);
     }
     if (CHK) block_reduce_store(red, A.partials + 4ll * (A.part_offset + blockIdx.x));
     if (blockIdx.x == 0 && threadIdx.x == 0) advance_clock(A.clock, 1, A.az0, A.omega_t);

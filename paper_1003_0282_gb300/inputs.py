@@ -103,7 +103,7 @@ def womersley(nr: int = 64, nz: int = 4, tau: float = 0.8, alpha: float = 5.0,
 
 
 def rotating_lid_cavity(nr: int = 128, aspect: float = 1.5, re: float = 990.0,
-                        u_lid: float = 0.1, rho0: float = 1.0) -> Problem:
+                        u_lid: float = 0.1, rho0: float = 1.0, collision: str = "bgk") -> Problem:
     """Closed cylinder of radius R = nr and height H = aspect R; the top lid
     rotates with Omega = u_lid / R, the bottom and side walls are at rest.
     Re = Omega R^2 / nu (Sec. IV B)."""
@@ -112,21 +112,26 @@ def rotating_lid_cavity(nr: int = 128, aspect: float = 1.5, re: float = 990.0,
     nu = omega * nr * nr / re
     tau = 3.0 * nu + 0.5
     return Problem(nr=nr, nz=nz, tau=tau, rho0=rho0, z_lo=WALL, z_hi=WALL, swirl=True,
-                   omega={"hi": omega}, name=f"cavity A={aspect} Re={re:g} {nr}x{nz}")
+                   omega={"hi": omega}, collision=collision, name=f"cavity A={aspect} Re={re:g} {nr}x{nz}")
 
 
-def wheeler_cell(nr: int = 128, re_x: float = 100.0, beta: float = 0.4, u_t: float = 0.1,
+def wheeler_cell(nr: int = 128, re_x: float = 100.0, beta: float = 0.4, u_ref: float = 0.1,
                  re_c_ratio: float = -0.25, prandtl: float = 0.05, grashof: float = 1e4,
-                 rho0: float = 1.0) -> Problem:
+                 rho0: float = 1.0, collision: str = "bgk") -> Problem:
     """Wheeler-type Czochralski cell (Sec. IV B): crucible of radius R_c = nr and
     height H = R_c rotating with Omega_c (side wall and bottom), crystal disk
     of radius beta R_c on top rotating with Omega_x, free surface beyond it.
-    Re_x = R_c^2 Omega_x / nu, U_t = beta R_c Omega_x.  The thermal part (hot
-    side wall T = 1, cold crystal T = 0, adiabatic elsewhere, Boussinesq force
-    with Gr = g beta dT R^3 / nu^2, Pr = nu / kappa) is not in the paper."""
+    Re_x = R_c^2 Omega_x / nu, crystal edge speed U_t = beta R_c Omega_x.  The
+    thermal part (hot side wall T = 1, cold crystal T = 0, adiabatic elsewhere,
+    Boussinesq force with Gr = g beta dT R^3 / nu^2, Pr = nu / kappa) is not in
+    the paper.
+
+    Lattice scaling: the larger of U_t = beta Re_x nu / R_c and the buoyancy
+    velocity U_b = sqrt(g beta dT R_c) = nu sqrt(Gr) / R_c is set to u_ref, so
+    that the flow stays at low Mach number whichever force drives it."""
     rc = float(nr)
-    omega_x = u_t / (beta * rc)
-    nu = rc * rc * omega_x / re_x
+    nu = u_ref * rc / max(beta * re_x, math.sqrt(grashof) if grashof > 0.0 else 0.0)
+    omega_x = re_x * nu / (rc * rc)
     omega_c = re_c_ratio * re_x * nu / (rc * rc)
     tau = 3.0 * nu + 0.5
     kappa = nu / prandtl
@@ -136,7 +141,7 @@ def wheeler_cell(nr: int = 128, re_x: float = 100.0, beta: float = 0.4, u_t: flo
                    temperature=True, tau_t=tau_t, gbeta=gbeta, t_ref=0.5,
                    r_split=beta * rc,
                    omega={"outer": omega_c, "lo": omega_c, "hi": omega_x},
-                   t_wall={"outer": 1.0, "hi": 0.0},
+                   t_wall={"outer": 1.0, "hi": 0.0}, collision=collision,
                    name=f"wheeler Re_x={re_x:g} Pr={prandtl:g} Gr={grashof:.3g} {nr}x{nr}")
 
 
@@ -148,11 +153,13 @@ def large_pipe(nr: int = 4096, nz: int = 8192, tau: float = 0.8, umax: float = 0
 
 
 def batch_sweep(seed: int = 20261202, n_cavities: int = 256, n_wheeler: int = 64,
-                scale: float = 1.0) -> List[Problem]:
+                scale: float = 1.0, collision: str = "mrt") -> List[Problem]:
     """Uneven batch: rotating-lid cavities with N_r ~ U{64..256}, H/R ~ U[1, 3.5],
     Re ~ U[500, 3000], plus Wheeler-type 128x128 cells with Pr alternating
     0.05 / 5, log10 Gr ~ U[4, 6], Re_x ~ U[100, 1000], Re_c = -Re_x / 4.
-    ``scale`` shrinks every radius (for small test batches)."""
+    ``scale`` shrinks every radius (for small test batches).  The high-Re draws
+    reach tau_s ~ 0.506, the low-viscosity regime where the paper's BGK scheme
+    is unstable (Sec. IV B); the sweep therefore uses its MRT scheme."""
     rng = np.random.default_rng(seed)
     out: List[Problem] = []
     for _ in range(n_cavities):
@@ -160,13 +167,13 @@ def batch_sweep(seed: int = 20261202, n_cavities: int = 256, n_wheeler: int = 64
         aspect = float(rng.uniform(1.0, 3.5))
         re = float(rng.uniform(500.0, 3000.0))
         nr_s = max(4, int(round(nr * scale)))
-        out.append(rotating_lid_cavity(nr=nr_s, aspect=aspect, re=re))
+        out.append(rotating_lid_cavity(nr=nr_s, aspect=aspect, re=re, collision=collision))
     for i in range(n_wheeler):
         pr = 0.05 if i % 2 == 0 else 5.0
         gr = 10.0 ** float(rng.uniform(4.0, 6.0))
         re_x = float(rng.uniform(100.0, 1000.0))
         nr_s = max(4, int(round(128 * scale)))
-        out.append(wheeler_cell(nr=nr_s, re_x=re_x, prandtl=pr, grashof=gr))
+        out.append(wheeler_cell(nr=nr_s, re_x=re_x, prandtl=pr, grashof=gr, collision=collision))
     return out
 
 

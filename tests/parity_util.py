@@ -25,7 +25,7 @@ BOUNDARY_MIXES = {
 }
 
 
-def problem(nr, nz, mix, swirl=True, temperature=True, tau=0.8, **extra):
+def problem(nr, nz, mix, swirl=True, temperature=True, tau=0.8, collision="bgk", **extra):
     kw = dict(BOUNDARY_MIXES[mix])
     if "r_split" in kw:
         kw["r_split"] = kw["r_split"] * nr + kw.get("r0", 0.0)
@@ -33,7 +33,7 @@ def problem(nr, nz, mix, swirl=True, temperature=True, tau=0.8, **extra):
     return I.Problem(nr=nr, nz=nz, tau=tau, swirl=swirl, temperature=temperature, tau_t=0.7,
                      az0=2e-6, omega_t=0.003, gbeta=3e-4, t_ref=0.5, rho0=1.0,
                      omega={"inner": 0.001, "outer": 0.002, "lo": -0.001, "hi": 0.003},
-                     t_wall={"outer": 1.0, "hi": 0.0}, **kw)
+                     t_wall={"outer": 1.0, "hi": 0.0}, collision=collision, **kw)
 
 
 def seeded_state(pb, seed):

@@ -184,3 +184,21 @@ def test_batch_packed_fields_match_per_domain_calls(B):
         assert np.array_equal(allm[off:off + 4 * pb.cells].reshape(4, pb.nz, pb.nr), one), d
         off += 4 * pb.cells
     batch.close()
+
+
+def test_batch_mixes_bgk_and_mrt_domains(B):
+    doms = mixed_batch()
+    doms = [dataclasses.replace(pb, collision="mrt") if i % 2 else pb for i, pb in enumerate(doms)]
+    batch = B.Batch(doms, "fp32")
+    states = []
+    for d, pb in enumerate(doms):
+        st = seeded_state(pb, 700 + d)
+        batch.set_populations(d, st.f, st.g, st.h if pb.temperature else None)
+        states.append(st)
+    batch.step(9)
+    for d, pb in enumerate(doms):
+        oracle.step(states[d], 9)
+        f, g, h = batch.get_populations(d)
+        assert rel_err(f, states[d].f) <= POP_TOL["fp32"], (d, pb.collision)
+        assert rel_err(g, states[d].g) <= POP_TOL["fp32"], (d, pb.collision)
+    batch.close()

@@ -11,6 +11,7 @@ Tolerances (relative max-norm): FP64 1e-10, FP32 1e-5 on populations; the
 macroscopic fields are checked against the same bounds scaled by their own
 magnitude.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -59,6 +60,19 @@ def test_population_parity_all_boundaries(B, mix, precision):
     worst, _ = run_and_compare(B, pb, precision, [1, 1, 2, 7, 29])
     tol = POP_TOL[precision]
     assert all(v <= tol for v in worst.values()), worst
+
+
+@pytest.mark.parametrize("mix", sorted(BOUNDARY_MIXES))
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_population_parity_mrt(B, mix, precision):
+    """The MRT collision (Sec. III B) under every boundary mix, default and
+    explicit rates."""
+    pb = problem(150, 37, mix, collision="mrt", tau=0.62, s_eps=1.3, s_q=1.1)
+    worst, _ = run_and_compare(B, pb, precision, [1, 1, 2, 17])
+    assert all(v <= POP_TOL[precision] for v in worst.values()), worst
+    pb = problem(61, 23, mix, collision="mrt", tau=0.55)
+    worst, _ = run_and_compare(B, pb, precision, [1, 6])
+    assert all(v <= POP_TOL[precision] for v in worst.values()), worst
 
 
 @pytest.mark.parametrize("swirl,temp", [(False, False), (True, False), (False, True)])
@@ -217,3 +231,37 @@ def test_full_size_sampled_parity(B, precision):
             want, _, _ = window_oracle((f0, g0, h0), pb, j, k, done, 0)
             assert np.max(np.abs(f1[:, k, j] - want)) <= POP_TOL[precision] * 0.5, (j, k, done)
     dom.close()
+
+
+def test_low_viscosity_bgk_versus_mrt(B):
+    """Sec. IV B's comparison: rotating-lid cylinder A = 1.5, Re = 1290, 100 x 150,
+    tau = 0.005 (nu = 1.67e-3, s_v = 1/(0.5 + 0.005)).  The MRT scheme with
+    s_e = s_v stays finite and converges; the BGK outcome is recorded."""
+    import json
+    import os
+    nr, re_ = 100, 1290.0
+    nu = 0.005 / 3.0
+    omega = re_ * nu / nr ** 2
+    base = I.Problem(nr=nr, nz=150, tau=0.505, z_lo="wall", z_hi="wall", swirl=True, omega={"hi": omega})
+    out = {}
+    for coll in ("bgk", "mrt"):
+        pb = dataclasses.replace(base, collision=coll)
+        dom = B.Domain(pb, "fp32")
+        finite = True
+        res = float("nan")
+        for _ in range(40):
+            dom.step(5000)
+            res, _, _ = dom.residual(allow_nonfinite=True)
+            if not np.isfinite(res):
+                finite = False
+                break
+        out[coll] = {"finite": finite, "residual": res, "steps": dom.time}
+        if coll == "mrt":
+            uz_axis = dom.moments(B.UZ)[0][:, 0]
+            out[coll]["uz_axis_max_over_omega_r"] = float(np.max(uz_axis) / (omega * nr))
+        dom.close()
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out", "low_viscosity.json")
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    with open(path, "w") as fh:
+        json.dump(out, fh, indent=1)
+    assert out["mrt"]["finite"], out

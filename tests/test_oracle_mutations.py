@@ -30,8 +30,8 @@ MUTATIONS = {
     "inertial force dropped (Sec. III C)":
         ("+ p->rho0 * uth * uth / r;\n    double fz", ";\n    double fz"),
     "second-order equilibrium coefficient (Eq. 6)":
-        ("4.5 * eu * eu - 1.5 * usq);\n        const double src",
-         "3.0 * eu * eu - 1.5 * usq);\n        const double src"),
+        ("4.5 * eu * eu - 1.5 * usq);\n            const double src",
+         "3.0 * eu * eu - 1.5 * usq);\n            const double src"),
     "trapezoidal factor of the source (Eq. 13)":
         ("(1.0 - 0.5 * om) * src;", "src;"),
     "nu/r term of S^g dropped (Eq. 54)":
