@@ -203,7 +203,7 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
     L.off_speed = off;
     off += al((size_t)L.plane * 4);
     L.off_tilepart = off;
-    off += al((size_t)maxtiles * axl::kSlots * 32);
+    off += al((size_t)maxtiles * axl::kSlots * axl::kConsumerWarps * 32);
     L.off_ringpart = off;
     off += al((size_t)L.nring * 32);
     L.off_result = off;
@@ -444,6 +444,8 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
     b->col0 = P.col0;
     b->row0 = P.row0;
     b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->side = nullptr;
+    b->fork = b->join = nullptr;
     b->L = P.L;
     b->shape = 0;
     memset(b->grid, 0, sizeof b->grid);
@@ -473,6 +475,14 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
         b->owns_mem = true;
     }
     axlbm_status st = AXLBM_OK;
+    {
+        int lo = 0, hi = 0;
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+        if (e != cudaSuccess) st = bcuda(b, e, "side stream");
+    }
     // descriptors and lists
     std::vector<axl::DomDesc> dd(n);
     std::vector<axl::SlotDesc> sd(n);
@@ -531,6 +541,9 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
     if (st != AXLBM_OK) {
         g_batch_error = b->err;
         if (b->owns_mem) cudaFree(b->mem);
+        if (b->fork) cudaEventDestroy(b->fork);
+        if (b->join) cudaEventDestroy(b->join);
+        if (b->side) cudaStreamDestroy(b->side);
         delete b;
         return st;
     }
@@ -783,6 +796,13 @@ axlbm_status axlbm_batch_kernel_times(axlbm_batch* b, int64_t* bulk_launches, do
 axlbm_status axlbm_batch_destroy(axlbm_batch* b) {
     if (!b) return AXLBM_EINVAL;
     cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (b->side) {
+        cudaError_t e2 = cudaStreamSynchronize(b->side);
+        if (e == cudaSuccess) e = e2;
+        cudaStreamDestroy(b->side);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
     for (auto ev : b->ev)
         if (ev) cudaEventDestroy(ev);
     if (b->owns_mem) {

@@ -96,7 +96,7 @@ struct BatchArgs {
     double* dom_az;          // [ndom][2]: a(t) of each domain by AA parity
     Clock* clock;            // time level and error word
     R* speed;                // |u| plane, atlas-shaped
-    double* tile_part;       // [ntiles][kSlots][4] check partials per tile slot
+    double* tile_part;       // [ntiles][kSlots][kConsumerWarps][4] check partials
     double* ring_part;       // [nring][4] check values of ring nodes
     int residual;
 };
@@ -111,14 +111,13 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
         : "memory");
 }
 
-// Per-slot reduction of one tile's check values (consumer warps only).  The
-// lanes of one slot form a contiguous run of each warp (slots are column
-// ranges), so a segmented scan leaves each run's total in its last lane; the
-// runs' totals are summed over the warps in a fixed order.  Uses named
-// barrier 1 over kBulkThreads threads.
+// Per-warp, per-slot totals of one tile's check values.  The lanes of one
+// slot form a contiguous run of the warp (slots are column ranges), so a
+// segmented scan leaves each run's total in its last lane, which stores it
+// at out[(slot * kConsumerWarps + warp) * 4 ..]; no block barrier is needed.
+// The fold adds, per (tile, slot), the warps whose columns meet the slot.
 template <class R>
-__device__ __forceinline__ void slot_reduce_store(RedR<R> v, int q, const TileRec& tr, const SlotDesc* sl,
-                                                  double* out, double (*sh)[4][kBulkThreads / 32]) {
+__device__ __forceinline__ void warp_slot_store(RedR<R> v, int q, const SlotDesc* sl, double* out) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -138,38 +137,13 @@ __device__ __forceinline__ void slot_reduce_store(RedR<R> v, int q, const TileRe
         }
     }
     const int qn = __shfl_down_sync(full, q, 1);
-#pragma unroll
-    for (int u = 0; u < kSlots; ++u) {
-        const unsigned m = __ballot_sync(full, q == u);
-        if (lane == u && m == 0u) {
-            sh[u][0][warp] = 0.0;
-            sh[u][1][warp] = 0.0;
-            sh[u][2][warp] = 0.0;
-            sh[u][3][warp] = 0.0;
-        }
-    }
     if (lane == 31 || qn != q) {
-        sh[q][0][warp] = (double)v.rmax;
-        sh[q][1][warp] = (double)v.count * sl[q].rho0 + (double)v.dmass;
-        sh[q][2][warp] = (double)v.budget;
-        sh[q][3][warp] = (double)v.bad;
+        double* o = out + 4ll * (q * kConsumerWarps + warp);
+        o[0] = (double)v.rmax;
+        o[1] = (double)v.count * sl[q].rho0 + (double)v.dmass;
+        o[2] = (double)v.budget;
+        o[3] = (double)v.bad;
     }
-    asm volatile("bar.sync 1, %0;" ::"r"(kBulkThreads) : "memory");
-    if (threadIdx.x < tr.nseg) {
-        const int u = threadIdx.x;
-        double r[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int w = 0; w < kBulkThreads / 32; ++w) {
-            r[0] = fmax(r[0], sh[u][0][w]);
-            r[1] += sh[u][1][w];
-            r[2] += sh[u][2][w];
-            r[3] += sh[u][3][w];
-        }
-        out[4 * u + 0] = r[0];
-        out[4 * u + 1] = r[1];
-        out[4 * u + 2] = r[2];
-        out[4 * u + 3] = r[3];
-    }
-    asm volatile("bar.sync 1, %0;" ::"r"(kBulkThreads) : "memory");
 }
 
 template <int PAR>
@@ -292,7 +266,7 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
         if (CHK) {
             const R vur = Lanes<RC>::get(c.ur, l), vuz = Lanes<RC>::get(c.uz, l), vrho = Lanes<RC>::get(c.rho, l);
             const R sp = sqrt(vur * vur + vuz * vuz);
-            if (A.residual) red.rmax = max(red.rmax, (R)fabs(sp - sp_old[(rr - threadIdx.x / TJ) / (TK / 2) + l]));
+            if (A.residual) red.rmax = max(red.rmax, (R)fabs(sp - sp_old[l]));
             A.speed[x] = sp;
             red.dmass += Lanes<RC>::get(c.ds0, l);
             red.budget += vrho * vur * inv_r;
@@ -325,7 +299,6 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
     __shared__ __align__(8) uint64_t full[NS];
     __shared__ __align__(8) uint64_t empty[NS];
     __shared__ volatile int abort_flag;
-    __shared__ double red_sh[kSlots][4][kBulkThreads / 32];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = A.ntiles;
@@ -388,14 +361,26 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
     } else {
         const int jj = tid % TJ;
         const int rr0 = tid / TJ;
+        // check steps with a residual: |u| of the previous level at this
+        // thread's two nodes of the next tile, loaded one tile ahead (every
+        // atlas position is valid memory; idle nodes ignore the value)
+        R sp_next[2] = {R(0), R(0)};
+        auto prefetch_speed = [&](int i) {
+            if (CHK && i < ntiles && A.residual) {
+                const int2 kj = *reinterpret_cast<const int2*>(A.tiles + batch_tile_at<PAR>(i, ntiles));
+#pragma unroll
+                for (int m = 0; m < 2; ++m)
+                    sp_next[m] = A.speed[(long long)(kj.x + rr0 + m * (TK / 2)) * A.pitch + kj.y + jj];
+            }
+        };
+        prefetch_speed(blockIdx.x);
         int it = 0;
         for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++it) {
             const int s = it % NS;
             const int tile = batch_tile_at<PAR>(i, ntiles);
-            bool fail = !mbar_wait_bounded(&full[s], (uint32_t)((it / NS) & 1), kWaitCycles) || abort_flag;
-            // check steps synchronise the consumers per tile: decide together
-            if (CHK) fail = bar_red_or(1, kBulkThreads, fail);
-            if (fail) {
+            const R sp_old[2] = {sp_next[0], sp_next[1]};
+            prefetch_speed(i + gridDim.x);
+            if (!mbar_wait_bounded(&full[s], (uint32_t)((it / NS) & 1), kWaitCycles) || abort_flag) {
                 abort_flag = 1;
                 break;
             }
@@ -408,23 +393,14 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
             const R az = R(M.az[q]);
             const int jl = j0 + jj - D.col0;
             const R inv_r = rcp(R(D.r0 + (double)jl + 0.5));
-            R sp_old[2] = {R(0), R(0)};
-            if (CHK && A.residual) {
-#pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    const int kl = k0 - D.row0 + rr0 + m * (TK / 2);
-                    if (jl < D.nr && kl < D.nz) sp_old[m] = A.speed[(long long)(k0 + rr0 + m * (TK / 2)) * A.pitch + j0 + jj];
-                }
-            }
             const S* st = sm + s * STAGE;
             RedR<R> red{R(0), R(0), R(0), 0, 0};
             const bool dth = TH && M.r.th;
-#pragma unroll
-            for (int rr = rr0; rr < TK / Lanes<RC>::n; rr += kBulkThreads / TJ) {
-                if (dth) batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ>(A, D, st, k0, j0, jj, rr, inv_r, az, sp_old, red);
-                else batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ>(A, D, st, k0, j0, jj, rr, inv_r, az, sp_old, red);
-            }
-            if (CHK) slot_reduce_store(red, q, M.r, slots + s * kSlots, A.tile_part + 4ll * kSlots * tile, red_sh);
+            // one node pair per thread: rows rr0 and rr0 + TK/2 of column jj
+            static_assert(kBulkThreads / TJ == TK / 2, "one pair per consumer thread");
+            if (dth) batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old, red);
+            else batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old, red);
+            if (CHK) warp_slot_store(red, q, slots + s * kSlots, A.tile_part + 4ll * kSlots * kConsumerWarps * tile);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
         }
@@ -450,8 +426,10 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
 // makes each class's arithmetic the same instruction sequence as the
 // single-domain ring kernel.  The launch with `advance` set moves every
 // domain's force and the time level to the next step.
+constexpr int kRingThreads = 128;
+
 template <class S, class R, bool SW, bool THD, bool CHK>
-__global__ void __launch_bounds__(kThreads) k_ring_batch(const BatchArgs<S, R> A, int advance) {
+__global__ void __launch_bounds__(kRingThreads) k_ring_batch(const BatchArgs<S, R> A, int advance) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < A.nring) {
         const int2 e = A.ring[i];
@@ -487,6 +465,42 @@ __global__ void __launch_bounds__(kThreads) k_ring_batch(const BatchArgs<S, R> A
         __syncthreads();
         if (threadIdx.x == 0) A.clock->t = t1;
     }
+}
+
+// Per-domain check values of a batch step: the (tile, slot) entries of each
+// domain (every consumer warp whose columns meet the slot, in warp order)
+// and, after an odd step, its ring nodes; one block per domain, fixed order.
+static __global__ void __launch_bounds__(kThreads)
+k_batch_fold(const int* tile_start, const int* tile_index, const TileRec* tiles, int tj, const double* tile_part,
+             const int* ring_start, const double* ring_part, int with_ring, double* result) {
+    const int d = blockIdx.x;
+    Red v{0.0, 0.0, 0.0, 0.0};
+    const int groups = tj / 32;
+    for (int i = tile_start[d] + threadIdx.x; i < tile_start[d + 1]; i += blockDim.x) {
+        const int e = tile_index[i];
+        const int tile = e / kSlots, q = e % kSlots;
+        const TileRec& tr = tiles[tile];
+        const int lo = tr.start[q], hi = q + 1 < tr.nseg ? tr.start[q + 1] : tj;
+        for (int w = 0; w < kConsumerWarps; ++w) {
+            const int c0 = 32 * (w % groups);
+            if (c0 >= hi || c0 + 32 <= lo) continue;
+            const double* p = tile_part + 4ll * (((long long)tile * kSlots + q) * kConsumerWarps + w);
+            v.rmax = fmax(v.rmax, p[0]);
+            v.mass += p[1];
+            v.budget += p[2];
+            v.bad += p[3];
+        }
+    }
+    if (with_ring) {
+        for (int i = ring_start[d] + threadIdx.x; i < ring_start[d + 1]; i += blockDim.x) {
+            const double* p = ring_part + 4ll * i;
+            v.rmax = fmax(v.rmax, p[0]);
+            v.mass += p[1];
+            v.budget += p[2];
+            v.bad += p[3];
+        }
+    }
+    block_reduce_store(v, result + 4ll * d);
 }
 
 }  // namespace axl

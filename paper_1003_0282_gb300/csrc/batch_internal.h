@@ -42,6 +42,10 @@ struct axlbm_batch {
     std::vector<axlbm_domain> desc;
     std::vector<int> col0, row0;
     cudaStream_t stream;
+    // odd steps run the ring kernels on `side`, concurrently with the bulk
+    // kernel on `stream` (disjoint slots), forked and joined with two events
+    cudaStream_t side;
+    cudaEvent_t fork, join;
     char* mem;
     bool owns_mem;
     axl::BatchLayout L;

@@ -103,19 +103,37 @@ cudaError_t batch_step_th(axlbm_batch* b, int check, int residual, cudaEvent_t e
         *nl = 1;
         return e;
     }
+    // odd step: the interior (bulk) and the outer rings touch disjoint slots.
+    // With 16-bit storage the bulk kernel is bound by issue, not by HBM, so
+    // the rings run concurrently on the side stream (their small blocks use
+    // the SMs' leftover registers); with FP32 storage the bulk kernel needs
+    // all of HBM and the rings' scattered accesses would slow it, so they
+    // follow it on the same stream.
+    const bool overlap = sizeof(S) == 2;
+    cudaStream_t rs = overlap ? b->side : b->stream;
+    if (overlap) {
+        e = cudaEventRecord(b->fork, b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
+        if (e != cudaSuccess) return e;
+    }
     e = check ? launch_bulk_batch_shape<S, R, TH, 1, true>(b, A) : launch_bulk_batch_shape<S, R, TH, 1, false>(b, A);
     if (ev1) cudaEventRecord(ev1, b->stream);
     if (e != cudaSuccess) return e;
-    const int blocks = (A.nring + kThreads - 1) / kThreads;
-    if (check) k_ring_batch<S, R, true, false, true><<<blocks, kThreads, 0, b->stream>>>(A, TH ? 0 : 1);
-    else k_ring_batch<S, R, true, false, false><<<blocks, kThreads, 0, b->stream>>>(A, TH ? 0 : 1);
+    const int blocks = (A.nring + kRingThreads - 1) / kRingThreads;
+    if (check) k_ring_batch<S, R, true, false, true><<<blocks, kRingThreads, 0, rs>>>(A, TH ? 0 : 1);
+    else k_ring_batch<S, R, true, false, false><<<blocks, kRingThreads, 0, rs>>>(A, TH ? 0 : 1);
     *nl = 2;
     if (TH) {
-        if (check) k_ring_batch<S, R, true, true, true><<<blocks, kThreads, 0, b->stream>>>(A, 1);
-        else k_ring_batch<S, R, true, true, false><<<blocks, kThreads, 0, b->stream>>>(A, 1);
+        if (check) k_ring_batch<S, R, true, true, true><<<blocks, kRingThreads, 0, rs>>>(A, 1);
+        else k_ring_batch<S, R, true, true, false><<<blocks, kRingThreads, 0, rs>>>(A, 1);
         *nl = 3;
     }
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (overlap) {
+        if (e == cudaSuccess) e = cudaEventRecord(b->join, b->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join, 0);
+    }
+    return e;
 }
 
 template <class S, class R>
@@ -128,11 +146,13 @@ template <class S, class R>
 cudaError_t batch_fold_impl(axlbm_batch* b, int with_ring) {
     const BatchLayout& L = b->L;
     const BatchTiles& T = L.shape[b->shape];
-    return launch_domain_fold(
-        b->n, reinterpret_cast<const int*>(b->mem + T.off_tstart), reinterpret_cast<const int*>(b->mem + T.off_tindex),
+    k_batch_fold<<<b->n, kThreads, 0, b->stream>>>(
+        reinterpret_cast<const int*>(b->mem + T.off_tstart), reinterpret_cast<const int*>(b->mem + T.off_tindex),
+        reinterpret_cast<const TileRec*>(b->mem + T.off_tiles), kShapeTJ[b->shape],
         reinterpret_cast<const double*>(b->mem + L.off_tilepart), reinterpret_cast<const int*>(b->mem + L.off_rstart),
         reinterpret_cast<const double*>(b->mem + L.off_ringpart), with_ring,
-        reinterpret_cast<double*>(b->mem + L.off_result), b->stream);
+        reinterpret_cast<double*>(b->mem + L.off_result));
+    return cudaGetLastError();
 }
 
 template <class S>
