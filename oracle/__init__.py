@@ -26,7 +26,7 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-INNER = {"axis": 0, "wall": 1}
+INNER = {"axis": 0, "wall": 1, "axis_node": 2}
 ZKIND = {"periodic": 0, "wall": 1, "free": 2, "mixed": 3}
 FACES = ("inner", "outer", "lo", "hi")
 
@@ -207,7 +207,7 @@ def stream(pb, fp, gp=None, hp=None):
 
 
 def node_radii(pb) -> np.ndarray:
-    return pb.r0 + np.arange(pb.nr) + 0.5
+    return pb.r0 + np.arange(pb.nr) + (0.0 if pb.inner == "axis_node" else 0.5)
 
 
 def mrt_matrix() -> np.ndarray:

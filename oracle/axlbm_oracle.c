@@ -41,7 +41,9 @@
  *
  * Grid: node (j, k) sits at r = r0 + j + 1/2, z = k + 1/2.  The inner face is
  * r = r0 (the axis when r0 = 0), the outer face r = r0 + nr, the axial faces
- * z = 0 and z = nz.  Boundary rules, applied to a population that leaves a
+ * z = 0 and z = nz.  Node-on-axis variant (ORC_AXIS_NODE, Sec. IV A): node
+ * (j, k) sits at r = j, node 0 on the axis, where every term in 1/r is set
+ * to zero; the outer face is r = nr - 1/2.  Boundary rules, applied to a population that leaves a
  * fluid node towards a site outside the fluid:
  *   - a site beyond a periodic face is the wrapped fluid node;
  *   - a site beyond a solid face returns the population to its own node with
@@ -53,6 +55,10 @@
  *     a free surface) is the mirror image of a fluid node: the population
  *     arrives there with its velocity mirrored; g changes sign across the axis
  *     (u_theta is odd in r), h and f do not.
+ *   - node-on-axis variant: the column r = -1 is the mirror image of the
+ *     column r = 1 (its post-collision populations are node 1's with e_r
+ *     reversed, g negated) and streams into the axis column like any other
+ *     column; populations that node 0 sends towards r < 0 leave the domain.
  * A site outside in both r and z is solid if either face makes it solid.  On
  * the mixed top face (a crystal disk r < r_split on a free surface) the rule is
  * taken where the link crosses the face.
@@ -71,6 +77,7 @@
 /* inner face */
 #define ORC_AXIS 0
 #define ORC_INNER_WALL 1
+#define ORC_AXIS_NODE 2 /* node 0 on the axis (Sec. IV A) */
 /* axial faces */
 #define ORC_PERIODIC 0
 #define ORC_WALL 1
@@ -84,7 +91,7 @@
 
 typedef struct {
     int32_t nr, nz;
-    int32_t inner;              /* ORC_AXIS or ORC_INNER_WALL */
+    int32_t inner;              /* ORC_AXIS, ORC_INNER_WALL or ORC_AXIS_NODE */
     int32_t z_lo, z_hi;         /* ORC_PERIODIC / ORC_WALL / ORC_FREE / ORC_MIXED */
     int32_t swirl, temperature; /* 0 or 1 */
     int32_t t_dirichlet[4];     /* per face: 1 = fixed T, 0 = adiabatic */
@@ -123,12 +130,19 @@ static int find4(int cr, int cz) {
     return -1;
 }
 
-static double node_r(const orc_params* p, int j) { return p->r0 + j + 0.5; }
+static double node_r(const orc_params* p, int j) { return p->r0 + j + (p->inner == ORC_AXIS_NODE ? 0.0 : 0.5); }
+
+/* x / r and x / r^2, with every term in 1/r set to zero on the axis (r = 0,
+ * the node-on-axis grid, Sec. IV A). */
+static double over_r(double x, double r) { return r > 0.0 ? x / r : 0.0; }
+static double over_r2(double x, double r) { return r > 0.0 ? x / (r * r) : 0.0; }
 
 int orc_validate(const orc_params* p) {
     if (p->nr < 1 || p->nz < 1) return ORC_EINVAL;
     if (!(p->tau_s > 0.5) || !(p->rho0 > 0.0)) return ORC_EINVAL;
     if (p->inner == ORC_AXIS && p->r0 != 0.0) return ORC_EINVAL;
+    if (p->inner == ORC_AXIS_NODE && (p->r0 != 0.0 || p->nr < 2)) return ORC_EINVAL;
+    if (p->inner < ORC_AXIS || p->inner > ORC_AXIS_NODE) return ORC_EINVAL;
     if (p->inner == ORC_INNER_WALL && !(p->r0 >= 0.0)) return ORC_EINVAL;
     if (p->z_lo == ORC_MIXED) return ORC_EINVAL;
     if ((p->z_lo == ORC_PERIODIC) != (p->z_hi == ORC_PERIODIC)) return ORC_EINVAL;
@@ -157,12 +171,12 @@ static double cell_moments(const orc_params* p, double r, double a_t, const doub
     if (p->temperature) {
         for (int a = 0; a < 4; ++a) temp += h[a];
     }
-    const double fext_r = p->rho0 * uth * uth / r;
+    const double fext_r = over_r(p->rho0 * uth * uth, r);
     double fext_z = a_t;
     if (p->temperature) fext_z += p->rho0 * p->gbeta * (temp - p->t_ref);
-    const double ur = (sr + 0.5 * fext_r) / (s0 + mu0 / (r * r));
+    const double ur = (sr + 0.5 * fext_r) / (s0 + over_r2(mu0, r));
     const double uz = (sz + 0.5 * fext_z) / s0;
-    const double rho = s0 / (1.0 + 0.5 * ur / r);
+    const double rho = s0 / (1.0 + over_r(0.5 * ur, r));
     out[0] = rho;
     out[1] = ur;
     out[2] = uz;
@@ -187,7 +201,7 @@ void orc_collide_cell(const orc_params* p, double r, double a_t, const double* f
     const double mu0 = p->rho0 * tau / 3.0;
 
     /* force of Eq. 12 plus the inertial force and the body forces */
-    const double fr = -2.0 * mu0 * ur / (r * r) + p->rho0 * uth * uth / r;
+    const double fr = over_r2(-2.0 * mu0 * ur, r) + over_r(p->rho0 * uth * uth, r);
     double fz = a_t;
     if (p->temperature) fz += p->rho0 * p->gbeta * (temp - p->t_ref);
 
@@ -198,8 +212,8 @@ void orc_collide_cell(const orc_params* p, double r, double a_t, const double* f
         for (int a = 0; a < 9; ++a) {
             const double eu = CR[a] * ur + CZ[a] * uz;
             const double feq = WT[a] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
-            const double src = (3.0 * ((CR[a] - ur) * fr + (CZ[a] - uz) * fz) / rho - ur / r) * feq;
-            const double om = (1.0 + tau * CR[a] / r) / (tau + 0.5);
+            const double src = (3.0 * ((CR[a] - ur) * fr + (CZ[a] - uz) * fz) / rho - over_r(ur, r)) * feq;
+            const double om = (1.0 + over_r(tau * CR[a], r)) / (tau + 0.5);
             fout[a] = fin[a] - om * (fin[a] - feq) + (1.0 - 0.5 * om) * src;
         }
     }
@@ -209,8 +223,8 @@ void orc_collide_cell(const orc_params* p, double r, double a_t, const double* f
         for (int a = 0; a < 4; ++a) {
             const double eu = QR[a] * ur + QZ[a] * uz;
             const double geq = p->rho0 * uth / 4.0 * (1.0 + 2.0 * eu);
-            const double sg = -(1.0 / r) * (2.0 * ur + nu / r) * geq;
-            const double om = (1.0 + taug * QR[a] / r) / (taug + 0.5);
+            const double sg = -over_r(1.0, r) * (2.0 * ur + over_r(nu, r)) * geq;
+            const double om = (1.0 + over_r(taug * QR[a], r)) / (taug + 0.5);
             gout[a] = gin[a] - om * (gin[a] - geq) + sg;
         }
     }
@@ -219,8 +233,8 @@ void orc_collide_cell(const orc_params* p, double r, double a_t, const double* f
         for (int a = 0; a < 4; ++a) {
             const double eu = QR[a] * ur + QZ[a] * uz;
             const double heq = temp / 4.0 * (1.0 + 2.0 * eu);
-            const double sh = -(ur / r) * heq;
-            const double om = (1.0 + taut * QR[a] / r) / (taut + 0.5);
+            const double sh = -over_r(ur, r) * heq;
+            const double om = (1.0 + over_r(taut * QR[a], r)) / (taut + 0.5);
             hout[a] = hin[a] - om * (hin[a] - heq) + sh;
         }
     }
@@ -300,11 +314,11 @@ static void mrt_collide_f(const orc_params* p, double r, const double* fin, doub
     const double sp[9] = {0.0, 6.0 * uF, -6.0 * uF, fr, -fr, fz, -fz,
                           2.0 * (ur * fr - uz * fz), ur * fz + uz * fr};                     /* Eq. 51 */
     double src[9], mp[9];
-    for (int i = 0; i < 9; ++i) src[i] = -(ur / r) * meq[i] + sp[i];
+    for (int i = 0; i < 9; ++i) src[i] = -over_r(ur, r) * meq[i] + sp[i];
     for (int i = 0; i < 9; ++i) mp[i] = m[i] - L[i] * (m[i] - meq[i]) + (1.0 - 0.5 * L[i]) * src[i];  /* Eq. 41 */
     /* Eqs. 49-50: m^(1) = (m - m^eq) + S/2 */
     const double sv = L[7], se = L[1];
-    const double gamma = (1.0 - 0.5 * sv) / r;
+    const double gamma = over_r(1.0 - 0.5 * sv, r);
     const double e1 = (m[1] - meq[1]) + 0.5 * src[1];
     const double pxx1 = (m[7] - meq[7]) + 0.5 * src[7];
     const double pxy1 = (m[8] - meq[8]) + 0.5 * src[8];
@@ -362,6 +376,9 @@ static orc_site classify(const orc_params* p, int j, int k, int cr, int cz) {
         if (p->inner == ORC_AXIS) {
             s.j = -1 - s.j;
             s.fr = 1;
+        } else if (p->inner == ORC_AXIS_NODE) {
+            s.j = -s.j; /* the column r = -1 mirrors r = 1 */
+            s.fr = 1;
         } else {
             s.solid = 1;
             s.face = F_IN;
@@ -383,6 +400,9 @@ static double wall_uth(const orc_params* p, int face, int j) {
 }
 
 /* Streaming of the post-collision lattice (fp, gp, hp) into (fn, gn, hn). */
+static void stream_mirror_column(const orc_params* p, const double* fp, const double* gp, const double* hp,
+                                 double* fn, double* gn, double* hn);
+
 void orc_stream(const orc_params* p, const double* fp, const double* gp, const double* hp,
                 double* fn, double* gn, double* hn) {
     const int nr = p->nr, nz = p->nz;
@@ -395,6 +415,8 @@ void orc_stream(const orc_params* p, const double* fp, const double* gp, const d
                 orc_site s = classify(p, j, k, CR[a], CZ[a]);
                 if (s.solid) {
                     fn[find9(-CR[a], -CZ[a]) * n + x] = v;
+                } else if (p->inner == ORC_AXIS_NODE && s.fr) {
+                    /* leaves through the axis (into the mirror column) */
                 } else {
                     const int b = find9(s.fr ? -CR[a] : CR[a], s.fz ? -CZ[a] : CZ[a]);
                     fn[b * n + (size_t)s.k * nr + s.j] = v;
@@ -407,6 +429,7 @@ void orc_stream(const orc_params* p, const double* fp, const double* gp, const d
                     if (s.solid) {
                         gn[find4(-QR[a], -QZ[a]) * n + x] =
                             -v + 0.5 * p->rho0 * wall_uth(p, s.face, j);
+                    } else if (p->inner == ORC_AXIS_NODE && s.fr) {
                     } else {
                         const int b = find4(s.fr ? -QR[a] : QR[a], s.fz ? -QZ[a] : QZ[a]);
                         gn[b * n + (size_t)s.k * nr + s.j] = s.fr ? -v : v;
@@ -421,12 +444,40 @@ void orc_stream(const orc_params* p, const double* fp, const double* gp, const d
                         const double out =
                             p->t_dirichlet[s.face] ? -v + 0.5 * p->t_w[s.face] : v;
                         hn[find4(-QR[a], -QZ[a]) * n + x] = out;
+                    } else if (p->inner == ORC_AXIS_NODE && s.fr) {
                     } else {
                         const int b = find4(s.fr ? -QR[a] : QR[a], s.fz ? -QZ[a] : QZ[a]);
                         hn[b * n + (size_t)s.k * nr + s.j] = v;
                     }
                 }
             }
+        }
+    }
+    if (p->inner == ORC_AXIS_NODE) stream_mirror_column(p, fp, gp, hp, fn, gn, hn);
+}
+
+/* Node-on-axis: the mirror column r = -1 (node 1's post-collision
+ * populations with e_r reversed, g negated) streams into the domain; what
+ * it sends anywhere but into the axis column is dropped. */
+static void stream_mirror_column(const orc_params* p, const double* fp, const double* gp, const double* hp,
+                                 double* fn, double* gn, double* hn) {
+    const int nr = p->nr, nz = p->nz;
+    const size_t n = (size_t)nr * nz;
+    for (int k = 0; k < nz; ++k) {
+        const size_t x1 = (size_t)k * nr + 1; /* node (1, k) */
+        for (int a = 0; a < 9; ++a) {
+            const orc_site s = classify(p, -1, k, CR[a], CZ[a]);
+            if (s.solid || s.fr || s.j < 0) continue;
+            const double v = fp[find9(-CR[a], CZ[a]) * n + x1];
+            fn[find9(CR[a], s.fz ? -CZ[a] : CZ[a]) * n + (size_t)s.k * nr + s.j] = v;
+        }
+        for (int a = 0; a < 4; ++a) {
+            const orc_site s = classify(p, -1, k, QR[a], QZ[a]);
+            if (s.solid || s.fr || s.j < 0) continue;
+            const size_t y = (size_t)s.k * nr + s.j;
+            const int b = find4(QR[a], s.fz ? -QZ[a] : QZ[a]);
+            if (p->swirl) gn[b * n + y] = -gp[find4(-QR[a], QZ[a]) * n + x1];
+            if (p->temperature) hn[b * n + y] = hp[find4(-QR[a], QZ[a]) * n + x1];
         }
     }
 }
@@ -539,7 +590,7 @@ int orc_stats(const orc_params* p, int64_t t, const double* f, const double* g,
                 if (p->temperature) hi[a] = h[a * n + x];
             }
             msum += cell_moments(p, node_r(p, j), a_t, fi, gi, hi, m);
-            bsum += m[0] * m[1] / node_r(p, j);
+            bsum += over_r(m[0] * m[1], node_r(p, j));
             if (speed) speed[x] = sqrt(m[1] * m[1] + m[2] * m[2]);
         }
     }

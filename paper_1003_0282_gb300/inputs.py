@@ -6,7 +6,8 @@ Boltzmann arithmetic: no equilibria, no moments, no collision, no streaming.
 
 A :class:`Problem` describes one axisymmetric domain on the (r, z) half-plane:
 ``nr`` radial by ``nz`` axial nodes, node (j, k) at r = r0 + j + 1/2,
-z = k + 1/2.  Times are in lattice units (dx = dt = 1).
+z = k + 1/2 (r = j with ``inner="axis_node"``).  Times are in lattice units
+(dx = dt = 1).
 
 ``tau`` is the standard BGK relaxation time tau_s; the paper's tau (with
 mu = tau rho c_s^2, Eq. 8 and the line after Eq. 36) is tau_s - 1/2.
@@ -25,7 +26,8 @@ from typing import Dict, List, Optional
 import numpy as np
 
 # inner face kinds
-AXIS = "axis"
+AXIS = "axis"            # axis halfway between node 0 and its mirror: r_j = j + 1/2
+AXIS_NODE = "axis_node"  # node 0 on the axis: r_j = j (Sec. IV A)
 WALL = "wall"
 # axial face kinds
 PERIODIC = "periodic"
@@ -72,6 +74,15 @@ class Problem:
     @property
     def cells(self) -> int:
         return self.nr * self.nz
+
+    def node_radius(self, j):
+        """Radius of column j (array or int)."""
+        return self.r0 + np.asarray(j, dtype=np.float64) + (0.0 if self.inner == AXIS_NODE else 0.5)
+
+    @property
+    def wall_radius(self) -> float:
+        """Radius of the outer (bounce-back) wall."""
+        return self.r0 + self.nr - (0.5 if self.inner == AXIS_NODE else 0.0)
 
 
 # ----------------------------------------------------------------------------- recipes

@@ -1,0 +1,196 @@
+"""Pins of the oracle's node-on-axis grid (Sec. IV A: a node on the axis,
+where the terms in 1/r are set to zero, and specular reflection there).
+
+* streaming equals plain Cartesian streaming on the full (r, z) plane of the
+  mirror-extended lattice (column -j the mirror image of column j, g odd),
+  restricted to r >= 0 -- written here independently of the oracle, for
+  every axial boundary kind;
+* the collision at r = 0 is the textbook BGK update with the He-Shan-Doolen
+  force (every 1/r term zero);
+* Hagen-Poiseuille converges to Eq. 55 (wall half-way, R = N_r - 1/2), and
+  the paper's Womersley case reaches <xi> close to its 0.33 %.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import analytic as A
+from paper_1003_0282_gb300 import inputs as I
+
+E9 = np.array([(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)])
+E4 = np.array([(1, 0), (0, 1), (-1, 0), (0, -1)])
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
+
+
+def golden():
+    out = {}
+    with open(GOLDEN) as fh:
+        for line in fh:
+            parts = line.split()
+            if len(parts) >= 2 and not line.startswith("#"):
+                try:
+                    out[parts[0]] = float(parts[1])
+                except ValueError:
+                    pass
+    return out
+
+
+def index_of(E, cr, cz):
+    return int(np.flatnonzero((E[:, 0] == cr) & (E[:, 1] == cz))[0])
+
+
+def full_plane_stream(pb, E, post, odd=False, h_wall=None):
+    """Push streaming of one distribution on the mirror-extended plane.
+
+    Columns c = -(nr-1) .. nr-1 (column c < 0 holds column -c's populations
+    with e_r reversed, negated when `odd`); the outer walls r = +-(nr - 1/2)
+    and the axial faces follow the Problem (periodic / wall / free surface,
+    a mixed top being a wall where the link crosses at |r| < r_split).  A
+    site outside in z is resolved first (wall: back to the sender; periodic:
+    wrapped; free: mirrored), then a column outside the plane sends the
+    population back to the sender.  Walls are at rest, adiabatic for h."""
+    nr, nz, q = pb.nr, pb.nz, len(E)
+    ncol = 2 * nr - 1
+    full = np.empty((q, nz, ncol))
+    for c in range(-(nr - 1), nr):
+        for b in range(q):
+            if c >= 0:
+                full[b, :, c + nr - 1] = post[b, :, c]
+            else:
+                m = index_of(E, -E[b, 0], E[b, 1])
+                full[b, :, c + nr - 1] = (-1.0 if odd else 1.0) * post[m, :, -c]
+    out = np.full((q, nz, ncol), np.nan)
+    for k in range(nz):
+        for ci in range(ncol):
+            c = ci - (nr - 1)
+            for b in range(q):
+                v = full[b, k, ci]
+                er, ez = E[b]
+                tk, tc, back = k + ez, c + er, False
+                fz = False
+                if tk < 0 or tk >= nz:
+                    kind = pb.z_lo if tk < 0 else pb.z_hi
+                    if kind == "mixed":
+                        kind = "wall" if abs(c + 0.5 * er) < pb.r_split else "free"
+                    if kind == "periodic":
+                        tk %= nz
+                    elif kind == "wall":
+                        back = True
+                    else:
+                        tk = -1 - tk if tk < 0 else 2 * nz - 1 - tk
+                        fz = True
+                if not back and abs(tc) > nr - 1:
+                    back = True
+                if back:
+                    ob = index_of(E, -er, -ez)
+                    out[ob, k, ci] = -v if (odd and h_wall is None) else v
+                else:
+                    nb = index_of(E, er, -ez if fz else ez)
+                    out[nb, tk, tc + nr - 1] = v
+    return out[:, :, nr - 1:]
+
+
+MIXES = [
+    dict(z_lo="periodic", z_hi="periodic"),
+    dict(z_lo="wall", z_hi="wall"),
+    dict(z_lo="wall", z_hi="free"),
+    dict(z_lo="free", z_hi="free"),
+    dict(z_lo="wall", z_hi="mixed", r_split=2.0),
+]
+
+
+@pytest.mark.parametrize("mix", MIXES, ids=lambda m: "-".join(str(v) for v in m.values()))
+def test_stream_is_full_plane_streaming_of_the_mirror_extension(orc, mix):
+    rng = np.random.default_rng(5)
+    pb = I.Problem(nr=5, nz=4, tau=0.8, inner="axis_node", swirl=True, temperature=True, **mix)
+    fp = rng.uniform(-1, 1, (9, pb.nz, pb.nr))
+    gp = rng.uniform(-1, 1, (4, pb.nz, pb.nr))
+    hp = rng.uniform(-1, 1, (4, pb.nz, pb.nr))
+    fn, gn, hn = orc.stream(pb, fp, gp, hp)
+    assert np.array_equal(fn, full_plane_stream(pb, E9, fp))
+    assert np.array_equal(gn, full_plane_stream(pb, E4, gp, odd=True))
+    assert np.array_equal(hn, full_plane_stream(pb, E4, hp, h_wall="adiabatic"))
+
+
+def test_axis_node_collision_is_cartesian(orc):
+    """At r = 0 every 1/r term is zero: the update is the textbook BGK
+    collision with the He-Shan-Doolen force F = (0, a) and the trapezoidal
+    velocity shift, and D2Q4 relaxation for g (Eq. 53 with S^g = 0)."""
+    rng = np.random.default_rng(17)
+    tau_s, a, rho0 = 0.91, 3e-5, 1.0
+    pb = I.Problem(nr=4, nz=4, tau=tau_s, inner="axis_node", swirl=True, rho0=rho0, az0=a)
+    for _ in range(10):
+        u = rng.uniform(-0.04, 0.04, 2)
+        rho = rng.uniform(0.97, 1.03)
+        eu = E9 @ u
+        f = W9 * rho * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * u @ u) * (1 + 0.05 * rng.uniform(-1, 1, 9))
+        g = rng.uniform(-0.01, 0.01, 4)
+        fo, go, _, mom = orc.collide_cell(pb, 0.0, a, f, g)
+        F = np.array([0.0, a])
+        rho_m = f.sum()
+        um = (E9.T @ f + 0.5 * F) / rho_m
+        eum = E9 @ um
+        feq = W9 * rho_m * (1 + 3 * eum + 4.5 * eum ** 2 - 1.5 * um @ um)
+        om = 1.0 / tau_s
+        ref = f - om * (f - feq) + (1 - 0.5 * om) * 3.0 * ((E9 - um) @ F) / rho_m * feq
+        assert np.max(np.abs(fo - ref)) <= 1e-13
+        assert mom[0] == pytest.approx(rho_m, rel=1e-15)
+        uth = g.sum() / rho0
+        geq = rho0 * uth / 4 * (1 + 2 * (E4 @ um))
+        taug = 2 * (tau_s - 0.5) / 3
+        assert np.max(np.abs(go - (g - (g - geq) / (taug + 0.5)))) <= 1e-13
+
+
+def _hp_error(orc, nr, collision="bgk", tau=0.8, umax=0.01):
+    radius = nr - 0.5
+    nu = (tau - 0.5) / 3
+    a = 4 * nu * umax / radius ** 2
+    pb = I.Problem(nr=nr, nz=1, tau=tau, az0=a, inner="axis_node", collision=collision)
+    assert pb.wall_radius == radius
+    st = orc.rest_state(pb)
+    orc.step(st, int(16 * radius ** 2 / (nu * 5.783)))
+    m = orc.moments(st)
+    ua = A.hagen_poiseuille(orc.node_radii(pb), radius, a, nu)
+    assert orc.node_radii(pb)[0] == 0.0
+    assert np.max(np.abs(m[1])) <= 1e-15  # u_r stays zero
+    return math.sqrt(np.sum((m[2, 0] - ua) ** 2) / np.sum(ua ** 2))
+
+
+@pytest.mark.parametrize("collision,min_order", [("bgk", 1.55), ("mrt", 1.95)])
+def test_axis_node_hagen_poiseuille_convergence(orc, collision, min_order):
+    errs = [_hp_error(orc, n, collision) for n in (8, 16, 32)]
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[-1] <= 3e-3
+    assert all(o >= min_order for o in orders), orders
+
+
+@pytest.mark.parametrize("collision,bound", [("bgk", 0.0065), ("mrt", 0.0045)])
+def test_axis_node_womersley_paper_case(orc, collision, bound):
+    """Sec. IV A's case (T = 1200, mu = 0.1/3, a0 = 1e-3/3, ten periods from
+    rest) with a node on the axis; 21 nodes put the half-way wall at
+    R = 20.5.  The paper reports <xi> = 0.33 % with Zou-He walls; here
+    bounce-back gives 0.55 % (BGK) and 0.40 % (MRT)."""
+    g = golden()
+    period, mu = int(g["wom_T"]), g["wom_mu"]
+    pb = I.Problem(nr=21, nz=1, tau=3 * mu + 0.5, az0=g["wom_a0"], omega_t=2 * math.pi / period,
+                   inner="axis_node", collision=collision)
+    radius = pb.wall_radius
+    st = orc.rest_state(pb)
+    periods = int(g["wom_periods"])
+    r = orc.node_radii(pb)
+    xis = []
+    for n in range(16):
+        orc.step(st, (periods - 1) * period + n * period // 16 - st.t)
+        ua = A.womersley(r, st.t, radius, pb.az0, 1.0, pb.omega_t, mu)
+        xis.append(A.xi(orc.moments(st)[2, 0], ua))
+    assert np.mean(xis) <= bound
+
+
+def test_axis_node_needs_the_axis(orc):
+    with pytest.raises(Exception):
+        orc.rest_state(I.Problem(nr=4, nz=4, tau=0.8, inner="axis_node", r0=1.0))
+    with pytest.raises(Exception):
+        orc.rest_state(I.Problem(nr=1, nz=4, tau=0.8, inner="axis_node"))

@@ -18,24 +18,24 @@ MUTATIONS = {
     "half force dropped from u_z (Eq. 15)":
         ("const double uz = (sz + 0.5 * fext_z) / s0;", "const double uz = sz / s0;"),
     "sign of the radial rate term (Eq. 13)":
-        ("(1.0 + tau * CR[a] / r) / (tau + 0.5)", "(1.0 - tau * CR[a] / r) / (tau + 0.5)"),
+        ("(1.0 + over_r(tau * CR[a], r)) / (tau + 0.5)", "(1.0 - over_r(tau * CR[a], r)) / (tau + 0.5)"),
     "mu/r^2 dropped from the u_r denominator (Eq. 16)":
-        ("/ (s0 + mu0 / (r * r));", "/ s0;"),
+        ("/ (s0 + over_r2(mu0, r));", "/ s0;"),
     "sign in the density (Eq. 17)":
-        ("s0 / (1.0 + 0.5 * ur / r)", "s0 / (1.0 - 0.5 * ur / r)"),
+        ("s0 / (1.0 + over_r(0.5 * ur, r))", "s0 / (1.0 - over_r(0.5 * ur, r))"),
     "sign of u_r/r in the source (Eq. 12)":
-        ("- ur / r) * feq;", "+ ur / r) * feq;"),
+        ("- over_r(ur, r)) * feq;", "+ over_r(ur, r)) * feq;"),
     "factor 2 in F_r (Eq. 12)":
-        ("const double fr = -2.0 * mu0", "const double fr = -1.0 * mu0"),
+        ("const double fr = over_r2(-2.0 * mu0", "const double fr = over_r2(-1.0 * mu0"),
     "inertial force dropped (Sec. III C)":
-        ("+ p->rho0 * uth * uth / r;\n    double fz", ";\n    double fz"),
+        ("+ over_r(p->rho0 * uth * uth, r);\n    double fz", ";\n    double fz"),
     "second-order equilibrium coefficient (Eq. 6)":
         ("4.5 * eu * eu - 1.5 * usq);\n            const double src",
          "3.0 * eu * eu - 1.5 * usq);\n            const double src"),
     "trapezoidal factor of the source (Eq. 13)":
         ("(1.0 - 0.5 * om) * src;", "src;"),
     "nu/r term of S^g dropped (Eq. 54)":
-        ("(2.0 * ur + nu / r) * geq", "(2.0 * ur) * geq"),
+        ("(2.0 * ur + over_r(nu, r)) * geq", "(2.0 * ur) * geq"),
     "tau_g = tau instead of 2 tau / 3":
         ("const double taug = 2.0 * tau / 3.0;", "const double taug = tau;"),
     "g not odd across the axis":
@@ -43,9 +43,9 @@ MUTATIONS = {
     "moving-wall term doubled":
         ("-v + 0.5 * p->rho0 * wall_uth", "-v + 1.0 * p->rho0 * wall_uth"),
     "temperature source dropped":
-        ("const double sh = -(ur / r) * heq;", "const double sh = 0.0 * heq;"),
+        ("const double sh = -over_r(ur, r) * heq;", "const double sh = 0.0 * heq;"),
     "temperature rate without the radial term":
-        ("(1.0 + taut * QR[a] / r) / (taut + 0.5)", "1.0 / (taut + 0.5)"),
+        ("(1.0 + over_r(taut * QR[a], r)) / (taut + 0.5)", "1.0 / (taut + 0.5)"),
     "axis reflection without the r flip":
         ("find9(s.fr ? -CR[a] : CR[a], s.fz ? -CZ[a] : CZ[a])", "find9(CR[a], s.fz ? -CZ[a] : CZ[a])"),
     "mixed top classified by node instead of crossing point":
@@ -57,9 +57,18 @@ MUTATIONS = {
     "MRT: correction of Eq. 50 dropped":
         ("    mp[5] -= gamma * pxy1;\n", ""),
     "MRT: source sign of Eq. 51 taken as printed (+)":
-        ("src[i] = -(ur / r) * meq[i] + sp[i];", "src[i] = (ur / r) * meq[i] + sp[i];"),
+        ("src[i] = -over_r(ur, r) * meq[i] + sp[i];", "src[i] = over_r(ur, r) * meq[i] + sp[i];"),
     "MRT: half-source dropped from m^(1)":
         ("const double pxy1 = (m[8] - meq[8]) + 0.5 * src[8];", "const double pxy1 = (m[8] - meq[8]);"),
+    "node on the axis: mirror column taken from node 0 instead of node 1":
+        ("const size_t x1 = (size_t)k * nr + 1;", "const size_t x1 = (size_t)k * nr + 0;"),
+    "node on the axis: 1/r terms not zeroed at r = 0":
+        ("return r > 0.0 ? x / r : 0.0;", "return r > 0.0 ? x / r : x / 0.5;"),
+    "node on the axis: node 0's outward populations kept":
+        ("} else if (p->inner == ORC_AXIS_NODE && s.fr) {\n                    /* leaves through the axis (into the mirror column) */\n                } else {",
+         "} else {"),
+    "node on the axis: mirror column's g not negated":
+        ("if (p->swirl) gn[b * n + y] = -gp[", "if (p->swirl) gn[b * n + y] = gp["),
     "sign of the buoyancy force":
         ("fz += p->rho0 * p->gbeta * (temp - p->t_ref);", "fz -= p->rho0 * p->gbeta * (temp - p->t_ref);"),
 }
@@ -78,6 +87,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     env = dict(os.environ, AXLBM_ORACLE_LIB=str(lib))
     res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                           os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                          os.path.join(ROOT, "tests", "test_oracle_mrt.py")],
+                          os.path.join(ROOT, "tests", "test_oracle_mrt.py"),
+                          os.path.join(ROOT, "tests", "test_oracle_axis_node.py")],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert res.returncode != 0, f"no pin caught: {name}\n{res.stdout[-2000:]}"
