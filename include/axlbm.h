@@ -13,13 +13,18 @@
  *     rho0 g beta (T - T_ref) added to F_z);
  *   - the axis by specular reflection (Sec. IV A), half-way bounce-back walls,
  *     lids turning about the axis (anti-bounce-back for g), free surfaces and
- *     periodic ends.
+ *     periodic ends;
+ *   - the paper's node-on-axis grid (Sec. IV A) as an alternative inner face:
+ *     node 0 on the axis, every term in 1/r zero there, specular reflection
+ *     by a mirror column at r = -1.
  *
  * Conventions used by every call:
  *   - Lattice units: dx = dt = 1, c_s^2 = 1/3 (Eq. 6).
  *   - Node (j, k), 0 <= j < nr, 0 <= k < nz, sits at r = r0 + j + 1/2,
  *     z = k + 1/2.  The inner face is r = r0 (the axis when r0 = 0), the outer
- *     face r = r0 + nr, the axial faces z = 0 ("lo") and z = nz ("hi").
+ *     face r = r0 + nr, the axial faces z = 0 ("lo") and z = nz ("hi").  With
+ *     AXLBM_INNER_AXIS_NODE node (j, k) sits at r = j and the outer face at
+ *     r = nr - 1/2.
  *   - tau arguments are the standard BGK relaxation time tau_s; the paper's
  *     tau (mu = tau rho c_s^2, Eq. 8) is tau_s - 1/2.
  *   - Host-facing arrays are dense, C order, [field or population][k][j]
@@ -51,7 +56,7 @@
 extern "C" {
 #endif
 
-#define AXLBM_ABI_VERSION 2
+#define AXLBM_ABI_VERSION 3
 
 typedef enum {
     AXLBM_OK = 0,
@@ -74,7 +79,13 @@ typedef enum {
     AXLBM_BF16_DEV = 3
 } axlbm_precision;
 
-enum { AXLBM_INNER_AXIS = 0, AXLBM_INNER_WALL = 1 };
+/* Inner face.  AXLBM_INNER_AXIS: the axis halfway between node 0 and its
+ * mirror image (r_j = j + 1/2).  AXLBM_INNER_WALL: a wall at r = r0 > 0 (an
+ * annulus).  AXLBM_INNER_AXIS_NODE: node 0 on the axis (r_j = j, Sec. IV A):
+ * the terms in 1/r are zero there, the column r = -1 is the mirror image of
+ * column 1 (e_r reversed, g negated) and streams into the axis column, and
+ * what node 0 sends towards r < 0 leaves the domain; needs r0 == 0, nr >= 2. */
+enum { AXLBM_INNER_AXIS = 0, AXLBM_INNER_WALL = 1, AXLBM_INNER_AXIS_NODE = 2 };
 enum {
     AXLBM_Z_PERIODIC = 0, /* both axial faces periodic, or neither */
     AXLBM_Z_WALL = 1,     /* half-way bounce-back; g sees the wall speed Omega r */
@@ -114,7 +125,7 @@ typedef struct {
 } axlbm_forcing;
 
 typedef struct {
-    int32_t inner;          /* AXLBM_INNER_AXIS (needs r0 == 0) or AXLBM_INNER_WALL */
+    int32_t inner;          /* AXLBM_INNER_AXIS or _AXIS_NODE (need r0 == 0), or AXLBM_INNER_WALL */
     int32_t z_lo, z_hi;     /* AXLBM_Z_*; z_lo may not be AXLBM_Z_MIXED */
     int32_t t_dirichlet[4]; /* per face (AXLBM_FACE_*): 1 fixed temperature, 0 adiabatic */
     int32_t reserved;       /* must be 0 */

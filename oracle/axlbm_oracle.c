@@ -394,7 +394,7 @@ static orc_site classify(const orc_params* p, int j, int k, int cr, int cz) {
 static double wall_uth(const orc_params* p, int face, int j) {
     switch (face) {
         case F_IN: return p->omega_w[F_IN] * p->r0;
-        case F_OUT: return p->omega_w[F_OUT] * (p->r0 + p->nr);
+        case F_OUT: return p->omega_w[F_OUT] * (node_r(p, p->nr - 1) + 0.5); /* half-way wall */
         default: return p->omega_w[face] * node_r(p, j);
     }
 }

@@ -171,8 +171,10 @@ bool validate_problem(const axlbm_grid* grid, double tau, const axlbm_forcing* f
     if (!(tau > 0.5) || !isfinite(tau)) return no("tau must be > 1/2");
     if (!(forcing->rho0 > 0.0) || !isfinite(forcing->rho0)) return no("rho0 must be > 0");
     if (grid->with_temperature && !(forcing->tau_t > 0.5)) return no("tau_t must be > 1/2");
-    if (bc->inner != AXLBM_INNER_AXIS && bc->inner != AXLBM_INNER_WALL) return no("bad inner face kind");
-    if (bc->inner == AXLBM_INNER_AXIS && grid->r0 != 0.0) return no("the axis needs r0 == 0");
+    if (bc->inner != AXLBM_INNER_AXIS && bc->inner != AXLBM_INNER_WALL && bc->inner != AXLBM_INNER_AXIS_NODE)
+        return no("bad inner face kind");
+    if (bc->inner != AXLBM_INNER_WALL && grid->r0 != 0.0) return no("the axis needs r0 == 0");
+    if (bc->inner == AXLBM_INNER_AXIS_NODE && grid->nr < 2) return no("a node on the axis needs nr >= 2");
     if (bc->z_lo < 0 || bc->z_lo > 2 || bc->z_hi < 0 || bc->z_hi > 3)
         return no("bad axial face kind (the bottom face cannot be mixed)");
     if ((bc->z_lo == AXLBM_Z_PERIODIC) != (bc->z_hi == AXLBM_Z_PERIODIC)) return no("periodic needs both axial faces periodic");

@@ -63,6 +63,7 @@ struct Plan {
     std::vector<axl::TileRec> tiles[axl::kBatchShapes];
     std::vector<int> tstart[axl::kBatchShapes], tindex[axl::kBatchShapes];
     std::vector<int> ring, rstart;                  // 2 ints per ring node
+    std::vector<int> axis;                          // domains with a node on the axis
     int thmax;
 };
 
@@ -196,6 +197,10 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
         P->rstart.push_back((int)(P->ring.size() / 2));
     }
     L.nring = (int)(P->ring.size() / 2);
+    P->axis.clear();
+    for (int d = 0; d < n; ++d)
+        if (dom[d].boundary.inner == AXLBM_INNER_AXIS_NODE) P->axis.push_back(d);
+    L.naxis = (int)P->axis.size();
     // offsets
     int maxtiles = 0;
     for (int s = 0; s < axl::kBatchShapes; ++s) maxtiles = std::max(maxtiles, L.shape[s].ntiles);
@@ -220,6 +225,8 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
     off += al((size_t)L.nring * 8);
     L.off_rstart = off;
     off += al((size_t)(n + 1) * 4);
+    L.off_axis = off;
+    off += al((size_t)std::max(L.naxis, 1) * 4);
     for (int s = 0; s < axl::kBatchShapes; ++s) {
         L.shape[s].off_tiles = off;
         off += al((size_t)L.shape[s].ntiles * sizeof(axl::TileRec));
@@ -513,6 +520,7 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
         y.col0 = x.col0;
         y.row0 = x.row0;
         y.temperature = x.temperature;
+        y.axis_node = D.boundary.inner == AXLBM_INNER_AXIS_NODE;
         y.r0 = x.r0;
         y.rho0 = D.forcing.rho0;
         y.c = x.cf;
@@ -522,6 +530,7 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
     if (st == AXLBM_OK) st = upload(b, L.off_slots, sd.data(), sd.size() * sizeof(axl::SlotDesc));
     if (st == AXLBM_OK) st = upload(b, L.off_ring, P.ring.data(), P.ring.size() * sizeof(int));
     if (st == AXLBM_OK) st = upload(b, L.off_rstart, P.rstart.data(), P.rstart.size() * sizeof(int));
+    if (st == AXLBM_OK) st = upload(b, L.off_axis, P.axis.data(), P.axis.size() * sizeof(int));
     for (int s = 0; s < axl::kBatchShapes && st == AXLBM_OK; ++s) {
         st = upload(b, L.shape[s].off_tiles, P.tiles[s].data(), P.tiles[s].size() * sizeof(axl::TileRec));
         if (st == AXLBM_OK) st = upload(b, L.shape[s].off_tstart, P.tstart[s].data(), P.tstart[s].size() * sizeof(int));

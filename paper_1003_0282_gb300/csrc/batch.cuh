@@ -35,7 +35,7 @@ struct DomDesc {
 // shared memory by a bulk copy next to the tile's data (16-byte multiple).
 struct __align__(16) SlotDesc {
     int nr, nz, col0, row0;
-    int temperature, pad0, pad1, pad2;
+    int temperature, axis_node, pad1, pad2;  // axis_node: node 0 on the axis (r_j = j)
     double r0, rho0;
     CoefCore<float> c;
 };
@@ -392,7 +392,8 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
             const SlotDesc& D = slots[s * kSlots + q];
             const R az = R(M.az[q]);
             const int jl = j0 + jj - D.col0;
-            const R inv_r = rcp(R(D.r0 + (double)jl + 0.5));
+            const double rj = D.r0 + (double)jl + (D.axis_node ? 0.0 : 0.5);
+            const R inv_r = rj > 0.0 ? rcp(R(rj)) : R(0);
             const S* st = sm + s * STAGE;
             RedR<R> red{R(0), R(0), R(0), 0, 0};
             const bool dth = TH && M.r.th;
@@ -464,6 +465,18 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_batch(const BatchArgs<S, 
             A.dom_az[2 * d] = A.doms[d].az0 * cos(A.doms[d].omega_t * (double)t1);
         __syncthreads();
         if (threadIdx.x == 0) A.clock->t = t1;
+    }
+}
+
+// Node-on-axis domains after an odd step: the mirror column's populations
+// into each axis column (see axis_mirror_row); one block per such domain.
+template <class S, bool SW, bool TH>
+__global__ void __launch_bounds__(kThreads) k_axis_mirror_batch(const BatchArgs<S, float> A, const int* axis_doms) {
+    const DomDesc& D = A.doms[axis_doms[blockIdx.x]];
+    const Geom G = dom_geom(D, A.pitch, A.plane);
+    for (int k = threadIdx.x; k < D.nz; k += blockDim.x) {
+        if (TH && D.temperature) axis_mirror_row<S, SW, true>(A.pop, G, 9, SW ? 13 : 9, k);
+        else axis_mirror_row<S, SW, false>(A.pop, G, 9, SW ? 13 : 9, k);
     }
 }
 

@@ -27,7 +27,8 @@ struct BatchLayout {
     long long pitch, rows, plane;
     int nring;
     size_t off_speed, off_tilepart, off_ringpart, off_result, off_az, off_clock, off_doms, off_slots, off_ring,
-        off_rstart;
+        off_rstart, off_axis;
+    int naxis;  // domains with a node on the axis (listed at off_axis)
     BatchTiles shape[kBatchShapes];
     size_t total;
 };

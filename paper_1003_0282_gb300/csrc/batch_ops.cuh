@@ -133,6 +133,12 @@ cudaError_t batch_step_th(axlbm_batch* b, int check, int residual, cudaEvent_t e
         if (e == cudaSuccess) e = cudaEventRecord(b->join, b->side);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join, 0);
     }
+    if (e == cudaSuccess && b->L.naxis > 0) {
+        k_axis_mirror_batch<S, true, TH><<<b->L.naxis, kThreads, 0, b->stream>>>(
+            A, reinterpret_cast<const int*>(b->mem + b->L.off_axis));
+        *nl += 1;
+        e = cudaGetLastError();
+    }
     return e;
 }
 

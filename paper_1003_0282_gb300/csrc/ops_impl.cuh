@@ -255,14 +255,24 @@ struct Site {
     int fr, fz; // mirrored in r / in z
 };
 
+// Radius of column j: r0 + j + 1/2, or j with a node on the axis (Sec. IV A).
+__host__ __device__ __forceinline__ double node_radius(const Geom& G, int j) {
+    return G.r0 + (double)j + (G.inner == AXLBM_INNER_AXIS_NODE ? 0.0 : 0.5);
+}
+
+// 1/r in R, zero on the axis, where Sec. IV A sets every term in 1/r to zero.
+template <class R>
+__device__ __forceinline__ R inv_of(double r) {
+    return r > 0.0 ? R(1) / R(r) : R(0);
+}
+
 // Where the population leaving fluid node (j, k) with velocity (ex, ez) lands.
 __device__ __forceinline__ Site classify(const Geom& G, int j, int k, int ex, int ez) {
     Site s{0, -1, j + ex, k + ez, 0, 0};
     if (s.k < 0 || s.k >= G.nz) {
         const int face = s.k < 0 ? AXLBM_FACE_LO : AXLBM_FACE_HI;
         int kind = s.k < 0 ? G.z_lo : G.z_hi;
-        if (kind == AXLBM_Z_MIXED)
-            kind = (G.r0 + (double)j + 0.5 + 0.5 * ex < G.r_split) ? AXLBM_Z_WALL : AXLBM_Z_FREE;
+        if (kind == AXLBM_Z_MIXED) kind = (node_radius(G, j) + 0.5 * ex < G.r_split) ? AXLBM_Z_WALL : AXLBM_Z_FREE;
         if (kind == AXLBM_Z_PERIODIC) {
             s.k += s.k < 0 ? G.nz : -G.nz;
         } else if (kind == AXLBM_Z_WALL) {
@@ -278,6 +288,9 @@ __device__ __forceinline__ Site classify(const Geom& G, int j, int k, int ex, in
         if (G.inner == AXLBM_INNER_AXIS) {
             s.j = -1 - s.j;
             s.fr = 1;
+        } else if (G.inner == AXLBM_INNER_AXIS_NODE) {
+            s.j = -s.j;  // the column r = -1 mirrors column 1
+            s.fr = 1;
         } else {
             s.solid = 1;
             s.face = AXLBM_FACE_INNER;
@@ -292,8 +305,8 @@ __device__ __forceinline__ Site classify(const Geom& G, int j, int k, int ex, in
 template <class R>
 __device__ __forceinline__ R wall_uth(const Geom& G, const Coef<R>& C, int face, int j) {
     if (face == AXLBM_FACE_INNER) return C.omega_w[face] * R(G.r0);
-    if (face == AXLBM_FACE_OUTER) return C.omega_w[face] * R(G.r0 + G.nr);
-    return C.omega_w[face] * R(G.r0 + j + 0.5);
+    if (face == AXLBM_FACE_OUTER) return C.omega_w[face] * R(node_radius(G, G.nr - 1) + 0.5);  // half-way wall
+    return C.omega_w[face] * R(node_radius(G, j));
 }
 
 // Value of a D2Q4 population sent into a solid face, in stored (deviation) form.
@@ -362,6 +375,8 @@ __device__ __forceinline__ void push_odd(const KArgs<S, R>& A, int j, int k, con
         const Site s = classify(G, j, k, cr9(a), cz9(a));
         if (s.solid) {
             Codec<S>::store(slot(A.pop, G, opp9(a), j, k), c.d[a]);
+        } else if (G.inner == AXLBM_INNER_AXIS_NODE && s.fr) {
+            // leaves through the axis into the mirror column
         } else {
             const int b = idx9(s.fr ? -cr9(a) : cr9(a), s.fz ? -cz9(a) : cz9(a));
             Codec<S>::store(slot(A.pop, G, b, s.j, s.k), c.d[a]);
@@ -373,6 +388,8 @@ __device__ __forceinline__ void push_odd(const KArgs<S, R>& A, int j, int k, con
             const Site s = classify(G, j, k, cr4(q), cz4(q));
             if (s.solid) {
                 Codec<S>::store(slot(A.pop, G, A.g_plane + opp4(q), j, k), bounce_g(G, A.C, s.face, j, c.g[q]));
+            } else if (G.inner == AXLBM_INNER_AXIS_NODE && s.fr) {
+                // leaves through the axis into the mirror column
             } else {
                 const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
                 Codec<S>::store(slot(A.pop, G, A.g_plane + b, s.j, s.k), s.fr ? -c.g[q] : c.g[q]);
@@ -385,6 +402,8 @@ __device__ __forceinline__ void push_odd(const KArgs<S, R>& A, int j, int k, con
             const Site s = classify(G, j, k, cr4(q), cz4(q));
             if (s.solid) {
                 Codec<S>::store(slot(A.pop, G, A.h_plane + opp4(q), j, k), bounce_h(A.C, s.face, c.h[q]));
+            } else if (G.inner == AXLBM_INNER_AXIS_NODE && s.fr) {
+                // leaves through the axis into the mirror column
             } else {
                 const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
                 Codec<S>::store(slot(A.pop, G, A.h_plane + b, s.j, s.k), c.h[q]);
@@ -480,7 +499,7 @@ __device__ __forceinline__ void advance_clock(Clock* clk, int parity, double az0
 
 template <class R>
 __device__ __forceinline__ R inv_radius(const Geom& G, int j) {
-    return R(1) / R(G.r0 + (double)j + 0.5);
+    return inv_of<R>(node_radius(G, j));
 }
 
 // ---------------------------------------------------------------------------- kernels
@@ -706,7 +725,8 @@ k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
                 break;
             }
             const S* st = sm + s * STAGE;
-            const Sc inv_r = rcp(Sc(G.r0 + (double)j + 0.5));
+            const double rj = node_radius(G, j);
+            const Sc inv_r = rj > 0.0 ? rcp(Sc(rj)) : Sc(0);
 #pragma unroll
             for (int rr = tid / kTileJ; rr < kTileK / NL; rr += kBulkThreads / kTileJ) {
                 bool act[NL];
@@ -850,6 +870,31 @@ __global__ void __launch_bounds__(kThreads) k_frame(const KArgs<S, R> A) {
     }
     if (CHK) block_reduce_store(red, A.partials + 4ll * (A.part_offset + blockIdx.x));
     if (blockIdx.x == 0 && threadIdx.x == 0) advance_clock(A.clock, 1, A.az0, A.omega_t);
+}
+
+// Node on the axis (Sec. IV A), after an odd step (every push done): the
+// mirror column r = -1 sends into the axis column, in direction a with
+// e_r = +1, the mirror image of what column 1 sent into it in direction
+// m(a) (e_r reversed), i.e. the value now in the axis node's slot m(a); g is
+// odd in r.  Where the link from r = -1 comes from beyond a wall (the top
+// or bottom corner), the axis node's own bounce-back already filled slot a.
+// Deviation storage is unchanged by the copy (w_a = w_m(a)).  One thread per
+// row; writes only slots that no other population of this step owns.
+template <class S, bool SW, bool TH>
+__device__ __forceinline__ void axis_mirror_row(S* pop, const Geom& G, int g_plane, int h_plane, int k) {
+    const bool lo_wall = G.z_lo == AXLBM_Z_WALL;
+    const bool hi_wall = G.z_hi == AXLBM_Z_WALL || G.z_hi == AXLBM_Z_MIXED;  // crossing at r = -1/2: crystal
+    *slot(pop, G, 1, 0, k) = *slot(pop, G, 3, 0, k);                                 // (1, 0) <- (-1, 0)
+    if (!(k == 0 && lo_wall)) *slot(pop, G, 5, 0, k) = *slot(pop, G, 6, 0, k);         // (1, 1) <- (-1, 1)
+    if (!(k == G.nz - 1 && hi_wall)) *slot(pop, G, 8, 0, k) = *slot(pop, G, 7, 0, k);  // (1, -1) <- (-1, -1)
+    if (SW) Codec<S>::store(slot(pop, G, g_plane + 0, 0, k), -Codec<S>::load(slot(pop, G, g_plane + 2, 0, k)));
+    if (TH) *slot(pop, G, h_plane + 0, 0, k) = *slot(pop, G, h_plane + 2, 0, k);
+}
+
+template <class S, class R, bool SW, bool TH>
+__global__ void __launch_bounds__(kThreads) k_axis_mirror(const KArgs<S, R> A) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < A.G.nz) axis_mirror_row<S, SW, TH>(A.pop, A.G, A.g_plane, A.h_plane, k);
 }
 
 // Macroscopic fields (Eqs. 16-17) at the current level, in either layout.
@@ -1110,6 +1155,11 @@ cudaError_t step_sw(axlbm_handle* h, int check, int residual, cudaEvent_t ev0, c
         *nlaunch += 1;
         if (check) h->check_parts = blocks + L.frame_blocks;
         e = cudaGetLastError();
+        if (e == cudaSuccess && h->bc.inner == AXLBM_INNER_AXIS_NODE) {
+            k_axis_mirror<S, R, SW, TH><<<(h->G.nz + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(A);
+            *nlaunch += 1;
+            e = cudaGetLastError();
+        }
     }
     return e;
 }

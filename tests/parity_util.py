@@ -22,6 +22,10 @@ BOUNDARY_MIXES = {
     "crystal": dict(inner="axis", z_lo="wall", z_hi="mixed", r_split=0.4),  # r_split scaled by nr below
     "annulus-mixed": dict(inner="wall", r0=5.0, z_lo="wall", z_hi="mixed", r_split=0.5),
     "annulus-pipe": dict(inner="wall", r0=2.0, z_lo="periodic", z_hi="periodic"),
+    # node on the axis (Sec. IV A)
+    "axis-node-pipe": dict(inner="axis_node", z_lo="periodic", z_hi="periodic"),
+    "axis-node-crystal": dict(inner="axis_node", z_lo="wall", z_hi="mixed", r_split=0.4),
+    "axis-node-free-top": dict(inner="axis_node", z_lo="free", z_hi="free"),
 }
 
 
@@ -77,7 +81,8 @@ def window_oracle(pops, pb, j0, k0, steps, t0):
     s = steps
     ja, jb = max(0, j0 - s), min(pb.nr, j0 + s + 1)
     inner = pb.inner if ja == 0 else "wall"
-    r0 = pb.r0 + ja
+    # a window away from the axis is an annulus with the same node radii
+    r0 = pb.r0 + ja - (0.5 if (pb.inner == "axis_node" and ja > 0) else 0.0)
     # z rows (periodic domains wrap; walls clip)
     if pb.z_lo == "periodic":
         rows = [(k0 + d) % pb.nz for d in range(-s, s + 1)] if pb.nz >= 2 * s + 1 else list(range(pb.nz))

@@ -189,6 +189,24 @@ def test_axis_node_womersley_paper_case(orc, collision, bound):
     assert np.mean(xis) <= bound
 
 
+def test_axis_node_solid_body_rotation(orc):
+    """A closed cylinder whose walls turn at Omega spins up to u_theta = Omega r
+    with the half-way side wall at R = N_r - 1/2 (it moves at Omega R); on
+    the axis node u_theta = 0 exactly (g is odd in r)."""
+    nr, nz, nu = 16, 12, 0.1
+    om = 0.02 / nr
+    pb = I.Problem(nr=nr, nz=nz, tau=3 * nu + 0.5, z_lo="wall", z_hi="wall", swirl=True, inner="axis_node",
+                   omega={"outer": om, "lo": om, "hi": om})
+    st = orc.rest_state(pb)
+    orc.step(st, 12000)
+    m = orc.moments(st)
+    r = orc.node_radii(pb)
+    err = np.abs(m[3] - om * r) / (om * pb.wall_radius)
+    assert np.max(err) <= 5e-3          # the node next to the axis carries ~0.3 %
+    assert np.max(err[:, 4:]) <= 1e-3   # away from the axis
+    assert np.max(np.abs(m[3, :, 0])) <= 1e-15
+
+
 def test_axis_node_needs_the_axis(orc):
     with pytest.raises(Exception):
         orc.rest_state(I.Problem(nr=4, nz=4, tau=0.8, inner="axis_node", r0=1.0))

@@ -69,6 +69,8 @@ MUTATIONS = {
          "} else {"),
     "node on the axis: mirror column's g not negated":
         ("if (p->swirl) gn[b * n + y] = -gp[", "if (p->swirl) gn[b * n + y] = gp["),
+    "node on the axis: outer wall speed taken at r0 + nr":
+        ("(node_r(p, p->nr - 1) + 0.5); /* half-way wall */", "(p->r0 + p->nr);"),
     "sign of the buoyancy force":
         ("fz += p->rho0 * p->gbeta * (temp - p->t_ref);", "fz -= p->rho0 * p->gbeta * (temp - p->t_ref);"),
 }
