@@ -90,9 +90,21 @@ enum {
     AXLBM_Z_PERIODIC = 0, /* both axial faces periodic, or neither */
     AXLBM_Z_WALL = 1,     /* half-way bounce-back; g sees the wall speed Omega r */
     AXLBM_Z_FREE = 2,     /* free surface: mirror in z (zero normal gradient) */
-    AXLBM_Z_MIXED = 3     /* "hi" only: wall where the link crosses at r < r_split
+    AXLBM_Z_MIXED = 3,    /* "hi" only: wall where the link crosses at r < r_split
                              (crystal disk), free surface beyond */
+    AXLBM_Z_NEE = 4       /* wet wall: node row 0 (lo) or nz - 1 (hi) lies on the wall and is
+                             rebuilt after every step by non-equilibrium extrapolation from the
+                             next row inwards (see AXLBM_OUTER_NEE); needs nz >= 3 */
 };
+/* Outer face (axlbm_boundary.outer).  AXLBM_OUTER_BB: half-way bounce-back
+ * wall at r_{nr-1} + 1/2.  AXLBM_OUTER_NEE: wet wall on column nr - 1 (the
+ * wall radius is r_{nr-1}), rebuilt after every step by non-equilibrium
+ * extrapolation (the wall treatment the paper uses in Sec. IV B, its Ref.
+ * [59]): f = f^eq(rho_f, 0) + f(x_f) - f^eq(rho_f, u_f), likewise g with the
+ * wall speed Omega r and h with T_w (Dirichlet) or T_f (adiabatic), x_f the
+ * next node inwards (diagonal at a corner of two wet walls, where the side
+ * wall's speed and temperature apply); needs nr >= 3. */
+enum { AXLBM_OUTER_BB = 0, AXLBM_OUTER_NEE = 1 };
 enum { AXLBM_FACE_INNER = 0, AXLBM_FACE_OUTER = 1, AXLBM_FACE_LO = 2, AXLBM_FACE_HI = 3 };
 
 /* Collision model of f.  AXLBM_MRT: moment-space relaxation with the source
@@ -128,7 +140,7 @@ typedef struct {
     int32_t inner;          /* AXLBM_INNER_AXIS or _AXIS_NODE (need r0 == 0), or AXLBM_INNER_WALL */
     int32_t z_lo, z_hi;     /* AXLBM_Z_*; z_lo may not be AXLBM_Z_MIXED */
     int32_t t_dirichlet[4]; /* per face (AXLBM_FACE_*): 1 fixed temperature, 0 adiabatic */
-    int32_t reserved;       /* must be 0 */
+    int32_t outer;          /* AXLBM_OUTER_BB (0) or AXLBM_OUTER_NEE */
     double r_split;         /* AXLBM_Z_MIXED: wall part of the top face is r < r_split */
     double omega[4];        /* per face: angular velocity; u_theta,wall = omega * r */
     double t_wall[4];       /* per face: temperature where t_dirichlet is 1 */

@@ -27,7 +27,8 @@ _lock = threading.Lock()
 _lib = None
 
 INNER = {"axis": 0, "wall": 1, "axis_node": 2}
-ZKIND = {"periodic": 0, "wall": 1, "free": 2, "mixed": 3}
+ZKIND = {"periodic": 0, "wall": 1, "free": 2, "mixed": 3, "nee": 4}
+OUTER = {"wall": 0, "nee": 1}
 FACES = ("inner", "outer", "lo", "hi")
 
 
@@ -36,7 +37,7 @@ class _Params(ctypes.Structure):
         ("nr", ctypes.c_int32), ("nz", ctypes.c_int32), ("inner", ctypes.c_int32),
         ("z_lo", ctypes.c_int32), ("z_hi", ctypes.c_int32), ("swirl", ctypes.c_int32),
         ("temperature", ctypes.c_int32), ("t_dirichlet", ctypes.c_int32 * 4),
-        ("pad", ctypes.c_int32), ("r0", ctypes.c_double), ("tau_s", ctypes.c_double),
+        ("outer", ctypes.c_int32), ("r0", ctypes.c_double), ("tau_s", ctypes.c_double),
         ("tau_t_s", ctypes.c_double), ("rho0", ctypes.c_double), ("az0", ctypes.c_double),
         ("omega_t", ctypes.c_double), ("gbeta", ctypes.c_double), ("t_ref", ctypes.c_double),
         ("r_split", ctypes.c_double), ("omega_w", ctypes.c_double * 4),
@@ -89,6 +90,7 @@ def params(pb) -> _Params:
     p.nr, p.nz = int(pb.nr), int(pb.nz)
     p.inner = INNER[pb.inner]
     p.z_lo, p.z_hi = ZKIND[pb.z_lo], ZKIND[pb.z_hi]
+    p.outer = OUTER[getattr(pb, "outer", "wall")]
     p.swirl, p.temperature = int(bool(pb.swirl)), int(bool(pb.temperature))
     for i, face in enumerate(FACES):
         p.t_dirichlet[i] = int(face in pb.t_wall)

@@ -83,6 +83,10 @@
 #define ORC_WALL 1
 #define ORC_FREE 2
 #define ORC_MIXED 3 /* wall for r < r_split, free surface beyond (top only) */
+#define ORC_NEE 4   /* wet wall: the node row lies on the wall (see nee_rebuild) */
+/* outer face */
+#define ORC_OUTER_BB 0  /* half-way bounce-back wall at r_{nr-1} + 1/2 */
+#define ORC_OUTER_NEE 1 /* wet wall: column nr - 1 lies on the wall */
 /* face ids */
 #define F_IN 0
 #define F_OUT 1
@@ -92,10 +96,10 @@
 typedef struct {
     int32_t nr, nz;
     int32_t inner;              /* ORC_AXIS, ORC_INNER_WALL or ORC_AXIS_NODE */
-    int32_t z_lo, z_hi;         /* ORC_PERIODIC / ORC_WALL / ORC_FREE / ORC_MIXED */
+    int32_t z_lo, z_hi;         /* ORC_PERIODIC / ORC_WALL / ORC_FREE / ORC_MIXED / ORC_NEE */
     int32_t swirl, temperature; /* 0 or 1 */
     int32_t t_dirichlet[4];     /* per face: 1 = fixed T, 0 = adiabatic */
-    int32_t pad;
+    int32_t outer;              /* ORC_OUTER_BB or ORC_OUTER_NEE */
     double r0;                  /* radius of the inner face */
     double tau_s;               /* standard relaxation time = tau + 1/2 */
     double tau_t_s;             /* same for the temperature distribution */
@@ -145,6 +149,11 @@ int orc_validate(const orc_params* p) {
     if (p->inner < ORC_AXIS || p->inner > ORC_AXIS_NODE) return ORC_EINVAL;
     if (p->inner == ORC_INNER_WALL && !(p->r0 >= 0.0)) return ORC_EINVAL;
     if (p->z_lo == ORC_MIXED) return ORC_EINVAL;
+    if (p->z_lo < ORC_PERIODIC || p->z_lo > ORC_NEE || p->z_hi < ORC_PERIODIC || p->z_hi > ORC_NEE) return ORC_EINVAL;
+    if (p->outer != ORC_OUTER_BB && p->outer != ORC_OUTER_NEE) return ORC_EINVAL;
+    /* a wet wall extrapolates from the next node row or column inwards */
+    if (p->outer == ORC_OUTER_NEE && p->nr < 3) return ORC_EINVAL;
+    if ((p->z_lo == ORC_NEE || p->z_hi == ORC_NEE) && p->nz < 3) return ORC_EINVAL;
     if ((p->z_lo == ORC_PERIODIC) != (p->z_hi == ORC_PERIODIC)) return ORC_EINVAL;
     if (p->temperature && !(p->tau_t_s > 0.5)) return ORC_EINVAL;
     if (p->collision != 0 && p->collision != 1) return ORC_EINVAL;
@@ -363,7 +372,8 @@ static orc_site classify(const orc_params* p, int j, int k, int cr, int cz) {
         const int kind = s.k < 0 ? p->z_lo : top_kind_at(p, node_r(p, j) + 0.5 * cr);
         if (kind == ORC_PERIODIC) {
             s.k = ((s.k % p->nz) + p->nz) % p->nz;
-        } else if (kind == ORC_WALL) {
+        } else if (kind == ORC_WALL || kind == ORC_NEE) {
+            /* (a wet-wall row only sends populations out; nee_rebuild replaces it) */
             s.solid = 1;
             s.face = face;
             return s;
@@ -486,6 +496,71 @@ static double force_at(const orc_params* p, int64_t t) {
     return p->az0 * cos(p->omega_t * (double)t);
 }
 
+/* Wet walls: non-equilibrium extrapolation (the treatment the paper takes
+ * from its Ref. [59] for the walls of Sec. IV B).  A wall node's populations
+ * are rebuilt after streaming from the nearest fluid node x_f inwards along
+ * the wall normal (the diagonal one at a corner of two wet walls):
+ *   f_a = f^eq_a(rho_f, u_w) + [f_a(x_f) - f^eq_a(rho_f, u_f)],
+ *   g_a = g^eq_a(u_theta,w; u_w) + [g_a(x_f) - g^eq_a(u_theta,f; u_f)],
+ *   h_a = h^eq_a(T_b; u_w) + [h_a(x_f) - h^eq_a(T_f; u_f)],
+ * with the moments of x_f from Eqs. 16-17 at time level t, u_w = 0 (walls
+ * move only azimuthally), u_theta,w = Omega r of the wall node, T_b = T_w on
+ * a Dirichlet face and T_f on an adiabatic one.  A corner node takes the
+ * side wall's speed and temperature.  A wall node on the axis (node-on-axis
+ * grid) keeps the axis rule for its e_r > 0 populations: they are the
+ * mirror images of its rebuilt e_r < 0 ones (g negated). */
+static void nee_rebuild(const orc_params* p, int64_t t, double* f, double* g, double* h) {
+    const int nr = p->nr, nz = p->nz;
+    const size_t n = (size_t)nr * nz;
+    const int out = p->outer == ORC_OUTER_NEE, lo = p->z_lo == ORC_NEE, hi = p->z_hi == ORC_NEE;
+    if (!out && !lo && !hi) return;
+    const double a_t = force_at(p, t);
+    for (int k = 0; k < nz; ++k) {
+        for (int j = 0; j < nr; ++j) {
+            const int on_out = out && j == nr - 1, on_lo = lo && k == 0, on_hi = hi && k == nz - 1;
+            if (!on_out && !on_lo && !on_hi) continue;
+            const int jf = on_out ? nr - 2 : j;
+            const int kf = on_lo ? 1 : (on_hi ? nz - 2 : k);
+            const int face = on_out ? F_OUT : (on_lo ? F_LO : F_HI);
+            const size_t xb = (size_t)k * nr + j, xf = (size_t)kf * nr + jf;
+            double fi[9], gi[4] = {0, 0, 0, 0}, hi4[4] = {0, 0, 0, 0}, m[5];
+            for (int a = 0; a < 9; ++a) fi[a] = f[a * n + xf];
+            for (int a = 0; a < 4; ++a) {
+                if (p->swirl) gi[a] = g[a * n + xf];
+                if (p->temperature) hi4[a] = h[a * n + xf];
+            }
+            cell_moments(p, node_r(p, jf), a_t, fi, gi, hi4, m);
+            const double rho = m[0], ur = m[1], uz = m[2], uth = m[3], temp = m[4];
+            const double usq = ur * ur + uz * uz;
+            for (int a = 0; a < 9; ++a) {
+                const double eu = CR[a] * ur + CZ[a] * uz;
+                const double feq_f = WT[a] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+                const double feq_w = WT[a] * rho;
+                f[a * n + xb] = feq_w + (fi[a] - feq_f);
+            }
+            const double uth_w = p->omega_w[face] * node_r(p, j);
+            const double t_b = p->t_dirichlet[face] ? p->t_w[face] : temp;
+            for (int a = 0; a < 4; ++a) {
+                const double eu = QR[a] * ur + QZ[a] * uz;
+                if (p->swirl) {
+                    const double geq_f = p->rho0 * uth / 4.0 * (1.0 + 2.0 * eu);
+                    g[a * n + xb] = p->rho0 * uth_w / 4.0 + (gi[a] - geq_f);
+                }
+                if (p->temperature) {
+                    const double heq_f = temp / 4.0 * (1.0 + 2.0 * eu);
+                    h[a * n + xb] = t_b / 4.0 + (hi4[a] - heq_f);
+                }
+            }
+            if (p->inner == ORC_AXIS_NODE && j == 0) {
+                for (int a = 0; a < 9; ++a)
+                    if (CR[a] == 1) f[a * n + xb] = f[find9(-1, CZ[a]) * n + xb];
+                if (p->swirl) g[0 * n + xb] = -g[2 * n + xb];
+                if (p->temperature) h[0 * n + xb] = h[2 * n + xb];
+            }
+        }
+    }
+}
+
 /* n time steps starting at time t0; f, g, h are updated in place. */
 int orc_step(const orc_params* p, int64_t t0, int64_t nsteps, double* f, double* g, double* h) {
     if (orc_validate(p) != ORC_OK) return ORC_EINVAL;
@@ -519,6 +594,7 @@ int orc_step(const orc_params* p, int64_t t0, int64_t nsteps, double* f, double*
             }
         }
         orc_stream(p, fp, gp, hp, f, g, h);
+        nee_rebuild(p, t0 + s + 1, f, g, h);
     }
     free(fp);
     free(gp);

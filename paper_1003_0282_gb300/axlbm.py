@@ -23,11 +23,13 @@ OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED = range(7)
 FP64, FP32, FP16_DEV, BF16_DEV = range(4)
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP16_DEV, "bf16": BF16_DEV}
 INNER_AXIS, INNER_WALL, INNER_AXIS_NODE = 0, 1, 2
-Z_PERIODIC, Z_WALL, Z_FREE, Z_MIXED = range(4)
+Z_PERIODIC, Z_WALL, Z_FREE, Z_MIXED, Z_NEE = range(5)
+OUTER_BB, OUTER_NEE = 0, 1
 RHO, UR, UZ, UTH, T = 1, 2, 4, 8, 16
 F64, F32 = 0, 1
 BGK, MRT = 0, 1
-_ZKIND = {"periodic": Z_PERIODIC, "wall": Z_WALL, "free": Z_FREE, "mixed": Z_MIXED}
+_ZKIND = {"periodic": Z_PERIODIC, "wall": Z_WALL, "free": Z_FREE, "mixed": Z_MIXED, "nee": Z_NEE}
+_OUTER = {"wall": OUTER_BB, "nee": OUTER_NEE}
 _INNER = {"axis": INNER_AXIS, "wall": INNER_WALL, "axis_node": INNER_AXIS_NODE}
 
 
@@ -45,7 +47,7 @@ class axlbm_forcing(ctypes.Structure):
 
 class axlbm_boundary(ctypes.Structure):
     _fields_ = [("inner", ctypes.c_int32), ("z_lo", ctypes.c_int32), ("z_hi", ctypes.c_int32),
-                ("t_dirichlet", ctypes.c_int32 * 4), ("reserved", ctypes.c_int32),
+                ("t_dirichlet", ctypes.c_int32 * 4), ("outer", ctypes.c_int32),
                 ("r_split", ctypes.c_double), ("omega", ctypes.c_double * 4),
                 ("t_wall", ctypes.c_double * 4)]
 
@@ -241,7 +243,7 @@ def structs(pb: "_inputs.Problem", precision: str = "fp32"):
     b = axlbm_boundary()
     b.inner = _INNER[pb.inner]
     b.z_lo, b.z_hi = _ZKIND[pb.z_lo], _ZKIND[pb.z_hi]
-    b.reserved = 0
+    b.outer = _OUTER[getattr(pb, "outer", "wall")]
     b.r_split = float(pb.r_split)
     for i, face in enumerate(_inputs.FACES):
         b.t_dirichlet[i] = int(pb.t_dirichlet(face))

@@ -175,10 +175,12 @@ bool validate_problem(const axlbm_grid* grid, double tau, const axlbm_forcing* f
         return no("bad inner face kind");
     if (bc->inner != AXLBM_INNER_WALL && grid->r0 != 0.0) return no("the axis needs r0 == 0");
     if (bc->inner == AXLBM_INNER_AXIS_NODE && grid->nr < 2) return no("a node on the axis needs nr >= 2");
-    if (bc->z_lo < 0 || bc->z_lo > 2 || bc->z_hi < 0 || bc->z_hi > 3)
+    if (bc->z_lo < 0 || bc->z_lo > AXLBM_Z_NEE || bc->z_lo == AXLBM_Z_MIXED || bc->z_hi < 0 || bc->z_hi > AXLBM_Z_NEE)
         return no("bad axial face kind (the bottom face cannot be mixed)");
     if ((bc->z_lo == AXLBM_Z_PERIODIC) != (bc->z_hi == AXLBM_Z_PERIODIC)) return no("periodic needs both axial faces periodic");
-    if (bc->reserved != 0) return no("boundary.reserved must be 0");
+    if (bc->outer != AXLBM_OUTER_BB && bc->outer != AXLBM_OUTER_NEE) return no("bad outer face kind");
+    if (bc->outer == AXLBM_OUTER_NEE && grid->nr < 3) return no("a wet outer wall needs nr >= 3");
+    if ((bc->z_lo == AXLBM_Z_NEE || bc->z_hi == AXLBM_Z_NEE) && grid->nz < 3) return no("a wet axial wall needs nz >= 3");
     for (int f = 0; f < 4; ++f) {
         if (bc->t_dirichlet[f] != 0 && bc->t_dirichlet[f] != 1) return no("t_dirichlet must be 0 or 1");
         if (!isfinite(bc->omega[f]) || !isfinite(bc->t_wall[f])) return no("wall values must be finite");
@@ -245,6 +247,7 @@ axlbm_status axlbm_create(const axlbm_grid* grid, double tau, const axlbm_forcin
     h->G.plane = L.plane;
     h->G.r0 = grid->r0;
     h->G.inner = bc->inner;
+    h->G.outer = bc->outer;
     h->G.z_lo = bc->z_lo;
     h->G.z_hi = bc->z_hi;
     h->G.r_split = bc->r_split;

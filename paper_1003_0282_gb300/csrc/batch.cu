@@ -64,6 +64,7 @@ struct Plan {
     std::vector<int> tstart[axl::kBatchShapes], tindex[axl::kBatchShapes];
     std::vector<int> ring, rstart;                  // 2 ints per ring node
     std::vector<int> axis;                          // domains with a node on the axis
+    std::vector<int> nee;                           // domains with a wet wall
     int thmax;
 };
 
@@ -201,6 +202,12 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
     for (int d = 0; d < n; ++d)
         if (dom[d].boundary.inner == AXLBM_INNER_AXIS_NODE) P->axis.push_back(d);
     L.naxis = (int)P->axis.size();
+    P->nee.clear();
+    for (int d = 0; d < n; ++d)
+        if (dom[d].boundary.outer == AXLBM_OUTER_NEE || dom[d].boundary.z_lo == AXLBM_Z_NEE ||
+            dom[d].boundary.z_hi == AXLBM_Z_NEE)
+            P->nee.push_back(d);
+    L.nnee = (int)P->nee.size();
     // offsets
     int maxtiles = 0;
     for (int s = 0; s < axl::kBatchShapes; ++s) maxtiles = std::max(maxtiles, L.shape[s].ntiles);
@@ -227,6 +234,8 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
     off += al((size_t)(n + 1) * 4);
     L.off_axis = off;
     off += al((size_t)std::max(L.naxis, 1) * 4);
+    L.off_nee = off;
+    off += al((size_t)std::max(L.nnee, 1) * 4);
     for (int s = 0; s < axl::kBatchShapes; ++s) {
         L.shape[s].off_tiles = off;
         off += al((size_t)L.shape[s].ntiles * sizeof(axl::TileRec));
@@ -502,6 +511,7 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
         x.col0 = P.col0[d];
         x.row0 = P.row0[d];
         x.inner = D.boundary.inner;
+        x.outer = D.boundary.outer;
         x.z_lo = D.boundary.z_lo;
         x.z_hi = D.boundary.z_hi;
         x.swirl = D.grid.with_swirl;
@@ -531,6 +541,7 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
     if (st == AXLBM_OK) st = upload(b, L.off_ring, P.ring.data(), P.ring.size() * sizeof(int));
     if (st == AXLBM_OK) st = upload(b, L.off_rstart, P.rstart.data(), P.rstart.size() * sizeof(int));
     if (st == AXLBM_OK) st = upload(b, L.off_axis, P.axis.data(), P.axis.size() * sizeof(int));
+    if (st == AXLBM_OK) st = upload(b, L.off_nee, P.nee.data(), P.nee.size() * sizeof(int));
     for (int s = 0; s < axl::kBatchShapes && st == AXLBM_OK; ++s) {
         st = upload(b, L.shape[s].off_tiles, P.tiles[s].data(), P.tiles[s].size() * sizeof(axl::TileRec));
         if (st == AXLBM_OK) st = upload(b, L.shape[s].off_tstart, P.tstart[s].data(), P.tstart[s].size() * sizeof(int));

@@ -24,7 +24,7 @@ constexpr int kRowAlign = 8;  // shelf rows start on multiples of this (>= every
 struct DomDesc {
     int nr, nz, col0, row0;
     int inner, z_lo, z_hi, swirl;
-    int temperature, pad0, pad1, pad2;
+    int temperature, outer, pad1, pad2;
     double r0, r_split;
     double az0, omega_t;
     Coef<float> cf;
@@ -74,6 +74,7 @@ __device__ __forceinline__ Geom dom_geom(const DomDesc& D, long long pitch, long
     G.plane = plane;
     G.r0 = D.r0;
     G.inner = D.inner;
+    G.outer = D.outer;
     G.z_lo = D.z_lo;
     G.z_hi = D.z_hi;
     G.r_split = D.r_split;
@@ -477,6 +478,28 @@ __global__ void __launch_bounds__(kThreads) k_axis_mirror_batch(const BatchArgs<
     for (int k = threadIdx.x; k < D.nz; k += blockDim.x) {
         if (TH && D.temperature) axis_mirror_row<S, SW, true>(A.pop, G, 9, SW ? 13 : 9, k);
         else axis_mirror_row<S, SW, false>(A.pop, G, 9, SW ? 13 : 9, k);
+    }
+}
+
+// Wet walls of the batch after a step (see nee_node); one block per domain
+// with a wet face.
+template <class S, bool SW, bool TH>
+__global__ void __launch_bounds__(kThreads) k_nee_batch(const BatchArgs<S, float> A, const int* nee_doms, int level) {
+    const int d = nee_doms[blockIdx.x];
+    const DomDesc& D = A.doms[d];
+    KArgs<S, float> K;
+    K.pop = A.pop;
+    K.G = dom_geom(D, A.pitch, A.plane);
+    K.C = D.cf;
+    K.az = A.dom_az + 2 * d;
+    K.g_plane = 9;
+    K.h_plane = SW ? 13 : 9;
+    const int n = nee_count(K.G);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int j, k;
+        nee_coord(K.G, i, j, k);
+        if (TH && D.temperature) nee_node<S, float, SW, true>(K, level, j, k);
+        else nee_node<S, float, SW, false>(K, level, j, k);
     }
 }
 

@@ -27,8 +27,9 @@ struct BatchLayout {
     long long pitch, rows, plane;
     int nring;
     size_t off_speed, off_tilepart, off_ringpart, off_result, off_az, off_clock, off_doms, off_slots, off_ring,
-        off_rstart, off_axis;
+        off_rstart, off_axis, off_nee;
     int naxis;  // domains with a node on the axis (listed at off_axis)
+    int nnee;   // domains with a wet wall (listed at off_nee)
     BatchTiles shape[kBatchShapes];
     size_t total;
 };

@@ -49,6 +49,7 @@ KArgs<S, R> domain_args(axlbm_batch* b, int d) {
     K.G.plane = L.plane;
     K.G.r0 = D.grid.r0;
     K.G.inner = D.boundary.inner;
+    K.G.outer = D.boundary.outer;
     K.G.z_lo = D.boundary.z_lo;
     K.G.z_hi = D.boundary.z_hi;
     K.G.r_split = D.boundary.r_split;
@@ -101,6 +102,12 @@ cudaError_t batch_step_th(axlbm_batch* b, int check, int residual, cudaEvent_t e
         e = check ? launch_bulk_batch_shape<S, R, TH, 0, true>(b, A) : launch_bulk_batch_shape<S, R, TH, 0, false>(b, A);
         if (ev1) cudaEventRecord(ev1, b->stream);
         *nl = 1;
+        if (e == cudaSuccess && b->L.nnee > 0) {
+            k_nee_batch<S, true, TH><<<b->L.nnee, kThreads, 0, b->stream>>>(
+                A, reinterpret_cast<const int*>(b->mem + b->L.off_nee), 1);
+            *nl += 1;
+            e = cudaGetLastError();
+        }
         return e;
     }
     // odd step: the interior (bulk) and the outer rings touch disjoint slots.
@@ -136,6 +143,12 @@ cudaError_t batch_step_th(axlbm_batch* b, int check, int residual, cudaEvent_t e
     if (e == cudaSuccess && b->L.naxis > 0) {
         k_axis_mirror_batch<S, true, TH><<<b->L.naxis, kThreads, 0, b->stream>>>(
             A, reinterpret_cast<const int*>(b->mem + b->L.off_axis));
+        *nl += 1;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && b->L.nnee > 0) {
+        k_nee_batch<S, true, TH><<<b->L.nnee, kThreads, 0, b->stream>>>(
+            A, reinterpret_cast<const int*>(b->mem + b->L.off_nee), 0);
         *nl += 1;
         e = cudaGetLastError();
     }

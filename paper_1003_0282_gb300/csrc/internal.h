@@ -25,6 +25,7 @@ struct Geom {
     long long plane;  // elements per population plane
     double r0;
     int inner, z_lo, z_hi;
+    int outer;        // AXLBM_OUTER_BB or AXLBM_OUTER_NEE
     double r_split;
     int col0, row0;   // position of node (0, 0) in the array (non-zero for a domain of a batch)
 };

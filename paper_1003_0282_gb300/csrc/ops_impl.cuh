@@ -275,7 +275,7 @@ __device__ __forceinline__ Site classify(const Geom& G, int j, int k, int ex, in
         if (kind == AXLBM_Z_MIXED) kind = (node_radius(G, j) + 0.5 * ex < G.r_split) ? AXLBM_Z_WALL : AXLBM_Z_FREE;
         if (kind == AXLBM_Z_PERIODIC) {
             s.k += s.k < 0 ? G.nz : -G.nz;
-        } else if (kind == AXLBM_Z_WALL) {
+        } else if (kind == AXLBM_Z_WALL || kind == AXLBM_Z_NEE) {  // (a wet row is rebuilt after the step)
             s.solid = 1;
             s.face = face;
             return s;
@@ -897,6 +897,161 @@ __global__ void __launch_bounds__(kThreads) k_axis_mirror(const KArgs<S, R> A) {
     if (k < A.G.nz) axis_mirror_row<S, SW, TH>(A.pop, A.G, A.g_plane, A.h_plane, k);
 }
 
+// ---------------------------------------------------------------------------- wet walls
+
+// Store the populations of node (j, k) where pull_odd reads them (the inverse
+// of pull_odd: the bounce-back transforms are involutions).  On the node-on-
+// axis grid the mirror column's populations share their slot with the
+// regular ones of the reversed direction and are not stored.
+template <class S, class R, bool SW, bool TH>
+__device__ __forceinline__ void store_pull(const KArgs<S, R>& A, int j, int k, const Cell<R, SW, TH>& c) {
+    const Geom& G = A.G;
+    const bool mirror_col = G.inner == AXLBM_INNER_AXIS_NODE;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const Site s = classify(G, j, k, -cr9(a), -cz9(a));
+        if (s.solid) {
+            Codec<S>::store(slot(A.pop, G, a, j, k), c.d[a]);
+        } else if (!(mirror_col && s.fr)) {
+            const int b = idx9(s.fr ? -cr9(a) : cr9(a), s.fz ? -cz9(a) : cz9(a));
+            Codec<S>::store(slot(A.pop, G, opp9(b), s.j, s.k), c.d[a]);
+        }
+    }
+    if (SW) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const Site s = classify(G, j, k, -cr4(q), -cz4(q));
+            if (s.solid) {
+                Codec<S>::store(slot(A.pop, G, A.g_plane + q, j, k), bounce_g(G, A.C, s.face, j, c.g[q]));
+            } else if (!(mirror_col && s.fr)) {
+                const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
+                Codec<S>::store(slot(A.pop, G, A.g_plane + opp4(b), s.j, s.k), s.fr ? -c.g[q] : c.g[q]);
+            }
+        }
+    }
+    if (TH) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const Site s = classify(G, j, k, -cr4(q), -cz4(q));
+            if (s.solid) {
+                Codec<S>::store(slot(A.pop, G, A.h_plane + q, j, k), bounce_h(A.C, s.face, c.h[q]));
+            } else if (!(mirror_col && s.fr)) {
+                const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
+                Codec<S>::store(slot(A.pop, G, A.h_plane + opp4(b), s.j, s.k), c.h[q]);
+            }
+        }
+    }
+}
+
+// Wall nodes of the wet faces, numbered: the outer column (if wet), then the
+// bottom row, then the top row (without the outer column's corners).
+__host__ __device__ __forceinline__ int nee_count(const Geom& G) {
+    const int out = G.outer == AXLBM_OUTER_NEE, w = G.nr - out;
+    return (out ? G.nz : 0) + (G.z_lo == AXLBM_Z_NEE ? w : 0) + (G.z_hi == AXLBM_Z_NEE ? w : 0);
+}
+__device__ __forceinline__ void nee_coord(const Geom& G, int i, int& j, int& k) {
+    const int out = G.outer == AXLBM_OUTER_NEE, w = G.nr - out;
+    if (out) {
+        if (i < G.nz) {
+            j = G.nr - 1;
+            k = i;
+            return;
+        }
+        i -= G.nz;
+    }
+    if (G.z_lo == AXLBM_Z_NEE) {
+        if (i < w) {
+            j = i;
+            k = 0;
+            return;
+        }
+        i -= w;
+    }
+    j = i;
+    k = G.nz - 1;
+}
+
+// Non-equilibrium extrapolation (the wall treatment of Sec. IV B, from the
+// paper's Ref. [59]) of wall node i after a step, the state being at a level
+// of layout `level` (0: natural, 1: AA odd):
+//   f = f^eq(rho_f, 0) + f(x_f) - f^eq(rho_f, u_f), g = g^eq(u_theta,w; 0) +
+//   g(x_f) - g^eq(u_theta,f; u_f), h = h^eq(T_b; 0) + h(x_f) - h^eq(T_f; u_f),
+// x_f the next node inwards (diagonal at a corner of two wet walls, where the
+// side wall's speed and temperature apply), moments of x_f from Eqs. 16-17 at
+// this level, T_b = T_w on a Dirichlet face, T_f on an adiabatic one.  A wall
+// node on the axis keeps the axis rule: its e_r > 0 populations mirror its
+// e_r < 0 ones.  Each wall node reads only fluid nodes and writes only its
+// own populations.
+template <class S, class R, bool SW, bool TH>
+__device__ __forceinline__ void nee_node(const KArgs<S, R>& A, int level, int j, int k) {
+    const Geom& G = A.G;
+    const CoefCore<R>& C = A.C;
+    const bool on_out = G.outer == AXLBM_OUTER_NEE && j == G.nr - 1;
+    const bool on_lo = G.z_lo == AXLBM_Z_NEE && k == 0, on_hi = G.z_hi == AXLBM_Z_NEE && k == G.nz - 1;
+    const int jf = on_out ? G.nr - 2 : j;
+    const int kf = on_lo ? 1 : (on_hi ? G.nz - 2 : k);
+    const int face = on_out ? AXLBM_FACE_OUTER : (on_lo ? AXLBM_FACE_LO : AXLBM_FACE_HI);
+    Cell<R, SW, TH> c;
+    if (level == 0) load_natural(A, jf, kf, c);
+    else pull_odd(A, jf, kf, c);
+    if (!SW)
+        for (int q = 0; q < 4; ++q) c.g[q] = R(0);
+    if (!TH)
+        for (int q = 0; q < 4; ++q) c.h[q] = R(0);
+    Cell<R, SW, TH> m = c;
+    m.collide(inv_radius<R>(G, jf), C, R(A.az[level]));  // sets rho, u_r, u_z of x_f
+    const R rho = m.rho, ur = m.ur, uz = m.uz, usq = ur * ur + uz * uz;
+    const R uth = ((c.g[0] + c.g[1]) + (c.g[2] + c.g[3])) * C.inv_rho0;
+    const R dtemp = (c.h[0] + c.h[1]) + (c.h[2] + c.h[3]);  // T_f - T_ref
+    Cell<R, SW, TH> w;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const R wa = R(w9(a));
+        const R eu = R(cr9(a)) * ur + R(cz9(a)) * uz;
+        const R feq_f = wa * (rho * (R(1) + R(3) * eu + R(4.5) * eu * eu - R(1.5) * usq) - C.rho0);  // deviations
+        const R feq_w = wa * (rho - C.rho0);
+        w.d[a] = feq_w + (c.d[a] - feq_f);
+    }
+    const R uth_w = A.C.omega_w[face] * R(node_radius(G, j));
+    const R t_b = A.C.t_dir[face] ? A.C.t_w[face] : dtemp + C.t_ref;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const R eu = R(cr4(q)) * ur + R(cz4(q)) * uz;
+        w.g[q] = SW ? C.rho0 * uth_w * R(0.25) + (c.g[q] - C.rho0 * uth * R(0.25) * (R(1) + R(2) * eu)) : R(0);
+        w.h[q] = TH ? t_b * R(0.25) + (c.h[q] - (dtemp + C.t_ref) * R(0.25) * (R(1) + R(2) * eu)) : R(0);
+    }
+    if (G.inner == AXLBM_INNER_AXIS_NODE && j == 0) {
+        w.d[1] = w.d[3];
+        w.d[5] = w.d[6];
+        w.d[8] = w.d[7];
+        w.g[0] = -w.g[2];
+        w.h[0] = w.h[2];
+    }
+    if (level == 0) {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) Codec<S>::store(slot(A.pop, G, a, j, k), w.d[a]);
+        if (SW) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Codec<S>::store(slot(A.pop, G, A.g_plane + q, j, k), w.g[q]);
+        }
+        if (TH) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Codec<S>::store(slot(A.pop, G, A.h_plane + q, j, k), w.h[q]);
+        }
+    } else {
+        store_pull(A, j, k, w);
+    }
+}
+
+template <class S, class R, bool SW, bool TH>
+__global__ void __launch_bounds__(kThreads) k_nee(const KArgs<S, R> A, int level) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nee_count(A.G)) return;
+    int j, k;
+    nee_coord(A.G, i, j, k);
+    nee_node<S, R, SW, TH>(A, level, j, k);
+}
+
 // Macroscopic fields (Eqs. 16-17) at the current level, in either layout.
 template <class S, class R, bool SW, bool TH, class O>
 __global__ void __launch_bounds__(kThreads) k_moments(const KArgs<S, R> A, int parity, unsigned mask, O* out) {
@@ -1160,6 +1315,13 @@ cudaError_t step_sw(axlbm_handle* h, int check, int residual, cudaEvent_t ev0, c
             *nlaunch += 1;
             e = cudaGetLastError();
         }
+    }
+    const int nw = nee_count(h->G);
+    if (e == cudaSuccess && nw > 0) {
+        // the step's kernels are done: rebuild the wet walls at the new level
+        k_nee<S, R, SW, TH><<<(nw + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(A, 1 - h->parity);
+        *nlaunch += 1;
+        e = cudaGetLastError();
     }
     return e;
 }

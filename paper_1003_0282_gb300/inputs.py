@@ -29,10 +29,12 @@ import numpy as np
 AXIS = "axis"            # axis halfway between node 0 and its mirror: r_j = j + 1/2
 AXIS_NODE = "axis_node"  # node 0 on the axis: r_j = j (Sec. IV A)
 WALL = "wall"
-# axial face kinds
+# axial face kinds (WALL too)
 PERIODIC = "periodic"
 FREE = "free"
 MIXED = "mixed"  # top only: wall for r < r_split, free surface beyond
+NEE = "nee"      # wet wall: the node row (or, as ``outer``, the last column) lies on the wall and is
+                 # rebuilt by non-equilibrium extrapolation from its inner neighbour
 
 FACES = ("inner", "outer", "lo", "hi")
 
@@ -47,6 +49,7 @@ class Problem:
     inner: str = AXIS
     z_lo: str = PERIODIC
     z_hi: str = PERIODIC
+    outer: str = WALL               # WALL (half-way bounce-back) or NEE (wet wall on column nr - 1)
     swirl: bool = False
     temperature: bool = False
     tau_t: float = 0.8              # standard relaxation time of the temperature field
@@ -81,8 +84,8 @@ class Problem:
 
     @property
     def wall_radius(self) -> float:
-        """Radius of the outer (bounce-back) wall."""
-        return self.r0 + self.nr - (0.5 if self.inner == AXIS_NODE else 0.0)
+        """Radius of the outer wall (half-way, or on the last column for NEE)."""
+        return float(self.node_radius(self.nr - 1)) + (0.0 if self.outer == NEE else 0.5)
 
 
 # ----------------------------------------------------------------------------- recipes

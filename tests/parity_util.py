@@ -26,6 +26,10 @@ BOUNDARY_MIXES = {
     "axis-node-pipe": dict(inner="axis_node", z_lo="periodic", z_hi="periodic"),
     "axis-node-crystal": dict(inner="axis_node", z_lo="wall", z_hi="mixed", r_split=0.4),
     "axis-node-free-top": dict(inner="axis_node", z_lo="free", z_hi="free"),
+    # wet walls (non-equilibrium extrapolation, Sec. IV B)
+    "nee-cavity": dict(inner="axis", outer="nee", z_lo="nee", z_hi="nee"),
+    "nee-axis-node": dict(inner="axis_node", outer="nee", z_lo="nee", z_hi="mixed", r_split=0.4),
+    "nee-annulus-pipe": dict(inner="wall", r0=3.0, outer="nee", z_lo="periodic", z_hi="periodic"),
 }
 
 
@@ -76,9 +80,11 @@ def window_oracle(pops, pb, j0, k0, steps, t0):
     A window of half-width `steps` around the node is advanced by the oracle.
     Where the window reaches a physical boundary the window uses it; its other
     edges (and a periodic wrap) only corrupt nodes within `steps` of those
-    edges, which the centre node never sees."""
+    edges, which the centre node never sees.  A wet wall rebuilds its nodes
+    from the next node inwards, so information travels one node further;
+    the window has one node of margin for that."""
     f, g, h = pops
-    s = steps
+    s = steps + 1
     ja, jb = max(0, j0 - s), min(pb.nr, j0 + s + 1)
     inner = pb.inner if ja == 0 else "wall"
     # a window away from the axis is an annulus with the same node radii
@@ -94,7 +100,8 @@ def window_oracle(pops, pb, j0, k0, steps, t0):
         z_lo = pb.z_lo if ka == 0 else "wall"
         z_hi = pb.z_hi if kb == pb.nz else "wall"
         kc = k0 - ka
-    sub = dataclasses.replace(pb, nr=jb - ja, nz=len(rows), inner=inner, r0=r0, z_lo=z_lo, z_hi=z_hi)
+    outer = pb.outer if jb == pb.nr else "wall"
+    sub = dataclasses.replace(pb, nr=jb - ja, nz=len(rows), inner=inner, r0=r0, z_lo=z_lo, z_hi=z_hi, outer=outer)
     cut = lambda a: None if a is None else np.ascontiguousarray(a[:, rows, ja:jb])
     st = oracle.State(sub, cut(f), cut(g), cut(h), t=t0)
     oracle.step(st, steps)

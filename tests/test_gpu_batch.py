@@ -204,15 +204,19 @@ def test_batch_mixes_bgk_and_mrt_domains(B):
     batch.close()
 
 
-def test_batch_with_node_on_axis_domains(B):
-    """Domains with a node on the axis (Sec. IV A) beside half-spacing ones,
-    BGK and MRT, against the oracle; the post-odd-step mirror pass runs for
-    the axis-node domains only."""
+def test_batch_with_node_on_axis_and_wet_wall_domains(B):
+    """Domains with a node on the axis (Sec. IV A) and with wet walls (Sec.
+    IV B) beside plain ones, BGK and MRT, against the oracle; the mirror and
+    rebuild passes run for those domains only."""
     doms = mixed_batch()[:4] + [
         dataclasses.replace(I.rotating_lid_cavity(nr=45, aspect=1.4, re=200.0), inner="axis_node"),
         dataclasses.replace(I.wheeler_cell(nr=38, re_x=200.0, prandtl=1.0, grashof=2e4), inner="axis_node",
                             collision="mrt"),
         dataclasses.replace(I.rotating_lid_cavity(nr=30, aspect=2.0, re=150.0), inner="axis_node", z_hi="free"),
+        # wet walls (non-equilibrium extrapolation)
+        dataclasses.replace(I.rotating_lid_cavity(nr=41, aspect=1.5, re=300.0), inner="axis_node", outer="nee",
+                            z_lo="nee", z_hi="nee", collision="mrt"),
+        dataclasses.replace(I.wheeler_cell(nr=36, re_x=150.0, prandtl=1.0, grashof=1e4), outer="nee", z_lo="nee"),
     ]
     batch = B.Batch(doms, "fp32")
     states = []

@@ -71,6 +71,14 @@ MUTATIONS = {
         ("if (p->swirl) gn[b * n + y] = -gp[", "if (p->swirl) gn[b * n + y] = gp["),
     "node on the axis: outer wall speed taken at r0 + nr":
         ("(node_r(p, p->nr - 1) + 0.5); /* half-way wall */", "(p->r0 + p->nr);"),
+    "wet wall: extrapolated from the wall column itself":
+        ("const int jf = on_out ? nr - 2 : j;", "const int jf = on_out ? nr - 1 : j;"),
+    "wet wall: wall speed not imposed on g":
+        ("const double uth_w = p->omega_w[face] * node_r(p, j);", "const double uth_w = 0.0;"),
+    "wet wall: Dirichlet temperature ignored":
+        ("const double t_b = p->t_dirichlet[face] ? p->t_w[face] : temp;", "const double t_b = temp;"),
+    "wet wall: equilibrium at the fluid velocity":
+        ("const double feq_w = WT[a] * rho;", "const double feq_w = feq_f;"),
     "sign of the buoyancy force":
         ("fz += p->rho0 * p->gbeta * (temp - p->t_ref);", "fz -= p->rho0 * p->gbeta * (temp - p->t_ref);"),
 }
@@ -90,6 +98,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                           os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                           os.path.join(ROOT, "tests", "test_oracle_mrt.py"),
-                          os.path.join(ROOT, "tests", "test_oracle_axis_node.py")],
+                          os.path.join(ROOT, "tests", "test_oracle_axis_node.py"),
+                          os.path.join(ROOT, "tests", "test_oracle_nee.py")],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert res.returncode != 0, f"no pin caught: {name}\n{res.stdout[-2000:]}"

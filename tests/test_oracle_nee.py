@@ -1,0 +1,125 @@
+"""Pins of the oracle's wet walls (non-equilibrium extrapolation, the wall
+treatment of Sec. IV B taken from the paper's Ref. [59]).
+
+* after a step every wall node holds f^eq(rho_f, 0) + f(x_f) - f^eq(rho_f,
+  u_f) (likewise g with the wall speed and h with the wall temperature) for
+  the right neighbour x_f, written here from the moments the oracle reports;
+* a wall node turns with the wall (u_theta = Omega r) and carries the wall
+  temperature exactly, and its meridional velocity is zero up to O(F);
+* Hagen-Poiseuille with the wall on the last column converges at second
+  order under MRT, and solid-body rotation is reproduced with wet lids and
+  side wall.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import analytic as A
+from paper_1003_0282_gb300 import inputs as I
+
+E9 = np.array([(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)])
+E4 = np.array([(1, 0), (0, 1), (-1, 0), (0, -1)])
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def feq(rho, u):
+    eu = E9 @ u
+    return W9 * rho * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * (u @ u))
+
+
+@pytest.mark.parametrize("inner", ["axis", "axis_node"])
+def test_wall_nodes_hold_the_extrapolation(orc, inner):
+    from parity_util import seeded_state
+    pb = I.Problem(nr=9, nz=7, tau=0.83, inner=inner, outer="nee", z_lo="nee", z_hi="nee", swirl=True,
+                   temperature=True, tau_t=0.7, rho0=1.0, gbeta=2e-4, t_ref=0.5,
+                   omega={"outer": 0.003, "lo": -0.002, "hi": 0.004}, t_wall={"hi": 1.0})
+    st = seeded_state(pb, 3)
+    orc.step(st, 3)
+    m = orc.moments(st)  # rho, u_r, u_z, u_theta, T at every node
+    r = orc.node_radii(pb)
+    for k in range(pb.nz):
+        for j in range(pb.nr):
+            out, lo, hi = j == pb.nr - 1, k == 0, k == pb.nz - 1
+            if not (out or lo or hi):
+                continue
+            jf, kf = (pb.nr - 2 if out else j), (1 if lo else (pb.nz - 2 if hi else k))
+            face = "outer" if out else ("lo" if lo else "hi")
+            rho, u = m[0, kf, jf], np.array([m[1, kf, jf], m[2, kf, jf]])
+            want_f = feq(rho, np.zeros(2)) + st.f[:, kf, jf] - feq(rho, u)
+            uth_w = pb.omega_of(face) * r[j]
+            want_g = pb.rho0 * uth_w / 4 + st.g[:, kf, jf] - pb.rho0 * m[3, kf, jf] / 4 * (1 + 2 * (E4 @ u))
+            t_b = pb.t_value(face) if pb.t_dirichlet(face) else m[4, kf, jf]
+            want_h = t_b / 4 + st.h[:, kf, jf] - m[4, kf, jf] / 4 * (1 + 2 * (E4 @ u))
+            if inner == "axis_node" and j == 0:  # the axis rule keeps the mirror symmetry
+                for a in (1, 5, 8):
+                    want_f[a] = want_f[{1: 3, 5: 6, 8: 7}[a]]
+                want_g[0], want_h[0] = -want_g[2], want_h[2]
+            assert np.max(np.abs(st.f[:, k, j] - want_f)) <= 1e-14, (j, k)
+            assert np.max(np.abs(st.g[:, k, j] - want_g)) <= 1e-14, (j, k)
+            assert np.max(np.abs(st.h[:, k, j] - want_h)) <= 1e-14, (j, k)
+
+
+def test_wall_nodes_move_with_the_wall(orc):
+    """Moments of a wall node: u_theta = Omega r and T = T_w exactly (the
+    non-equilibrium parts of g and h carry no zeroth moment); the meridional
+    velocity is zero up to the half-force terms of Eqs. 15-16, which the
+    extrapolated non-equilibrium part does not cancel (O(F): at most 4e-4,
+    next to the axis, against a flow of 1e-2)."""
+    from parity_util import seeded_state
+    pb = I.Problem(nr=8, nz=6, tau=0.9, outer="nee", z_lo="nee", z_hi="nee", swirl=True, temperature=True,
+                   tau_t=0.8, omega={"outer": 0.004, "lo": 0.001, "hi": -0.003}, t_wall={"outer": 0.8, "hi": 0.2},
+                   t_ref=0.5)
+    st = seeded_state(pb, 7)
+    orc.step(st, 2)
+    m = orc.moments(st)
+    r = orc.node_radii(pb)
+    walls = [(pb.nr - 1, k, "outer") for k in range(pb.nz)] + \
+            [(j, 0, "lo") for j in range(pb.nr - 1)] + [(j, pb.nz - 1, "hi") for j in range(pb.nr - 1)]
+    for j, k, face in walls:
+        assert abs(m[1, k, j]) <= 1e-3 and abs(m[2, k, j]) <= 1e-3, (j, k)
+        assert m[3, k, j] == pytest.approx(pb.omega_of(face) * r[j], abs=1e-15), (j, k)
+        if pb.t_dirichlet(face):
+            assert m[4, k, j] == pytest.approx(pb.t_value(face), abs=1e-14), (j, k)
+
+
+def _hp_error(orc, nr, collision, tau=0.8, umax=0.01):
+    pb = I.Problem(nr=nr, nz=1, tau=tau, outer="nee", collision=collision)
+    radius = pb.wall_radius
+    nu = (tau - 0.5) / 3
+    pb.az0 = 4 * nu * umax / radius ** 2
+    st = orc.rest_state(pb)
+    orc.step(st, int(16 * radius ** 2 / (nu * 5.783)))
+    m = orc.moments(st)
+    ua = A.hagen_poiseuille(orc.node_radii(pb), radius, pb.az0, nu)
+    assert abs(m[2, 0, -1]) <= 1e-15  # the wall node does not move
+    return math.sqrt(np.sum((m[2, 0] - ua) ** 2) / np.sum(ua ** 2))
+
+
+def test_hagen_poiseuille_with_a_wet_wall(orc):
+    errs = [_hp_error(orc, n, "mrt") for n in (9, 17, 33)]
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[-1] <= 1e-3
+    assert all(o >= 1.75 for o in orders), orders
+    assert _hp_error(orc, 33, "bgk") <= 2e-3
+
+
+def test_solid_body_rotation_with_wet_walls(orc):
+    nr, nz, nu = 17, 13, 0.1
+    om = 0.02 / nr
+    pb = I.Problem(nr=nr, nz=nz, tau=3 * nu + 0.5, outer="nee", z_lo="nee", z_hi="nee", swirl=True,
+                   omega={"outer": om, "lo": om, "hi": om})
+    st = orc.rest_state(pb)
+    orc.step(st, 12000)
+    m = orc.moments(st)
+    r = orc.node_radii(pb)
+    err = np.abs(m[3] - om * r) / (om * pb.wall_radius)
+    assert np.max(err) <= 1e-2
+    assert np.max(err[:, 3:]) <= 1e-3
+
+
+def test_wet_walls_need_room(orc):
+    with pytest.raises(Exception):
+        orc.rest_state(I.Problem(nr=2, nz=4, tau=0.8, outer="nee"))
+    with pytest.raises(Exception):
+        orc.rest_state(I.Problem(nr=4, nz=2, tau=0.8, z_lo="nee", z_hi="nee"))
