@@ -94,16 +94,20 @@ enum {
                              (crystal disk), free surface beyond */
     AXLBM_Z_NEE = 4       /* wet wall: node row 0 (lo) or nz - 1 (hi) lies on the wall and is
                              rebuilt after every step by non-equilibrium extrapolation from the
-                             next row inwards (see AXLBM_OUTER_NEE); needs nz >= 3 */
+                             next rows inwards (see AXLBM_OUTER_NEE); needs nz >= 3, nz >= 4
+                             when both axial faces are wet */
 };
 /* Outer face (axlbm_boundary.outer).  AXLBM_OUTER_BB: half-way bounce-back
  * wall at r_{nr-1} + 1/2.  AXLBM_OUTER_NEE: wet wall on column nr - 1 (the
- * wall radius is r_{nr-1}), rebuilt after every step by non-equilibrium
- * extrapolation (the wall treatment the paper uses in Sec. IV B, its Ref.
- * [59]): f = f^eq(rho_f, 0) + f(x_f) - f^eq(rho_f, u_f), likewise g with the
- * wall speed Omega r and h with T_w (Dirichlet) or T_f (adiabatic), x_f the
- * next node inwards (diagonal at a corner of two wet walls, where the side
- * wall's speed and temperature apply); needs nr >= 3. */
+ * wall radius is r_{nr-1}).  Wet-wall nodes do not collide; after every step
+ * they receive, by non-equilibrium extrapolation (the wall treatment the
+ * paper uses in Sec. IV B, its Ref. [59], post-collision form), the state
+ * they stream next: f_a = f^eq_a(rho_b, 0) + (1 - w_a)(f_a(x_f) -
+ * f^eq_a(rho_f, u_f)), rho_b = 2 rho_f - rho_ff, likewise g with the wall
+ * speed Omega r and h with T_w (Dirichlet) or T_f (adiabatic), w the rates of
+ * Eqs. 13 and 53 at the wall node, x_f and x_ff the next two nodes inwards
+ * (diagonal at a corner of two wet walls, where the side wall's speed and
+ * temperature apply); needs nr >= 3. */
 enum { AXLBM_OUTER_BB = 0, AXLBM_OUTER_NEE = 1 };
 enum { AXLBM_FACE_INNER = 0, AXLBM_FACE_OUTER = 1, AXLBM_FACE_LO = 2, AXLBM_FACE_HI = 3 };
 
@@ -357,6 +361,54 @@ AXLBM_API axlbm_status axlbm_destroy(axlbm_handle* h);
 /* Text of the last error on `h`, or of the last failed axlbm_create when h is
  * NULL.  Never NULL; valid until the next call on the same handle. */
 AXLBM_API const char* axlbm_last_error(const axlbm_handle* h);
+
+/* ------------------------------------------------------------------ warm start
+ * Learned warm start of a batch (not in the paper).  A small U-Net (weights
+ * in BF16, FP32 accumulation; architecture fixed, see csrc/warmstart.cu) maps
+ * each domain's feature vector, broadcast on a 256 (z) x 128 (r) canvas with
+ * the normalised coordinates, to u_r, u_z, u_theta (in units of the lid
+ * speed) and T - T_ref.  The predicted fields are resampled onto each domain
+ * and handed to axlbm_batch_set_fields_all, so the batch starts from their
+ * equilibria instead of from rest.
+ *
+ * Features (AXLBM_WS_FEATURES floats per domain): kind (0 rotating-lid
+ * cavity, 1 Wheeler-type cell), H/R / 3.5, log10(Re) - 3 (Re = Omega_lid
+ * R^2 / nu), log10(1 + Gr) / 6, log10(Pr) / 2 (0 without temperature),
+ * Omega_side / Omega_lid.  Weights: for each of the 11 layers in order, the
+ * kernel [Cout][ky][kx][Cin] then the bias [Cout], BF16 bit patterns;
+ * axlbm_ws_weight_count() values in all. */
+#define AXLBM_WS_FEATURES 6
+typedef struct axlbm_ws axlbm_ws;
+
+typedef struct {
+    int32_t nr, nz;   /* domain nodes */
+    double r_first;   /* radius of column 0 */
+    double r_wall;    /* radius of the side wall (canvas r = 1) */
+    double z_first;   /* height of row 0 */
+    double z_bottom;  /* height of the bottom wall (canvas z = 0) */
+    double height;    /* distance bottom -> top wall (canvas z = 1) */
+    double rho0, u_scale, t_ref;  /* rho = rho0; u = u_scale * canvas; T = t_ref + canvas */
+} axlbm_ws_domain;
+
+/* Values in a weight array. */
+AXLBM_API size_t axlbm_ws_weight_count(void);
+/* Upload the weights (host array of `count` BF16 bit patterns, copied) and set
+ * up work buffers on the current device; work runs on `cuda_stream`.
+ * AXLBM_EINVAL if count != axlbm_ws_weight_count(); AXLBM_ENOMEM; AXLBM_ECUDA. */
+AXLBM_API axlbm_status axlbm_ws_create(const uint16_t* weights, size_t count, void* cuda_stream, axlbm_ws** out);
+/* Canvases of n feature vectors (host, [n][AXLBM_WS_FEATURES]) into the
+ * caller's device array canvas [n][4][256][128] (FP32).  Synchronises. */
+AXLBM_API axlbm_status axlbm_ws_predict(axlbm_ws* w, const float* features, int32_t n, float* canvas);
+/* Resample n canvases (device) onto n domains (host descriptions): fields
+ * rho, u_r, u_z, u_theta, T of each domain, packed as [5][nz][nr] one domain
+ * after another, into the caller's device array (the layout of
+ * axlbm_batch_set_fields_all).  Bilinear in (r / r_wall, (z - z_bottom) /
+ * height), clamped at the canvas edges.  Synchronises. */
+AXLBM_API axlbm_status axlbm_ws_fields(axlbm_ws* w, const float* canvas, int32_t n, const axlbm_ws_domain* doms,
+                                       float* fields);
+AXLBM_API axlbm_status axlbm_ws_destroy(axlbm_ws* w);
+/* Text of the last error on w (w == NULL: of the last failed create). */
+AXLBM_API const char* axlbm_ws_last_error(const axlbm_ws* w);
 
 #ifdef __cplusplus
 }

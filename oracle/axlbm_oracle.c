@@ -154,6 +154,7 @@ int orc_validate(const orc_params* p) {
     /* a wet wall extrapolates from the next node row or column inwards */
     if (p->outer == ORC_OUTER_NEE && p->nr < 3) return ORC_EINVAL;
     if ((p->z_lo == ORC_NEE || p->z_hi == ORC_NEE) && p->nz < 3) return ORC_EINVAL;
+    if (p->z_lo == ORC_NEE && p->z_hi == ORC_NEE && p->nz < 4) return ORC_EINVAL; /* two fluid rows */
     if ((p->z_lo == ORC_PERIODIC) != (p->z_hi == ORC_PERIODIC)) return ORC_EINVAL;
     if (p->temperature && !(p->tau_t_s > 0.5)) return ORC_EINVAL;
     if (p->collision != 0 && p->collision != 1) return ORC_EINVAL;
@@ -496,16 +497,25 @@ static double force_at(const orc_params* p, int64_t t) {
     return p->az0 * cos(p->omega_t * (double)t);
 }
 
+/* Node (j, k) lies on a wet wall. */
+static int on_wet_wall(const orc_params* p, int j, int k) {
+    return (p->outer == ORC_OUTER_NEE && j == p->nr - 1) || (p->z_lo == ORC_NEE && k == 0) ||
+           (p->z_hi == ORC_NEE && k == p->nz - 1);
+}
+
 /* Wet walls: non-equilibrium extrapolation (the treatment the paper takes
- * from its Ref. [59] for the walls of Sec. IV B).  A wall node's populations
- * are rebuilt after streaming from the nearest fluid node x_f inwards along
- * the wall normal (the diagonal one at a corner of two wet walls):
- *   f_a = f^eq_a(rho_f, u_w) + [f_a(x_f) - f^eq_a(rho_f, u_f)],
- *   g_a = g^eq_a(u_theta,w; u_w) + [g_a(x_f) - g^eq_a(u_theta,f; u_f)],
- *   h_a = h^eq_a(T_b; u_w) + [h_a(x_f) - h^eq_a(T_f; u_f)],
- * with the moments of x_f from Eqs. 16-17 at time level t, u_w = 0 (walls
- * move only azimuthally), u_theta,w = Omega r of the wall node, T_b = T_w on
- * a Dirichlet face and T_f on an adiabatic one.  A corner node takes the
+ * from its Ref. [59] for the walls of Sec. IV B), in its post-collision
+ * form.  A wall node does not collide: after streaming its populations are
+ * replaced by the post-collision state it is to stream next,
+ *   f_a = f^eq_a(rho_f, u_w) + (1 - w_a) [f_a(x_f) - f^eq_a(rho_f, u_f)],
+ *   g_a = g^eq_a(u_theta,w; u_w) + (1 - w_g,a) [g_a(x_f) - g^eq_a(u_theta,f; u_f)],
+ *   h_a = h^eq_a(T_b; u_w) + (1 - w_h,a) [h_a(x_f) - h^eq_a(T_f; u_f)],
+ * x_f the nearest fluid node inwards along the wall normal (the diagonal
+ * one at a corner of two wet walls), its moments from Eqs. 16-17 at time
+ * level t, the rates w of Eqs. 13 and 53 at the wall node's radius (also
+ * under MRT), u_w = 0 (walls move only azimuthally), u_theta,w = Omega r of
+ * the wall node, T_b = T_w on a Dirichlet face and T_f on an adiabatic one.
+ * So no body or inertial force acts on a wall node.  A corner node takes the
  * side wall's speed and temperature.  A wall node on the axis (node-on-axis
  * grid) keeps the axis rule for its e_r > 0 populations: they are the
  * mirror images of its rebuilt e_r < 0 ones (g negated). */
@@ -521,34 +531,53 @@ static void nee_rebuild(const orc_params* p, int64_t t, double* f, double* g, do
             if (!on_out && !on_lo && !on_hi) continue;
             const int jf = on_out ? nr - 2 : j;
             const int kf = on_lo ? 1 : (on_hi ? nz - 2 : k);
+            const int jff = on_out ? nr - 3 : j;
+            const int kff = on_lo ? 2 : (on_hi ? nz - 3 : k);
             const int face = on_out ? F_OUT : (on_lo ? F_LO : F_HI);
-            const size_t xb = (size_t)k * nr + j, xf = (size_t)kf * nr + jf;
-            double fi[9], gi[4] = {0, 0, 0, 0}, hi4[4] = {0, 0, 0, 0}, m[5];
-            for (int a = 0; a < 9; ++a) fi[a] = f[a * n + xf];
+            const size_t xb = (size_t)k * nr + j, xf = (size_t)kf * nr + jf, xff = (size_t)kff * nr + jff;
+            double fi[9], gi[4] = {0, 0, 0, 0}, hi4[4] = {0, 0, 0, 0}, m[5], m2[5];
+            double f2[9], g2[4] = {0, 0, 0, 0}, h2[4] = {0, 0, 0, 0};
+            for (int a = 0; a < 9; ++a) {
+                fi[a] = f[a * n + xf];
+                f2[a] = f[a * n + xff];
+            }
             for (int a = 0; a < 4; ++a) {
-                if (p->swirl) gi[a] = g[a * n + xf];
-                if (p->temperature) hi4[a] = h[a * n + xf];
+                if (p->swirl) {
+                    gi[a] = g[a * n + xf];
+                    g2[a] = g[a * n + xff];
+                }
+                if (p->temperature) {
+                    hi4[a] = h[a * n + xf];
+                    h2[a] = h[a * n + xff];
+                }
             }
             cell_moments(p, node_r(p, jf), a_t, fi, gi, hi4, m);
+            cell_moments(p, node_r(p, jff), a_t, f2, g2, h2, m2);
+            const double rho_b = 2.0 * m[0] - m2[0]; /* linear extrapolation of the pressure */
             const double rho = m[0], ur = m[1], uz = m[2], uth = m[3], temp = m[4];
             const double usq = ur * ur + uz * uz;
+            const double rb = node_r(p, j);
+            const double tau = p->tau_s - 0.5, taug = 2.0 * tau / 3.0, taut = p->tau_t_s - 0.5;
             for (int a = 0; a < 9; ++a) {
                 const double eu = CR[a] * ur + CZ[a] * uz;
                 const double feq_f = WT[a] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
-                const double feq_w = WT[a] * rho;
-                f[a * n + xb] = feq_w + (fi[a] - feq_f);
+                const double feq_w = WT[a] * rho_b;
+                const double om = (1.0 + over_r(tau * CR[a], rb)) / (tau + 0.5);
+                f[a * n + xb] = feq_w + (1.0 - om) * (fi[a] - feq_f);
             }
-            const double uth_w = p->omega_w[face] * node_r(p, j);
+            const double uth_w = p->omega_w[face] * rb;
             const double t_b = p->t_dirichlet[face] ? p->t_w[face] : temp;
             for (int a = 0; a < 4; ++a) {
                 const double eu = QR[a] * ur + QZ[a] * uz;
                 if (p->swirl) {
                     const double geq_f = p->rho0 * uth / 4.0 * (1.0 + 2.0 * eu);
-                    g[a * n + xb] = p->rho0 * uth_w / 4.0 + (gi[a] - geq_f);
+                    const double om = (1.0 + over_r(taug * QR[a], rb)) / (taug + 0.5);
+                    g[a * n + xb] = p->rho0 * uth_w / 4.0 + (1.0 - om) * (gi[a] - geq_f);
                 }
                 if (p->temperature) {
                     const double heq_f = temp / 4.0 * (1.0 + 2.0 * eu);
-                    h[a * n + xb] = t_b / 4.0 + (hi4[a] - heq_f);
+                    const double om = (1.0 + over_r(taut * QR[a], rb)) / (taut + 0.5);
+                    h[a * n + xb] = t_b / 4.0 + (1.0 - om) * (hi4[a] - heq_f);
                 }
             }
             if (p->inner == ORC_AXIS_NODE && j == 0) {
@@ -585,7 +614,13 @@ int orc_step(const orc_params* p, int64_t t0, int64_t nsteps, double* f, double*
                     gi[a] = p->swirl ? g[a * n + x] : 0.0;
                     hi[a] = p->temperature ? h[a * n + x] : 0.0;
                 }
-                orc_collide_cell(p, node_r(p, j), a_t, fi, gi, hi, fo, go, ho, NULL);
+                if (on_wet_wall(p, j, k)) { /* holds its post-collision state already */
+                    memcpy(fo, fi, sizeof fo);
+                    memcpy(go, gi, sizeof go);
+                    memcpy(ho, hi, sizeof ho);
+                } else {
+                    orc_collide_cell(p, node_r(p, j), a_t, fi, gi, hi, fo, go, ho, NULL);
+                }
                 for (int a = 0; a < 9; ++a) fp[a * n + x] = fo[a];
                 for (int a = 0; a < 4; ++a) {
                     if (p->swirl) gp[a * n + x] = go[a];

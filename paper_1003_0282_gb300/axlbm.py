@@ -45,6 +45,13 @@ class axlbm_forcing(ctypes.Structure):
                 ("t_init", ctypes.c_double), ("mrt_s_eps", ctypes.c_double), ("mrt_s_q", ctypes.c_double)]
 
 
+class axlbm_ws_domain(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int32), ("nz", ctypes.c_int32), ("r_first", ctypes.c_double),
+                ("r_wall", ctypes.c_double), ("z_first", ctypes.c_double), ("z_bottom", ctypes.c_double),
+                ("height", ctypes.c_double), ("rho0", ctypes.c_double), ("u_scale", ctypes.c_double),
+                ("t_ref", ctypes.c_double)]
+
+
 class axlbm_boundary(ctypes.Structure):
     _fields_ = [("inner", ctypes.c_int32), ("z_lo", ctypes.c_int32), ("z_hi", ctypes.c_int32),
                 ("t_dirichlet", ctypes.c_int32 * 4), ("outer", ctypes.c_int32),
@@ -119,6 +126,17 @@ def lib() -> ctypes.CDLL:
         L.axlbm_batch_destroy.argtypes = [H]
         L.axlbm_batch_last_error.restype = ctypes.c_char_p
         L.axlbm_batch_last_error.argtypes = [H]
+        V = ctypes.c_void_p
+        L.axlbm_ws_weight_count.restype = ctypes.c_size_t
+        L.axlbm_ws_weight_count.argtypes = []
+        L.axlbm_ws_create.argtypes = [V, ctypes.c_size_t, V, ctypes.POINTER(V)]
+        L.axlbm_ws_predict.argtypes = [V, V, ctypes.c_int32, V]
+        L.axlbm_ws_fields.argtypes = [V, V, ctypes.c_int32, ctypes.POINTER(axlbm_ws_domain), V]
+        L.axlbm_ws_destroy.argtypes = [V]
+        L.axlbm_ws_last_error.restype = ctypes.c_char_p
+        L.axlbm_ws_last_error.argtypes = [V]
+        for name in ("axlbm_ws_create", "axlbm_ws_predict", "axlbm_ws_fields", "axlbm_ws_destroy"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("axlbm_batch_state_bytes", "axlbm_batch_create", "axlbm_batch_step", "axlbm_batch_residuals",
                      "axlbm_batch_moments", "axlbm_batch_set_fields", "axlbm_batch_get_populations",
                      "axlbm_batch_set_populations", "axlbm_batch_time", "axlbm_batch_tile_shape",
@@ -520,3 +538,74 @@ class Batch:
     def set_populations(self, d: int, f, g, h=None) -> None:
         cast = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
         axlbm_batch_set_populations(self.handle, d, cast(f), cast(g), cast(h))
+
+
+# ----------------------------------------------------------------------------- warm start
+
+WS_FEATURES = 6
+WS_CANVAS = (256, 128)  # rows (z), columns (r)
+
+
+def ws_domain(pb) -> axlbm_ws_domain:
+    """Canvas geometry of a Problem (see inputs.warm_start_geometry)."""
+    g = _inputs.warm_start_geometry(pb)
+    return axlbm_ws_domain(nr=pb.nr, nz=pb.nz, r_first=g["r_first"], r_wall=g["r_wall"], z_first=g["z_first"],
+                           z_bottom=g["z_bottom"], height=g["height"], rho0=pb.rho0, u_scale=g["u_scale"],
+                           t_ref=pb.t_ref)
+
+
+class WarmStart:
+    """The warm-start network on the current CUDA device (weights: uint16 BF16
+    bit patterns, axlbm_ws_weight_count() of them, packed as in axlbm.h)."""
+
+    def __init__(self, weights, stream=None):
+        import torch
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.uint16).ravel())
+        self.count = int(lib().axlbm_ws_weight_count())
+        if w.size != self.count:
+            raise ValueError(f"need {self.count} weights, got {w.size}")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = lib().axlbm_ws_create(w.ctypes.data, w.size, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != OK:
+            raise AxlbmError(st, lib().axlbm_ws_last_error(None).decode(errors="replace"))
+        self.handle = h
+
+    def _check(self, st):
+        if st != OK:
+            raise AxlbmError(st, lib().axlbm_ws_last_error(self.handle).decode(errors="replace"))
+
+    def predict(self, features):
+        """Canvases [n][4][256][128] (torch FP32 on the device) of features [n][6]."""
+        import torch
+        f = np.ascontiguousarray(np.asarray(features, dtype=np.float32).reshape(-1, WS_FEATURES))
+        out = torch.empty((f.shape[0], 4) + WS_CANVAS, dtype=torch.float32, device="cuda")
+        self._check(lib().axlbm_ws_predict(self.handle, f.ctypes.data, f.shape[0], out.data_ptr()))
+        return out
+
+    def fields(self, canvas, problems):
+        """Packed fields of every problem (torch FP32 on the device, the layout of
+        axlbm_batch_set_fields_all) from their canvases."""
+        import torch
+        doms = (axlbm_ws_domain * len(problems))(*[ws_domain(pb) for pb in problems])
+        out = torch.empty(sum(5 * pb.cells for pb in problems), dtype=torch.float32, device="cuda")
+        self._check(lib().axlbm_ws_fields(self.handle, canvas.data_ptr(), len(problems), doms, out.data_ptr()))
+        return out
+
+    def start(self, batch, problems):
+        """Initialise a Batch (at an even level) from the network's fields."""
+        canvas = self.predict([_inputs.warm_start_features(pb) for pb in problems])
+        fields = self.fields(canvas, problems)
+        axlbm_batch_set_fields_all(batch.handle, fields.data_ptr(), F32, 1)
+        return canvas
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().axlbm_ws_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -181,6 +181,7 @@ bool validate_problem(const axlbm_grid* grid, double tau, const axlbm_forcing* f
     if (bc->outer != AXLBM_OUTER_BB && bc->outer != AXLBM_OUTER_NEE) return no("bad outer face kind");
     if (bc->outer == AXLBM_OUTER_NEE && grid->nr < 3) return no("a wet outer wall needs nr >= 3");
     if ((bc->z_lo == AXLBM_Z_NEE || bc->z_hi == AXLBM_Z_NEE) && grid->nz < 3) return no("a wet axial wall needs nz >= 3");
+    if (bc->z_lo == AXLBM_Z_NEE && bc->z_hi == AXLBM_Z_NEE && grid->nz < 4) return no("two wet axial walls need nz >= 4");
     for (int f = 0; f < 4; ++f) {
         if (bc->t_dirichlet[f] != 0 && bc->t_dirichlet[f] != 1) return no("t_dirichlet must be 0 or 1");
         if (!isfinite(bc->omega[f]) || !isfinite(bc->t_wall[f])) return no("wall values must be finite");

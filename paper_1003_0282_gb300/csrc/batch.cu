@@ -531,6 +531,8 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
         y.row0 = x.row0;
         y.temperature = x.temperature;
         y.axis_node = D.boundary.inner == AXLBM_INNER_AXIS_NODE;
+        y.wet = (D.boundary.outer == AXLBM_OUTER_NEE ? 1 : 0) | (D.boundary.z_lo == AXLBM_Z_NEE ? 2 : 0) |
+                (D.boundary.z_hi == AXLBM_Z_NEE ? 4 : 0);
         y.r0 = x.r0;
         y.rho0 = D.forcing.rho0;
         y.c = x.cf;

@@ -35,7 +35,7 @@ struct DomDesc {
 // shared memory by a bulk copy next to the tile's data (16-byte multiple).
 struct __align__(16) SlotDesc {
     int nr, nz, col0, row0;
-    int temperature, axis_node, pad1, pad2;  // axis_node: node 0 on the axis (r_j = j)
+    int temperature, axis_node, wet, pad2;  // axis_node: node 0 on the axis (r_j = j); wet: 1 outer, 2 lo, 4 hi
     double r0, rho0;
     CoefCore<float> c;
 };
@@ -193,7 +193,7 @@ __device__ __forceinline__ uint32_t batch_tile_bytes(bool th) {
 }
 
 // Update one node pair (or one node) of a tile from its stage.
-template <class S, class R, class RC, bool SW, bool THD, int PAR, bool CHK, int TK, int TJ>
+template <class S, class R, class RC, bool SW, bool THD, int PAR, bool CHK, int TK, int TJ, bool WET>
 __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const SlotDesc& D, const S* st, int k0, int j0,
                                             int jj, int rr, R inv_r, R az, const R* sp_old, RedR<R>& red) {
     constexpr int NL = Lanes<RC>::n;
@@ -233,12 +233,23 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
         }
     }
     c.collide(inv_r, D.c, az);
+    // even step: a wet-wall node holds its post-collision state and keeps it
+    // (copied straight from the stage below instead of its collided state)
+    bool keep[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const int kl = k0 - D.row0 + rr + l * (TK / NL);
+        keep[l] = WET && PAR == 0 && D.wet && act[l] &&
+                  (((D.wet & 1) && jl == D.nr - 1) || ((D.wet & 2) && kl == 0) || ((D.wet & 4) && kl == D.nz - 1));
+    }
     const long long pl = A.plane;
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
         if (!act[l]) continue;
         const long long x = (long long)(k0 + rr + l * (TK / NL)) * A.pitch + (j0 + jj);
-        if (PAR == 0) {
+        if (PAR == 0 && keep[l]) {
+            // stored by the copy below, after the collided state is dead
+        } else if (PAR == 0) {
 #pragma unroll
             for (int a = 0; a < 9; ++a) Codec<S>::store(A.pop + opp9(a) * pl + x, Lanes<RC>::get(c.d[a], l));
             if (SW) {
@@ -275,6 +286,24 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
             red.count += 1;
         }
     }
+    if (WET && PAR == 0 && D.wet) {
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            if (!keep[l]) continue;
+            const long long x = (long long)(k0 + rr + l * (TK / NL)) * A.pitch + (j0 + jj);
+            const S* src = row + l * LROW;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) A.pop[opp9(a) * pl + x] = src[a * TK * BW];
+            if (SW) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) A.pop[(9 + opp4(q)) * pl + x] = src[(9 + q) * TK * BW];
+            }
+            if (THD) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) A.pop[(HP + opp4(q)) * pl + x] = src[(HP + q) * TK * BW];
+            }
+        }
+    }
 }
 
 // Persistent, warp-specialised bulk update of every domain of the batch
@@ -282,8 +311,9 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
 // stages, per tile, the population boxes (TMA), each slot's domain
 // descriptor (bulk copy) and the tile record with the slots' a(t) (plain
 // shared stores), all completing on the stage's full barrier.  SW: every
-// domain carries g; TH: shelves may carry h (per-tile flag).
-template <class S, class R, bool SW, bool TH, int PAR, bool CHK, int TK, int TJ>
+// domain carries g; TH: shelves may carry h (per-tile flag); WET: some domain
+// has a wet wall (its wall nodes keep their state in even steps).
+template <class S, class R, bool SW, bool TH, int PAR, bool CHK, int TK, int TJ, bool WET>
 __global__ void __launch_bounds__(kBulkThreads + 32, 2)
 k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
     constexpr int NS = batch_nstages<S, SW, TH, TK, TJ>();
@@ -400,8 +430,8 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
             const bool dth = TH && M.r.th;
             // one node pair per thread: rows rr0 and rr0 + TK/2 of column jj
             static_assert(kBulkThreads / TJ == TK / 2, "one pair per consumer thread");
-            if (dth) batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old, red);
-            else batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old, red);
+            if (dth) batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old, red);
+            else batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old, red);
             if (CHK) warp_slot_store(red, q, slots + s * kSlots, A.tile_part + 4ll * kSlots * kConsumerWarps * tile);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);

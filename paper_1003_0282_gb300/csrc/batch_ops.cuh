@@ -66,10 +66,10 @@ KArgs<S, R> domain_args(axlbm_batch* b, int d) {
     return K;
 }
 
-template <class S, class R, bool TH, int PAR, bool CHK, int SH>
+template <class S, class R, bool TH, int PAR, bool CHK, int SH, bool WET>
 cudaError_t launch_bulk_batch(axlbm_batch* b, const BatchArgs<S, R>& A) {
     constexpr int TK = kShapeTK[SH], TJ = kShapeTJ[SH];
-    auto kern = k_bulk_batch<S, R, true, TH, PAR, CHK, TK, TJ>;
+    auto kern = k_bulk_batch<S, R, true, TH, PAR, CHK, TK, TJ, WET>;
     constexpr size_t smem = batch_smem_bytes<S, true, TH, TK, TJ>();
     int& grid = b->grid[SH][PAR][CHK ? 1 : 0];
     if (grid == 0) {
@@ -89,7 +89,12 @@ cudaError_t launch_bulk_batch(axlbm_batch* b, const BatchArgs<S, R>& A) {
 
 template <class S, class R, bool TH, int PAR, bool CHK>
 cudaError_t launch_bulk_batch_shape(axlbm_batch* b, const BatchArgs<S, R>& A) {
-    return b->shape == 0 ? launch_bulk_batch<S, R, TH, PAR, CHK, 0>(b, A) : launch_bulk_batch<S, R, TH, PAR, CHK, 1>(b, A);
+    // wet walls matter only in even steps (odd steps leave the rings to the ring kernels)
+    if (PAR == 0 && b->L.nnee > 0)
+        return b->shape == 0 ? launch_bulk_batch<S, R, TH, PAR, CHK, 0, true>(b, A)
+                             : launch_bulk_batch<S, R, TH, PAR, CHK, 1, true>(b, A);
+    return b->shape == 0 ? launch_bulk_batch<S, R, TH, PAR, CHK, 0, false>(b, A)
+                         : launch_bulk_batch<S, R, TH, PAR, CHK, 1, false>(b, A);
 }
 
 template <class S, class R, bool TH>

@@ -260,6 +260,15 @@ __host__ __device__ __forceinline__ double node_radius(const Geom& G, int j) {
     return G.r0 + (double)j + (G.inner == AXLBM_INNER_AXIS_NODE ? 0.0 : 0.5);
 }
 
+// Node (j, k) lies on a wet wall (it does not collide).
+__host__ __device__ __forceinline__ bool on_wet_wall(const Geom& G, int j, int k) {
+    return (G.outer == AXLBM_OUTER_NEE && j == G.nr - 1) || (G.z_lo == AXLBM_Z_NEE && k == 0) ||
+           (G.z_hi == AXLBM_Z_NEE && k == G.nz - 1);
+}
+__host__ __device__ __forceinline__ bool has_wet_wall(const Geom& G) {
+    return G.outer == AXLBM_OUTER_NEE || G.z_lo == AXLBM_Z_NEE || G.z_hi == AXLBM_Z_NEE;
+}
+
 // 1/r in R, zero on the axis, where Sec. IV A sets every term in 1/r to zero.
 template <class R>
 __device__ __forceinline__ R inv_of(double r) {
@@ -767,7 +776,20 @@ k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
                 for (int l = 0; l < NL; ++l) {
                     if (!act[l]) continue;
                     const long long x = (long long)kk[l] * G.pitch + j;
-                    if (PAR == 0) {
+                    if (PAR == 0 && has_wet_wall(G) && on_wet_wall(G, j, kk[l])) {
+                        // a wet-wall node holds its post-collision state and keeps it
+                        const S* src = row + l * LROW;
+#pragma unroll
+                        for (int a = 0; a < 9; ++a) A.pop[opp9(a) * G.plane + x] = src[a * kTileK * BW];
+                        if (SW) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) A.pop[(9 + opp4(q)) * G.plane + x] = src[(9 + q) * kTileK * BW];
+                        }
+                        if (TH) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) A.pop[(HP + opp4(q)) * G.plane + x] = src[(HP + q) * kTileK * BW];
+                        }
+                    } else if (PAR == 0) {
 #pragma unroll
                         for (int a = 0; a < 9; ++a) Codec<S>::store(A.pop + opp9(a) * G.plane + x, Lanes<RC>::get(c.d[a], l));
                         if (SW) {
@@ -852,6 +874,14 @@ __device__ __noinline__ void ring_node(const KArgs<S, R>& A, int j, int k, R az,
     Cell<R, SW, TH> c;
     pull_odd(A, j, k, c);
     const R inv_r = inv_radius<R>(A.G, j);
+    if (on_wet_wall(A.G, j, k)) {
+        // a wet-wall node holds its post-collision state: stream it as it is
+        Cell<R, SW, TH> m = c;
+        m.collide(inv_r, A.C, az);  // moments for the check values
+        push_odd(A, j, k, c);
+        if (CHK) check_cell(A, j, k, inv_r, m, red);
+        return;
+    }
     c.collide(inv_r, A.C, az);
     push_odd(A, j, k, c);
     if (CHK) check_cell(A, j, k, inv_r, c, red);
@@ -972,53 +1002,70 @@ __device__ __forceinline__ void nee_coord(const Geom& G, int i, int& j, int& k) 
 }
 
 // Non-equilibrium extrapolation (the wall treatment of Sec. IV B, from the
-// paper's Ref. [59]) of wall node i after a step, the state being at a level
-// of layout `level` (0: natural, 1: AA odd):
-//   f = f^eq(rho_f, 0) + f(x_f) - f^eq(rho_f, u_f), g = g^eq(u_theta,w; 0) +
-//   g(x_f) - g^eq(u_theta,f; u_f), h = h^eq(T_b; 0) + h(x_f) - h^eq(T_f; u_f),
-// x_f the next node inwards (diagonal at a corner of two wet walls, where the
-// side wall's speed and temperature apply), moments of x_f from Eqs. 16-17 at
-// this level, T_b = T_w on a Dirichlet face, T_f on an adiabatic one.  A wall
-// node on the axis keeps the axis rule: its e_r > 0 populations mirror its
-// e_r < 0 ones.  Each wall node reads only fluid nodes and writes only its
-// own populations.
+// paper's Ref. [59]) in its post-collision form: wall node (j, k) does not
+// collide; after a step, the state being at a level of layout `level` (0:
+// natural, 1: AA odd), it receives the state it streams next,
+//   f_a = f^eq_a(rho_b, 0) + (1 - w_a)(f_a(x_f) - f^eq_a(rho_f, u_f)),
+//   g_a = g^eq_a(u_theta,w; 0) + (1 - w_g,a)(g_a(x_f) - g^eq_a(u_theta,f; u_f)),
+//   h_a = h^eq_a(T_b; 0) + (1 - w_h,a)(h_a(x_f) - h^eq_a(T_f; u_f)),
+// rho_b = 2 rho_f - rho_ff (linear extrapolation of the pressure), x_f and
+// x_ff the next two nodes inwards (diagonal at a corner of two wet walls,
+// where the side wall's speed and temperature apply), moments from Eqs.
+// 16-17 at this level, w the rates of Eqs. 13 and 53 at the wall node,
+// u_theta,w = Omega r, T_b = T_w on a Dirichlet face, T_f on an adiabatic
+// one.  A wall node on the axis keeps the axis rule: its e_r > 0
+// populations mirror its e_r < 0 ones.  Wall nodes read only fluid nodes
+// and write only their own populations.
 template <class S, class R, bool SW, bool TH>
 __device__ __forceinline__ void nee_node(const KArgs<S, R>& A, int level, int j, int k) {
     const Geom& G = A.G;
     const CoefCore<R>& C = A.C;
     const bool on_out = G.outer == AXLBM_OUTER_NEE && j == G.nr - 1;
     const bool on_lo = G.z_lo == AXLBM_Z_NEE && k == 0, on_hi = G.z_hi == AXLBM_Z_NEE && k == G.nz - 1;
-    const int jf = on_out ? G.nr - 2 : j;
-    const int kf = on_lo ? 1 : (on_hi ? G.nz - 2 : k);
+    const int jf = on_out ? G.nr - 2 : j, jff = on_out ? G.nr - 3 : j;
+    const int kf = on_lo ? 1 : (on_hi ? G.nz - 2 : k), kff = on_lo ? 2 : (on_hi ? G.nz - 3 : k);
     const int face = on_out ? AXLBM_FACE_OUTER : (on_lo ? AXLBM_FACE_LO : AXLBM_FACE_HI);
-    Cell<R, SW, TH> c;
-    if (level == 0) load_natural(A, jf, kf, c);
-    else pull_odd(A, jf, kf, c);
-    if (!SW)
-        for (int q = 0; q < 4; ++q) c.g[q] = R(0);
-    if (!TH)
-        for (int q = 0; q < 4; ++q) c.h[q] = R(0);
+    Cell<R, SW, TH> c, c2;
+    if (level == 0) {
+        load_natural(A, jf, kf, c);
+        load_natural(A, jff, kff, c2);
+    } else {
+        pull_odd(A, jf, kf, c);
+        pull_odd(A, jff, kff, c2);
+    }
+    for (int q = 0; q < 4; ++q) {
+        if (!SW) c.g[q] = c2.g[q] = R(0);
+        if (!TH) c.h[q] = c2.h[q] = R(0);
+    }
+    const R az = R(A.az[level]);
     Cell<R, SW, TH> m = c;
-    m.collide(inv_radius<R>(G, jf), C, R(A.az[level]));  // sets rho, u_r, u_z of x_f
+    m.collide(inv_radius<R>(G, jf), C, az);  // sets rho, u_r, u_z of x_f
+    c2.collide(inv_radius<R>(G, jff), C, az);
     const R rho = m.rho, ur = m.ur, uz = m.uz, usq = ur * ur + uz * uz;
+    const R rho_b = R(2) * rho - c2.rho;
     const R uth = ((c.g[0] + c.g[1]) + (c.g[2] + c.g[3])) * C.inv_rho0;
     const R dtemp = (c.h[0] + c.h[1]) + (c.h[2] + c.h[3]);  // T_f - T_ref
+    const R inv_rb = inv_radius<R>(G, j);
     Cell<R, SW, TH> w;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
         const R wa = R(w9(a));
         const R eu = R(cr9(a)) * ur + R(cz9(a)) * uz;
         const R feq_f = wa * (rho * (R(1) + R(3) * eu + R(4.5) * eu * eu - R(1.5) * usq) - C.rho0);  // deviations
-        const R feq_w = wa * (rho - C.rho0);
-        w.d[a] = feq_w + (c.d[a] - feq_f);
+        const R feq_w = wa * (rho_b - C.rho0);
+        const R om = C.c0 + C.c1 * R(cr9(a)) * inv_rb;
+        w.d[a] = feq_w + (R(1) - om) * (c.d[a] - feq_f);
     }
     const R uth_w = A.C.omega_w[face] * R(node_radius(G, j));
     const R t_b = A.C.t_dir[face] ? A.C.t_w[face] : dtemp + C.t_ref;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const R eu = R(cr4(q)) * ur + R(cz4(q)) * uz;
-        w.g[q] = SW ? C.rho0 * uth_w * R(0.25) + (c.g[q] - C.rho0 * uth * R(0.25) * (R(1) + R(2) * eu)) : R(0);
-        w.h[q] = TH ? t_b * R(0.25) + (c.h[q] - (dtemp + C.t_ref) * R(0.25) * (R(1) + R(2) * eu)) : R(0);
+        const R omg = C.g0 + C.g1 * R(cr4(q)) * inv_rb, omh = C.h0 + C.h1 * R(cr4(q)) * inv_rb;
+        w.g[q] = SW ? C.rho0 * uth_w * R(0.25) + (R(1) - omg) * (c.g[q] - C.rho0 * uth * R(0.25) * (R(1) + R(2) * eu))
+                    : R(0);
+        w.h[q] = TH ? t_b * R(0.25) + (R(1) - omh) * (c.h[q] - (dtemp + C.t_ref) * R(0.25) * (R(1) + R(2) * eu))
+                    : R(0);
     }
     if (G.inner == AXLBM_INNER_AXIS_NODE && j == 0) {
         w.d[1] = w.d[3];

@@ -191,6 +191,39 @@ def batch_sweep(seed: int = 20261202, n_cavities: int = 256, n_wheeler: int = 64
     return out
 
 
+# ----------------------------------------------------------------------------- warm-start inputs
+
+
+def warm_start_geometry(pb: Problem) -> Dict[str, float]:
+    """Where a Problem sits on the warm-start canvas: radius of column 0 and of
+    the side wall (canvas r = 1), height of row 0, of the bottom wall (canvas
+    z = 0) and the bottom-to-top distance (canvas z = 1), and the velocity
+    scale (the lid's speed at the side wall)."""
+    z_first = 0.0 if pb.z_lo == NEE else 0.5
+    z_top = (pb.nz - 1) + z_first + (0.0 if pb.z_hi == NEE else 0.5)
+    r_wall = pb.wall_radius
+    return dict(r_first=float(pb.node_radius(0)), r_wall=r_wall, z_first=z_first, z_bottom=0.0, height=z_top,
+                u_scale=pb.omega_of("hi") * r_wall)
+
+
+def warm_start_features(pb: Problem) -> List[float]:
+    """The six features of a Problem for the warm-start network: kind (0 cavity,
+    1 Wheeler-type cell), H/R / 3.5, log10(Re) - 3 with Re = Omega_lid R^2 / nu,
+    log10(1 + Gr) / 6 with Gr = g beta R^3 / nu^2 (dT = 1), log10(Pr) / 2, and
+    Omega_side / Omega_lid."""
+    g = warm_start_geometry(pb)
+    radius = g["r_wall"]
+    nu = (pb.tau - 0.5) / 3.0
+    om = pb.omega_of("hi")
+    re = abs(om) * radius * radius / nu if om != 0.0 else 1.0
+    kind = 1.0 if (pb.temperature or pb.z_hi == MIXED) else 0.0
+    gr = pb.gbeta * radius ** 3 / nu ** 2 if pb.temperature else 0.0
+    pr = nu / ((pb.tau_t - 0.5) / 2.0) if pb.temperature else 1.0
+    ratio = pb.omega_of("outer") / om if om != 0.0 else 0.0
+    return [kind, g["height"] / radius / 3.5, math.log10(re) - 3.0, math.log10(1.0 + max(gr, 0.0)) / 6.0,
+            math.log10(pr) / 2.0, ratio]
+
+
 # ----------------------------------------------------------------------------- random fields
 
 

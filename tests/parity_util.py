@@ -81,10 +81,10 @@ def window_oracle(pops, pb, j0, k0, steps, t0):
     Where the window reaches a physical boundary the window uses it; its other
     edges (and a periodic wrap) only corrupt nodes within `steps` of those
     edges, which the centre node never sees.  A wet wall rebuilds its nodes
-    from the next node inwards, so information travels one node further;
-    the window has one node of margin for that."""
+    from the next two nodes inwards, so information travels two nodes
+    further; the window has that margin."""
     f, g, h = pops
-    s = steps + 1
+    s = steps + 2
     ja, jb = max(0, j0 - s), min(pb.nr, j0 + s + 1)
     inner = pb.inner if ja == 0 else "wall"
     # a window away from the axis is an annulus with the same node radii

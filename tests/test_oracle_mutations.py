@@ -74,11 +74,15 @@ MUTATIONS = {
     "wet wall: extrapolated from the wall column itself":
         ("const int jf = on_out ? nr - 2 : j;", "const int jf = on_out ? nr - 1 : j;"),
     "wet wall: wall speed not imposed on g":
-        ("const double uth_w = p->omega_w[face] * node_r(p, j);", "const double uth_w = 0.0;"),
+        ("const double uth_w = p->omega_w[face] * rb;", "const double uth_w = 0.0;"),
     "wet wall: Dirichlet temperature ignored":
         ("const double t_b = p->t_dirichlet[face] ? p->t_w[face] : temp;", "const double t_b = temp;"),
     "wet wall: equilibrium at the fluid velocity":
-        ("const double feq_w = WT[a] * rho;", "const double feq_w = feq_f;"),
+        ("const double feq_w = WT[a] * rho_b;", "const double feq_w = feq_f;"),
+    "wet wall: non-equilibrium part not relaxed":
+        ("f[a * n + xb] = feq_w + (1.0 - om) * (fi[a] - feq_f);", "f[a * n + xb] = feq_w + (fi[a] - feq_f);"),
+    "wet wall: density not extrapolated":
+        ("const double rho_b = 2.0 * m[0] - m2[0];", "const double rho_b = m[0];"),
     "sign of the buoyancy force":
         ("fz += p->rho0 * p->gbeta * (temp - p->t_ref);", "fz -= p->rho0 * p->gbeta * (temp - p->t_ref);"),
 }
