@@ -47,13 +47,17 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--inner", type=int, default=50, help="lattice time steps per benchmark step")
-    p.add_argument("--workload", choices=["batch", "pipe"], default="batch")
+    p.add_argument("--workload", choices=["batch", "pipe", "warmstart"], default="batch",
+                   help="warmstart: time to a steady state from rest and from the warm-start network")
     p.add_argument("--scale", type=float, default=1.0, help="batch: shrink every domain (small profiling cases)")
     p.add_argument("--nr", type=int, default=4096)
     p.add_argument("--nz", type=int, default=8192)
     p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--tol", type=float, default=1e-7, help="warmstart: per-domain residual (Eq. 57) of a steady state")
+    p.add_argument("--max-steps", type=int, default=1500000, help="warmstart: give up after this many steps")
+    p.add_argument("--ws-seed", type=int, default=8, help="warmstart: seed of the held-out sweep")
     p.add_argument("--shard", choices=["weak", "strong"], default="weak",
                    help="batch under torchrun: a sweep per rank (weak) or one sweep split over the ranks (strong)")
     return p.parse_args()
@@ -184,10 +188,80 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_warmstart(args):
+    """Steps and wall time until every domain of a held-out sweep reaches a
+    steady state (residual of Eq. 57 <= tol), from rest and from the fields of
+    the warm-start network (its inference and the initialisation inside the
+    timed region).  Domains that converge in neither arm within max_steps are
+    reported and left out of both."""
+    import torch
+    from paper_1003_0282_gb300 import axlbm as B
+    from paper_1003_0282_gb300 import inputs as I
+
+    path = os.path.join(ROOT, "paper_1003_0282_gb300", "warm_start_weights.npz")
+    if not os.path.exists(path):
+        print(json.dumps({"workload": "warmstart", "unavailable": "no trained weights (run warm_start_train)"}))
+        return
+    weights = np.load(path)["weights"]
+    scale = args.scale if args.scale != 1.0 else 0.5
+    probs = I.batch_sweep(seed=args.ws_seed, scale=scale)
+    chunk = 5000
+    arms = {}
+    for arm in ("rest", "warm"):
+        batch = B.Batch(probs, "fp32")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if arm == "warm":
+            ws = B.WarmStart(weights)
+            ws.start(batch, probs)
+            ws.close()
+        reached = np.full(len(probs), -1, dtype=np.int64)
+        blown = np.zeros(len(probs), dtype=bool)
+        when = np.full(len(probs), np.nan)
+        steps = 0
+        while steps < args.max_steps and np.any((reached < 0) & ~blown):
+            batch.step(chunk)
+            steps += chunk
+            res = batch.residuals(allow_nonfinite=True)[:, 0]
+            now = time.perf_counter() - t0
+            newly = (reached < 0) & (res <= args.tol) & np.isfinite(res)
+            reached[newly] = steps
+            when[newly] = now
+            blown |= ~np.isfinite(batch.residuals(allow_nonfinite=True)[:, 1])
+        uz = [batch.moments(d, B.UZ, dtype=np.float32)[0] for d in range(len(probs))]
+        batch.close()
+        arms[arm] = dict(reached=reached, when=when, uz=uz)
+    both = (arms["rest"]["reached"] > 0) & (arms["warm"]["reached"] > 0)
+    n_ok = int(both.sum())
+    out = {}
+    for arm in ("rest", "warm"):
+        a = arms[arm]
+        out[arm] = dict(steps_median=float(np.median(a["reached"][both])) if n_ok else None,
+                        steps_max=int(a["reached"][both].max()) if n_ok else None,
+                        time_s=float(np.nanmax(a["when"][both])) if n_ok else None)
+    dif = max(float(np.max(np.abs(arms["rest"]["uz"][d] - arms["warm"]["uz"][d])) / (p.omega_of("hi") * p.wall_radius))
+              for d, p in enumerate(probs) if both[d]) if n_ok else None
+    line = {
+        "metric": "time_to_steady", "value": out["warm"]["time_s"], "unit": "s", "higher_is_better": False,
+        "n_gpus": 1, "dtype": "f32", "data": "synthetic", "vs_baseline": None,
+        "config": {"workload": f"held-out uneven sweep (seed {args.ws_seed}, radii x{scale}), {len(probs)} domains, "
+                               f"to residual <= {args.tol:g}",
+                   "rest": out["rest"], "warm_start": out["warm"], "converged_in_both": n_ok,
+                   "not_converged": int(len(probs) - n_ok),
+                   "steady_uz_difference_over_lid_speed": dif,
+                   "speedup_steps_median": (out["rest"]["steps_median"] / out["warm"]["steps_median"]) if n_ok else None,
+                   "speedup_time": (out["rest"]["time_s"] / out["warm"]["time_s"]) if n_ok else None},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "warmstart":
+        run_warmstart(args)
         return
     import torch
     import torch.distributed as dist
@@ -211,12 +285,14 @@ def main():
                                        dtype=torch.float32, device="cuda"))
         timing_on = lambda on: B.axlbm_kernel_timing(solver.handle, on)
         kernel_times = lambda: B.axlbm_kernel_times(solver.handle)
+        tile = (4, 128)
         workload = (f"pipe {pb.nr}x{pb.nz} D2Q9 (Hagen-Poiseuille force, axis + bounce-back wall, periodic z)")
     else:
         problems = S.rank_problems(I.batch_sweep, world, rank, args.shard, scale=args.scale)
         solver = B.Batch(problems, args.precision)
         timing_on = lambda on: B.axlbm_batch_kernel_timing(solver.handle, on)
         kernel_times = lambda: B.axlbm_batch_kernel_times(solver.handle)
+        tile = solver.tile_shape()
         workload = (f"batched uneven sweep: {sum(not p.temperature for p in problems)} rotating-lid cavities + "
                     f"{sum(p.temperature for p in problems)} Wheeler-type cells with temperature, one persistent "
                     f"launch per step" + (f" (radii scaled by {args.scale})" if args.scale != 1.0 else ""))
@@ -297,6 +373,7 @@ def main():
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": workload, "precision": args.precision, "nodes": all_nodes,
                        "domains": len(problems), "lattice_steps_per_step": args.inner,
+                       "bulk_tile": f"{tile[0]}x{tile[1]}",
                        "cache": "inputs larger than L2 (no flush)",
                        "parallelism": (f"independent domains on {world} ranks ({args.shard})" if world > 1
                                        else "one GPU")},

@@ -1064,7 +1064,9 @@ __device__ __forceinline__ void nee_node(const KArgs<S, R>& A, int level, int j,
         const R omg = C.g0 + C.g1 * R(cr4(q)) * inv_rb, omh = C.h0 + C.h1 * R(cr4(q)) * inv_rb;
         w.g[q] = SW ? C.rho0 * uth_w * R(0.25) + (R(1) - omg) * (c.g[q] - C.rho0 * uth * R(0.25) * (R(1) + R(2) * eu))
                     : R(0);
-        w.h[q] = TH ? t_b * R(0.25) + (R(1) - omh) * (c.h[q] - (dtemp + C.t_ref) * R(0.25) * (R(1) + R(2) * eu))
+        // (h stored as the deviation h - T_ref/4)
+        w.h[q] = TH ? (t_b - C.t_ref) * R(0.25) +
+                          (R(1) - omh) * (c.h[q] + C.t_ref * R(0.25) - (dtemp + C.t_ref) * R(0.25) * (R(1) + R(2) * eu))
                     : R(0);
     }
     if (G.inner == AXLBM_INNER_AXIS_NODE && j == 0) {
