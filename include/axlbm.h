@@ -108,7 +108,13 @@ enum {
  * Eqs. 13 and 53 at the wall node, x_f and x_ff the next two nodes inwards
  * (diagonal at a corner of two wet walls, where the side wall's speed and
  * temperature apply); needs nr >= 3. */
-enum { AXLBM_OUTER_BB = 0, AXLBM_OUTER_NEE = 1 };
+/* AXLBM_OUTER_ZOUHE: Zou-He wall through column nr - 1 (the paper's pipe walls,
+ * Sec. IV A, its Ref. [47]; wall radius r_{nr-1}): after every step the three
+ * populations entering the wall node from beyond the wall are set so that its
+ * velocity (Eqs. 16-17) is zero -- S_r = 0, S_z = -a(t)/2 -- with the normal
+ * non-equilibrium parts bounced back; the node collides like any other.  Only
+ * without g and h, with periodic axial faces. */
+enum { AXLBM_OUTER_BB = 0, AXLBM_OUTER_NEE = 1, AXLBM_OUTER_ZOUHE = 2 };
 enum { AXLBM_FACE_INNER = 0, AXLBM_FACE_OUTER = 1, AXLBM_FACE_LO = 2, AXLBM_FACE_HI = 3 };
 
 /* Collision model of f.  AXLBM_MRT: moment-space relaxation with the source
@@ -144,7 +150,7 @@ typedef struct {
     int32_t inner;          /* AXLBM_INNER_AXIS or _AXIS_NODE (need r0 == 0), or AXLBM_INNER_WALL */
     int32_t z_lo, z_hi;     /* AXLBM_Z_*; z_lo may not be AXLBM_Z_MIXED */
     int32_t t_dirichlet[4]; /* per face (AXLBM_FACE_*): 1 fixed temperature, 0 adiabatic */
-    int32_t outer;          /* AXLBM_OUTER_BB (0) or AXLBM_OUTER_NEE */
+    int32_t outer;          /* AXLBM_OUTER_BB (0), AXLBM_OUTER_NEE or AXLBM_OUTER_ZOUHE */
     double r_split;         /* AXLBM_Z_MIXED: wall part of the top face is r < r_split */
     double omega[4];        /* per face: angular velocity; u_theta,wall = omega * r */
     double t_wall[4];       /* per face: temperature where t_dirichlet is 1 */

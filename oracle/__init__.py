@@ -28,7 +28,7 @@ _lib = None
 
 INNER = {"axis": 0, "wall": 1, "axis_node": 2}
 ZKIND = {"periodic": 0, "wall": 1, "free": 2, "mixed": 3, "nee": 4}
-OUTER = {"wall": 0, "nee": 1}
+OUTER = {"wall": 0, "nee": 1, "zou_he": 2}
 FACES = ("inner", "outer", "lo", "hi")
 
 

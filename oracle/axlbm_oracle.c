@@ -87,6 +87,7 @@
 /* outer face */
 #define ORC_OUTER_BB 0  /* half-way bounce-back wall at r_{nr-1} + 1/2 */
 #define ORC_OUTER_NEE 1 /* wet wall: column nr - 1 lies on the wall */
+#define ORC_OUTER_ZOUHE 2 /* Zou-He wall through column nr - 1 (pipes: no g, h, periodic z) */
 /* face ids */
 #define F_IN 0
 #define F_OUT 1
@@ -99,7 +100,7 @@ typedef struct {
     int32_t z_lo, z_hi;         /* ORC_PERIODIC / ORC_WALL / ORC_FREE / ORC_MIXED / ORC_NEE */
     int32_t swirl, temperature; /* 0 or 1 */
     int32_t t_dirichlet[4];     /* per face: 1 = fixed T, 0 = adiabatic */
-    int32_t outer;              /* ORC_OUTER_BB or ORC_OUTER_NEE */
+    int32_t outer;              /* ORC_OUTER_BB, ORC_OUTER_NEE or ORC_OUTER_ZOUHE */
     double r0;                  /* radius of the inner face */
     double tau_s;               /* standard relaxation time = tau + 1/2 */
     double tau_t_s;             /* same for the temperature distribution */
@@ -150,7 +151,9 @@ int orc_validate(const orc_params* p) {
     if (p->inner == ORC_INNER_WALL && !(p->r0 >= 0.0)) return ORC_EINVAL;
     if (p->z_lo == ORC_MIXED) return ORC_EINVAL;
     if (p->z_lo < ORC_PERIODIC || p->z_lo > ORC_NEE || p->z_hi < ORC_PERIODIC || p->z_hi > ORC_NEE) return ORC_EINVAL;
-    if (p->outer != ORC_OUTER_BB && p->outer != ORC_OUTER_NEE) return ORC_EINVAL;
+    if (p->outer != ORC_OUTER_BB && p->outer != ORC_OUTER_NEE && p->outer != ORC_OUTER_ZOUHE) return ORC_EINVAL;
+    if (p->outer == ORC_OUTER_ZOUHE && (p->swirl || p->temperature || p->z_lo != ORC_PERIODIC || p->nr < 2))
+        return ORC_EINVAL;
     /* a wet wall extrapolates from the next node row or column inwards */
     if (p->outer == ORC_OUTER_NEE && p->nr < 3) return ORC_EINVAL;
     if ((p->z_lo == ORC_NEE || p->z_hi == ORC_NEE) && p->nz < 3) return ORC_EINVAL;
@@ -590,6 +593,32 @@ static void nee_rebuild(const orc_params* p, int64_t t, double* f, double* g, do
     }
 }
 
+/* Zou-He wall (Sec. IV A uses it for the pipes, its Ref. [47]) through the
+ * last column: after streaming, the three populations that enter the wall
+ * node from beyond the wall (e_r = -1) are set so that its first moments
+ * give zero velocity as Eqs. 16-17 define it (S_r = 0 without an inertial
+ * force, S_z = -a(t)/2) with the normal non-equilibrium parts bounced back
+ * (f_3 - f_3^eq = f_1 - f_1^eq); the wall node collides like any node. */
+static void zou_he_wall(const orc_params* p, int64_t t, double* f) {
+    if (p->outer != ORC_OUTER_ZOUHE) return;
+    const size_t n = (size_t)p->nr * p->nz;
+    const double mz = -0.5 * force_at(p, t);  /* S_z of zero velocity */
+    for (int k = 0; k < p->nz; ++k) {
+        const size_t x = (size_t)k * p->nr + p->nr - 1;
+        double v[9];
+        for (int a = 0; a < 9; ++a) v[a] = f[a * n + x];
+        const double out = v[1] + v[5] + v[8]; /* e_r = +1 */
+        v[3] = v[1];
+        const double sum67 = out - v[3];                        /* S_r = 0 */
+        const double dif67 = mz - (v[2] - v[4]) - (v[5] - v[8]); /* S_z = mz */
+        v[6] = 0.5 * (sum67 + dif67);
+        v[7] = 0.5 * (sum67 - dif67);
+        f[3 * n + x] = v[3];
+        f[6 * n + x] = v[6];
+        f[7 * n + x] = v[7];
+    }
+}
+
 /* n time steps starting at time t0; f, g, h are updated in place. */
 int orc_step(const orc_params* p, int64_t t0, int64_t nsteps, double* f, double* g, double* h) {
     if (orc_validate(p) != ORC_OK) return ORC_EINVAL;
@@ -630,6 +659,7 @@ int orc_step(const orc_params* p, int64_t t0, int64_t nsteps, double* f, double*
         }
         orc_stream(p, fp, gp, hp, f, g, h);
         nee_rebuild(p, t0 + s + 1, f, g, h);
+        zou_he_wall(p, t0 + s + 1, f);
     }
     free(fp);
     free(gp);

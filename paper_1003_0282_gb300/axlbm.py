@@ -24,12 +24,12 @@ FP64, FP32, FP16_DEV, BF16_DEV = range(4)
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP16_DEV, "bf16": BF16_DEV}
 INNER_AXIS, INNER_WALL, INNER_AXIS_NODE = 0, 1, 2
 Z_PERIODIC, Z_WALL, Z_FREE, Z_MIXED, Z_NEE = range(5)
-OUTER_BB, OUTER_NEE = 0, 1
+OUTER_BB, OUTER_NEE, OUTER_ZOUHE = 0, 1, 2
 RHO, UR, UZ, UTH, T = 1, 2, 4, 8, 16
 F64, F32 = 0, 1
 BGK, MRT = 0, 1
 _ZKIND = {"periodic": Z_PERIODIC, "wall": Z_WALL, "free": Z_FREE, "mixed": Z_MIXED, "nee": Z_NEE}
-_OUTER = {"wall": OUTER_BB, "nee": OUTER_NEE}
+_OUTER = {"wall": OUTER_BB, "nee": OUTER_NEE, "zou_he": OUTER_ZOUHE}
 _INNER = {"axis": INNER_AXIS, "wall": INNER_WALL, "axis_node": INNER_AXIS_NODE}
 
 

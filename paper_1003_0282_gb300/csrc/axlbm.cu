@@ -178,7 +178,11 @@ bool validate_problem(const axlbm_grid* grid, double tau, const axlbm_forcing* f
     if (bc->z_lo < 0 || bc->z_lo > AXLBM_Z_NEE || bc->z_lo == AXLBM_Z_MIXED || bc->z_hi < 0 || bc->z_hi > AXLBM_Z_NEE)
         return no("bad axial face kind (the bottom face cannot be mixed)");
     if ((bc->z_lo == AXLBM_Z_PERIODIC) != (bc->z_hi == AXLBM_Z_PERIODIC)) return no("periodic needs both axial faces periodic");
-    if (bc->outer != AXLBM_OUTER_BB && bc->outer != AXLBM_OUTER_NEE) return no("bad outer face kind");
+    if (bc->outer != AXLBM_OUTER_BB && bc->outer != AXLBM_OUTER_NEE && bc->outer != AXLBM_OUTER_ZOUHE)
+        return no("bad outer face kind");
+    if (bc->outer == AXLBM_OUTER_ZOUHE &&
+        (grid->with_swirl || grid->with_temperature || bc->z_lo != AXLBM_Z_PERIODIC || grid->nr < 2))
+        return no("a Zou-He wall needs no g or h, periodic axial faces and nr >= 2");
     if (bc->outer == AXLBM_OUTER_NEE && grid->nr < 3) return no("a wet outer wall needs nr >= 3");
     if ((bc->z_lo == AXLBM_Z_NEE || bc->z_hi == AXLBM_Z_NEE) && grid->nz < 3) return no("a wet axial wall needs nz >= 3");
     if (bc->z_lo == AXLBM_Z_NEE && bc->z_hi == AXLBM_Z_NEE && grid->nz < 4) return no("two wet axial walls need nz >= 4");

@@ -1092,6 +1092,31 @@ __device__ __forceinline__ void nee_node(const KArgs<S, R>& A, int level, int j,
     }
 }
 
+// Zou-He wall through the last column (the paper's pipe walls, Sec. IV A,
+// its Ref. [47]), after a step: the populations entering wall node (nr-1, k)
+// from beyond the wall (3: (-1,0), 6: (-1,1), 7: (-1,-1)) are set so that its
+// velocity of Eqs. 16-17 is zero, S_r = 0 and S_z = -a/2, with the normal
+// non-equilibrium part bounced back (f_3 - f_3^eq = f_1 - f_1^eq).  Written
+// on the stored deviations (the weights cancel).  Beyond the wall lies a
+// solid site, so in either layout those populations sit in the node's own
+// slots.
+template <class S, class R>
+__global__ void __launch_bounds__(kThreads) k_zou_he(const KArgs<S, R> A, int level) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const Geom& G = A.G;
+    if (k >= G.nz) return;
+    const int j = G.nr - 1;
+    Cell<R, false, false> c;
+    if (level == 0) load_natural(A, j, k, c);
+    else pull_odd(A, j, k, c);
+    const R mz = R(-0.5) * R(A.az[level]);
+    const R dif = mz - (c.d[2] - c.d[4]) - (c.d[5] - c.d[8]);
+    const R sum = c.d[5] + c.d[8];
+    Codec<S>::store(slot(A.pop, G, 3, j, k), c.d[1]);
+    Codec<S>::store(slot(A.pop, G, 6, j, k), R(0.5) * (sum + dif));
+    Codec<S>::store(slot(A.pop, G, 7, j, k), R(0.5) * (sum - dif));
+}
+
 template <class S, class R, bool SW, bool TH>
 __global__ void __launch_bounds__(kThreads) k_nee(const KArgs<S, R> A, int level) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1369,6 +1394,11 @@ cudaError_t step_sw(axlbm_handle* h, int check, int residual, cudaEvent_t ev0, c
     if (e == cudaSuccess && nw > 0) {
         // the step's kernels are done: rebuild the wet walls at the new level
         k_nee<S, R, SW, TH><<<(nw + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(A, 1 - h->parity);
+        *nlaunch += 1;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && h->G.outer == AXLBM_OUTER_ZOUHE) {
+        k_zou_he<S, R><<<(h->G.nz + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(A, 1 - h->parity);
         *nlaunch += 1;
         e = cudaGetLastError();
     }

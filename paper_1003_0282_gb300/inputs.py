@@ -33,6 +33,7 @@ WALL = "wall"
 PERIODIC = "periodic"
 FREE = "free"
 MIXED = "mixed"  # top only: wall for r < r_split, free surface beyond
+ZOU_HE = "zou_he"  # outer face only: Zou-He wall through the last column (pipes)
 NEE = "nee"      # wet wall: the node row (or, as ``outer``, the last column) lies on the wall and is
                  # rebuilt by non-equilibrium extrapolation from its inner neighbour
 
@@ -49,7 +50,8 @@ class Problem:
     inner: str = AXIS
     z_lo: str = PERIODIC
     z_hi: str = PERIODIC
-    outer: str = WALL               # WALL (half-way bounce-back) or NEE (wet wall on column nr - 1)
+    outer: str = WALL               # WALL (half-way bounce-back), NEE (wet wall on column nr - 1) or
+                                    # ZOU_HE (Zou-He wall through column nr - 1)
     swirl: bool = False
     temperature: bool = False
     tau_t: float = 0.8              # standard relaxation time of the temperature field
@@ -85,7 +87,7 @@ class Problem:
     @property
     def wall_radius(self) -> float:
         """Radius of the outer wall (half-way, or on the last column for NEE)."""
-        return float(self.node_radius(self.nr - 1)) + (0.0 if self.outer == NEE else 0.5)
+        return float(self.node_radius(self.nr - 1)) + (0.0 if self.outer in (NEE, ZOU_HE) else 0.5)
 
 
 # ----------------------------------------------------------------------------- recipes

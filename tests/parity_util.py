@@ -30,11 +30,15 @@ BOUNDARY_MIXES = {
     "nee-cavity": dict(inner="axis", outer="nee", z_lo="nee", z_hi="nee"),
     "nee-axis-node": dict(inner="axis_node", outer="nee", z_lo="nee", z_hi="mixed", r_split=0.4),
     "nee-annulus-pipe": dict(inner="wall", r0=3.0, outer="nee", z_lo="periodic", z_hi="periodic"),
+    # Zou-He pipe wall (Sec. IV A; D2Q9 only)
+    "zou-he-pipe": dict(inner="axis_node", outer="zou_he", z_lo="periodic", z_hi="periodic"),
 }
 
 
 def problem(nr, nz, mix, swirl=True, temperature=True, tau=0.8, collision="bgk", **extra):
     kw = dict(BOUNDARY_MIXES[mix])
+    if kw.get("outer") == "zou_he":  # a Zou-He pipe carries f only
+        swirl = temperature = False
     if "r_split" in kw:
         kw["r_split"] = kw["r_split"] * nr + kw.get("r0", 0.0)
     kw.update(extra)

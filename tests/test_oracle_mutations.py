@@ -83,6 +83,10 @@ MUTATIONS = {
         ("f[a * n + xb] = feq_w + (1.0 - om) * (fi[a] - feq_f);", "f[a * n + xb] = feq_w + (fi[a] - feq_f);"),
     "wet wall: density not extrapolated":
         ("const double rho_b = 2.0 * m[0] - m2[0];", "const double rho_b = m[0];"),
+    "Zou-He: normal population not bounced back":
+        ("        v[3] = v[1];\n", "        v[3] = 0.0;\n"),
+    "Zou-He: half-force term missing from the wall velocity":
+        ("const double mz = -0.5 * force_at(p, t);", "const double mz = 0.0 * force_at(p, t);"),
     "sign of the buoyancy force":
         ("fz += p->rho0 * p->gbeta * (temp - p->t_ref);", "fz -= p->rho0 * p->gbeta * (temp - p->t_ref);"),
 }
