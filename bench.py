@@ -238,11 +238,14 @@ def run_warmstart(args):
         a = arms[arm]
         out[arm] = dict(steps_median=float(np.median(a["reached"][both])) if n_ok else None,
                         steps_max=int(a["reached"][both].max()) if n_ok else None,
-                        time_s=float(np.nanmax(a["when"][both])) if n_ok else None)
-    dif = max(float(np.max(np.abs(arms["rest"]["uz"][d] - arms["warm"]["uz"][d])) / (p.omega_of("hi") * p.wall_radius))
-              for d, p in enumerate(probs) if both[d]) if n_ok else None
+                        time_median_s=float(np.median(a["when"][both])) if n_ok else None,
+                        time_all_s=float(np.max(a["when"][both])) if n_ok else None)
+    difs = [float(np.nanmax(np.abs(arms["rest"]["uz"][d] - arms["warm"]["uz"][d]))) / (p.omega_of("hi") * p.wall_radius)
+            for d, p in enumerate(probs) if both[d]]
+    dif = max(difs) if difs else None
     line = {
-        "metric": "time_to_steady", "value": out["warm"]["time_s"], "unit": "s", "higher_is_better": False,
+        "metric": "time_to_steady_median", "value": out["warm"]["time_median_s"], "unit": "s",
+        "higher_is_better": False,
         "n_gpus": 1, "dtype": "f32", "data": "synthetic", "vs_baseline": None,
         "config": {"workload": f"held-out uneven sweep (seed {args.ws_seed}, radii x{scale}), {len(probs)} domains, "
                                f"to residual <= {args.tol:g}",
@@ -250,7 +253,8 @@ def run_warmstart(args):
                    "not_converged": int(len(probs) - n_ok),
                    "steady_uz_difference_over_lid_speed": dif,
                    "speedup_steps_median": (out["rest"]["steps_median"] / out["warm"]["steps_median"]) if n_ok else None,
-                   "speedup_time": (out["rest"]["time_s"] / out["warm"]["time_s"]) if n_ok else None},
+                   "speedup_time_median": (out["rest"]["time_median_s"] / out["warm"]["time_median_s"]) if n_ok else None,
+                   "speedup_time_all": (out["rest"]["time_all_s"] / out["warm"]["time_all_s"]) if n_ok else None},
     }
     print(json.dumps(line), flush=True)
 
@@ -292,7 +296,7 @@ def main():
         solver = B.Batch(problems, args.precision)
         timing_on = lambda on: B.axlbm_batch_kernel_timing(solver.handle, on)
         kernel_times = lambda: B.axlbm_batch_kernel_times(solver.handle)
-        tile = solver.tile_shape()
+        tile = solver.tile_shape
         workload = (f"batched uneven sweep: {sum(not p.temperature for p in problems)} rotating-lid cavities + "
                     f"{sum(p.temperature for p in problems)} Wheeler-type cells with temperature, one persistent "
                     f"launch per step" + (f" (radii scaled by {args.scale})" if args.scale != 1.0 else ""))

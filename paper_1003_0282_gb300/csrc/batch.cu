@@ -62,7 +62,8 @@ struct Plan {
     std::vector<int> col0, row0;
     std::vector<axl::TileRec> tiles[axl::kBatchShapes];
     std::vector<int> tstart[axl::kBatchShapes], tindex[axl::kBatchShapes];
-    std::vector<int> ring, rstart;                  // 2 ints per ring node
+    std::vector<int> ring;                          // 2 ints per ring node: domains without h, then with h
+    std::vector<int> rstart;                        // [2 n]: first and end ring entry of each domain
     std::vector<int> axis;                          // domains with a node on the axis
     std::vector<int> nee;                           // domains with a wet wall
     int thmax;
@@ -188,14 +189,20 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
         L.shape[s].nentries = (int)P->tindex[s].size();
         if (T.empty()) { *why = "internal: no tiles"; return false; }
     }
-    // outer rings, domain by domain
+    // outer rings, domain by domain: domains without temperature first, so
+    // that each ring kernel (one per class) covers one contiguous range
     P->ring.clear();
-    P->rstart.assign(1, 0);
-    for (int d = 0; d < n; ++d) {
-        const int nr = dom[d].grid.nr, nz = dom[d].grid.nz;
-        const int nf = nz == 1 ? nr : 2 * nr + (nz - 2) * (nr > 1 ? 2 : 1);
-        for (int i = 0; i < nf; ++i) P->ring.insert(P->ring.end(), {d, i});
-        P->rstart.push_back((int)(P->ring.size() / 2));
+    P->rstart.assign(2 * (size_t)n, 0);
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int d = 0; d < n; ++d) {
+            if ((dom[d].grid.with_temperature != 0) != (pass == 1)) continue;
+            const int nr = dom[d].grid.nr, nz = dom[d].grid.nz;
+            const int nf = nz == 1 ? nr : 2 * nr + (nz - 2) * (nr > 1 ? 2 : 1);
+            P->rstart[2 * d] = (int)(P->ring.size() / 2);
+            for (int i = 0; i < nf; ++i) P->ring.insert(P->ring.end(), {d, i});
+            P->rstart[2 * d + 1] = (int)(P->ring.size() / 2);
+        }
+        if (pass == 0) L.nring_cold = (int)(P->ring.size() / 2);
     }
     L.nring = (int)(P->ring.size() / 2);
     P->axis.clear();
@@ -231,7 +238,7 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
     L.off_ring = off;
     off += al((size_t)L.nring * 8);
     L.off_rstart = off;
-    off += al((size_t)(n + 1) * 4);
+    off += al((size_t)(2 * n) * 4);
     L.off_axis = off;
     off += al((size_t)std::max(L.naxis, 1) * 4);
     L.off_nee = off;

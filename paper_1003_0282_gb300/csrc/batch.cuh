@@ -461,9 +461,9 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
 constexpr int kRingThreads = 128;
 
 template <class S, class R, bool SW, bool THD, bool CHK>
-__global__ void __launch_bounds__(kRingThreads) k_ring_batch(const BatchArgs<S, R> A, int advance) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < A.nring) {
+__global__ void __launch_bounds__(kRingThreads) k_ring_batch(const BatchArgs<S, R> A, int first, int end, int advance) {
+    const int i = first + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < end) {
         const int2 e = A.ring[i];
         const DomDesc& D = A.doms[e.x];
         if ((D.temperature != 0) == THD) {
@@ -558,7 +558,7 @@ k_batch_fold(const int* tile_start, const int* tile_index, const TileRec* tiles,
         }
     }
     if (with_ring) {
-        for (int i = ring_start[d] + threadIdx.x; i < ring_start[d + 1]; i += blockDim.x) {
+        for (int i = ring_start[2 * d] + threadIdx.x; i < ring_start[2 * d + 1]; i += blockDim.x) {
             const double* p = ring_part + 4ll * i;
             v.rmax = fmax(v.rmax, p[0]);
             v.mass += p[1];

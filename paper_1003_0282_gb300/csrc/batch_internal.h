@@ -26,6 +26,7 @@ struct BatchLayout {
     int nplanes;
     long long pitch, rows, plane;
     int nring;
+    int nring_cold;  // ring entries of domains without temperature (listed first)
     size_t off_speed, off_tilepart, off_ringpart, off_result, off_az, off_clock, off_doms, off_slots, off_ring,
         off_rstart, off_axis, off_nee;
     int naxis;  // domains with a node on the axis (listed at off_axis)

@@ -131,14 +131,22 @@ cudaError_t batch_step_th(axlbm_batch* b, int check, int residual, cudaEvent_t e
     e = check ? launch_bulk_batch_shape<S, R, TH, 1, true>(b, A) : launch_bulk_batch_shape<S, R, TH, 1, false>(b, A);
     if (ev1) cudaEventRecord(ev1, b->stream);
     if (e != cudaSuccess) return e;
-    const int blocks = (A.nring + kRingThreads - 1) / kRingThreads;
-    if (check) k_ring_batch<S, R, true, false, true><<<blocks, kRingThreads, 0, rs>>>(A, TH ? 0 : 1);
-    else k_ring_batch<S, R, true, false, false><<<blocks, kRingThreads, 0, rs>>>(A, TH ? 0 : 1);
-    *nl = 2;
-    if (TH) {
-        if (check) k_ring_batch<S, R, true, true, true><<<blocks, kRingThreads, 0, rs>>>(A, 1);
-        else k_ring_batch<S, R, true, true, false><<<blocks, kRingThreads, 0, rs>>>(A, 1);
-        *nl = 3;
+    // one ring kernel per class over its contiguous range (the second one, or
+    // the only one, also moves the force and the time level on)
+    const int cold = b->L.nring_cold, hot = A.nring - cold;
+    const bool two = TH && hot > 0 && cold > 0;
+    *nl = 1;
+    if (cold > 0 || !TH) {
+        const int blocks = (cold + kRingThreads - 1) / kRingThreads;
+        if (check) k_ring_batch<S, R, true, false, true><<<blocks > 0 ? blocks : 1, kRingThreads, 0, rs>>>(A, 0, cold, two ? 0 : 1);
+        else k_ring_batch<S, R, true, false, false><<<blocks > 0 ? blocks : 1, kRingThreads, 0, rs>>>(A, 0, cold, two ? 0 : 1);
+        *nl += 1;
+    }
+    if (TH && hot > 0) {
+        const int blocks = (hot + kRingThreads - 1) / kRingThreads;
+        if (check) k_ring_batch<S, R, true, true, true><<<blocks, kRingThreads, 0, rs>>>(A, cold, A.nring, 1);
+        else k_ring_batch<S, R, true, true, false><<<blocks, kRingThreads, 0, rs>>>(A, cold, A.nring, 1);
+        *nl += 1;
     }
     e = cudaGetLastError();
     if (overlap) {

@@ -845,8 +845,10 @@ k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
     if (PAR == 0 && blockIdx.x == 0 && tid == 0) advance_clock(A.clock, PAR, A.az0, A.omega_t);
 }
 
-// Coordinates of the i-th node of the outer ring (bottom row, top row, then
-// the first and last column of the rows in between).
+// Coordinates of the i-th node of the outer ring: bottom row, top row, then
+// the first column and the last column of the rows in between, each column
+// in row order (neighbouring threads then read neighbouring rows of one
+// column, which share the cached sectors of their pulls).
 __device__ __forceinline__ void frame_coord(const Geom& G, int i, int& j, int& k) {
     if (i < G.nr) {
         j = i;
@@ -860,9 +862,14 @@ __device__ __forceinline__ void frame_coord(const Geom& G, int i, int& j, int& k
         return;
     }
     i -= G.nr;
-    const int cols = G.nr > 1 ? 2 : 1;
-    k = 1 + i / cols;
-    j = (i % cols) == 0 ? 0 : G.nr - 1;
+    const int inner = G.nz - 2;  // rows between bottom and top
+    if (i < inner) {
+        j = 0;
+        k = 1 + i;
+        return;
+    }
+    j = G.nr - 1;
+    k = 1 + (i - inner);
 }
 
 // Odd-step update of one outer-ring node (j, k): pull with the boundary

@@ -98,7 +98,11 @@ def solve_sweep(seed, scale, steps, device):
     res = batch.residuals(allow_nonfinite=True)
     canv, keep = [], []
     for d, pb in enumerate(probs):
-        m = batch.moments(d, B.UR | B.UZ | B.UTH | B.T, dtype=np.float32)
+        if pb.temperature:
+            m = batch.moments(d, B.UR | B.UZ | B.UTH | B.T, dtype=np.float32)
+        else:  # no temperature: T = T_ref
+            m3 = batch.moments(d, B.UR | B.UZ | B.UTH, dtype=np.float32)
+            m = np.concatenate([m3, np.full((1,) + m3.shape[1:], pb.t_ref, dtype=np.float32)])
         if np.all(np.isfinite(m)):  # a draw that blew up (grid Reynolds number too high) is dropped
             canv.append(to_canvas(pb, m, device))
             keep.append(d)
