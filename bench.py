@@ -37,7 +37,10 @@ sys.path.insert(0, ROOT)
 # (dram__bytes_read.sum + dram__bytes_write.sum) / algorithmic bytes of the
 # captured launch, keyed by kernel and the SHA-256 prefix of the kernel source
 # at capture time.  Reported as null once the source has changed.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/k_bulk_batch_fp32_sweep320_launches.md: one even and one odd launch of the full sweep
+    "batch fp32": {"src_sha": "8fd2afcc04f1603d", "dram_per_alg_byte": 0.9928},
+}
 
 
 def parse():
