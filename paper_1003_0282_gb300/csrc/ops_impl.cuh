@@ -311,11 +311,19 @@ __device__ __forceinline__ Site classify(const Geom& G, int j, int k, int ex, in
     return s;
 }
 
+// Entry `face` of a per-face array, selected without indexing (so that a
+// locally built coefficient block can stay in registers).
+template <class T>
+__device__ __forceinline__ T pick4(const T (&a)[4], int face) {
+    return face == 0 ? a[0] : (face == 1 ? a[1] : (face == 2 ? a[2] : a[3]));
+}
+
 template <class R>
 __device__ __forceinline__ R wall_uth(const Geom& G, const Coef<R>& C, int face, int j) {
-    if (face == AXLBM_FACE_INNER) return C.omega_w[face] * R(G.r0);
-    if (face == AXLBM_FACE_OUTER) return C.omega_w[face] * R(node_radius(G, G.nr - 1) + 0.5);  // half-way wall
-    return C.omega_w[face] * R(node_radius(G, j));
+    const R om = pick4(C.omega_w, face);
+    if (face == AXLBM_FACE_INNER) return om * R(G.r0);
+    if (face == AXLBM_FACE_OUTER) return om * R(node_radius(G, G.nr - 1) + 0.5);  // half-way wall
+    return om * R(node_radius(G, j));
 }
 
 // Value of a D2Q4 population sent into a solid face, in stored (deviation) form.
@@ -326,7 +334,7 @@ __device__ __forceinline__ R bounce_g(const Geom& G, const Coef<R>& C, int face,
 template <class R>
 __device__ __forceinline__ R bounce_h(const Coef<R>& C, int face, R v) {
     // true value h = v + T_ref/4; Dirichlet: -h + T_w/2; adiabatic: h
-    return C.t_dir[face] ? -v - R(0.5) * C.t_ref + R(0.5) * C.t_w[face] : v;
+    return pick4(C.t_dir, face) ? -v - R(0.5) * C.t_ref + R(0.5) * pick4(C.t_w, face) : v;
 }
 
 template <class S>
@@ -873,11 +881,10 @@ __device__ __forceinline__ void frame_coord(const Geom& G, int i, int& j, int& k
 }
 
 // Odd-step update of one outer-ring node (j, k): pull with the boundary
-// rules, collide, push, check values.  Kept out of line so that the
-// single-domain and batch ring kernels run one compiled instruction sequence
-// (a domain gets the same bits whichever of the two updates it).
+// rules, collide, push, check values.  Shared by the single-domain and batch
+// ring kernels, each of which instantiates it for one cell type only.
 template <class S, class R, bool SW, bool TH, bool CHK>
-__device__ __noinline__ void ring_node(const KArgs<S, R>& A, int j, int k, R az, Red& red) {
+__device__ __forceinline__ void ring_node(const KArgs<S, R>& A, int j, int k, R az, Red& red) {
     Cell<R, SW, TH> c;
     pull_odd(A, j, k, c);
     const R inv_r = inv_radius<R>(A.G, j);
@@ -1063,8 +1070,8 @@ __device__ __forceinline__ void nee_node(const KArgs<S, R>& A, int level, int j,
         const R om = C.c0 + C.c1 * R(cr9(a)) * inv_rb;
         w.d[a] = feq_w + (R(1) - om) * (c.d[a] - feq_f);
     }
-    const R uth_w = A.C.omega_w[face] * R(node_radius(G, j));
-    const R t_b = A.C.t_dir[face] ? A.C.t_w[face] : dtemp + C.t_ref;
+    const R uth_w = pick4(A.C.omega_w, face) * R(node_radius(G, j));
+    const R t_b = pick4(A.C.t_dir, face) ? pick4(A.C.t_w, face) : dtemp + C.t_ref;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const R eu = R(cr4(q)) * ur + R(cz4(q)) * uz;
