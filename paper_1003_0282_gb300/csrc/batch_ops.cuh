@@ -135,6 +135,15 @@ cudaError_t batch_step_th(axlbm_batch* b, int check, int residual, cudaEvent_t e
     // the only one, also moves the force and the time level on)
     const int cold = b->L.nring_cold, hot = A.nring - cold;
     const bool two = TH && hot > 0 && cold > 0;
+    // with FP32 storage the two ring classes (disjoint domains) run side by
+    // side: the thermal one on the side stream, forked after the bulk kernel
+    cudaStream_t hs = rs;
+    if (!overlap && two) {
+        e = cudaEventRecord(b->fork, b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
+        if (e != cudaSuccess) return e;
+        hs = b->side;
+    }
     *nl = 1;
     if (cold > 0 || !TH) {
         const int blocks = (cold + kRingThreads - 1) / kRingThreads;
@@ -144,12 +153,12 @@ cudaError_t batch_step_th(axlbm_batch* b, int check, int residual, cudaEvent_t e
     }
     if (TH && hot > 0) {
         const int blocks = (hot + kRingThreads - 1) / kRingThreads;
-        if (check) k_ring_batch<S, R, true, true, true><<<blocks, kRingThreads, 0, rs>>>(A, cold, A.nring, 1);
-        else k_ring_batch<S, R, true, true, false><<<blocks, kRingThreads, 0, rs>>>(A, cold, A.nring, 1);
+        if (check) k_ring_batch<S, R, true, true, true><<<blocks, kRingThreads, 0, hs>>>(A, cold, A.nring, 1);
+        else k_ring_batch<S, R, true, true, false><<<blocks, kRingThreads, 0, hs>>>(A, cold, A.nring, 1);
         *nl += 1;
     }
     e = cudaGetLastError();
-    if (overlap) {
+    if (overlap || hs != rs) {
         if (e == cudaSuccess) e = cudaEventRecord(b->join, b->side);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join, 0);
     }
