@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 # at capture time.  Reported as null once the source has changed.
 NCU_TRAFFIC = {
     # profiles/k_bulk_batch_fp32_sweep320_launches.md: one even and one odd launch of the full sweep
-    "batch fp32": {"src_sha": "5e200c8478323daa", "dram_per_alg_byte": 0.9929},
+    "batch fp32": {"src_sha": "95187a53c6ea0ed2", "dram_per_alg_byte": 0.9929},
 }
 
 
@@ -292,6 +292,7 @@ def main():
                                        dtype=torch.float32, device="cuda"))
         timing_on = lambda on: B.axlbm_kernel_timing(solver.handle, on)
         kernel_times = lambda: B.axlbm_kernel_times(solver.handle)
+        parity_times = None
         tile = (4, 128)
         workload = (f"pipe {pb.nr}x{pb.nz} D2Q9 (Hagen-Poiseuille force, axis + bounce-back wall, periodic z)")
     else:
@@ -299,6 +300,7 @@ def main():
         solver = B.Batch(problems, args.precision)
         timing_on = lambda on: B.axlbm_batch_kernel_timing(solver.handle, on)
         kernel_times = lambda: B.axlbm_batch_kernel_times(solver.handle)
+        parity_times = lambda: B.axlbm_batch_kernel_times_by_parity(solver.handle)
         tile = solver.tile_shape
         workload = (f"batched uneven sweep: {sum(not p.temperature for p in problems)} rotating-lid cavities + "
                     f"{sum(p.temperature for p in problems)} Wheeler-type cells with temperature, one persistent "
@@ -325,6 +327,7 @@ def main():
         barrier()
     ms = ev0.elapsed_time(ev1)
     bulk_n, bulk_ms, bulk_bytes, all_launches = kernel_times()
+    by_parity = parity_times() if parity_times else None
     timing_on(False)
     if args.workload == "pipe":
         res, mass, _ = solver.residual()
@@ -395,6 +398,12 @@ def main():
             "clocks": clk.summary(),
             "check": {"residual": res, "mass": mass},
         }
+        if by_parity:  # the even (in place) and odd (neighbour to neighbour) launches apart
+            n2, ms2, by2 = by_parity
+            line["roofline"]["by_parity"] = {
+                name: {"launches": n2[p], "avg_launch_ms": ms2[p] / max(n2[p], 1),
+                       "achieved": by2[p] / (ms2[p] / 1e3) / 1e9 if ms2[p] > 0 else 0.0}
+                for p, name in enumerate(("even", "odd"))}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.workload, args.inner)
         print(json.dumps(line), flush=True)

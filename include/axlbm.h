@@ -354,6 +354,13 @@ AXLBM_API axlbm_status axlbm_batch_kernel_timing(axlbm_batch* b, int32_t enable)
 AXLBM_API axlbm_status axlbm_batch_kernel_times(axlbm_batch* b, int64_t* bulk_launches, double* bulk_ms,
                                                 double* bulk_bytes, int64_t* all_launches);
 
+/* The same bulk totals split by the AA parity of the timed lattice steps:
+ * each argument (or NULL) points to two values, [0] for even steps (every
+ * node updated in place) and [1] for odd steps (interior nodes, read from and
+ * written to their neighbours).  Synchronises the batch's stream. */
+AXLBM_API axlbm_status axlbm_batch_kernel_times_by_parity(axlbm_batch* b, int64_t* bulk_launches, double* bulk_ms,
+                                                          double* bulk_bytes);
+
 /* Free the batch (after synchronising its stream). */
 AXLBM_API axlbm_status axlbm_batch_destroy(axlbm_batch* b);
 

@@ -123,6 +123,7 @@ def lib() -> ctypes.CDLL:
         L.axlbm_batch_tile_shape.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         L.axlbm_batch_kernel_timing.argtypes = [H, ctypes.c_int32]
         L.axlbm_batch_kernel_times.argtypes = [H, ctypes.POINTER(ctypes.c_int64), dp, dp, ctypes.POINTER(ctypes.c_int64)]
+        L.axlbm_batch_kernel_times_by_parity.argtypes = [H, ctypes.POINTER(ctypes.c_int64), dp, dp]
         L.axlbm_batch_destroy.argtypes = [H]
         L.axlbm_batch_last_error.restype = ctypes.c_char_p
         L.axlbm_batch_last_error.argtypes = [H]
@@ -140,7 +141,8 @@ def lib() -> ctypes.CDLL:
         for name in ("axlbm_batch_state_bytes", "axlbm_batch_create", "axlbm_batch_step", "axlbm_batch_residuals",
                      "axlbm_batch_moments", "axlbm_batch_set_fields", "axlbm_batch_get_populations",
                      "axlbm_batch_set_populations", "axlbm_batch_time", "axlbm_batch_tile_shape",
-                     "axlbm_batch_kernel_timing", "axlbm_batch_kernel_times", "axlbm_batch_destroy",
+                     "axlbm_batch_kernel_timing", "axlbm_batch_kernel_times", "axlbm_batch_kernel_times_by_parity",
+                     "axlbm_batch_destroy",
                      "axlbm_batch_set_fields_all", "axlbm_batch_moments_all"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("axlbm_state_bytes", "axlbm_create", "axlbm_step", "axlbm_moments", "axlbm_residual",
@@ -443,6 +445,14 @@ def axlbm_batch_kernel_times(b):
     _bcheck(lib().axlbm_batch_kernel_times(b, ctypes.byref(nb), ctypes.byref(ms), ctypes.byref(by),
                                            ctypes.byref(na)), b)
     return int(nb.value), ms.value, by.value, int(na.value)
+
+
+def axlbm_batch_kernel_times_by_parity(b):
+    """([even, odd] launches, [even, odd] ms, [even, odd] algorithmic bytes) of the bulk kernel."""
+    nb = (ctypes.c_int64 * 2)()
+    ms, by = (ctypes.c_double * 2)(), (ctypes.c_double * 2)()
+    _bcheck(lib().axlbm_batch_kernel_times_by_parity(b, nb, ms, by), b)
+    return list(nb), list(ms), list(by)
 
 
 def axlbm_batch_destroy(b) -> None:

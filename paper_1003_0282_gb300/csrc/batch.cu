@@ -324,9 +324,14 @@ axlbm_status batch_fold_timing(axlbm_batch* b) {
         if (e != cudaSuccess) return bcuda(b, e, "timing");
         b->bulk_ms += ms;
         b->bulk_bytes += b->ev_bytes[i];
+        const int p = b->ev_parity[i];
+        b->par_ms[p] += ms;
+        b->par_bytes[p] += b->ev_bytes[i];
+        b->par_launches[p] += 1;
     }
     b->ev_used = 0;
     b->ev_bytes.clear();
+    b->ev_parity.clear();
     return AXLBM_OK;
 }
 
@@ -359,6 +364,7 @@ axlbm_status batch_step_n(axlbm_batch* b, int64_t n) {
             axlbm_status st = batch_timing_slot(b, &ev0, &ev1);
             if (st != AXLBM_OK) return st;
             b->ev_bytes.push_back(batch_bulk_bytes(b, check, residual));
+            b->ev_parity.push_back(b->parity);
         }
         int nl = 0;
         cudaError_t e = ops->step(b, check, residual, ev0, ev1, &nl);
@@ -480,6 +486,10 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
     b->ev_used = 0;
     b->bulk_launches = b->all_launches = 0;
     b->bulk_ms = b->bulk_bytes = 0.0;
+    for (int p = 0; p < 2; ++p) {
+        b->par_ms[p] = b->par_bytes[p] = 0.0;
+        b->par_launches[p] = 0;
+    }
     b->last_check_parity = 0;
     {
         int dev = 0;
@@ -809,6 +819,10 @@ axlbm_status axlbm_batch_kernel_timing(axlbm_batch* b, int32_t enable) {
         if (st != AXLBM_OK) return st;
         b->bulk_launches = b->all_launches = 0;
         b->bulk_ms = b->bulk_bytes = 0.0;
+        for (int p = 0; p < 2; ++p) {
+            b->par_ms[p] = b->par_bytes[p] = 0.0;
+            b->par_launches[p] = 0;
+        }
     }
     b->timing = enable != 0;
     return AXLBM_OK;
@@ -823,6 +837,19 @@ axlbm_status axlbm_batch_kernel_times(axlbm_batch* b, int64_t* bulk_launches, do
     if (bulk_ms) *bulk_ms = b->bulk_ms;
     if (bulk_bytes) *bulk_bytes = b->bulk_bytes;
     if (all_launches) *all_launches = b->all_launches;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_kernel_times_by_parity(axlbm_batch* b, int64_t* bulk_launches, double* bulk_ms,
+                                                double* bulk_bytes) {
+    if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
+    axlbm_status st = batch_fold_timing(b);
+    if (st != AXLBM_OK) return st;
+    for (int p = 0; p < 2; ++p) {
+        if (bulk_launches) bulk_launches[p] = b->par_launches[p];
+        if (bulk_ms) bulk_ms[p] = b->par_ms[p];
+        if (bulk_bytes) bulk_bytes[p] = b->par_bytes[p];
+    }
     return AXLBM_OK;
 }
 

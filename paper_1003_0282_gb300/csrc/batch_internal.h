@@ -63,9 +63,12 @@ struct axlbm_batch {
     bool timing;
     std::vector<cudaEvent_t> ev;
     std::vector<double> ev_bytes;
+    std::vector<int> ev_parity;  // AA parity of each timed step
     size_t ev_used;
     int64_t bulk_launches, all_launches;
     double bulk_ms, bulk_bytes;
+    double par_ms[2], par_bytes[2];  // the same split by parity
+    int64_t par_launches[2];
     std::string err;
 };
 

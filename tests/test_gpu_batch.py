@@ -234,3 +234,23 @@ def test_batch_with_node_on_axis_and_wet_wall_domains(B):
             if pb.temperature:
                 assert rel_err(h, states[d].h) <= POP_TOL["fp32"], (d, pb.inner)
     batch.close()
+
+
+def test_kernel_times_split_by_parity(B):
+    """The per-parity bulk totals add up to the overall ones; an even number
+    of steps from an even level times as many even as odd launches, and the
+    odd launches count the interior nodes only."""
+    doms = mixed_batch()
+    batch = B.Batch(doms, "fp32")
+    B.axlbm_batch_kernel_timing(batch.handle, True)
+    batch.step(10)
+    n, ms, by, _ = B.axlbm_batch_kernel_times(batch.handle)
+    n2, ms2, by2 = B.axlbm_batch_kernel_times_by_parity(batch.handle)
+    assert n2 == [5, 5] and n == 10
+    assert abs(sum(ms2) - ms) <= 1e-9 * max(ms, 1.0) and min(ms2) > 0.0
+    assert abs(sum(by2) - by) <= 1e-6 * by
+    interior = sum((pb.nr - 2) * (pb.nz - 2) for pb in doms)
+    assert by2[1] < by2[0] and by2[1] >= 5 * interior * 2 * 13 * 4
+    B.axlbm_batch_kernel_timing(batch.handle, True)  # re-enabling clears the totals
+    assert B.axlbm_batch_kernel_times_by_parity(batch.handle)[0] == [0, 0]
+    batch.close()
