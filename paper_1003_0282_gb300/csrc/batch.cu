@@ -227,8 +227,8 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
     off += al((size_t)L.nring * 32);
     L.off_result = off;
     off += al((size_t)n * 32);
-    L.off_az = off;
-    off += al((size_t)n * 16);
+    L.off_az = off;  // [n][2] a(t) by parity, then the same one per 16-byte word ([n][2][2])
+    off += al((size_t)n * 48);
     L.off_clock = off;
     off += 256;
     L.off_doms = off;
@@ -271,8 +271,11 @@ axlbm_status reset_rest(axlbm_batch* b) {
     const BatchLayout& L = b->L;
     cudaError_t e = cudaMemsetAsync(b->mem, 0, L.off_clock + 256, b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "memset");
-    std::vector<double> az(2 * b->n, 0.0);
-    for (int d = 0; d < b->n; ++d) az[2 * d] = b->desc[d].forcing.az0;  // a(0) = az0 cos(0)
+    std::vector<double> az(6 * b->n, 0.0);
+    for (int d = 0; d < b->n; ++d) {  // a(0) = az0 cos(0)
+        az[2 * d] = b->desc[d].forcing.az0;
+        az[2 * b->n + 4 * d] = b->desc[d].forcing.az0;
+    }
     axlbm_status st = upload(b, L.off_az, az.data(), az.size() * sizeof(double));
     if (st != AXLBM_OK) return st;
     for (int d = 0; d < b->n; ++d) {

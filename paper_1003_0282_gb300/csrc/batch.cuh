@@ -52,12 +52,14 @@ struct TileRec {
 };
 static_assert(sizeof(TileRec) == 48, "tile records are three 16-byte words");
 
-// The tile record plus each slot's force a(t), as the producer leaves them in
-// shared memory for the consumers.
+// The tile record plus each slot's force a(t) at the step's parity (one
+// 16-byte word per slot, the value first), as the issuing thread has them
+// copied into shared memory for the consumers.
 struct TileMeta {
     TileRec r;
-    float az[kSlots];
+    double az[kSlots][2];
 };
+static_assert(sizeof(TileMeta) % 16 == 0 && offsetof(TileMeta, az) % 16 == 0, "bulk-copy targets are 16-byte aligned");
 
 template <class R>
 __device__ __forceinline__ const Coef<R>& dom_coef(const DomDesc& D);
@@ -95,6 +97,7 @@ struct BatchArgs {
     const int2* ring;        // {domain, index in the domain's outer ring}
     int nring;
     double* dom_az;          // [ndom][2]: a(t) of each domain by AA parity
+    double* dom_az16;        // [ndom][2][2]: the same, each in its own 16-byte word (bulk-copy source)
     Clock* clock;            // time level and error word
     R* speed;                // |u| plane, atlas-shaped
     double* tile_part;       // [ntiles][kSlots][kConsumerWarps][4] check partials
@@ -156,9 +159,14 @@ __host__ __device__ constexpr int batch_box_w() { return TJ + 2 * (16 / (int)siz
 template <class S, bool SW, bool TH, int TK, int TJ>
 __host__ __device__ constexpr int batch_stage_elems() { return nplanes<SW, TH>() * TK * batch_box_w<S, TK, TJ>(); }
 
+// Three stages where they leave room for two CTAs per SM (228 KB of shared
+// memory per SM, 1 KB of it reserved per CTA), else two.
 template <class S, bool SW, bool TH, int TK, int TJ>
 __host__ __device__ constexpr int batch_nstages() {
-    return 3 * batch_stage_elems<S, SW, TH, TK, TJ>() * (int)sizeof(S) <= 200 * 1024 ? 3 : 2;
+    return 3 * (batch_stage_elems<S, SW, TH, TK, TJ>() * (int)sizeof(S) + kSlots * (int)sizeof(SlotDesc) +
+                (int)sizeof(TileMeta)) + 128 <= 112 * 1024
+               ? 3
+               : 2;
 }
 
 // Dynamic shared memory: the stages (128-byte aligned), then the slot
@@ -306,18 +314,31 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
     }
 }
 
-// Persistent, warp-specialised bulk update of every domain of the batch
-// (even step: every node; odd step: interior nodes).  The producer lane
-// stages, per tile, the population boxes (TMA), each slot's domain
-// descriptor (bulk copy) and the tile record with the slots' a(t) (plain
-// shared stores), all completing on the stage's full barrier.  SW: every
-// domain carries g; TH: shelves may carry h (per-tile flag); WET: some domain
-// has a wet wall (its wall nodes keep their state in even steps).
+// Whether the bulk kernel has a producer warp.  With one, a lane of a ninth
+// warp issues the tiles and the eight consumer warps only compute; two CTAs
+// of nine warps leave each thread 96 registers.  Without one, thread 0 of
+// the eight warps issues between its own tiles, leaving 128 registers per
+// thread: the odd step with FP32 storage (its shifted stores keep more
+// addresses live) runs faster that way, the other kernels with the producer.
+template <class S, int PAR>
+__host__ __device__ constexpr bool batch_producer_warp() { return !(PAR == 1 && sizeof(S) == 4); }
+template <class S, int PAR>
+__host__ __device__ constexpr int batch_threads() { return kBulkThreads + (batch_producer_warp<S, PAR>() ? 32 : 0); }
+
+// Persistent bulk update of every domain of the batch (even step: every
+// node; odd step: interior nodes).  Per tile, the issuing thread stages the
+// population boxes (TMA), the tile record, each slot's domain descriptor and
+// its a(t) (bulk copies), all completing on the stage's full barrier, and
+// refills a stage with the tile NS ahead once every consumer warp has
+// released it.  SW: every domain carries g; TH: shelves may carry h
+// (per-tile flag); WET: some domain has a wet wall (its wall nodes keep
+// their state in even steps).
 template <class S, class R, bool SW, bool TH, int PAR, bool CHK, int TK, int TJ, bool WET>
-__global__ void __launch_bounds__(kBulkThreads + 32, 2)
+__global__ void __launch_bounds__(batch_threads<S, PAR>(), 2)
 k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
     constexpr int NS = batch_nstages<S, SW, TH, TK, TJ>();
     constexpr int STAGE = batch_stage_elems<S, SW, TH, TK, TJ>();
+    constexpr bool PW = batch_producer_warp<S, PAR>();
     using RC = typename std::conditional<std::is_same<R, float>::value, F2, R>::type;
     static_assert(std::is_same<R, float>::value, "batch arithmetic is FP32");
     static_assert(TK * TJ == 2 * kBulkThreads, "two nodes of one column per consumer thread");
@@ -330,6 +351,9 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
     __shared__ __align__(8) uint64_t full[NS];
     __shared__ __align__(8) uint64_t empty[NS];
     __shared__ volatile int abort_flag;
+    // records of the tiles thread 0 issues next, fetched one tile ahead (no
+    // producer warp; two buffers: the one being filled is never the one read)
+    __shared__ __align__(16) TileRec rec[2];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = A.ntiles;
@@ -343,11 +367,32 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
     }
     __syncthreads();
 
-    if (warp == kConsumerWarps) {
+    // The issuing thread: stage u % NS gets the block's u-th tile, at atlas
+    // position pos, from its record rc.
+    const bool issuer = PW ? (warp == kConsumerWarps && lane == 0) : tid == 0;
+    unsigned issued = 0u, issued_par = 0u;  // stages issued (bit s), parity of the last phase of each
+    auto issue = [&](int u, int pos, const TileRec& rc) {
+        const int s = u % NS;
+        TileMeta& M = meta[s];
+        const int nseg = rc.nseg;
+        mbar_arrive_expect_tx(&full[s], batch_tile_bytes<S, SW, TH, TK, TJ>(rc.th != 0) + (uint32_t)sizeof(TileRec) +
+                                            (uint32_t)(nseg * (sizeof(SlotDesc) + sizeof(M.az[0]))));
+        bulk_copy_g2s(&M.r, A.tiles + pos, sizeof(TileRec), &full[s]);
+#pragma unroll
+        for (int q = 0; q < kSlots; ++q) {
+            if (q < nseg) {
+                bulk_copy_g2s(&slots[s * kSlots + q], A.slots + rc.dom[q], sizeof(SlotDesc), &full[s]);
+                bulk_copy_g2s(&M.az[q][0], A.dom_az16 + 4 * rc.dom[q] + 2 * PAR, sizeof(M.az[0]), &full[s]);
+            }
+        }
+        batch_issue<S, SW, TH, PAR, TK, TJ>(&map, sm + s * STAGE, &full[s], rc.j0, rc.k0, rc.th != 0);
+        issued |= 1u << s;
+        issued_par = (issued_par & ~(1u << s)) | ((unsigned)((u / NS) & 1) << s);
+    };
+
+    if (PW && warp == kConsumerWarps) {
         if (lane == 0) {
             prefetch_tensormap(&map);
-            int last_par[NS];
-            for (int s = 0; s < NS; ++s) last_par[s] = -1;
             int it = 0;
             for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++it) {
                 const int s = it % NS;
@@ -356,40 +401,22 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
                     break;
                 }
                 if (abort_flag) break;
-                const int4* src = reinterpret_cast<const int4*>(A.tiles + batch_tile_at<PAR>(i, ntiles));
-                const int4 w0 = src[0], w1 = src[1], w2 = src[2];
-                TileMeta& M = meta[s];
-                M.r.k0 = w0.x;
-                M.r.j0 = w0.y;
-                M.r.nseg = w0.z;
-                M.r.th = w0.w;
-                M.r.start[0] = w1.x;
-                M.r.start[1] = w1.y;
-                M.r.start[2] = w1.z;
-                M.r.start[3] = w1.w;
-                M.r.dom[0] = w2.x;
-                M.r.dom[1] = w2.y;
-                M.r.dom[2] = w2.z;
-                M.r.dom[3] = w2.w;
-                const int dom[kSlots] = {w2.x, w2.y, w2.z, w2.w};
-#pragma unroll
-                for (int q = 0; q < kSlots; ++q)
-                    if (q < w0.z) M.az[q] = (float)A.dom_az[2 * dom[q] + PAR];
-                // the plain stores above are released by the arrive below
-                mbar_arrive_expect_tx(&full[s], batch_tile_bytes<S, SW, TH, TK, TJ>(w0.w != 0) +
-                                                    (uint32_t)(w0.z * sizeof(SlotDesc)));
-#pragma unroll
-                for (int q = 0; q < kSlots; ++q)
-                    if (q < w0.z) bulk_copy_g2s(&slots[s * kSlots + q], A.slots + dom[q], sizeof(SlotDesc), &full[s]);
-                batch_issue<S, SW, TH, PAR, TK, TJ>(&map, sm + s * STAGE, &full[s], w0.y, w0.x, w0.w != 0);
-                last_par[s] = (it / NS) & 1;
-            }
-            if (abort_flag) {
-                for (int s = 0; s < NS; ++s)
-                    if (last_par[s] >= 0) mbar_wait_bounded(&full[s], (uint32_t)last_par[s], kWaitCycles);
+                const int pos = batch_tile_at<PAR>(i, ntiles);
+                const TileRec rc = A.tiles[pos];
+                issue(it, pos, rc);
             }
         }
     } else {
+        if (!PW && tid == 0) {
+            prefetch_tensormap(&map);
+            for (int u = 0; u < NS; ++u) {
+                const int i = blockIdx.x + u * gridDim.x;
+                if (i >= ntiles) break;
+                const int pos = batch_tile_at<PAR>(i, ntiles);
+                rec[0] = A.tiles[pos];
+                issue(u, pos, rec[0]);
+            }
+        }
         const int jj = tid % TJ;
         const int rr0 = tid / TJ;
         // check steps with a residual: |u| of the previous level at this
@@ -411,6 +438,14 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
             const int tile = batch_tile_at<PAR>(i, ntiles);
             const R sp_old[2] = {sp_next[0], sp_next[1]};
             prefetch_speed(i + gridDim.x);
+            const int inext = i + NS * gridDim.x;  // the tile that refills stage s (no producer warp)
+            if (!PW && tid == 0 && inext < ntiles) {
+                const int4* src = reinterpret_cast<const int4*>(A.tiles + batch_tile_at<PAR>(inext, ntiles));
+                int4* dst = reinterpret_cast<int4*>(&rec[it & 1]);
+#pragma unroll
+                for (int w = 0; w < 3; ++w) cp_async16(dst + w, src + w);
+                cp_async_commit();
+            }
             if (!mbar_wait_bounded(&full[s], (uint32_t)((it / NS) & 1), kWaitCycles) || abort_flag) {
                 abort_flag = 1;
                 break;
@@ -421,7 +456,7 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
 #pragma unroll
             for (int u = 1; u < kSlots; ++u) q += (u < nseg && jj >= M.r.start[u]) ? 1 : 0;
             const SlotDesc& D = slots[s * kSlots + q];
-            const R az = R(M.az[q]);
+            const R az = R(M.az[q][0]);
             const int jl = j0 + jj - D.col0;
             const double rj = D.r0 + (double)jl + (D.axis_node ? 0.0 : 0.5);
             const R inv_r = rj > 0.0 ? rcp(R(rj)) : R(0);
@@ -435,7 +470,19 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
             if (CHK) warp_slot_store(red, q, slots + s * kSlots, A.tile_part + 4ll * kSlots * kConsumerWarps * tile);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
+            // no producer warp: thread 0 refills this stage once every warp is done with it
+            if (!PW && tid == 0 && inext < ntiles) {
+                cp_async_wait_all();
+                if (mbar_wait_bounded(&empty[s], (uint32_t)((it / NS) & 1), kWaitCycles))
+                    issue(it + NS, batch_tile_at<PAR>(inext, ntiles), rec[it & 1]);
+                else
+                    abort_flag = 1;
+            }
         }
+    }
+    if (issuer && abort_flag) {  // let the copies in flight land before the block exits
+        for (int s = 0; s < NS; ++s)
+            if ((issued >> s) & 1u) mbar_wait_bounded(&full[s], (issued_par >> s) & 1u, kWaitCycles);
     }
     __syncthreads();
     if (abort_flag) {
@@ -445,8 +492,11 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
     // the even step is the last kernel of its step: move every domain's force to the next level
     if (PAR == 0 && blockIdx.x == 0) {
         const long long t1 = A.clock->t + 1;
-        for (int d = tid; d < A.ndom; d += blockDim.x)
-            A.dom_az[2 * d + 1] = A.doms[d].az0 * cos(A.doms[d].omega_t * (double)t1);
+        for (int d = tid; d < A.ndom; d += blockDim.x) {
+            const double a = A.doms[d].az0 * cos(A.doms[d].omega_t * (double)t1);
+            A.dom_az[2 * d + 1] = a;
+            A.dom_az16[4 * d + 2] = a;
+        }
         __syncthreads();
         if (tid == 0) A.clock->t = t1;
     }
@@ -492,8 +542,11 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_batch(const BatchArgs<S, 
     // level (other blocks read only the odd slot)
     if (advance && blockIdx.x == 0) {
         const long long t1 = A.clock->t + 1;
-        for (int d = threadIdx.x; d < A.ndom; d += blockDim.x)
-            A.dom_az[2 * d] = A.doms[d].az0 * cos(A.doms[d].omega_t * (double)t1);
+        for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) {
+            const double a = A.doms[d].az0 * cos(A.doms[d].omega_t * (double)t1);
+            A.dom_az[2 * d] = a;
+            A.dom_az16[4 * d] = a;
+        }
         __syncthreads();
         if (threadIdx.x == 0) A.clock->t = t1;
     }

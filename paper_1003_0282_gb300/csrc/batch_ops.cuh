@@ -21,6 +21,7 @@ BatchArgs<S, R> batch_args(axlbm_batch* b) {
     A.ring = reinterpret_cast<const int2*>(b->mem + L.off_ring);
     A.nring = L.nring;
     A.dom_az = reinterpret_cast<double*>(b->mem + L.off_az);
+    A.dom_az16 = A.dom_az + 2 * b->n;
     A.clock = reinterpret_cast<Clock*>(b->mem + L.off_clock);
     A.speed = reinterpret_cast<R*>(b->mem + L.off_speed);
     A.tile_part = reinterpret_cast<double*>(b->mem + L.off_tilepart);
@@ -76,14 +77,14 @@ cudaError_t launch_bulk_batch(axlbm_batch* b, const BatchArgs<S, R>& A) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBulkThreads + 32, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, batch_threads<S, PAR>(), smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         long long g = (long long)b->num_sms * per_sm;
         if (g > A.ntiles) g = A.ntiles;
         grid = (int)(g < 1 ? 1 : g);
     }
-    kern<<<grid, kBulkThreads + 32, smem, b->stream>>>(b->tmap[SH], A);
+    kern<<<grid, batch_threads<S, PAR>(), smem, b->stream>>>(b->tmap[SH], A);
     return cudaGetLastError();
 }
 
