@@ -38,8 +38,8 @@ sys.path.insert(0, ROOT)
 # captured launch, keyed by kernel and the SHA-256 prefix of the kernel source
 # at capture time.  Reported as null once the source has changed.
 NCU_TRAFFIC = {
-    # profiles/k_bulk_batch_fp32_sweep320_launches.md: one even and one odd launch of the full sweep
-    "batch fp32": {"src_sha": "95187a53c6ea0ed2", "dram_per_alg_byte": 0.9929},
+    # profiles/k_bulk_batch_fp32_sweep320_launches.md: one even and one odd launch of the full sweep, 4 x 128 tiles
+    "batch fp32": {"src_sha": "5ba539b382dbcd8d", "dram_per_alg_byte": 0.9892},
 }
 
 
@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--workload", choices=["batch", "pipe", "warmstart"], default="batch",
                    help="warmstart: time to a steady state from rest and from the warm-start network")
     p.add_argument("--scale", type=float, default=1.0, help="batch: shrink every domain (small profiling cases)")
+    p.add_argument("--tile", default=None, help="batch: bulk tile shape RxN (4x128 or 8x64) instead of the timed one")
     p.add_argument("--nr", type=int, default=4096)
     p.add_argument("--nz", type=int, default=8192)
     p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
@@ -301,6 +302,8 @@ def main():
         timing_on = lambda on: B.axlbm_batch_kernel_timing(solver.handle, on)
         kernel_times = lambda: B.axlbm_batch_kernel_times(solver.handle)
         parity_times = lambda: B.axlbm_batch_kernel_times_by_parity(solver.handle)
+        if args.tile:
+            solver.tile_shape = tuple(int(v) for v in args.tile.split("x"))
         tile = solver.tile_shape
         workload = (f"batched uneven sweep: {sum(not p.temperature for p in problems)} rotating-lid cavities + "
                     f"{sum(p.temperature for p in problems)} Wheeler-type cells with temperature, one persistent "

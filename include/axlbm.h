@@ -349,6 +349,11 @@ AXLBM_API axlbm_status axlbm_batch_set_populations(axlbm_batch* b, int32_t d, co
 AXLBM_API axlbm_status axlbm_batch_time(const axlbm_batch* b, int64_t* time);
 AXLBM_API axlbm_status axlbm_batch_tile_shape(const axlbm_batch* b, int32_t* rows, int32_t* nodes);
 
+/* Use the bulk tile shape rows x nodes (4 x 128 or 8 x 64) from the next
+ * step on, instead of the one timed at creation (for profiling a given
+ * shape; results do not depend on it).  AXLBM_EINVAL for another shape. */
+AXLBM_API axlbm_status axlbm_batch_set_tile_shape(axlbm_batch* b, int32_t rows, int32_t nodes);
+
 /* Bulk-kernel timing of the batch, as axlbm_kernel_timing / axlbm_kernel_times. */
 AXLBM_API axlbm_status axlbm_batch_kernel_timing(axlbm_batch* b, int32_t enable);
 AXLBM_API axlbm_status axlbm_batch_kernel_times(axlbm_batch* b, int64_t* bulk_launches, double* bulk_ms,

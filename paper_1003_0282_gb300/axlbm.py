@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
         L.axlbm_batch_set_populations.argtypes = [H, ctypes.c_int32, dp, dp, dp]
         L.axlbm_batch_time.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_batch_tile_shape.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+        L.axlbm_batch_set_tile_shape.argtypes = [H, ctypes.c_int32, ctypes.c_int32]
         L.axlbm_batch_kernel_timing.argtypes = [H, ctypes.c_int32]
         L.axlbm_batch_kernel_times.argtypes = [H, ctypes.POINTER(ctypes.c_int64), dp, dp, ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_batch_kernel_times_by_parity.argtypes = [H, ctypes.POINTER(ctypes.c_int64), dp, dp]
@@ -141,6 +142,7 @@ def lib() -> ctypes.CDLL:
         for name in ("axlbm_batch_state_bytes", "axlbm_batch_create", "axlbm_batch_step", "axlbm_batch_residuals",
                      "axlbm_batch_moments", "axlbm_batch_set_fields", "axlbm_batch_get_populations",
                      "axlbm_batch_set_populations", "axlbm_batch_time", "axlbm_batch_tile_shape",
+                     "axlbm_batch_set_tile_shape",
                      "axlbm_batch_kernel_timing", "axlbm_batch_kernel_times", "axlbm_batch_kernel_times_by_parity",
                      "axlbm_batch_destroy",
                      "axlbm_batch_set_fields_all", "axlbm_batch_moments_all"):
@@ -495,6 +497,10 @@ class Batch:
     @property
     def tile_shape(self):
         return axlbm_batch_tile_shape(self.handle)
+
+    @tile_shape.setter
+    def tile_shape(self, shape):
+        _bcheck(lib().axlbm_batch_set_tile_shape(self.handle, int(shape[0]), int(shape[1])), self.handle)
 
     def residuals(self, allow_nonfinite: bool = False) -> np.ndarray:
         """[n][3]: residual (Eq. 57), mass, budget of each domain's last check step."""

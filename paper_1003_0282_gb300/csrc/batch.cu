@@ -815,6 +815,17 @@ axlbm_status axlbm_batch_tile_shape(const axlbm_batch* b, int32_t* rows, int32_t
     return AXLBM_OK;
 }
 
+axlbm_status axlbm_batch_set_tile_shape(axlbm_batch* b, int32_t rows, int32_t nodes) {
+    if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
+    for (int s = 0; s < axl::kBatchShapes; ++s) {
+        if (axl::kShapeTK[s] == rows && axl::kShapeTJ[s] == nodes) {
+            b->shape = s;
+            return AXLBM_OK;
+        }
+    }
+    return bfail(b, AXLBM_EINVAL, "no bulk tile shape " + std::to_string(rows) + " x " + std::to_string(nodes));
+}
+
 axlbm_status axlbm_batch_kernel_timing(axlbm_batch* b, int32_t enable) {
     if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
     if (enable) {

@@ -254,3 +254,32 @@ def test_kernel_times_split_by_parity(B):
     B.axlbm_batch_kernel_timing(batch.handle, True)  # re-enabling clears the totals
     assert B.axlbm_batch_kernel_times_by_parity(batch.handle)[0] == [0, 0]
     batch.close()
+
+
+def test_results_do_not_depend_on_the_tile_shape(B):
+    """Every bulk tile shape gives the same populations and residuals bit for
+    bit (each node's update depends only on its own inputs), including a
+    switch of shape between calls; the mass and budget sums differ only by
+    their summation order.  An unknown shape is refused."""
+    doms = mixed_batch()
+    runs = []
+    for shapes in ([(4, 128), (4, 128)], [(8, 64), (8, 64)], [(8, 64), (4, 128)]):
+        batch = B.Batch(doms, "fp32")
+        for d, pb in enumerate(doms):
+            st = seeded_state(pb, seed=70 + d)
+            batch.set_populations(d, st.f, st.g, st.h if pb.temperature else None)
+        for shape in shapes:
+            batch.tile_shape = shape
+            assert batch.tile_shape == shape
+            batch.step(3)
+        with pytest.raises(B.AxlbmError):
+            batch.tile_shape = (4, 64)
+        runs.append(([batch.get_populations(d) for d in range(len(doms))], batch.residuals()))
+        batch.close()
+    pops0, res0 = runs[0]
+    for pops, res in runs[1:]:
+        assert np.array_equal(res[:, 0], res0[:, 0])
+        assert np.all(np.abs(res[:, 1:] - res0[:, 1:]) <= 1e-9 * res0[:, 1:2])
+        for d in range(len(doms)):
+            for x, y in zip(pops[d], pops0[d]):
+                assert (x is None and y is None) or np.array_equal(x, y), d
