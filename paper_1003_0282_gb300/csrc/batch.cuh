@@ -446,29 +446,38 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
                 for (int w = 0; w < 3; ++w) cp_async16(dst + w, src + w);
                 cp_async_commit();
             }
-            if (!mbar_wait_bounded(&full[s], (uint32_t)((it / NS) & 1), kWaitCycles) || abort_flag) {
+            // a lane whose wait gave up skips the tile; the warp leaves the loop
+            // together below (its lanes meet in warp-wide operations)
+            const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((it / NS) & 1), kWaitCycles);
+            if (CHK ? __all_sync(0xffffffffu, ok) : ok) {
+                const TileMeta& M = meta[s];
+                const int k0 = M.r.k0, j0 = M.r.j0, nseg = M.r.nseg;
+                int q = 0;
+#pragma unroll
+                for (int u = 1; u < kSlots; ++u) q += (u < nseg && jj >= M.r.start[u]) ? 1 : 0;
+                const SlotDesc& D = slots[s * kSlots + q];
+                const R az = R(M.az[q][0]);
+                const int jl = j0 + jj - D.col0;
+                const double rj = D.r0 + (double)jl + (D.axis_node ? 0.0 : 0.5);
+                const R inv_r = rj > 0.0 ? rcp(R(rj)) : R(0);
+                const S* st = sm + s * STAGE;
+                RedR<R> red{R(0), R(0), R(0), 0, 0};
+                const bool dth = TH && M.r.th;
+                // one node pair per thread: rows rr0 and rr0 + TK/2 of column jj
+                static_assert(kBulkThreads / TJ == TK / 2, "one pair per consumer thread");
+                if (dth)
+                    batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old, red);
+                else
+                    batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old,
+                                                                             red);
+                if (CHK)
+                    warp_slot_store(red, q, slots + s * kSlots, A.tile_part + 4ll * kSlots * kConsumerWarps * tile);
+            }
+            __syncwarp();
+            if (!__all_sync(0xffffffffu, ok && !abort_flag)) {
                 abort_flag = 1;
                 break;
             }
-            const TileMeta& M = meta[s];
-            const int k0 = M.r.k0, j0 = M.r.j0, nseg = M.r.nseg;
-            int q = 0;
-#pragma unroll
-            for (int u = 1; u < kSlots; ++u) q += (u < nseg && jj >= M.r.start[u]) ? 1 : 0;
-            const SlotDesc& D = slots[s * kSlots + q];
-            const R az = R(M.az[q][0]);
-            const int jl = j0 + jj - D.col0;
-            const double rj = D.r0 + (double)jl + (D.axis_node ? 0.0 : 0.5);
-            const R inv_r = rj > 0.0 ? rcp(R(rj)) : R(0);
-            const S* st = sm + s * STAGE;
-            RedR<R> red{R(0), R(0), R(0), 0, 0};
-            const bool dth = TH && M.r.th;
-            // one node pair per thread: rows rr0 and rr0 + TK/2 of column jj
-            static_assert(kBulkThreads / TJ == TK / 2, "one pair per consumer thread");
-            if (dth) batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old, red);
-            else batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old, red);
-            if (CHK) warp_slot_store(red, q, slots + s * kSlots, A.tile_part + 4ll * kSlots * kConsumerWarps * tile);
-            __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
             // no producer warp: thread 0 refills this stage once every warp is done with it
             if (!PW && tid == 0 && inext < ntiles) {

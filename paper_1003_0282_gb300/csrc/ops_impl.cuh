@@ -737,15 +737,14 @@ k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
                     sp_old[m] = (A.residual && j < G.nr && k < G.nz) ? A.speed[(long long)k * G.pitch + j] : R(0);
                 }
             }
-            if (!mbar_wait_bounded(&full[s], (uint32_t)((it / NS) & 1), kWaitCycles) || abort_flag) {
-                abort_flag = 1;
-                break;
-            }
+            // a lane whose wait gave up skips the tile; the warp leaves the loop
+            // together below (its lanes meet in __syncwarp)
+            const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((it / NS) & 1), kWaitCycles);
             const S* st = sm + s * STAGE;
             const double rj = node_radius(G, j);
             const Sc inv_r = rj > 0.0 ? rcp(Sc(rj)) : Sc(0);
 #pragma unroll
-            for (int rr = tid / kTileJ; rr < kTileK / NL; rr += kBulkThreads / kTileJ) {
+            for (int rr = tid / kTileJ; ok && rr < kTileK / NL; rr += kBulkThreads / kTileJ) {
                 bool act[NL];
                 int kk[NL];
                 bool any = false;
@@ -841,6 +840,10 @@ k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
                 }
             }
             __syncwarp();
+            if (!__all_sync(0xffffffffu, ok && !abort_flag)) {
+                abort_flag = 1;
+                break;
+            }
             if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with stage s
         }
     }
