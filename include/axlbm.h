@@ -273,6 +273,16 @@ AXLBM_API axlbm_status axlbm_check_static(const axlbm_grid* grid, double tau, co
                                           const double* speed_prev, double* speed_out, double* out,
                                           void* cuda_stream);
 
+/* Self-test of the error path of the bounded device waits (every wait of the
+ * bulk kernels on a TMA copy gives up after a cycle budget, and the call then
+ * returns AXLBM_ETIMEOUT).  Runs one warp that waits on an mbarrier phase
+ * nothing completes, with a budget of max_cycles SM clock cycles (1e3 ..
+ * 4e9; 2e6 is about 1 ms), on a stream of its own, and synchronises.
+ *   gave_up: receives how many of the 32 threads gave up (32 when the path
+ *     works);  err_word: receives the error word the warp raised (1).
+ * AXLBM_EINVAL for a budget out of range or NULL outputs. */
+AXLBM_API axlbm_status axlbm_selftest_bounded_wait(int64_t max_cycles, int32_t* gave_up, uint32_t* err_word);
+
 /* ------------------------------------------------------------------ batches
  * Many independent domains of uneven size advanced together: every step is
  * one persistent launch over a packed tile list of all domains (plus one

@@ -121,6 +121,8 @@ def lib() -> ctypes.CDLL:
         L.axlbm_batch_set_populations.argtypes = [H, ctypes.c_int32, dp, dp, dp]
         L.axlbm_batch_time.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_batch_tile_shape.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+        L.axlbm_selftest_bounded_wait.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                                                  ctypes.POINTER(ctypes.c_uint32)]
         L.axlbm_batch_set_tile_shape.argtypes = [H, ctypes.c_int32, ctypes.c_int32]
         L.axlbm_batch_kernel_timing.argtypes = [H, ctypes.c_int32]
         L.axlbm_batch_kernel_times.argtypes = [H, ctypes.POINTER(ctypes.c_int64), dp, dp, ctypes.POINTER(ctypes.c_int64)]
@@ -149,7 +151,8 @@ def lib() -> ctypes.CDLL:
             getattr(L, name).restype = ctypes.c_int
         for name in ("axlbm_state_bytes", "axlbm_create", "axlbm_step", "axlbm_moments", "axlbm_residual",
                      "axlbm_set_fields", "axlbm_get_populations", "axlbm_set_populations", "axlbm_time",
-                     "axlbm_destroy", "axlbm_kernel_timing", "axlbm_kernel_times", "axlbm_check_static"):
+                     "axlbm_destroy", "axlbm_kernel_timing", "axlbm_kernel_times", "axlbm_check_static",
+                     "axlbm_selftest_bounded_wait"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -455,6 +458,13 @@ def axlbm_batch_kernel_times_by_parity(b):
     ms, by = (ctypes.c_double * 2)(), (ctypes.c_double * 2)()
     _bcheck(lib().axlbm_batch_kernel_times_by_parity(b, nb, ms, by), b)
     return list(nb), list(ms), list(by)
+
+
+def axlbm_selftest_bounded_wait(max_cycles: int):
+    """(threads that gave up, error word) of a warp whose bounded wait can never complete."""
+    n, err = ctypes.c_int32(), ctypes.c_uint32()
+    _check(lib().axlbm_selftest_bounded_wait(int(max_cycles), ctypes.byref(n), ctypes.byref(err)), None)
+    return int(n.value), int(err.value)
 
 
 def axlbm_batch_destroy(b) -> None:
