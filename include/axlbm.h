@@ -359,6 +359,18 @@ AXLBM_API axlbm_status axlbm_batch_set_populations(axlbm_batch* b, int32_t d, co
 AXLBM_API axlbm_status axlbm_batch_time(const axlbm_batch* b, int64_t* time);
 AXLBM_API axlbm_status axlbm_batch_tile_shape(const axlbm_batch* b, int32_t* rows, int32_t* nodes);
 
+/* Runs of plain lattice steps (all but the two check steps that end every
+ * axlbm_batch_step call) are replayed from CUDA graphs captured on first use
+ * (8 and 1 pairs of an even and an odd step; recaptured after a tile shape
+ * change) when enable != 0, the default, and while kernel timing is off;
+ * enable = 0 launches every kernel directly.  The results are the same bit
+ * for bit.  The first capture synchronises nothing but takes a few ms. */
+AXLBM_API axlbm_status axlbm_batch_use_graphs(axlbm_batch* b, int32_t enable);
+
+/* How many times the step graphs were captured and launched since creation
+ * (either pointer may be NULL). */
+AXLBM_API axlbm_status axlbm_batch_graph_stats(const axlbm_batch* b, int64_t* captures, int64_t* launches);
+
 /* Use the bulk tile shape rows x nodes (4 x 128 or 8 x 64) from the next
  * step on, instead of the one timed at creation (for profiling a given
  * shape; results do not depend on it).  AXLBM_EINVAL for another shape. */

@@ -124,6 +124,8 @@ def lib() -> ctypes.CDLL:
         L.axlbm_selftest_bounded_wait.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
                                                   ctypes.POINTER(ctypes.c_uint32)]
         L.axlbm_batch_set_tile_shape.argtypes = [H, ctypes.c_int32, ctypes.c_int32]
+        L.axlbm_batch_use_graphs.argtypes = [H, ctypes.c_int32]
+        L.axlbm_batch_graph_stats.argtypes = [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_batch_kernel_timing.argtypes = [H, ctypes.c_int32]
         L.axlbm_batch_kernel_times.argtypes = [H, ctypes.POINTER(ctypes.c_int64), dp, dp, ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_batch_kernel_times_by_parity.argtypes = [H, ctypes.POINTER(ctypes.c_int64), dp, dp]
@@ -144,7 +146,7 @@ def lib() -> ctypes.CDLL:
         for name in ("axlbm_batch_state_bytes", "axlbm_batch_create", "axlbm_batch_step", "axlbm_batch_residuals",
                      "axlbm_batch_moments", "axlbm_batch_set_fields", "axlbm_batch_get_populations",
                      "axlbm_batch_set_populations", "axlbm_batch_time", "axlbm_batch_tile_shape",
-                     "axlbm_batch_set_tile_shape",
+                     "axlbm_batch_set_tile_shape", "axlbm_batch_use_graphs", "axlbm_batch_graph_stats",
                      "axlbm_batch_kernel_timing", "axlbm_batch_kernel_times", "axlbm_batch_kernel_times_by_parity",
                      "axlbm_batch_destroy",
                      "axlbm_batch_set_fields_all", "axlbm_batch_moments_all"):
@@ -511,6 +513,16 @@ class Batch:
     @tile_shape.setter
     def tile_shape(self, shape):
         _bcheck(lib().axlbm_batch_set_tile_shape(self.handle, int(shape[0]), int(shape[1])), self.handle)
+
+    def use_graphs(self, enable: bool) -> None:
+        """Replay runs of plain steps from captured CUDA graphs (default) or launch every kernel."""
+        _bcheck(lib().axlbm_batch_use_graphs(self.handle, int(bool(enable))), self.handle)
+
+    def graph_stats(self):
+        """(captures, launches) of the step graphs since creation."""
+        c, n = ctypes.c_int64(), ctypes.c_int64()
+        _bcheck(lib().axlbm_batch_graph_stats(self.handle, ctypes.byref(c), ctypes.byref(n)), self.handle)
+        return int(c.value), int(n.value)
 
     def residuals(self, allow_nonfinite: bool = False) -> np.ndarray:
         """[n][3]: residual (Eq. 57), mass, budget of each domain's last check step."""

@@ -69,6 +69,15 @@ struct axlbm_batch {
     double bulk_ms, bulk_bytes;
     double par_ms[2], par_bytes[2];  // the same split by parity
     int64_t par_launches[2];
+    // runs of plain lattice steps replayed from captured CUDA graphs,
+    // captured on a stream of the library's own (the caller's stream may be
+    // the legacy default stream, which cannot be captured)
+    bool use_graphs;
+    cudaStream_t cap;
+    int graph_shape;                // tile shape the graphs were captured with (-1: none)
+    cudaGraphExec_t graph_many;     // kGraphPairs (even, odd) step pairs
+    cudaGraphExec_t graph_one;      // one pair
+    int64_t graph_captures, graph_launches;
     std::string err;
 };
 

@@ -283,3 +283,40 @@ def test_results_do_not_depend_on_the_tile_shape(B):
         for d in range(len(doms)):
             for x, y in zip(pops[d], pops0[d]):
                 assert (x is None and y is None) or np.array_equal(x, y), d
+
+
+def test_graph_replay_matches_direct_launches(B):
+    """Runs of plain steps replayed from captured CUDA graphs give the same
+    populations and check values bit for bit as launching every kernel, from
+    an odd start, across a tile-shape change (recapture) and with wet-wall
+    and node-on-axis domains in the batch (their passes are in the graph)."""
+    doms = mixed_batch() + [
+        dataclasses.replace(I.wheeler_cell(nr=21, re_x=200.0, prandtl=1.0, grashof=1e4), inner="axis_node"),
+        dataclasses.replace(I.rotating_lid_cavity(nr=17, aspect=1.5, re=200.0), outer="nee", z_lo="nee"),
+    ]
+    out = []
+    for graphs in (True, False):
+        batch = B.Batch(doms, "fp32")
+        batch.use_graphs(graphs)
+        for d, pb in enumerate(doms):
+            st = seeded_state(pb, seed=90 + d)
+            batch.set_populations(d, st.f, st.g, st.h if pb.temperature else None)
+        batch.step(1)
+        for n in (23, 30):
+            batch.step(n)
+        batch.tile_shape = (8, 64) if batch.tile_shape == (4, 128) else (4, 128)
+        batch.step(21)  # sizes the new shape's kernels if no tuning run did
+        batch.step(21)
+        caps, launches = batch.graph_stats()
+        if graphs:
+            assert caps == 2 and launches >= 3, (caps, launches)
+        else:
+            assert caps == 0 and launches == 0
+        out.append(([batch.get_populations(d) for d in range(len(doms))], batch.residuals(), batch.time))
+        batch.close()
+    (p0, r0, t0), (p1, r1, t1) = out
+    assert t0 == t1 == 96
+    assert np.array_equal(r0, r1)
+    for d in range(len(doms)):
+        for x, y in zip(p0[d], p1[d]):
+            assert (x is None and y is None) or np.array_equal(x, y), d
