@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 # at capture time.  Reported as null once the source has changed.
 NCU_TRAFFIC = {
     # profiles/k_bulk_batch_fp32_sweep320_launches.md: one even and one odd launch of the full sweep, 4 x 128 tiles
-    "batch fp32": {"src_sha": "57e90e41c355e912", "dram_per_alg_byte": 0.9896},
+    "batch fp32": {"src_sha": "8a84e93db924f223", "dram_per_alg_byte": 0.9896},
 }
 
 
