@@ -337,12 +337,9 @@ def main():
         by_parity = parity_times() if parity_times else None
         timing_on(False)
     ms = ev0.elapsed_time(ev1)
-    if args.workload == "pipe":
-        graphs = "kernel by kernel"
-    else:
-        caps, glaunch = solver.graph_stats()
-        graphs = (f"plain step pairs from captured CUDA graphs ({glaunch} graph launches, {caps} captures)"
-                  if glaunch else "kernel by kernel")
+    caps, glaunch = solver.graph_stats()
+    graphs = (f"plain step pairs from captured CUDA graphs ({glaunch} graph launches, {caps} captures)"
+              if glaunch else "kernel by kernel")
     if args.workload == "pipe":
         res, mass, _ = solver.residual()
     else:

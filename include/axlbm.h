@@ -234,6 +234,18 @@ AXLBM_API axlbm_status axlbm_set_populations(axlbm_handle* h, const double* f, c
 /* Current time level. */
 AXLBM_API axlbm_status axlbm_time(const axlbm_handle* h, int64_t* time);
 
+/* Runs of plain steps (all but the two check steps that end every
+ * axlbm_step call) are replayed from CUDA graphs captured on first use (8
+ * and 1 pairs of an even and an odd step, on a stream of the library's own,
+ * launched on the handle's stream) when enable != 0, the default, and while
+ * kernel timing is off; enable = 0 launches every kernel directly.  The
+ * results are the same bit for bit. */
+AXLBM_API axlbm_status axlbm_use_graphs(axlbm_handle* h, int32_t enable);
+
+/* How many times the step graphs were captured and launched since creation
+ * (either pointer may be NULL). */
+AXLBM_API axlbm_status axlbm_graph_stats(const axlbm_handle* h, int64_t* captures, int64_t* launches);
+
 /* Device timing of the bulk update kernel (the kernel that moves almost all
  * bytes), for throughput and roofline reporting.  enable = 1 clears the
  * totals and starts recording a CUDA event pair around every bulk-kernel

@@ -99,6 +99,8 @@ def lib() -> ctypes.CDLL:
         L.axlbm_time.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_destroy.argtypes = [H]
         L.axlbm_kernel_timing.argtypes = [H, ctypes.c_int32]
+        L.axlbm_use_graphs.argtypes = [H, ctypes.c_int32]
+        L.axlbm_graph_stats.argtypes = [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_kernel_times.argtypes = [H, ctypes.POINTER(ctypes.c_int64), dp, dp, ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_check_static.argtypes = [ctypes.POINTER(axlbm_grid), ctypes.c_double,
                                          ctypes.POINTER(axlbm_forcing), ctypes.c_void_p, ctypes.c_void_p,
@@ -154,6 +156,7 @@ def lib() -> ctypes.CDLL:
         for name in ("axlbm_state_bytes", "axlbm_create", "axlbm_step", "axlbm_moments", "axlbm_residual",
                      "axlbm_set_fields", "axlbm_get_populations", "axlbm_set_populations", "axlbm_time",
                      "axlbm_destroy", "axlbm_kernel_timing", "axlbm_kernel_times", "axlbm_check_static",
+                     "axlbm_use_graphs", "axlbm_graph_stats",
                      "axlbm_selftest_bounded_wait"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -313,6 +316,16 @@ class Domain:
     # -- stepping
     def step(self, n: int) -> None:
         axlbm_step(self.handle, n)
+
+    def use_graphs(self, enable: bool) -> None:
+        """Replay runs of plain steps from captured CUDA graphs (default) or launch every kernel."""
+        _check(lib().axlbm_use_graphs(self.handle, int(bool(enable))), self.handle)
+
+    def graph_stats(self):
+        """(captures, launches) of the step graphs since creation."""
+        c, n = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().axlbm_graph_stats(self.handle, ctypes.byref(c), ctypes.byref(n)), self.handle)
+        return int(c.value), int(n.value)
 
     @property
     def time(self) -> int:

@@ -264,6 +264,11 @@ axlbm_status axlbm_create(const axlbm_grid* grid, double tau, const axlbm_forcin
     h->have_check = false;
     h->last_residual_valid = false;
     h->timing = false;
+    h->use_graphs = true;
+    h->graphs_ready = false;
+    h->cap = nullptr;
+    h->graph_many = h->graph_one = nullptr;
+    h->graph_captures = h->graph_launches = 0;
     h->check_parts = 0;
     h->bulk_grid[0][0] = h->bulk_grid[0][1] = h->bulk_grid[1][0] = h->bulk_grid[1][1] = 0;
     {
@@ -334,11 +339,95 @@ axlbm_status axlbm_create(const axlbm_grid* grid, double tau, const axlbm_forcin
     return AXLBM_OK;
 }
 
+constexpr int kGraphPairs = 8;     // step pairs per launch of the larger graph
+constexpr int kMinGraphPairs = 4;  // shorter runs of plain steps are launched kernel by kernel
+
+void drop_graphs(axlbm_handle* h) {
+    if (h->graph_many) cudaGraphExecDestroy(h->graph_many);
+    if (h->graph_one) cudaGraphExecDestroy(h->graph_one);
+    h->graph_many = h->graph_one = nullptr;
+    h->graphs_ready = false;
+}
+
+// Capture `pairs` plain (even, odd) step pairs and instantiate them; the
+// step functions launch on h->stream, which points at the capture stream
+// meanwhile.
+cudaError_t capture_pairs(axlbm_handle* h, const Ops* ops, int pairs, cudaGraphExec_t* out) {
+    const int saved = h->parity;
+    cudaStream_t caller = h->stream;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!h->cap) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    h->stream = h->cap;
+    for (int p = 0; p < pairs && e == cudaSuccess; ++p) {
+        for (int par = 0; par < 2 && e == cudaSuccess; ++par) {
+            h->parity = par;
+            int nl = 0;
+            e = ops->step(h, 0, 0, nullptr, nullptr, &nl);
+        }
+    }
+    h->stream = caller;
+    h->parity = saved;
+    const cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+// `pairs` plain step pairs from an even level, from the graphs.
+axlbm_status graph_pairs(axlbm_handle* h, const Ops* ops, int64_t pairs) {
+    if (!h->graphs_ready) {
+        cudaError_t e = capture_pairs(h, ops, kGraphPairs, &h->graph_many);
+        if (e == cudaSuccess) e = capture_pairs(h, ops, 1, &h->graph_one);
+        if (e != cudaSuccess) {
+            cudaGetLastError();  // the failed capture must not surface in a later call
+            drop_graphs(h);
+            return cuda_fail(h, e, "graph capture");
+        }
+        h->graphs_ready = true;
+        h->graph_captures += 1;
+    }
+    for (int64_t p = 0; p < pairs;) {
+        const bool many = pairs - p >= kGraphPairs;
+        const cudaError_t e = cudaGraphLaunch(many ? h->graph_many : h->graph_one, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+        p += many ? kGraphPairs : 1;
+        h->graph_launches += 1;
+    }
+    h->t += 2 * pairs;
+    h->speed_valid = false;
+    return AXLBM_OK;
+}
+
 axlbm_status axlbm_step(axlbm_handle* h, int64_t n) {
     if (!h) return fail(nullptr, AXLBM_EINVAL, "handle is NULL");
     if (n < 0) return fail(h, AXLBM_EINVAL, "n must be >= 0");
     const Ops* ops = ops_for(h->grid.precision);
-    for (int64_t s = 0; s < n; ++s) {
+    int64_t s = 0;
+    // every step but the last two (the check steps) is plain: with timing
+    // off, whole (even, odd) pairs of them replay captured graphs once the
+    // plain bulk kernels have been sized by earlier launches
+    const bool odd_bulk = h->G.nr > 2 && h->G.nz > 2;
+    const bool sized = h->bulk_grid[0][0] > 0 && (h->bulk_grid[1][0] > 0 || !odd_bulk);
+    if (h->use_graphs && !h->timing && sized && n - 2 - h->parity >= 2 * kMinGraphPairs) {
+        if (h->parity == 1) {
+            int nl = 0;
+            const cudaError_t e = ops->step(h, 0, 0, nullptr, nullptr, &nl);
+            if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+            h->speed_valid = false;
+            h->parity = 0;
+            h->t += 1;
+            s = 1;
+        }
+        const int64_t pairs = (n - 2 - s) / 2;
+        const axlbm_status st = graph_pairs(h, ops, pairs);
+        if (st != AXLBM_OK) return st;
+        s += 2 * pairs;
+    }
+    for (; s < n; ++s) {
         const bool last = s == n - 1;
         const bool before_last = s == n - 2;
         const int check = (last || before_last) ? 1 : 0;
@@ -370,6 +459,19 @@ axlbm_status axlbm_step(axlbm_handle* h, int64_t n) {
         h->parity ^= 1;
         h->t += 1;
     }
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_use_graphs(axlbm_handle* h, int32_t enable) {
+    if (!h) return fail(nullptr, AXLBM_EINVAL, "handle is NULL");
+    h->use_graphs = enable != 0;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_graph_stats(const axlbm_handle* h, int64_t* captures, int64_t* launches) {
+    if (!h) return AXLBM_EINVAL;
+    if (captures) *captures = h->graph_captures;
+    if (launches) *launches = h->graph_launches;
     return AXLBM_OK;
 }
 
@@ -548,6 +650,8 @@ axlbm_status axlbm_time(const axlbm_handle* h, int64_t* t) {
 axlbm_status axlbm_destroy(axlbm_handle* h) {
     if (!h) return AXLBM_EINVAL;
     cudaError_t e = cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    if (h->cap) cudaStreamDestroy(h->cap);
     for (auto ev : h->ev)
         if (ev) cudaEventDestroy(ev);
     if (h->owns_mem) {

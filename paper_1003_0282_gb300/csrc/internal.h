@@ -107,6 +107,13 @@ struct axlbm_handle {
     size_t ev_used;
     int64_t bulk_launches, all_launches;
     double bulk_ms, bulk_bytes;
+    // runs of plain steps replayed from captured CUDA graphs (captured on a
+    // stream of the library's own: the caller's may be the legacy stream)
+    bool use_graphs;
+    bool graphs_ready;
+    cudaStream_t cap;
+    cudaGraphExec_t graph_many, graph_one;  // kGraphPairs step pairs; one pair
+    int64_t graph_captures, graph_launches;
     std::string err;
 };
 
