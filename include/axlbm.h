@@ -458,6 +458,36 @@ AXLBM_API axlbm_status axlbm_ws_predict(axlbm_ws* w, const float* features, int3
  * height), clamped at the canvas edges.  Synchronises. */
 AXLBM_API axlbm_status axlbm_ws_fields(axlbm_ws* w, const float* canvas, int32_t n, const axlbm_ws_domain* doms,
                                        float* fields);
+/* Inverse of axlbm_ws_fields, for building training targets: n domains'
+ * moments (device, u_r, u_z, u_theta, T packed as [4][nz][nr] one domain
+ * after another) onto n canvases (device [n][4][256][128]): pixel (iz, ir)
+ * at r = (ir + 1/2)/128 r_wall, z = z_bottom + (iz + 1/2)/256 height,
+ * bilinear in the node values, clamped to the grid; velocities divided by
+ * u_scale, t_ref subtracted from T.  Synchronises. */
+AXLBM_API axlbm_status axlbm_ws_to_canvas(axlbm_ws* w, const float* moments, int32_t n, const axlbm_ws_domain* doms,
+                                          float* canvas);
+/* One training step of the network on n (1..16) canvases with the library's
+ * kernels: forward pass keeping the activations, mean squared error against
+ * target, backward pass (ReLU, pooling, upsampling and concatenation, im2col
+ * and its adjoint; weight and input gradients as BF16 GEMMs with FP32
+ * accumulation), then Adam (lr, beta1, beta2, eps; no weight decay) on FP32
+ * master weights, which start from the weights passed to axlbm_ws_create and
+ * are rounded to BF16 for every later forward pass.
+ *   features: device [n][AXLBM_WS_FEATURES]; target: device [n][4][256][128];
+ *   loss: receives the mean squared error before the update (or NULL).
+ * The first call allocates about 3 GB of training buffers.  Synchronises. */
+AXLBM_API axlbm_status axlbm_ws_train_step(axlbm_ws* w, const float* features, const float* target, int32_t n,
+                                           float lr, float beta1, float beta2, float eps, double* loss);
+/* Mean squared error of the network on n canvases (device features and
+ * targets as axlbm_ws_train_step; no update).  Synchronises. */
+AXLBM_API axlbm_status axlbm_ws_loss(axlbm_ws* w, const float* features, const float* target, int32_t n, double* loss);
+/* Gradient of the last training step's loss with respect to every weight
+ * (FP32, axlbm_ws_weight_count() values in the weight packing) into a host
+ * array.  AXLBM_EINVAL before the first step.  Synchronises. */
+AXLBM_API axlbm_status axlbm_ws_last_gradient(axlbm_ws* w, float* grad);
+/* The current weights (BF16 bit patterns, axlbm_ws_weight_count() values, in
+ * the packing of axlbm_ws_create) into a host array.  Synchronises. */
+AXLBM_API axlbm_status axlbm_ws_get_weights(axlbm_ws* w, uint16_t* weights);
 AXLBM_API axlbm_status axlbm_ws_destroy(axlbm_ws* w);
 /* Text of the last error on w (w == NULL: of the last failed create). */
 AXLBM_API const char* axlbm_ws_last_error(const axlbm_ws* w);

@@ -141,9 +141,16 @@ def lib() -> ctypes.CDLL:
         L.axlbm_ws_predict.argtypes = [V, V, ctypes.c_int32, V]
         L.axlbm_ws_fields.argtypes = [V, V, ctypes.c_int32, ctypes.POINTER(axlbm_ws_domain), V]
         L.axlbm_ws_destroy.argtypes = [V]
+        L.axlbm_ws_to_canvas.argtypes = [V, V, ctypes.c_int32, ctypes.POINTER(axlbm_ws_domain), V]
+        L.axlbm_ws_train_step.argtypes = [V, V, V, ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                          ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+        L.axlbm_ws_loss.argtypes = [V, V, V, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+        L.axlbm_ws_get_weights.argtypes = [V, V]
+        L.axlbm_ws_last_gradient.argtypes = [V, V]
         L.axlbm_ws_last_error.restype = ctypes.c_char_p
         L.axlbm_ws_last_error.argtypes = [V]
-        for name in ("axlbm_ws_create", "axlbm_ws_predict", "axlbm_ws_fields", "axlbm_ws_destroy"):
+        for name in ("axlbm_ws_create", "axlbm_ws_predict", "axlbm_ws_fields", "axlbm_ws_destroy", "axlbm_ws_to_canvas",
+                     "axlbm_ws_train_step", "axlbm_ws_loss", "axlbm_ws_get_weights", "axlbm_ws_last_gradient"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("axlbm_batch_state_bytes", "axlbm_batch_create", "axlbm_batch_step", "axlbm_batch_residuals",
                      "axlbm_batch_moments", "axlbm_batch_set_fields", "axlbm_batch_get_populations",
@@ -641,6 +648,43 @@ class WarmStart:
         doms = (axlbm_ws_domain * len(problems))(*[ws_domain(pb) for pb in problems])
         out = torch.empty(sum(5 * pb.cells for pb in problems), dtype=torch.float32, device="cuda")
         self._check(lib().axlbm_ws_fields(self.handle, canvas.data_ptr(), len(problems), doms, out.data_ptr()))
+        return out
+
+    def to_canvas(self, moments, problems):
+        """Canvases [n][4][256][128] (torch FP32 on the device) of every problem's
+        moments (device FP32, u_r, u_z, u_theta, T as [4][nz][nr] per problem, packed)."""
+        import torch
+        doms = (axlbm_ws_domain * len(problems))(*[ws_domain(pb) for pb in problems])
+        out = torch.empty((len(problems), 4) + WS_CANVAS, dtype=torch.float32, device="cuda")
+        self._check(lib().axlbm_ws_to_canvas(self.handle, moments.data_ptr(), len(problems), doms, out.data_ptr()))
+        return out
+
+    def train_step(self, features, target, lr, betas=(0.9, 0.999), eps=1e-8) -> float:
+        """One Adam step on 1..16 canvases (features and targets as torch FP32 on the
+        device); returns the mean squared error before the update."""
+        loss = ctypes.c_double()
+        self._check(lib().axlbm_ws_train_step(self.handle, features.data_ptr(), target.data_ptr(), features.shape[0],
+                                              float(lr), float(betas[0]), float(betas[1]), float(eps),
+                                              ctypes.byref(loss)))
+        return loss.value
+
+    def loss(self, features, target) -> float:
+        """Mean squared error on any number of canvases (torch FP32 on the device)."""
+        loss = ctypes.c_double()
+        self._check(lib().axlbm_ws_loss(self.handle, features.data_ptr(), target.data_ptr(), features.shape[0],
+                                        ctypes.byref(loss)))
+        return loss.value
+
+    def last_gradient(self) -> np.ndarray:
+        """FP32 gradient of the last training step's loss, in the weight packing."""
+        out = np.empty(self.count, dtype=np.float32)
+        self._check(lib().axlbm_ws_last_gradient(self.handle, out.ctypes.data))
+        return out
+
+    def weights(self) -> np.ndarray:
+        """The current weights as BF16 bit patterns (uint16)."""
+        out = np.empty(self.count, dtype=np.uint16)
+        self._check(lib().axlbm_ws_get_weights(self.handle, out.ctypes.data))
         return out
 
     def start(self, batch, problems):

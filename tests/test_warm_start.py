@@ -135,3 +135,136 @@ def test_batch_started_from_the_network(Bgpu):
     a.close()
     b.close()
     ws.close()
+
+
+def torch_reference(bits, feats):
+    """FP32 PyTorch reference of the network (weights widened from BF16 and
+    leaf tensors that take gradients), for the training tests."""
+    import torch
+    import torch.nn.functional as F
+    v = torch.tensor(WS.bf16_to_float(bits), dtype=torch.float32, device="cuda")
+    params, off = [], 0
+    for ci, co, k in WS.LAYERS:
+        n = co * ci * k * k
+        w = v[off:off + n].reshape(co, k, k, ci).permute(0, 3, 1, 2).contiguous() if k == 3 else \
+            v[off:off + n].reshape(co, ci, 1, 1).contiguous()
+        off += n
+        b = v[off:off + co].clone()
+        off += co
+        params += [w.requires_grad_(True), b.requires_grad_(True)]
+    f = torch.as_tensor(np.asarray(feats, dtype=np.float32), device="cuda")
+    n = f.shape[0]
+    x = torch.empty((n, 8, WS.H, WS.W), device="cuda")
+    x[:, :6] = f[:, :, None, None]
+    x[:, 6] = ((torch.arange(WS.W, device="cuda") + 0.5) / WS.W)[None, None, :]
+    x[:, 7] = ((torch.arange(WS.H, device="cuda") + 0.5) / WS.H)[None, :, None]
+    x = x.to(torch.bfloat16).float()
+    c = lambda i, t: F.conv2d(t, params[2 * i], params[2 * i + 1], padding=1 if WS.LAYERS[i][2] == 3 else 0)
+    e1 = F.relu(c(1, F.relu(c(0, x))))
+    e2 = F.relu(c(3, F.relu(c(2, F.avg_pool2d(e1, 2)))))
+    e3 = F.relu(c(5, F.relu(c(4, F.avg_pool2d(e2, 2)))))
+    d2 = F.relu(c(7, F.relu(c(6, torch.cat([F.interpolate(e3, scale_factor=2, mode="nearest"), e2], 1)))))
+    d1 = F.relu(c(9, F.relu(c(8, torch.cat([F.interpolate(d2, scale_factor=2, mode="nearest"), e1], 1)))))
+    return c(10, d1), params
+
+
+def packed_grad(params):
+    """Gradients of the reference's parameters in the library's weight packing."""
+    out = []
+    for i, (ci, co, k) in enumerate(WS.LAYERS):
+        g = params[2 * i].grad
+        out.append((g.permute(0, 2, 3, 1) if k == 3 else g).reshape(-1))
+        out.append(params[2 * i + 1].grad.reshape(-1))
+    import torch
+    return torch.cat(out).cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.gpu
+def test_training_gradient_matches_autograd(Bgpu):
+    """The library's backward pass against PyTorch autograd in FP32 (the
+    library keeps activations and their gradients in BF16): the loss, and per
+    layer the kernel and bias gradients in norm and direction; lr = 0 leaves
+    the weights as they were."""
+    import torch
+    bits = random_weights(21)
+    rng = np.random.default_rng(22)
+    feats = rng.uniform(-1, 1, (3, 6)).astype(np.float32)
+    target = torch.tensor(rng.normal(0.0, 0.1, (3, 4, WS.H, WS.W)), dtype=torch.float32, device="cuda")
+    ws = Bgpu.WarmStart(bits)
+    loss = ws.train_step(torch.tensor(feats, device="cuda"), target, lr=0.0)
+    g = ws.last_gradient().astype(np.float64)
+    assert np.array_equal(ws.weights(), bits)
+    ws.close()
+    out, params = torch_reference(bits, feats)
+    ref = torch.mean((out - target) ** 2)
+    ref.backward()
+    assert abs(loss - ref.item()) <= 2e-2 * ref.item()
+    gr = packed_grad(params)
+    off = 0
+    for ci, co, k in WS.LAYERS:
+        for n in (co * ci * k * k, co):
+            a, b = g[off:off + n], gr[off:off + n]
+            off += n
+            rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+            cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+            assert rel <= 0.08 and cos >= 0.995, (ci, co, k, n, rel, cos)
+    assert off == g.size
+
+
+@pytest.mark.gpu
+def test_training_reduces_the_loss_deterministically(Bgpu):
+    """A few Adam steps on a learnable target (each canvas channel a smooth
+    function of the features) lower the loss; two runs give the same weights
+    bit for bit."""
+    import torch
+    rng = np.random.default_rng(23)
+    feats = torch.tensor(rng.uniform(-1, 1, (8, 6)), dtype=torch.float32, device="cuda")
+    r = (torch.arange(WS.W, device="cuda") + 0.5) / WS.W
+    z = (torch.arange(WS.H, device="cuda") + 0.5) / WS.H
+    target = torch.stack([feats[:, c, None, None] * torch.sin(np.pi * r)[None, None, :] * z[None, :, None]
+                          for c in range(4)], dim=1).contiguous()
+    runs = []
+    for _ in range(2):
+        ws = Bgpu.WarmStart(random_weights(24, gain=0.5))
+        first = ws.loss(feats, target)
+        for _ in range(40):
+            ws.train_step(feats, target, lr=3e-3)
+        runs.append((first, ws.loss(feats, target), ws.weights()))
+        ws.close()
+    (l0, l1, w1), (m0, m1, w2) = runs
+    assert l0 == m0 and l1 == m1 and np.array_equal(w1, w2)
+    assert l1 <= 0.5 * l0, (l0, l1)
+
+
+@pytest.mark.gpu
+def test_canvas_from_fields_matches_numpy(Bgpu):
+    """axlbm_ws_to_canvas (the training targets) against a numpy bilinear
+    sample of the node values at every pixel centre."""
+    import torch
+    probs = [I.rotating_lid_cavity(nr=37, aspect=2.0, re=500.0),
+             I.wheeler_cell(nr=29, re_x=300.0, prandtl=5.0, grashof=1e5),
+             I.Problem(nr=19, nz=27, tau=0.7, inner="axis_node", outer="nee", z_lo="nee", z_hi="nee", swirl=True,
+                       omega={"hi": 0.002})]
+    rng = np.random.default_rng(25)
+    moms = [rng.normal(size=(4, pb.nz, pb.nr)) for pb in probs]
+    packed = torch.tensor(np.concatenate([m.ravel() for m in moms]), dtype=torch.float32, device="cuda")
+    ws = Bgpu.WarmStart(random_weights(1))
+    got = ws.to_canvas(packed, probs).cpu().numpy()
+    ws.close()
+    for d, pb in enumerate(probs):
+        g = I.warm_start_geometry(pb)
+        m = moms[d].astype(np.float32).astype(np.float64)
+        r = (np.arange(WS.W) + 0.5) / WS.W * g["r_wall"]
+        z = g["z_bottom"] + (np.arange(WS.H) + 0.5) / WS.H * g["height"]
+        x = np.clip(r - g["r_first"], 0, pb.nr - 1)
+        y = np.clip(z - g["z_first"], 0, pb.nz - 1)
+        x0 = np.minimum(x.astype(int), pb.nr - 1)
+        y0 = np.minimum(y.astype(int), pb.nz - 1)
+        x1, y1 = np.minimum(x0 + 1, pb.nr - 1), np.minimum(y0 + 1, pb.nz - 1)
+        fx, fy = (x - x0)[None, :], (y - y0)[:, None]
+        for c in range(4):
+            p = m[c]
+            v = ((1 - fy) * ((1 - fx) * p[np.ix_(y0, x0)] + fx * p[np.ix_(y0, x1)])
+                 + fy * ((1 - fx) * p[np.ix_(y1, x0)] + fx * p[np.ix_(y1, x1)]))
+            want = v / g["u_scale"] if c < 3 else v - pb.t_ref
+            assert np.max(np.abs(got[d, c] - want)) <= 1e-5 * max(1.0, np.max(np.abs(want))), (d, c)
