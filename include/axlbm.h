@@ -367,6 +367,20 @@ AXLBM_API axlbm_status axlbm_batch_get_populations(axlbm_batch* b, int32_t d, do
 AXLBM_API axlbm_status axlbm_batch_set_populations(axlbm_batch* b, int32_t d, const double* f, const double* g,
                                                    const double* t_pop);
 
+/* Move a batch that is at an even level to the even time level t (the clock
+ * and every domain's force a(t) follow; the populations are not touched), so
+ * that domains copied from another batch continue in time.  AXLBM_EINVAL for
+ * an odd t, t < 0, or a batch at an odd level.  Synchronises. */
+AXLBM_API axlbm_status axlbm_batch_set_time(axlbm_batch* b, int64_t t);
+
+/* Copy domain sd of batch src into domain dd of batch dst (device to device,
+ * every population plane; queued on dst's stream after src's work has
+ * finished).  Both batches must use the same storage and be at the same time
+ * level, and the two domains must have the same grid (nr, nz, g, h); the
+ * destination keeps its own parameters.  With this a caller can retire
+ * converged domains by repacking the rest into a smaller batch. */
+AXLBM_API axlbm_status axlbm_batch_copy_domain(axlbm_batch* dst, int32_t dd, axlbm_batch* src, int32_t sd);
+
 /* Time level of the batch, and the bulk tile shape (rows x nodes) in use. */
 AXLBM_API axlbm_status axlbm_batch_time(const axlbm_batch* b, int64_t* time);
 AXLBM_API axlbm_status axlbm_batch_tile_shape(const axlbm_batch* b, int32_t* rows, int32_t* nodes);

@@ -127,6 +127,8 @@ def lib() -> ctypes.CDLL:
                                                   ctypes.POINTER(ctypes.c_uint32)]
         L.axlbm_batch_set_tile_shape.argtypes = [H, ctypes.c_int32, ctypes.c_int32]
         L.axlbm_batch_use_graphs.argtypes = [H, ctypes.c_int32]
+        L.axlbm_batch_set_time.argtypes = [H, ctypes.c_int64]
+        L.axlbm_batch_copy_domain.argtypes = [H, ctypes.c_int32, H, ctypes.c_int32]
         L.axlbm_batch_graph_stats.argtypes = [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_batch_kernel_timing.argtypes = [H, ctypes.c_int32]
         L.axlbm_batch_kernel_times.argtypes = [H, ctypes.POINTER(ctypes.c_int64), dp, dp, ctypes.POINTER(ctypes.c_int64)]
@@ -156,6 +158,7 @@ def lib() -> ctypes.CDLL:
                      "axlbm_batch_moments", "axlbm_batch_set_fields", "axlbm_batch_get_populations",
                      "axlbm_batch_set_populations", "axlbm_batch_time", "axlbm_batch_tile_shape",
                      "axlbm_batch_set_tile_shape", "axlbm_batch_use_graphs", "axlbm_batch_graph_stats",
+                     "axlbm_batch_set_time", "axlbm_batch_copy_domain",
                      "axlbm_batch_kernel_timing", "axlbm_batch_kernel_times", "axlbm_batch_kernel_times_by_parity",
                      "axlbm_batch_destroy",
                      "axlbm_batch_set_fields_all", "axlbm_batch_moments_all"):
@@ -537,6 +540,14 @@ class Batch:
     def use_graphs(self, enable: bool) -> None:
         """Replay runs of plain steps from captured CUDA graphs (default) or launch every kernel."""
         _bcheck(lib().axlbm_batch_use_graphs(self.handle, int(bool(enable))), self.handle)
+
+    def set_time(self, t: int) -> None:
+        """Move the batch (at an even level) to the even time level t."""
+        _bcheck(lib().axlbm_batch_set_time(self.handle, int(t)), self.handle)
+
+    def copy_domain(self, d: int, src: "Batch", sd: int) -> None:
+        """Copy domain sd of batch src (same storage, time level and grid) into domain d."""
+        _bcheck(lib().axlbm_batch_copy_domain(self.handle, int(d), src.handle, int(sd)), self.handle)
 
     def graph_stats(self):
         """(captures, launches) of the step graphs since creation."""

@@ -893,6 +893,45 @@ axlbm_status axlbm_batch_set_populations(axlbm_batch* b, int32_t d, const double
     return AXLBM_OK;
 }
 
+axlbm_status axlbm_batch_set_time(axlbm_batch* b, int64_t t) {
+    if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
+    if (t < 0 || t % 2 != 0) return bfail(b, AXLBM_EINVAL, "the time level must be even and >= 0");
+    if (b->parity != 0) return bfail(b, AXLBM_EINVAL, "set_time needs the batch at an even level");
+    const BatchLayout& L = b->L;
+    double* az = reinterpret_cast<double*>(b->mem + L.off_az);
+    axl::k_batch_set_time<<<1, 256, 0, b->stream>>>(reinterpret_cast<const axl::DomDesc*>(b->mem + L.off_doms), b->n,
+                                                    reinterpret_cast<axl::Clock*>(b->mem + L.off_clock), az,
+                                                    az + 2 * b->n, (long long)t);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "set_time");
+    b->t = t;
+    b->speed_valid = false;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_copy_domain(axlbm_batch* dst, int32_t dd, axlbm_batch* src, int32_t sd) {
+    if (!domain_ok(dst, dd) || !domain_ok(src, sd)) return bfail(dst, AXLBM_EINVAL, "bad batch or domain index");
+    const axlbm_grid &gd = dst->desc[dd].grid, &gs = src->desc[sd].grid;
+    if (dst->precision != src->precision) return bfail(dst, AXLBM_EINVAL, "the batches' storage differs");
+    if (dst->t != src->t) return bfail(dst, AXLBM_EINVAL, "the batches are at different time levels");
+    if (gd.nr != gs.nr || gd.nz != gs.nz || gd.with_swirl != gs.with_swirl || gd.with_temperature != gs.with_temperature)
+        return bfail(dst, AXLBM_EINVAL, "the domains' grids differ");
+    cudaError_t e = cudaStreamSynchronize(src->stream);
+    const size_t el = dst->L.elem;
+    const int planes = 13 + (gd.with_temperature ? 4 : 0);
+    for (int p = 0; p < planes && e == cudaSuccess; ++p) {
+        char* to = dst->mem + ((size_t)p * dst->L.plane + (size_t)dst->row0[dd] * dst->L.pitch + dst->col0[dd]) * el;
+        const char* from =
+            src->mem + ((size_t)p * src->L.plane + (size_t)src->row0[sd] * src->L.pitch + src->col0[sd]) * el;
+        e = cudaMemcpy2DAsync(to, (size_t)dst->L.pitch * el, from, (size_t)src->L.pitch * el, (size_t)gd.nr * el, gd.nz,
+                              cudaMemcpyDeviceToDevice, dst->stream);
+    }
+    if (e != cudaSuccess) return bcuda(dst, e, "copy_domain");
+    dst->speed_valid = false;
+    return AXLBM_OK;
+}
+
 axlbm_status axlbm_batch_time(const axlbm_batch* b, int64_t* t) {
     if (!b || !t) return AXLBM_EINVAL;
     *t = b->t;

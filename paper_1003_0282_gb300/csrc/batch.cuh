@@ -561,6 +561,17 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_batch(const BatchArgs<S, 
     }
 }
 
+// Move a batch to the even time level t: the clock, and every domain's
+// force a(t) for the even step, as the step kernels compute it.
+static __global__ void k_batch_set_time(const DomDesc* doms, int ndom, Clock* clock, double* az, double* az16, long long t) {
+    for (int d = threadIdx.x; d < ndom; d += blockDim.x) {
+        const double a = doms[d].az0 * cos(doms[d].omega_t * (double)t);
+        az[2 * d] = a;
+        az16[4 * d] = a;
+    }
+    if (threadIdx.x == 0) clock->t = t;
+}
+
 // Node-on-axis domains after an odd step: the mirror column's populations
 // into each axis column (see axis_mirror_row); one block per such domain.
 template <class S, bool SW, bool TH>
