@@ -222,7 +222,7 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
     L.off_speed = off;
     off += al((size_t)L.plane * 4);
     L.off_tilepart = off;
-    off += al((size_t)maxtiles * axl::kSlots * axl::kConsumerWarps * 32);
+    off += al((size_t)maxtiles * axl::kSlots * axl::kBatchWarps * 32);
     L.off_ringpart = off;
     off += al((size_t)L.nring * 32);
     L.off_result = off;

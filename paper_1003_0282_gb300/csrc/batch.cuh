@@ -18,6 +18,9 @@ namespace axl {
 
 constexpr int kSlots = 4;     // domains a tile may meet
 constexpr int kRowAlign = 8;  // shelf rows start on multiples of this (>= every tile height)
+constexpr int kBatchThreads = 256;  // computing threads of a bulk CTA (two nodes of one column each)
+constexpr int kBatchWarps = kBatchThreads / 32;
+constexpr int kBatchMinBlocks = 2;  // bulk CTAs per SM the kernel is compiled for
 
 // Per-domain description the ring and per-domain kernels read (coefficients
 // in both arithmetic types).
@@ -100,7 +103,7 @@ struct BatchArgs {
     double* dom_az16;        // [ndom][2][2]: the same, each in its own 16-byte word (bulk-copy source)
     Clock* clock;            // time level and error word
     R* speed;                // |u| plane, atlas-shaped
-    double* tile_part;       // [ntiles][kSlots][kConsumerWarps][4] check partials
+    double* tile_part;       // [ntiles][kSlots][kBatchWarps][4] check partials
     double* ring_part;       // [nring][4] check values of ring nodes
     int residual;
 };
@@ -118,7 +121,7 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
 // Per-warp, per-slot totals of one tile's check values.  The lanes of one
 // slot form a contiguous run of the warp (slots are column ranges), so a
 // segmented scan leaves each run's total in its last lane, which stores it
-// at out[(slot * kConsumerWarps + warp) * 4 ..]; no block barrier is needed.
+// at out[(slot * kBatchWarps + warp) * 4 ..]; no block barrier is needed.
 // The fold adds, per (tile, slot), the warps whose columns meet the slot.
 template <class R>
 __device__ __forceinline__ void warp_slot_store(RedR<R> v, int q, const SlotDesc* sl, double* out) {
@@ -142,7 +145,7 @@ __device__ __forceinline__ void warp_slot_store(RedR<R> v, int q, const SlotDesc
     }
     const int qn = __shfl_down_sync(full, q, 1);
     if (lane == 31 || qn != q) {
-        double* o = out + 4ll * (q * kConsumerWarps + warp);
+        double* o = out + 4ll * (q * kBatchWarps + warp);
         o[0] = (double)v.rmax;
         o[1] = (double)v.count * sl[q].rho0 + (double)v.dmass;
         o[2] = (double)v.budget;
@@ -156,15 +159,24 @@ __device__ __forceinline__ int batch_tile_at(int i, int ntiles) { return PAR ? n
 template <class S, int TK, int TJ>
 __host__ __device__ constexpr int batch_box_w() { return TJ + 2 * (16 / (int)sizeof(S)); }
 
-template <class S, bool SW, bool TH, int TK, int TJ>
-__host__ __device__ constexpr int batch_stage_elems() { return nplanes<SW, TH>() * TK * batch_box_w<S, TK, TJ>(); }
+// Shared-memory stride of one plane's box: TMA writes each box to a 128-byte
+// aligned address, so the stride is rounded up to 128 bytes.
+template <class S, int TK, int TJ>
+__host__ __device__ constexpr int batch_plane_elems() {
+    return (TK * batch_box_w<S, TK, TJ>() + 128 / (int)sizeof(S) - 1) / (128 / (int)sizeof(S)) * (128 / (int)sizeof(S));
+}
 
-// Three stages where they leave room for two CTAs per SM (228 KB of shared
-// memory per SM, 1 KB of it reserved per CTA), else two.
+template <class S, bool SW, bool TH, int TK, int TJ>
+__host__ __device__ constexpr int batch_stage_elems() { return nplanes<SW, TH>() * batch_plane_elems<S, TK, TJ>(); }
+
+// Three stages where they leave room for kBatchMinBlocks CTAs per SM (228 KB
+// of shared memory per SM, 1 KB of it reserved per CTA, 1 KB kept for static
+// shared memory), else two.
+constexpr int kBatchSmemPerCta = 228 * 1024 / kBatchMinBlocks - 2048;
 template <class S, bool SW, bool TH, int TK, int TJ>
 __host__ __device__ constexpr int batch_nstages() {
     return 3 * (batch_stage_elems<S, SW, TH, TK, TJ>() * (int)sizeof(S) + kSlots * (int)sizeof(SlotDesc) +
-                (int)sizeof(TileMeta)) + 128 <= 112 * 1024
+                (int)sizeof(TileMeta)) + 128 <= kBatchSmemPerCta
                ? 3
                : 2;
 }
@@ -189,7 +201,7 @@ __device__ __forceinline__ void batch_issue(const CUtensorMap* map, S* dst, uint
     const int P = 9 + (SW ? 4 : 0) + ((TH && th) ? 4 : 0);
     for (int p = 0; p < P; ++p) {
         const int dy = PAR ? plane_cz<SW>(p) : 0;
-        tma_load_3d(dst + p * TK * BW, map, bar, j0 - HB, k0 + dy, p);
+        tma_load_3d(dst + p * batch_plane_elems<S, TK, TJ>(), map, bar, j0 - HB, k0 + dy, p);
     }
 }
 
@@ -206,6 +218,7 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
                                             int jj, int rr, R inv_r, R az, const R* sp_old, RedR<R>& red) {
     constexpr int NL = Lanes<RC>::n;
     constexpr int BW = batch_box_w<S, TK, TJ>(), HB = 16 / (int)sizeof(S);
+    constexpr int PS = batch_plane_elems<S, TK, TJ>();
     constexpr int HP = SW ? 13 : 9;
     const int jl = j0 + jj - D.col0;  // local column (>= 0: the slot starts at or before this column)
     bool act[NL];
@@ -224,20 +237,20 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
         const int p = PAR ? opp9(a) : a;
-        c.d[a] = Lanes<RC>::template load<S>(row + p * TK * BW + (PAR ? cr9(p) : 0), LROW);
+        c.d[a] = Lanes<RC>::template load<S>(row + p * PS + (PAR ? cr9(p) : 0), LROW);
     }
     if (SW) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int p = PAR ? opp4(q) : q;
-            c.g[q] = Lanes<RC>::template load<S>(row + (9 + p) * TK * BW + (PAR ? cr4(p) : 0), LROW);
+            c.g[q] = Lanes<RC>::template load<S>(row + (9 + p) * PS + (PAR ? cr4(p) : 0), LROW);
         }
     }
     if (THD) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int p = PAR ? opp4(q) : q;
-            c.h[q] = Lanes<RC>::template load<S>(row + (HP + p) * TK * BW + (PAR ? cr4(p) : 0), LROW);
+            c.h[q] = Lanes<RC>::template load<S>(row + (HP + p) * PS + (PAR ? cr4(p) : 0), LROW);
         }
     }
     c.collide(inv_r, D.c, az);
@@ -301,14 +314,14 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
             const long long x = (long long)(k0 + rr + l * (TK / NL)) * A.pitch + (j0 + jj);
             const S* src = row + l * LROW;
 #pragma unroll
-            for (int a = 0; a < 9; ++a) A.pop[opp9(a) * pl + x] = src[a * TK * BW];
+            for (int a = 0; a < 9; ++a) A.pop[opp9(a) * pl + x] = src[a * PS];
             if (SW) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) A.pop[(9 + opp4(q)) * pl + x] = src[(9 + q) * TK * BW];
+                for (int q = 0; q < 4; ++q) A.pop[(9 + opp4(q)) * pl + x] = src[(9 + q) * PS];
             }
             if (THD) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) A.pop[(HP + opp4(q)) * pl + x] = src[(HP + q) * TK * BW];
+                for (int q = 0; q < 4; ++q) A.pop[(HP + opp4(q)) * pl + x] = src[(HP + q) * PS];
             }
         }
     }
@@ -323,7 +336,7 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
 template <class S, int PAR>
 __host__ __device__ constexpr bool batch_producer_warp() { return !(PAR == 1 && sizeof(S) == 4); }
 template <class S, int PAR>
-__host__ __device__ constexpr int batch_threads() { return kBulkThreads + (batch_producer_warp<S, PAR>() ? 32 : 0); }
+__host__ __device__ constexpr int batch_threads() { return kBatchThreads + (batch_producer_warp<S, PAR>() ? 32 : 0); }
 
 // Persistent bulk update of every domain of the batch (even step: every
 // node; odd step: interior nodes).  Per tile, the issuing thread stages the
@@ -334,14 +347,14 @@ __host__ __device__ constexpr int batch_threads() { return kBulkThreads + (batch
 // (per-tile flag); WET: some domain has a wet wall (its wall nodes keep
 // their state in even steps).
 template <class S, class R, bool SW, bool TH, int PAR, bool CHK, int TK, int TJ, bool WET>
-__global__ void __launch_bounds__(batch_threads<S, PAR>(), 2)
+__global__ void __launch_bounds__(batch_threads<S, PAR>(), kBatchMinBlocks)
 k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
     constexpr int NS = batch_nstages<S, SW, TH, TK, TJ>();
     constexpr int STAGE = batch_stage_elems<S, SW, TH, TK, TJ>();
     constexpr bool PW = batch_producer_warp<S, PAR>();
     using RC = typename std::conditional<std::is_same<R, float>::value, F2, R>::type;
     static_assert(std::is_same<R, float>::value, "batch arithmetic is FP32");
-    static_assert(TK * TJ == 2 * kBulkThreads, "two nodes of one column per consumer thread");
+    static_assert(TK * TJ == 2 * kBatchThreads, "two nodes of one column per consumer thread");
     static_assert(TK <= kRowAlign && kRowAlign % TK == 0, "a tile row band stays inside one shelf");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -360,7 +373,7 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kConsumerWarps);
+            mbar_init(&empty[s], kBatchWarps);
         }
         abort_flag = 0;
         fence_barrier_init();
@@ -369,7 +382,7 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
 
     // The issuing thread: stage u % NS gets the block's u-th tile, at atlas
     // position pos, from its record rc.
-    const bool issuer = PW ? (warp == kConsumerWarps && lane == 0) : tid == 0;
+    const bool issuer = PW ? (warp == kBatchWarps && lane == 0) : tid == 0;
     unsigned issued = 0u, issued_par = 0u;  // stages issued (bit s), parity of the last phase of each
     auto issue = [&](int u, int pos, const TileRec& rc) {
         const int s = u % NS;
@@ -390,7 +403,7 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
         issued_par = (issued_par & ~(1u << s)) | ((unsigned)((u / NS) & 1) << s);
     };
 
-    if (PW && warp == kConsumerWarps) {
+    if (PW && warp == kBatchWarps) {
         if (lane == 0) {
             prefetch_tensormap(&map);
             int it = 0;
@@ -464,14 +477,14 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
                 RedR<R> red{R(0), R(0), R(0), 0, 0};
                 const bool dth = TH && M.r.th;
                 // one node pair per thread: rows rr0 and rr0 + TK/2 of column jj
-                static_assert(kBulkThreads / TJ == TK / 2, "one pair per consumer thread");
+                static_assert(kBatchThreads / TJ == TK / 2, "one pair per consumer thread");
                 if (dth)
                     batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old, red);
                 else
                     batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old,
                                                                              red);
                 if (CHK)
-                    warp_slot_store(red, q, slots + s * kSlots, A.tile_part + 4ll * kSlots * kConsumerWarps * tile);
+                    warp_slot_store(red, q, slots + s * kSlots, A.tile_part + 4ll * kSlots * kBatchWarps * tile);
             }
             __syncwarp();
             if (!__all_sync(0xffffffffu, ok && !abort_flag)) {
@@ -620,10 +633,10 @@ k_batch_fold(const int* tile_start, const int* tile_index, const TileRec* tiles,
         const int tile = e / kSlots, q = e % kSlots;
         const TileRec& tr = tiles[tile];
         const int lo = tr.start[q], hi = q + 1 < tr.nseg ? tr.start[q + 1] : tj;
-        for (int w = 0; w < kConsumerWarps; ++w) {
+        for (int w = 0; w < kBatchWarps; ++w) {
             const int c0 = 32 * (w % groups);
             if (c0 >= hi || c0 + 32 <= lo) continue;
-            const double* p = tile_part + 4ll * (((long long)tile * kSlots + q) * kConsumerWarps + w);
+            const double* p = tile_part + 4ll * (((long long)tile * kSlots + q) * kBatchWarps + w);
             v.rmax = fmax(v.rmax, p[0]);
             v.mass += p[1];
             v.budget += p[2];

@@ -8,7 +8,7 @@
 
 namespace axl {
 
-// Candidate bulk tile shapes (rows x nodes), 512 nodes each.
+// Candidate bulk tile shapes (rows x nodes), 2 kBatchThreads nodes each.
 constexpr int kBatchShapes = 2;
 constexpr int kShapeTK[kBatchShapes] = {4, 8};
 constexpr int kShapeTJ[kBatchShapes] = {128, 64};

@@ -539,6 +539,11 @@ __host__ __device__ constexpr int nplanes() { return 9 + (SW ? 4 : 0) + (TH ? 4 
 template <class S, bool SW, bool TH>
 __host__ __device__ constexpr int stage_elems() { return nplanes<SW, TH>() * kTileK * kBoxW<S>; }
 
+// TMA writes each plane's box to a 128-byte aligned shared-memory address.
+static_assert(kTileK * kBoxW<float> * sizeof(float) % 128 == 0 && kTileK * kBoxW<double> * sizeof(double) % 128 == 0 &&
+                  kTileK * kBoxW<__half> * sizeof(__half) % 128 == 0,
+              "plane boxes are whole multiples of 128 bytes");
+
 // Pipeline depth: three stages when they fit in ~200 KB, else two.
 template <class S, bool SW, bool TH>
 __host__ __device__ constexpr int nstages() { return 3 * stage_elems<S, SW, TH>() * (int)sizeof(S) <= 200 * 1024 ? 3 : 2; }
