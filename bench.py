@@ -38,8 +38,8 @@ sys.path.insert(0, ROOT)
 # captured launch, keyed by kernel and the SHA-256 prefix of the kernel source
 # at capture time.  Reported as null once the source has changed.
 NCU_TRAFFIC = {
-    # profiles/k_bulk_batch_fp32_sweep320_launches.md: one even and one odd launch of the full sweep, 4 x 128 tiles
-    "batch fp32": {"src_sha": "8a84e93db924f223", "dram_per_alg_byte": 0.9896},
+    # profiles/k_bulk_batch_fp32_sweep320_launches.md: one even (4 x 128 tiles) and one odd (2 x 128) launch
+    "batch fp32": {"src_sha": "33e50de1f4c1a61e", "dram_per_alg_byte": 0.9896},
 }
 
 
@@ -53,7 +53,9 @@ def parse():
     p.add_argument("--workload", choices=["batch", "pipe", "warmstart"], default="batch",
                    help="warmstart: time to a steady state from rest and from the warm-start network")
     p.add_argument("--scale", type=float, default=1.0, help="batch: shrink every domain (small profiling cases)")
-    p.add_argument("--tile", default=None, help="batch: bulk tile shape RxN (4x128 or 8x64) instead of the timed one")
+    p.add_argument("--tile", default=None,
+                   help="batch: bulk tile shapes RxN[,RxN] instead of the timed ones (even steps 4x128 or 8x64; "
+                        "odd steps with FP32 storage 2x128 or 4x64)")
     p.add_argument("--nr", type=int, default=4096)
     p.add_argument("--nz", type=int, default=8192)
     p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
@@ -308,8 +310,9 @@ def main():
         kernel_times = lambda: B.axlbm_batch_kernel_times(solver.handle)
         parity_times = lambda: B.axlbm_batch_kernel_times_by_parity(solver.handle)
         if args.tile:
-            solver.tile_shape = tuple(int(v) for v in args.tile.split("x"))
-        tile = solver.tile_shape
+            for t in args.tile.split(","):
+                solver.tile_shape = tuple(int(v) for v in t.split("x"))
+        tile = solver.tile_shapes
         workload = (f"batched uneven sweep: {sum(not p.temperature for p in problems)} rotating-lid cavities + "
                     f"{sum(p.temperature for p in problems)} Wheeler-type cells with temperature, one persistent "
                     f"launch per step" + (f" (radii scaled by {args.scale})" if args.scale != 1.0 else ""))
@@ -399,7 +402,8 @@ def main():
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": workload, "precision": args.precision, "nodes": all_nodes,
                        "domains": len(problems), "lattice_steps_per_step": args.inner,
-                       "bulk_tile": f"{tile[0]}x{tile[1]}",
+                       "bulk_tile": (f"{tile[0]}x{tile[1]}" if args.workload == "pipe" else
+                                     f"{tile[0][0]}x{tile[0][1]} even, {tile[1][0]}x{tile[1][1]} odd"),
                        "launch": graphs,
                        "cache": "inputs larger than L2 (no flush)",
                        "parallelism": (f"independent domains on {world} ranks ({args.shard})" if world > 1

@@ -381,7 +381,7 @@ AXLBM_API axlbm_status axlbm_batch_set_time(axlbm_batch* b, int64_t t);
  * converged domains by repacking the rest into a smaller batch. */
 AXLBM_API axlbm_status axlbm_batch_copy_domain(axlbm_batch* dst, int32_t dd, axlbm_batch* src, int32_t sd);
 
-/* Time level of the batch, and the bulk tile shape (rows x nodes) in use. */
+/* Time level of the batch, and the bulk tile shape (rows x nodes) of its even steps. */
 AXLBM_API axlbm_status axlbm_batch_time(const axlbm_batch* b, int64_t* time);
 AXLBM_API axlbm_status axlbm_batch_tile_shape(const axlbm_batch* b, int32_t* rows, int32_t* nodes);
 
@@ -397,10 +397,15 @@ AXLBM_API axlbm_status axlbm_batch_use_graphs(axlbm_batch* b, int32_t enable);
  * (either pointer may be NULL). */
 AXLBM_API axlbm_status axlbm_batch_graph_stats(const axlbm_batch* b, int64_t* captures, int64_t* launches);
 
-/* Use the bulk tile shape rows x nodes (4 x 128 or 8 x 64) from the next
- * step on, instead of the one timed at creation (for profiling a given
- * shape; results do not depend on it).  AXLBM_EINVAL for another shape. */
+/* Use the bulk tile shape rows x nodes from the next step on, instead of the
+ * one timed at creation (for profiling a given shape; results do not depend
+ * on it), for the steps whose candidates include it: 512-node tiles (4 x 128,
+ * 8 x 64) run CTAs of eight computing warps and serve every step except the
+ * odd steps with FP32 storage, which run 256-node tiles (2 x 128, 4 x 64) in
+ * CTAs of four.  AXLBM_EINVAL for a shape no step of this batch uses. */
 AXLBM_API axlbm_status axlbm_batch_set_tile_shape(axlbm_batch* b, int32_t rows, int32_t nodes);
+/* The tile shapes of even ([0]) and odd ([1]) steps (arrays of two). */
+AXLBM_API axlbm_status axlbm_batch_tile_shapes(const axlbm_batch* b, int32_t* rows, int32_t* nodes);
 
 /* Bulk-kernel timing of the batch, as axlbm_kernel_timing / axlbm_kernel_times. */
 AXLBM_API axlbm_status axlbm_batch_kernel_timing(axlbm_batch* b, int32_t enable);

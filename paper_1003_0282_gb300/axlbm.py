@@ -126,6 +126,7 @@ def lib() -> ctypes.CDLL:
         L.axlbm_selftest_bounded_wait.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
                                                   ctypes.POINTER(ctypes.c_uint32)]
         L.axlbm_batch_set_tile_shape.argtypes = [H, ctypes.c_int32, ctypes.c_int32]
+        L.axlbm_batch_tile_shapes.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         L.axlbm_batch_use_graphs.argtypes = [H, ctypes.c_int32]
         L.axlbm_batch_set_time.argtypes = [H, ctypes.c_int64]
         L.axlbm_batch_copy_domain.argtypes = [H, ctypes.c_int32, H, ctypes.c_int32]
@@ -157,7 +158,7 @@ def lib() -> ctypes.CDLL:
         for name in ("axlbm_batch_state_bytes", "axlbm_batch_create", "axlbm_batch_step", "axlbm_batch_residuals",
                      "axlbm_batch_moments", "axlbm_batch_set_fields", "axlbm_batch_get_populations",
                      "axlbm_batch_set_populations", "axlbm_batch_time", "axlbm_batch_tile_shape",
-                     "axlbm_batch_set_tile_shape", "axlbm_batch_use_graphs", "axlbm_batch_graph_stats",
+                     "axlbm_batch_set_tile_shape", "axlbm_batch_tile_shapes", "axlbm_batch_use_graphs", "axlbm_batch_graph_stats",
                      "axlbm_batch_set_time", "axlbm_batch_copy_domain",
                      "axlbm_batch_kernel_timing", "axlbm_batch_kernel_times", "axlbm_batch_kernel_times_by_parity",
                      "axlbm_batch_destroy",
@@ -535,7 +536,15 @@ class Batch:
 
     @tile_shape.setter
     def tile_shape(self, shape):
+        """Use this tile shape for the steps whose candidates include it."""
         _bcheck(lib().axlbm_batch_set_tile_shape(self.handle, int(shape[0]), int(shape[1])), self.handle)
+
+    @property
+    def tile_shapes(self):
+        """((rows, nodes) of even steps, (rows, nodes) of odd steps)."""
+        r, n = (ctypes.c_int32 * 2)(), (ctypes.c_int32 * 2)()
+        _bcheck(lib().axlbm_batch_tile_shapes(self.handle, r, n), self.handle)
+        return (int(r[0]), int(n[0])), (int(r[1]), int(n[1]))
 
     def use_graphs(self, enable: bool) -> None:
         """Replay runs of plain steps from captured CUDA graphs (default) or launch every kernel."""

@@ -222,7 +222,7 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
     L.off_speed = off;
     off += al((size_t)L.plane * 4);
     L.off_tilepart = off;
-    off += al((size_t)maxtiles * axl::kSlots * axl::kBatchWarps * 32);
+    off += al((size_t)maxtiles * axl::kSlots * axl::kBatchMaxWarps * 32);
     L.off_ringpart = off;
     off += al((size_t)L.nring * 32);
     L.off_result = off;
@@ -398,7 +398,8 @@ cudaError_t batch_capture_pairs(axlbm_batch* b, const BatchOps* ops, int pairs, 
 // `pairs` plain step pairs from an even level, from the graphs (captured on
 // first use for the tile shape in use).
 axlbm_status batch_graph_pairs(axlbm_batch* b, const BatchOps* ops, int64_t pairs) {
-    if (b->graph_shape != b->shape) {
+    const int key = 4 * b->shape[0] + b->shape[1];
+    if (b->graph_shape != key) {
         batch_drop_graphs(b);
         cudaError_t e = batch_capture_pairs(b, ops, kGraphPairs, &b->graph_many);
         if (e == cudaSuccess) e = batch_capture_pairs(b, ops, 1, &b->graph_one);
@@ -407,7 +408,7 @@ axlbm_status batch_graph_pairs(axlbm_batch* b, const BatchOps* ops, int64_t pair
             batch_drop_graphs(b);
             return bcuda(b, e, "graph capture");
         }
-        b->graph_shape = b->shape;
+        b->graph_shape = key;
         b->graph_captures += 1;
     }
     for (int64_t p = 0; p < pairs;) {
@@ -428,7 +429,7 @@ axlbm_status batch_step_n(axlbm_batch* b, int64_t n) {
     // every step but the last two (the check steps) is plain: with timing off,
     // whole (even, odd) pairs of them replay captured graphs once the plain
     // kernels of the shape have been sized by earlier launches
-    const bool sized = b->grid[b->shape][0][0] > 0 && b->grid[b->shape][1][0] > 0;
+    const bool sized = b->grid[b->shape[0]][0][0] > 0 && b->grid[b->shape[1]][1][0] > 0;
     if (b->use_graphs && !b->timing && sized && n - 2 - b->parity >= 2 * kMinGraphPairs) {
         if (b->parity == 1) {
             int nl = 0;
@@ -491,7 +492,8 @@ axlbm_status tune(axlbm_batch* b) {
         std::lock_guard<std::mutex> g(g_tune_lock);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            b->shape = it->second;
+            b->shape[0] = it->second / 4;
+            b->shape[1] = it->second % 4;
             return AXLBM_OK;
         }
     }
@@ -501,8 +503,12 @@ axlbm_status tune(axlbm_batch* b) {
     float best = 1e30f;
     int best_shape = 0;
     axlbm_status st = AXLBM_OK;
-    for (int s = 0; s < axl::kBatchShapes && st == AXLBM_OK; ++s) {
-        b->shape = s;
+    // every pair of an even-step and an odd-step candidate shape
+    const int e0s = axl::shape_first(b->L.elem, 0), o0s = axl::shape_first(b->L.elem, 1);
+    for (int c = 0; c < 4 && st == AXLBM_OK; ++c) {
+        const int s = 4 * (e0s + c / 2) + (o0s + c % 2);
+        b->shape[0] = s / 4;
+        b->shape[1] = s % 4;
         // warm-up: every kernel variant of the shape (plain and check steps
         // of both parities) is loaded and sized before the timed calls
         st = batch_step_n(b, 4);
@@ -527,7 +533,8 @@ axlbm_status tune(axlbm_batch* b) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != AXLBM_OK) return st;
-    b->shape = best_shape;
+    b->shape[0] = best_shape / 4;
+    b->shape[1] = best_shape % 4;
     std::lock_guard<std::mutex> g(g_tune_lock);
     g_tune_cache[key] = best_shape;
     return AXLBM_OK;
@@ -569,7 +576,8 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
     b->side = nullptr;
     b->fork = b->join = nullptr;
     b->L = P.L;
-    b->shape = 0;
+    b->shape[0] = 0;
+    b->shape[1] = axl::shape_first(b->L.elem, 1);
     memset(b->grid, 0, sizeof b->grid);
     b->timing = false;
     b->ev_used = 0;
@@ -940,20 +948,37 @@ axlbm_status axlbm_batch_time(const axlbm_batch* b, int64_t* t) {
 
 axlbm_status axlbm_batch_tile_shape(const axlbm_batch* b, int32_t* rows, int32_t* nodes) {
     if (!b) return AXLBM_EINVAL;
-    if (rows) *rows = axl::kShapeTK[b->shape];
-    if (nodes) *nodes = axl::kShapeTJ[b->shape];
+    if (rows) *rows = axl::kShapeTK[b->shape[0]];
+    if (nodes) *nodes = axl::kShapeTJ[b->shape[0]];
     return AXLBM_OK;
 }
 
 axlbm_status axlbm_batch_set_tile_shape(axlbm_batch* b, int32_t rows, int32_t nodes) {
     if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
+    bool any = false;
     for (int s = 0; s < axl::kBatchShapes; ++s) {
-        if (axl::kShapeTK[s] == rows && axl::kShapeTJ[s] == nodes) {
-            b->shape = s;
-            return AXLBM_OK;
+        if (axl::kShapeTK[s] != rows || axl::kShapeTJ[s] != nodes) continue;
+        for (int par = 0; par < 2; ++par) {  // every parity whose candidates include the shape
+            const int first = axl::shape_first(b->L.elem, par);
+            if (s == first || s == first + 1) {
+                b->shape[par] = s;
+                any = true;
+            }
         }
     }
-    return bfail(b, AXLBM_EINVAL, "no bulk tile shape " + std::to_string(rows) + " x " + std::to_string(nodes));
+    if (!any)
+        return bfail(b, AXLBM_EINVAL, "no bulk tile shape " + std::to_string(rows) + " x " + std::to_string(nodes) +
+                                          " for this storage");
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_tile_shapes(const axlbm_batch* b, int32_t* rows, int32_t* nodes) {
+    if (!b || !rows || !nodes) return AXLBM_EINVAL;
+    for (int par = 0; par < 2; ++par) {
+        rows[par] = axl::kShapeTK[b->shape[par]];
+        nodes[par] = axl::kShapeTJ[b->shape[par]];
+    }
+    return AXLBM_OK;
 }
 
 axlbm_status axlbm_batch_use_graphs(axlbm_batch* b, int32_t enable) {

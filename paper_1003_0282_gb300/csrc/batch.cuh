@@ -18,9 +18,18 @@ namespace axl {
 
 constexpr int kSlots = 4;     // domains a tile may meet
 constexpr int kRowAlign = 8;  // shelf rows start on multiples of this (>= every tile height)
-constexpr int kBatchThreads = 256;  // computing threads of a bulk CTA (two nodes of one column each)
-constexpr int kBatchWarps = kBatchThreads / 32;
-constexpr int kBatchMinBlocks = 2;  // bulk CTAs per SM the kernel is compiled for
+constexpr int kBatchMaxWarps = 8;  // computing warps of the widest bulk CTA (stride of the check partials)
+
+// A bulk CTA of a TK x TJ tile: TK TJ / 2 computing threads (two nodes of one
+// column each) plus one producer warp.  512-node tiles run eight computing
+// warps, two CTAs per SM (96 registers per thread); 256-node tiles run four,
+// three CTAs per SM (128 registers per thread).
+template <int TK, int TJ>
+__host__ __device__ constexpr int batch_nthreads() { return TK * TJ / 2; }
+template <int TK, int TJ>
+__host__ __device__ constexpr int batch_nwarps() { return TK * TJ / 64; }
+template <int TK, int TJ>
+__host__ __device__ constexpr int batch_min_blocks() { return TK * TJ >= 512 ? 2 : 3; }
 
 // Per-domain description the ring and per-domain kernels read (coefficients
 // in both arithmetic types).
@@ -103,7 +112,7 @@ struct BatchArgs {
     double* dom_az16;        // [ndom][2][2]: the same, each in its own 16-byte word (bulk-copy source)
     Clock* clock;            // time level and error word
     R* speed;                // |u| plane, atlas-shaped
-    double* tile_part;       // [ntiles][kSlots][kBatchWarps][4] check partials
+    double* tile_part;       // [ntiles][kSlots][kBatchMaxWarps][4] check partials
     double* ring_part;       // [nring][4] check values of ring nodes
     int residual;
 };
@@ -121,7 +130,7 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
 // Per-warp, per-slot totals of one tile's check values.  The lanes of one
 // slot form a contiguous run of the warp (slots are column ranges), so a
 // segmented scan leaves each run's total in its last lane, which stores it
-// at out[(slot * kBatchWarps + warp) * 4 ..]; no block barrier is needed.
+// at out[(slot * kBatchMaxWarps + warp) * 4 ..]; no block barrier is needed.
 // The fold adds, per (tile, slot), the warps whose columns meet the slot.
 template <class R>
 __device__ __forceinline__ void warp_slot_store(RedR<R> v, int q, const SlotDesc* sl, double* out) {
@@ -145,7 +154,7 @@ __device__ __forceinline__ void warp_slot_store(RedR<R> v, int q, const SlotDesc
     }
     const int qn = __shfl_down_sync(full, q, 1);
     if (lane == 31 || qn != q) {
-        double* o = out + 4ll * (q * kBatchWarps + warp);
+        double* o = out + 4ll * (q * kBatchMaxWarps + warp);
         o[0] = (double)v.rmax;
         o[1] = (double)v.count * sl[q].rho0 + (double)v.dmass;
         o[2] = (double)v.budget;
@@ -169,14 +178,13 @@ __host__ __device__ constexpr int batch_plane_elems() {
 template <class S, bool SW, bool TH, int TK, int TJ>
 __host__ __device__ constexpr int batch_stage_elems() { return nplanes<SW, TH>() * batch_plane_elems<S, TK, TJ>(); }
 
-// Three stages where they leave room for kBatchMinBlocks CTAs per SM (228 KB
-// of shared memory per SM, 1 KB of it reserved per CTA, 1 KB kept for static
+// Three stages where they leave room for the shape's CTAs per SM (228 KB of
+// shared memory per SM, 1 KB of it reserved per CTA, 1 KB kept for static
 // shared memory), else two.
-constexpr int kBatchSmemPerCta = 228 * 1024 / kBatchMinBlocks - 2048;
 template <class S, bool SW, bool TH, int TK, int TJ>
 __host__ __device__ constexpr int batch_nstages() {
     return 3 * (batch_stage_elems<S, SW, TH, TK, TJ>() * (int)sizeof(S) + kSlots * (int)sizeof(SlotDesc) +
-                (int)sizeof(TileMeta)) + 128 <= kBatchSmemPerCta
+                (int)sizeof(TileMeta)) + 128 <= 228 * 1024 / batch_min_blocks<TK, TJ>() - 2048
                ? 3
                : 2;
 }
@@ -327,34 +335,23 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
     }
 }
 
-// Whether the bulk kernel has a producer warp.  With one, a lane of a ninth
-// warp issues the tiles and the eight consumer warps only compute; two CTAs
-// of nine warps leave each thread 96 registers.  Without one, thread 0 of
-// the eight warps issues between its own tiles, leaving 128 registers per
-// thread: the odd step with FP32 storage (its shifted stores keep more
-// addresses live) runs faster that way, the other kernels with the producer.
-template <class S, int PAR>
-__host__ __device__ constexpr bool batch_producer_warp() { return !(PAR == 1 && sizeof(S) == 4); }
-template <class S, int PAR>
-__host__ __device__ constexpr int batch_threads() { return kBatchThreads + (batch_producer_warp<S, PAR>() ? 32 : 0); }
-
 // Persistent bulk update of every domain of the batch (even step: every
-// node; odd step: interior nodes).  Per tile, the issuing thread stages the
-// population boxes (TMA), the tile record, each slot's domain descriptor and
-// its a(t) (bulk copies), all completing on the stage's full barrier, and
-// refills a stage with the tile NS ahead once every consumer warp has
-// released it.  SW: every domain carries g; TH: shelves may carry h
-// (per-tile flag); WET: some domain has a wet wall (its wall nodes keep
-// their state in even steps).
+// node; odd step: interior nodes), warp-specialised.  A lane of the producer
+// warp stages, per tile, the population boxes (TMA), the tile record, each
+// slot's domain descriptor and its a(t) (bulk copies), all completing on the
+// stage's full barrier, and refills a stage with the tile NS ahead once every
+// computing warp has released it; the computing warps only compute.  SW:
+// every domain carries g; TH: shelves may carry h (per-tile flag); WET: some
+// domain has a wet wall (its wall nodes keep their state in even steps).
 template <class S, class R, bool SW, bool TH, int PAR, bool CHK, int TK, int TJ, bool WET>
-__global__ void __launch_bounds__(batch_threads<S, PAR>(), kBatchMinBlocks)
+__global__ void __launch_bounds__(batch_nthreads<TK, TJ>() + 32, batch_min_blocks<TK, TJ>())
 k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
     constexpr int NS = batch_nstages<S, SW, TH, TK, TJ>();
     constexpr int STAGE = batch_stage_elems<S, SW, TH, TK, TJ>();
-    constexpr bool PW = batch_producer_warp<S, PAR>();
+    constexpr int NW = batch_nwarps<TK, TJ>();  // computing warps; warp NW is the producer
     using RC = typename std::conditional<std::is_same<R, float>::value, F2, R>::type;
     static_assert(std::is_same<R, float>::value, "batch arithmetic is FP32");
-    static_assert(TK * TJ == 2 * kBatchThreads, "two nodes of one column per consumer thread");
+    static_assert(NW <= kBatchMaxWarps && NW * 32 / TJ == TK / 2, "two nodes of one column per computing thread");
     static_assert(TK <= kRowAlign && kRowAlign % TK == 0, "a tile row band stays inside one shelf");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -364,47 +361,23 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
     __shared__ __align__(8) uint64_t full[NS];
     __shared__ __align__(8) uint64_t empty[NS];
     __shared__ volatile int abort_flag;
-    // records of the tiles thread 0 issues next, fetched one tile ahead (no
-    // producer warp; two buffers: the one being filled is never the one read)
-    __shared__ __align__(16) TileRec rec[2];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = A.ntiles;
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kBatchWarps);
+            mbar_init(&empty[s], NW);
         }
         abort_flag = 0;
         fence_barrier_init();
     }
     __syncthreads();
 
-    // The issuing thread: stage u % NS gets the block's u-th tile, at atlas
-    // position pos, from its record rc.
-    const bool issuer = PW ? (warp == kBatchWarps && lane == 0) : tid == 0;
-    unsigned issued = 0u, issued_par = 0u;  // stages issued (bit s), parity of the last phase of each
-    auto issue = [&](int u, int pos, const TileRec& rc) {
-        const int s = u % NS;
-        TileMeta& M = meta[s];
-        const int nseg = rc.nseg;
-        mbar_arrive_expect_tx(&full[s], batch_tile_bytes<S, SW, TH, TK, TJ>(rc.th != 0) + (uint32_t)sizeof(TileRec) +
-                                            (uint32_t)(nseg * (sizeof(SlotDesc) + sizeof(M.az[0]))));
-        bulk_copy_g2s(&M.r, A.tiles + pos, sizeof(TileRec), &full[s]);
-#pragma unroll
-        for (int q = 0; q < kSlots; ++q) {
-            if (q < nseg) {
-                bulk_copy_g2s(&slots[s * kSlots + q], A.slots + rc.dom[q], sizeof(SlotDesc), &full[s]);
-                bulk_copy_g2s(&M.az[q][0], A.dom_az16 + 4 * rc.dom[q] + 2 * PAR, sizeof(M.az[0]), &full[s]);
-            }
-        }
-        batch_issue<S, SW, TH, PAR, TK, TJ>(&map, sm + s * STAGE, &full[s], rc.j0, rc.k0, rc.th != 0);
-        issued |= 1u << s;
-        issued_par = (issued_par & ~(1u << s)) | ((unsigned)((u / NS) & 1) << s);
-    };
-
-    if (PW && warp == kBatchWarps) {
+    if (warp == NW) {
         if (lane == 0) {
+            // stage it % NS gets the block's it-th tile, at atlas position pos
+            unsigned issued = 0u, issued_par = 0u;  // stages issued (bit s), parity of the last phase of each
             prefetch_tensormap(&map);
             int it = 0;
             for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++it) {
@@ -416,20 +389,29 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
                 if (abort_flag) break;
                 const int pos = batch_tile_at<PAR>(i, ntiles);
                 const TileRec rc = A.tiles[pos];
-                issue(it, pos, rc);
+                TileMeta& M = meta[s];
+                const int nseg = rc.nseg;
+                mbar_arrive_expect_tx(&full[s], batch_tile_bytes<S, SW, TH, TK, TJ>(rc.th != 0) +
+                                                    (uint32_t)sizeof(TileRec) +
+                                                    (uint32_t)(nseg * (sizeof(SlotDesc) + sizeof(M.az[0]))));
+                bulk_copy_g2s(&M.r, A.tiles + pos, sizeof(TileRec), &full[s]);
+#pragma unroll
+                for (int q = 0; q < kSlots; ++q) {
+                    if (q < nseg) {
+                        bulk_copy_g2s(&slots[s * kSlots + q], A.slots + rc.dom[q], sizeof(SlotDesc), &full[s]);
+                        bulk_copy_g2s(&M.az[q][0], A.dom_az16 + 4 * rc.dom[q] + 2 * PAR, sizeof(M.az[0]), &full[s]);
+                    }
+                }
+                batch_issue<S, SW, TH, PAR, TK, TJ>(&map, sm + s * STAGE, &full[s], rc.j0, rc.k0, rc.th != 0);
+                issued |= 1u << s;
+                issued_par = (issued_par & ~(1u << s)) | ((unsigned)((it / NS) & 1) << s);
+            }
+            if (abort_flag) {  // let the copies in flight land before the block exits
+                for (int s = 0; s < NS; ++s)
+                    if ((issued >> s) & 1u) mbar_wait_bounded(&full[s], (issued_par >> s) & 1u, kWaitCycles);
             }
         }
     } else {
-        if (!PW && tid == 0) {
-            prefetch_tensormap(&map);
-            for (int u = 0; u < NS; ++u) {
-                const int i = blockIdx.x + u * gridDim.x;
-                if (i >= ntiles) break;
-                const int pos = batch_tile_at<PAR>(i, ntiles);
-                rec[0] = A.tiles[pos];
-                issue(u, pos, rec[0]);
-            }
-        }
         const int jj = tid % TJ;
         const int rr0 = tid / TJ;
         // check steps with a residual: |u| of the previous level at this
@@ -451,14 +433,6 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
             const int tile = batch_tile_at<PAR>(i, ntiles);
             const R sp_old[2] = {sp_next[0], sp_next[1]};
             prefetch_speed(i + gridDim.x);
-            const int inext = i + NS * gridDim.x;  // the tile that refills stage s (no producer warp)
-            if (!PW && tid == 0 && inext < ntiles) {
-                const int4* src = reinterpret_cast<const int4*>(A.tiles + batch_tile_at<PAR>(inext, ntiles));
-                int4* dst = reinterpret_cast<int4*>(&rec[it & 1]);
-#pragma unroll
-                for (int w = 0; w < 3; ++w) cp_async16(dst + w, src + w);
-                cp_async_commit();
-            }
             // a lane whose wait gave up skips the tile; the warp leaves the loop
             // together below (its lanes meet in warp-wide operations)
             const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((it / NS) & 1), kWaitCycles);
@@ -477,14 +451,13 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
                 RedR<R> red{R(0), R(0), R(0), 0, 0};
                 const bool dth = TH && M.r.th;
                 // one node pair per thread: rows rr0 and rr0 + TK/2 of column jj
-                static_assert(kBatchThreads / TJ == TK / 2, "one pair per consumer thread");
                 if (dth)
                     batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old, red);
                 else
                     batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old,
                                                                              red);
                 if (CHK)
-                    warp_slot_store(red, q, slots + s * kSlots, A.tile_part + 4ll * kSlots * kBatchWarps * tile);
+                    warp_slot_store(red, q, slots + s * kSlots, A.tile_part + 4ll * kSlots * kBatchMaxWarps * tile);
             }
             __syncwarp();
             if (!__all_sync(0xffffffffu, ok && !abort_flag)) {
@@ -492,19 +465,7 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
                 break;
             }
             if (lane == 0) mbar_arrive(&empty[s]);
-            // no producer warp: thread 0 refills this stage once every warp is done with it
-            if (!PW && tid == 0 && inext < ntiles) {
-                cp_async_wait_all();
-                if (mbar_wait_bounded(&empty[s], (uint32_t)((it / NS) & 1), kWaitCycles))
-                    issue(it + NS, batch_tile_at<PAR>(inext, ntiles), rec[it & 1]);
-                else
-                    abort_flag = 1;
-            }
         }
-    }
-    if (issuer && abort_flag) {  // let the copies in flight land before the block exits
-        for (int s = 0; s < NS; ++s)
-            if ((issued >> s) & 1u) mbar_wait_bounded(&full[s], (issued_par >> s) & 1u, kWaitCycles);
     }
     __syncthreads();
     if (abort_flag) {
@@ -623,20 +584,20 @@ __global__ void __launch_bounds__(kThreads) k_nee_batch(const BatchArgs<S, float
 // domain (every consumer warp whose columns meet the slot, in warp order)
 // and, after an odd step, its ring nodes; one block per domain, fixed order.
 static __global__ void __launch_bounds__(kThreads)
-k_batch_fold(const int* tile_start, const int* tile_index, const TileRec* tiles, int tj, const double* tile_part,
+k_batch_fold(const int* tile_start, const int* tile_index, const TileRec* tiles, int tk, int tj, const double* tile_part,
              const int* ring_start, const double* ring_part, int with_ring, double* result) {
     const int d = blockIdx.x;
     Red v{0.0, 0.0, 0.0, 0.0};
-    const int groups = tj / 32;
+    const int groups = tj / 32, nwarps = tk * tj / 64;
     for (int i = tile_start[d] + threadIdx.x; i < tile_start[d + 1]; i += blockDim.x) {
         const int e = tile_index[i];
         const int tile = e / kSlots, q = e % kSlots;
         const TileRec& tr = tiles[tile];
         const int lo = tr.start[q], hi = q + 1 < tr.nseg ? tr.start[q + 1] : tj;
-        for (int w = 0; w < kBatchWarps; ++w) {
+        for (int w = 0; w < nwarps; ++w) {
             const int c0 = 32 * (w % groups);
             if (c0 >= hi || c0 + 32 <= lo) continue;
-            const double* p = tile_part + 4ll * (((long long)tile * kSlots + q) * kBatchWarps + w);
+            const double* p = tile_part + 4ll * (((long long)tile * kSlots + q) * kBatchMaxWarps + w);
             v.rmax = fmax(v.rmax, p[0]);
             v.mass += p[1];
             v.budget += p[2];

@@ -8,10 +8,18 @@
 
 namespace axl {
 
-// Candidate bulk tile shapes (rows x nodes), 2 kBatchThreads nodes each.
-constexpr int kBatchShapes = 2;
-constexpr int kShapeTK[kBatchShapes] = {4, 8};
-constexpr int kShapeTJ[kBatchShapes] = {128, 64};
+// Candidate bulk tile shapes (rows x nodes): 512-node tiles for CTAs of
+// eight computing warps (shapes 0, 1) and 256-node tiles for CTAs of four
+// (shapes 2, 3).
+constexpr int kBatchShapes = 4;
+constexpr int kShapeTK[kBatchShapes] = {4, 8, 2, 4};
+constexpr int kShapeTJ[kBatchShapes] = {128, 64, 128, 64};
+
+// The two candidate shapes of a step of parity par with storage of elem bytes
+// are shape_first(...) and the one after it.  The odd step with FP32 storage
+// runs the narrow CTAs (its shifted stores keep more addresses live: at 96
+// registers per thread they spilled); every other step runs the wide ones.
+inline int shape_first(size_t elem, int par) { return (elem == 4 && par == 1) ? 2 : 0; }
 
 struct BatchTiles {
     int ntiles;
@@ -52,7 +60,7 @@ struct axlbm_batch {
     char* mem;
     bool owns_mem;
     axl::BatchLayout L;
-    int shape;                        // tile shape in use
+    int shape[2];                     // tile shape of even and odd steps
     int grid[axl::kBatchShapes][2][2];  // persistent grid per (shape, parity, check)
     int num_sms;
     int parity;
@@ -74,7 +82,7 @@ struct axlbm_batch {
     // the legacy default stream, which cannot be captured)
     bool use_graphs;
     cudaStream_t cap;
-    int graph_shape;                // tile shape the graphs were captured with (-1: none)
+    int graph_shape;                // 4 * even shape + odd shape the graphs were captured with (-1: none)
     cudaGraphExec_t graph_many;     // kGraphPairs (even, odd) step pairs
     cudaGraphExec_t graph_one;      // one pair
     int64_t graph_captures, graph_launches;

@@ -16,8 +16,9 @@ BatchArgs<S, R> batch_args(axlbm_batch* b) {
     A.doms = reinterpret_cast<const DomDesc*>(b->mem + L.off_doms);
     A.slots = reinterpret_cast<const SlotDesc*>(b->mem + L.off_slots);
     A.ndom = b->n;
-    A.tiles = reinterpret_cast<const TileRec*>(b->mem + L.shape[b->shape].off_tiles);
-    A.ntiles = L.shape[b->shape].ntiles;
+    const int sh = b->shape[b->parity];  // the tile list of the step about to run
+    A.tiles = reinterpret_cast<const TileRec*>(b->mem + L.shape[sh].off_tiles);
+    A.ntiles = L.shape[sh].ntiles;
     A.ring = reinterpret_cast<const int2*>(b->mem + L.off_ring);
     A.nring = L.nring;
     A.dom_az = reinterpret_cast<double*>(b->mem + L.off_az);
@@ -77,25 +78,32 @@ cudaError_t launch_bulk_batch(axlbm_batch* b, const BatchArgs<S, R>& A) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, batch_threads<S, PAR>(), smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, batch_nthreads<TK, TJ>() + 32, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         long long g = (long long)b->num_sms * per_sm;
         if (g > A.ntiles) g = A.ntiles;
         grid = (int)(g < 1 ? 1 : g);
     }
-    kern<<<grid, batch_threads<S, PAR>(), smem, b->stream>>>(b->tmap[SH], A);
+    kern<<<grid, batch_nthreads<TK, TJ>() + 32, smem, b->stream>>>(b->tmap[SH], A);
     return cudaGetLastError();
+}
+
+template <class S, class R, bool TH, int PAR, bool CHK, bool WET>
+cudaError_t launch_bulk_batch_wet(axlbm_batch* b, const BatchArgs<S, R>& A) {
+    // the odd step with FP32 storage runs the narrow CTAs (shapes 2, 3), every other step the wide ones (0, 1)
+    constexpr int first = (PAR == 1 && sizeof(S) == 4) ? 2 : 0;
+    return b->shape[PAR] == first ? launch_bulk_batch<S, R, TH, PAR, CHK, first, WET>(b, A)
+                                  : launch_bulk_batch<S, R, TH, PAR, CHK, first + 1, WET>(b, A);
 }
 
 template <class S, class R, bool TH, int PAR, bool CHK>
 cudaError_t launch_bulk_batch_shape(axlbm_batch* b, const BatchArgs<S, R>& A) {
     // wet walls matter only in even steps (odd steps leave the rings to the ring kernels)
-    if (PAR == 0 && b->L.nnee > 0)
-        return b->shape == 0 ? launch_bulk_batch<S, R, TH, PAR, CHK, 0, true>(b, A)
-                             : launch_bulk_batch<S, R, TH, PAR, CHK, 1, true>(b, A);
-    return b->shape == 0 ? launch_bulk_batch<S, R, TH, PAR, CHK, 0, false>(b, A)
-                         : launch_bulk_batch<S, R, TH, PAR, CHK, 1, false>(b, A);
+    if constexpr (PAR == 0) {
+        if (b->L.nnee > 0) return launch_bulk_batch_wet<S, R, TH, PAR, CHK, true>(b, A);
+    }
+    return launch_bulk_batch_wet<S, R, TH, PAR, CHK, false>(b, A);
 }
 
 template <class S, class R, bool TH>
@@ -187,10 +195,11 @@ cudaError_t batch_step_impl(axlbm_batch* b, int check, int residual, cudaEvent_t
 template <class S, class R>
 cudaError_t batch_fold_impl(axlbm_batch* b, int with_ring) {
     const BatchLayout& L = b->L;
-    const BatchTiles& T = L.shape[b->shape];
+    const int sh = b->shape[b->parity];  // the shape of the check step that just ran
+    const BatchTiles& T = L.shape[sh];
     k_batch_fold<<<b->n, kThreads, 0, b->stream>>>(
         reinterpret_cast<const int*>(b->mem + T.off_tstart), reinterpret_cast<const int*>(b->mem + T.off_tindex),
-        reinterpret_cast<const TileRec*>(b->mem + T.off_tiles), kShapeTJ[b->shape],
+        reinterpret_cast<const TileRec*>(b->mem + T.off_tiles), kShapeTK[sh], kShapeTJ[sh],
         reinterpret_cast<const double*>(b->mem + L.off_tilepart), reinterpret_cast<const int*>(b->mem + L.off_rstart),
         reinterpret_cast<const double*>(b->mem + L.off_ringpart), with_ring,
         reinterpret_cast<double*>(b->mem + L.off_result));
