@@ -162,6 +162,16 @@ def cpu_baseline(workload: str, inner: int, budget_s: float = 12.0):
             "sample": f"FP64 oracle, {what}, {steps} lattice steps, {dt:.1f} s, single thread"}
 
 
+def workload_name(args, problems):
+    """The workload of a run (the same text for both arms)."""
+    if args.workload == "pipe":
+        pb = problems[0]
+        return f"pipe {pb.nr}x{pb.nz} D2Q9 (Hagen-Poiseuille force, axis + bounce-back wall, periodic z)"
+    return (f"batched uneven sweep: {sum(not p.temperature for p in problems)} rotating-lid cavities + "
+            f"{sum(p.temperature for p in problems)} Wheeler-type cells with temperature, one persistent "
+            f"launch per step" + (f" (radii scaled by {args.scale})" if args.scale != 1.0 else ""))
+
+
 def run_reference(args):
     """--impl reference: the oracle timed on the host cores, one bounded
     sample of the workload per benchmark step."""
@@ -185,8 +195,9 @@ def run_reference(args):
         "impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload} (bounded sample: {what}, {inner} lattice steps per step)",
-                   "precision": "fp64 oracle"},
+        "config": {"workload": workload_name(args, [I.large_pipe(nr=args.nr, nz=args.nz)] if args.workload == "pipe"
+                                             else I.batch_sweep(scale=args.scale)),
+                   "precision": "fp64 oracle", "sample": f"{what}, {inner} lattice steps per benchmark step"},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                          "sample": f"{what} x {inner} lattice steps per benchmark step"},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -302,7 +313,7 @@ def main():
         kernel_times = lambda: B.axlbm_kernel_times(solver.handle)
         parity_times = None
         tile = (4, 128)
-        workload = (f"pipe {pb.nr}x{pb.nz} D2Q9 (Hagen-Poiseuille force, axis + bounce-back wall, periodic z)")
+        workload = workload_name(args, [pb])
     else:
         problems = S.rank_problems(I.batch_sweep, world, rank, args.shard, scale=args.scale)
         solver = B.Batch(problems, args.precision)
@@ -313,9 +324,7 @@ def main():
             for t in args.tile.split(","):
                 solver.tile_shape = tuple(int(v) for v in t.split("x"))
         tile = solver.tile_shapes
-        workload = (f"batched uneven sweep: {sum(not p.temperature for p in problems)} rotating-lid cavities + "
-                    f"{sum(p.temperature for p in problems)} Wheeler-type cells with temperature, one persistent "
-                    f"launch per step" + (f" (radii scaled by {args.scale})" if args.scale != 1.0 else ""))
+        workload = workload_name(args, problems)
     nodes = sum(p.cells for p in problems)
     stream = torch.cuda.current_stream()
 
