@@ -202,7 +202,9 @@ AXLBM_API axlbm_status axlbm_step(axlbm_handle* h, int64_t n);
  * T = sum h).  field_mask selects fields (AXLBM_RHO | ...); `out` receives
  * the selected fields in mask-bit order, each [nz][nr], as out_dtype
  * (AXLBM_F64 / AXLBM_F32), caller-owned, on the device when out_on_device is
- * 1 (queued asynchronously) and on the host otherwise (synchronises).
+ * 1 (queued asynchronously) and on the host otherwise (synchronises; host
+ * arrays pass through a device staging buffer that the handle keeps, grown
+ * as needed, until it is destroyed).
  * Requesting u_theta without swirl or T without temperature is AXLBM_EINVAL. */
 AXLBM_API axlbm_status axlbm_moments(axlbm_handle* h, uint32_t field_mask, void* out, int32_t out_dtype,
                            int32_t out_on_device);
@@ -216,8 +218,9 @@ AXLBM_API axlbm_status axlbm_residual(axlbm_handle* h, double* residual, double*
 /* Reset the state to the equilibria of given macroscopic fields
  * [5][nz][nr] (rho, u_r, u_z, u_theta, T) of element type in_dtype, on the
  * device (on_device = 1, read asynchronously) or the host (copied before the
- * call returns).  Fields of disabled distributions are ignored.  Time is
- * kept.  This is the warm-start entry point. */
+ * call returns, through the handle's staging buffer as in axlbm_moments).
+ * Fields of disabled distributions are ignored.  Time is kept.  This is the
+ * warm-start entry point. */
 AXLBM_API axlbm_status axlbm_set_fields(axlbm_handle* h, const void* fields, int32_t in_dtype,
                               int32_t on_device);
 
@@ -349,9 +352,9 @@ AXLBM_API axlbm_status axlbm_batch_set_fields(axlbm_batch* b, int32_t d, const v
 
 /* Every domain at once: fields of all domains packed one after another in
  * domain order, each [5][nz][nr] (set) or [nfields][nz][nr] (moments), of
- * element type dtype, on the device or the host (one staging copy for the
- * whole batch).  Same rules as the per-domain calls; set_fields_all needs an
- * even time level. */
+ * element type dtype, on the device or the host (one copy through the
+ * batch's staging buffer, kept until the batch is destroyed).  Same rules as
+ * the per-domain calls; set_fields_all needs an even time level. */
 AXLBM_API axlbm_status axlbm_batch_set_fields_all(axlbm_batch* b, const void* fields, int32_t in_dtype,
                                                   int32_t on_device);
 AXLBM_API axlbm_status axlbm_batch_moments_all(axlbm_batch* b, uint32_t field_mask, void* out, int32_t out_dtype,

@@ -13,6 +13,7 @@
 
 using axl::Layout;
 using axl::Ops;
+using axl::staging;
 
 namespace {
 
@@ -269,6 +270,8 @@ axlbm_status axlbm_create(const axlbm_grid* grid, double tau, const axlbm_forcin
     h->cap = nullptr;
     h->graph_many = h->graph_one = nullptr;
     h->graph_captures = h->graph_launches = 0;
+    h->stage = nullptr;
+    h->stage_bytes = 0;
     h->check_parts = 0;
     h->bulk_grid[0][0] = h->bulk_grid[0][1] = h->bulk_grid[1][0] = h->bulk_grid[1][1] = 0;
     {
@@ -532,15 +535,11 @@ axlbm_status axlbm_moments(axlbm_handle* h, uint32_t mask, void* out, int32_t ou
         return AXLBM_OK;
     }
     void* tmp = nullptr;
-    cudaError_t e = cudaMalloc(&tmp, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(h, AXLBM_ENOMEM, "staging buffer");
-    }
+    cudaError_t e = staging(h, bytes, &tmp);
+    if (e != cudaSuccess) return fail(h, AXLBM_ENOMEM, "staging buffer");
     e = ops->moments(h, tmp, mask, out_dtype == AXLBM_F32);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(h, e, "moments");
     return AXLBM_OK;
 }
@@ -555,15 +554,11 @@ axlbm_status axlbm_set_fields(axlbm_handle* h, const void* fields, int32_t in_dt
         e = ops->init_fields(h, fields, in_dtype == AXLBM_F32);
     } else {
         void* tmp = nullptr;
-        e = cudaMalloc(&tmp, bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(h, AXLBM_ENOMEM, "staging buffer");
-        }
+        e = staging(h, bytes, &tmp);
+        if (e != cudaSuccess) return fail(h, AXLBM_ENOMEM, "staging buffer");
         e = cudaMemcpyAsync(tmp, fields, bytes, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess) e = ops->init_fields(h, tmp, in_dtype == AXLBM_F32);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        cudaFree(tmp);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "set_fields");
     h->parity = 0;
@@ -652,6 +647,7 @@ axlbm_status axlbm_destroy(axlbm_handle* h) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     drop_graphs(h);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->stage) cudaFree(h->stage);
     for (auto ev : h->ev)
         if (ev) cudaEventDestroy(ev);
     if (h->owns_mem) {

@@ -26,6 +26,7 @@
 
 using axl::BatchLayout;
 using axl::BatchOps;
+using axl::staging;
 
 namespace {
 
@@ -592,6 +593,8 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
     b->graph_shape = -1;
     b->graph_many = b->graph_one = nullptr;
     b->graph_captures = b->graph_launches = 0;
+    b->stage = nullptr;
+    b->stage_bytes = 0;
     b->cap = nullptr;
     {
         int dev = 0;
@@ -740,15 +743,11 @@ axlbm_status axlbm_batch_moments(axlbm_batch* b, int32_t d, uint32_t mask, void*
         return e == cudaSuccess ? AXLBM_OK : bcuda(b, e, "moments");
     }
     void* tmp = nullptr;
-    cudaError_t e = cudaMalloc(&tmp, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return bfail(b, AXLBM_ENOMEM, "staging buffer");
-    }
+    cudaError_t e = staging(b, bytes, &tmp);
+    if (e != cudaSuccess) return bfail(b, AXLBM_ENOMEM, "staging buffer");
     e = ops->moments(b, d, tmp, mask, out_dtype == AXLBM_F32);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    cudaFree(tmp);
     return e == cudaSuccess ? AXLBM_OK : bcuda(b, e, "moments");
 }
 
@@ -765,15 +764,11 @@ axlbm_status axlbm_batch_set_fields(axlbm_batch* b, int32_t d, const void* field
         e = ops->init(b, d, fields, in_dtype == AXLBM_F32);
     } else {
         void* tmp = nullptr;
-        e = cudaMalloc(&tmp, bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return bfail(b, AXLBM_ENOMEM, "staging buffer");
-        }
+        e = staging(b, bytes, &tmp);
+        if (e != cudaSuccess) return bfail(b, AXLBM_ENOMEM, "staging buffer");
         e = cudaMemcpyAsync(tmp, fields, bytes, cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = ops->init(b, d, tmp, in_dtype == AXLBM_F32);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-        cudaFree(tmp);
     }
     if (e != cudaSuccess) return bcuda(b, e, "set_fields");
     b->speed_valid = false;
@@ -791,11 +786,8 @@ axlbm_status axlbm_batch_set_fields_all(axlbm_batch* b, const void* fields, int3
     void* tmp = nullptr;
     cudaError_t e = cudaSuccess;
     if (!on_device) {
-        e = cudaMalloc(&tmp, total * es);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return bfail(b, AXLBM_ENOMEM, "staging buffer");
-        }
+        e = staging(b, total * es, &tmp);
+        if (e != cudaSuccess) return bfail(b, AXLBM_ENOMEM, "staging buffer");
         e = cudaMemcpyAsync(tmp, fields, total * es, cudaMemcpyHostToDevice, b->stream);
         src = static_cast<const char*>(tmp);
     }
@@ -805,10 +797,7 @@ axlbm_status axlbm_batch_set_fields_all(axlbm_batch* b, const void* fields, int3
         e = ops->init(b, d, src + off * es, in_dtype == AXLBM_F32);
         off += (size_t)5 * b->desc[d].grid.nr * b->desc[d].grid.nz;
     }
-    if (tmp) {
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-        cudaFree(tmp);
-    }
+    if (tmp && e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // the caller may reuse its array
     if (e != cudaSuccess) return bcuda(b, e, "set_fields_all");
     b->speed_valid = false;
     return AXLBM_OK;
@@ -828,11 +817,8 @@ axlbm_status axlbm_batch_moments_all(axlbm_batch* b, uint32_t mask, void* out, i
     char* dst = static_cast<char*>(out);
     void* tmp = nullptr;
     if (!out_on_device) {
-        cudaError_t e = cudaMalloc(&tmp, total * es);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return bfail(b, AXLBM_ENOMEM, "staging buffer");
-        }
+        cudaError_t e = staging(b, total * es, &tmp);
+        if (e != cudaSuccess) return bfail(b, AXLBM_ENOMEM, "staging buffer");
         dst = static_cast<char*>(tmp);
     }
     const BatchOps* ops = batch_ops_for(b->precision);
@@ -845,7 +831,6 @@ axlbm_status axlbm_batch_moments_all(axlbm_batch* b, uint32_t mask, void* out, i
     if (tmp) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, total * es, cudaMemcpyDeviceToHost, b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-        cudaFree(tmp);
     }
     return e == cudaSuccess ? AXLBM_OK : bcuda(b, e, "moments_all");
 }
@@ -1045,6 +1030,7 @@ axlbm_status axlbm_batch_destroy(axlbm_batch* b) {
     }
     batch_drop_graphs(b);
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->stage) cudaFree(b->stage);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->join) cudaEventDestroy(b->join);
     for (auto ev : b->ev)

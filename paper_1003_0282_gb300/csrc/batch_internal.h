@@ -86,6 +86,8 @@ struct axlbm_batch {
     cudaGraphExec_t graph_many;     // kGraphPairs (even, odd) step pairs
     cudaGraphExec_t graph_one;      // one pair
     int64_t graph_captures, graph_launches;
+    void* stage;  // device staging buffer of host-side field I/O, kept between calls
+    size_t stage_bytes;
     std::string err;
 };
 

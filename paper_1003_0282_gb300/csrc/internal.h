@@ -114,10 +114,36 @@ struct axlbm_handle {
     cudaStream_t cap;
     cudaGraphExec_t graph_many, graph_one;  // kGraphPairs step pairs; one pair
     int64_t graph_captures, graph_launches;
+    void* stage;  // device staging buffer of host-side field I/O, kept between calls
+    size_t stage_bytes;
     std::string err;
 };
 
 namespace axl {
+
+// A device staging buffer of at least `bytes` for host-side I/O of handle h
+// (an axlbm_handle or an axlbm_batch), kept between calls and grown on demand.
+template <class H>
+cudaError_t staging(H* h, size_t bytes, void** out) {
+    if (h->stage_bytes < bytes) {
+        if (h->stage) {
+            cudaError_t e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) return e;
+            cudaFree(h->stage);
+            h->stage = nullptr;
+            h->stage_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&h->stage, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->stage = nullptr;
+            return e;
+        }
+        h->stage_bytes = bytes;
+    }
+    *out = h->stage;
+    return cudaSuccess;
+}
 
 // Precision-specific launchers (one set per storage type, see ops_impl.cuh).
 struct Ops {
