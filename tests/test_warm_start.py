@@ -268,3 +268,22 @@ def test_canvas_from_fields_matches_numpy(Bgpu):
                  + fy * ((1 - fx) * p[np.ix_(y1, x0)] + fx * p[np.ix_(y1, x1)]))
             want = v / g["u_scale"] if c < 3 else v - pb.t_ref
             assert np.max(np.abs(got[d, c] - want)) <= 1e-5 * max(1.0, np.max(np.abs(want))), (d, c)
+
+
+def test_training_script_initial_weights():
+    """The trainer's starting weights: the library's packing and count, every
+    value inside its layer's bound 1/sqrt(fan_in), and the BF16 rounding of
+    the trainer equal to the reference's."""
+    from paper_1003_0282_gb300 import warm_start_train as T
+    assert T.LAYERS == WS.LAYERS
+    bits = T.initial_weights(5)
+    assert bits.dtype == np.uint16 and bits.size == WS.weight_count()
+    off = 0
+    v = WS.bf16_to_float(bits)
+    for ci, co, k in WS.LAYERS:
+        n = co * ci * k * k + co
+        bound = 1.0 / np.sqrt(ci * k * k)
+        assert np.max(np.abs(v[off:off + n])) <= bound * (1 + 2 ** -7)
+        off += n
+    x = np.random.default_rng(6).normal(size=1000)
+    assert np.array_equal(T.bf16_bits(x), WS.float_to_bf16(x))
