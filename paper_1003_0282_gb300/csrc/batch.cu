@@ -3,14 +3,16 @@
 // Packing: domains are sorted by temperature flag and height and placed left
 // to right in shelves of a common-pitch array, side by side without gaps,
 // each shelf starting on a row that is a multiple of kRowAlign, so one TMA
-// descriptor covers every domain.  The bulk tiles form a regular grid over
+// descriptor per tile shape covers every domain.  The bulk tiles form a regular grid over
 // the occupied part of the array: a tile may straddle several domains of a
 // shelf (up to kSlots: every domain is given at least kMinCols columns), so
 // only the shelves' ragged ends are loaded without being updated.  Tiles are
 // listed row-major, so concurrently running CTAs sweep neighbouring rows
-// together (shared rows of the TMA boxes then hit L2).  Tile shape: the
-// candidates are timed on the batch at creation and the fastest kept (cached
-// per GPU, precision, mix).
+// together (shared rows of the TMA boxes then hit L2).  Tile shapes: each
+// parity has two candidates (512-node tiles for CTAs of eight computing
+// warps; 256-node tiles in CTAs of four for FP32 odd steps); the four pairs
+// are timed on the batch at creation and the fastest kept (cached per GPU,
+// precision, mix).
 #include <math.h>
 #include <string.h>
 
@@ -367,7 +369,7 @@ void batch_drop_graphs(axlbm_batch* b) {
     b->graph_shape = -1;
 }
 
-// Capture `pairs` plain (even, odd) step pairs of the current tile shape and
+// Capture `pairs` plain (even, odd) step pairs with the current tile shapes and
 // instantiate them.  The step functions launch on b->stream, which points at
 // the capture stream meanwhile; the odd steps' side-stream work joins the
 // capture through the fork and join events.
@@ -397,7 +399,7 @@ cudaError_t batch_capture_pairs(axlbm_batch* b, const BatchOps* ops, int pairs, 
 }
 
 // `pairs` plain step pairs from an even level, from the graphs (captured on
-// first use for the tile shape in use).
+// first use for the pair of tile shapes in use).
 axlbm_status batch_graph_pairs(axlbm_batch* b, const BatchOps* ops, int64_t pairs) {
     const int key = 4 * b->shape[0] + b->shape[1];
     if (b->graph_shape != key) {
@@ -429,7 +431,7 @@ axlbm_status batch_step_n(axlbm_batch* b, int64_t n) {
     int64_t s = 0;
     // every step but the last two (the check steps) is plain: with timing off,
     // whole (even, odd) pairs of them replay captured graphs once the plain
-    // kernels of the shape have been sized by earlier launches
+    // kernels of the shapes in use have been sized by earlier launches
     const bool sized = b->grid[b->shape[0]][0][0] > 0 && b->grid[b->shape[1]][1][0] > 0;
     if (b->use_graphs && !b->timing && sized && n - 2 - b->parity >= 2 * kMinGraphPairs) {
         if (b->parity == 1) {
@@ -482,7 +484,8 @@ axlbm_status batch_step_n(axlbm_batch* b, int64_t n) {
     return AXLBM_OK;
 }
 
-// Time the candidate tile shapes on this batch and keep the fastest.
+// Time the pairs of candidate tile shapes (even step, odd step) on this batch
+// and keep the fastest.
 axlbm_status tune(axlbm_batch* b) {
     int dev = 0;
     cudaDeviceProp prop;
@@ -510,7 +513,7 @@ axlbm_status tune(axlbm_batch* b) {
         const int s = 4 * (e0s + c / 2) + (o0s + c % 2);
         b->shape[0] = s / 4;
         b->shape[1] = s % 4;
-        // warm-up: every kernel variant of the shape (plain and check steps
+        // warm-up: every kernel variant of the shapes (plain and check steps
         // of both parities) is loaded and sized before the timed calls
         st = batch_step_n(b, 4);
         if (st != AXLBM_OK) break;
