@@ -265,3 +265,15 @@ def test_low_viscosity_bgk_versus_mrt(B):
     with open(path, "w") as fh:
         json.dump(out, fh, indent=1)
     assert out["mrt"]["finite"], out
+
+
+@pytest.mark.parametrize("mix", ["crystal", "nee-axis-node", "annulus-mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_population_parity_after_1000_steps(B, mix, precision):
+    """1000 steps from the same seeded state (swirl and temperature, the
+    paper's axis variants and walls, BGK and MRT): every population within
+    1e-10 (FP64) or 1e-5 (FP32) of the oracle, relative to the field's scale,
+    after 10, 100 and 1000 steps."""
+    pb = problem(70, 45, mix, collision="mrt" if mix.startswith("nee") else "bgk")
+    worst, _ = run_and_compare(B, pb, precision, [10, 90, 900])
+    assert max(worst.values()) <= POP_TOL[precision], worst
