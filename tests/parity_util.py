@@ -111,3 +111,23 @@ def window_oracle(pops, pb, j0, k0, steps, t0):
     oracle.step(st, steps)
     jc = j0 - ja
     return st.f[:, kc, jc], (st.g[:, kc, jc] if pb.swirl else None), (st.h[:, kc, jc] if pb.temperature else None)
+
+
+def record(filename, name, value):
+    """Merge `value` under `name` into the JSON file `filename` of the
+    directory named by the AXLBM_TEST_RECORD environment variable (measured
+    values the tests see, for reports); nothing is written when it is unset."""
+    import json
+    import os
+    folder = os.environ.get("AXLBM_TEST_RECORD")
+    if not folder:
+        return
+    os.makedirs(folder, exist_ok=True)
+    path = os.path.join(folder, filename)
+    data = {}
+    if os.path.exists(path):
+        with open(path) as fh:
+            data = json.load(fh)
+    data[name] = value
+    with open(path, "w") as fh:
+        json.dump(data, fh, indent=1)

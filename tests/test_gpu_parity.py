@@ -20,8 +20,8 @@ import pytest
 import oracle
 from oracle import analytic as A
 from paper_1003_0282_gb300 import inputs as I
-from parity_util import (BOUNDARY_MIXES, POP_TOL, compare_populations, problem, rel_err, seeded_state, upload,
-                         window_oracle)
+from parity_util import (BOUNDARY_MIXES, POP_TOL, compare_populations, problem, record, rel_err, seeded_state,
+                         upload, window_oracle)
 
 pytestmark = pytest.mark.gpu
 
@@ -260,10 +260,7 @@ def test_low_viscosity_bgk_versus_mrt(B):
             uz_axis = dom.moments(B.UZ)[0][:, 0]
             out[coll]["uz_axis_max_over_omega_r"] = float(np.max(uz_axis) / (omega * nr))
         dom.close()
-    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out", "low_viscosity.json")
-    os.makedirs(os.path.dirname(path), exist_ok=True)
-    with open(path, "w") as fh:
-        json.dump(out, fh, indent=1)
+    record("low_viscosity.json", "bgk_versus_mrt", out)
     assert out["mrt"]["finite"], out
 
 

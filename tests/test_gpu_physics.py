@@ -15,13 +15,12 @@ steady to ~1e-6 per step).  The build's walls differ from the paper's
 paper uses, with the node on the axis), so the bounds are a few per cent.
 """
 import dataclasses
-import json
-import os
 
 import numpy as np
 import pytest
 
 from paper_1003_0282_gb300 import inputs as I
+from parity_util import record
 
 pytestmark = pytest.mark.gpu
 
@@ -121,12 +120,35 @@ def test_table1_wheeler_stream_function(steady):
 
 
 def _record(name, got):
-    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out", "tables.json")
-    os.makedirs(os.path.dirname(path), exist_ok=True)
-    data = {}
-    if os.path.exists(path):
-        with open(path) as fh:
-            data = json.load(fh)
-    data[name] = {f"{k[0]:g} {k[1]}": [float(x) for x in v] for k, v in got.items()}
-    with open(path, "w") as fh:
-        json.dump(data, fh, indent=1)
+    record("tables.json", name, {f"{k[0]:g} {k[1]}": [float(x) for x in v] for k, v in got.items()})
+
+
+def test_cavity_128x192_to_steady_state(B):
+    """The rotating-lid cylinder at the smallest grid of the benchmark's
+    cavity family (128 x 192, A = 1.5, Re = 990, lid speed 0.1): FP32 reaches
+    the Eq. 57 residual 1e-8 and Table 2's axial peak; FP16 deviation storage
+    run as long stays within its rounding floor of the FP32 fields."""
+    pb = I.rotating_lid_cavity(nr=128, aspect=1.5, re=990.0)
+    dom = B.Domain(pb, "fp32")
+    steps = 0
+    res = 1.0
+    while res > 1e-8 and steps < 4_000_000:
+        dom.step(50_000)
+        steps += 50_000
+        res = dom.residual()[0]
+    assert res <= 1e-8, (steps, res)
+    m32 = dom.moments(B.RHO | B.UR | B.UZ | B.UTH)
+    dom.close()
+    umax, h = axis_peak(pb, m32)
+    want_u, want_h = TABLE2[990.0]
+    assert abs(umax - want_u) <= 0.05 * want_u and abs(h - want_h) <= 0.02, (umax, h)
+    half = B.Domain(pb, "fp16")
+    half.step(steps)
+    m16 = half.moments(B.RHO | B.UR | B.UZ | B.UTH)
+    res16 = half.residual()[0]
+    half.close()
+    lid = pb.omega_of("hi") * pb.wall_radius
+    err = float(np.max(np.abs(m16[1:] - m32[1:]))) / lid
+    record("tables.json", "cavity_128x192", {"steps_to_1e-8": steps, "fp32_residual": res, "fp16_residual": res16,
+                                            "fp16_max_velocity_error_over_lid": err, "uz_max": umax, "h_over_H": h})
+    assert err <= 5e-3, err

@@ -9,14 +9,14 @@ the rounding of a stored deviation of size ~1e-2 is ~1e-2 * 2^-11 (FP16) or
 ~1e-2 * 2^-8 (BF16) per step, damped by the collision; the bounds below leave
 room for the accumulated rounding over the run.
 """
-import json
-import os
 
 import numpy as np
 import pytest
 
 import oracle
 from paper_1003_0282_gb300 import inputs as I
+
+from parity_util import record
 
 pytestmark = pytest.mark.gpu
 
@@ -25,8 +25,6 @@ BOUNDS = {  # relative max-norm after 200 steps
     "bf16": {"rho": 2e-3, "u_r": 5e-2, "u_z": 5e-2, "u_theta": 5e-2, "T": 2e-2},
     "fp32": {"rho": 1e-6, "u_r": 1e-5, "u_z": 1e-5, "u_theta": 1e-5, "T": 1e-5},
 }
-REPORT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out",
-                      "precision_errors.json")
 
 
 @pytest.fixture(scope="module")
@@ -66,15 +64,7 @@ def test_reduced_storage_error_per_field(B, precision):
 
 
 def _record(key, value):
-    os.makedirs(os.path.dirname(REPORT), exist_ok=True)
-    try:
-        with open(REPORT) as fh:
-            report = json.load(fh)
-    except (OSError, ValueError):
-        report = {}
-    report[key] = value
-    with open(REPORT, "w") as fh:
-        json.dump(report, fh, indent=1)
+    record("precision_errors.json", key, value)
 
 
 CAVITY_BOUNDS = {"fp32": 1e-5, "fp16": 2e-2, "bf16": 1e-1}  # relative max-norm on u_r, u_z, u_theta
