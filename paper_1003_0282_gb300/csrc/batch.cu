@@ -246,6 +246,8 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
     off += al((size_t)std::max(L.naxis, 1) * 4);
     L.off_nee = off;
     off += al((size_t)std::max(L.nnee, 1) * 4);
+    L.off_nodes = off;
+    off += al((size_t)(n + 1) * 8);
     for (int s = 0; s < axl::kBatchShapes; ++s) {
         L.shape[s].off_tiles = off;
         off += al((size_t)L.shape[s].ntiles * sizeof(axl::TileRec));
@@ -674,6 +676,11 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
     if (st == AXLBM_OK) st = upload(b, L.off_rstart, P.rstart.data(), P.rstart.size() * sizeof(int));
     if (st == AXLBM_OK) st = upload(b, L.off_axis, P.axis.data(), P.axis.size() * sizeof(int));
     if (st == AXLBM_OK) st = upload(b, L.off_nee, P.nee.data(), P.nee.size() * sizeof(int));
+    if (st == AXLBM_OK) {  // first packed node of every domain, in domain order
+        std::vector<long long> nodes(n + 1, 0);
+        for (int d = 0; d < n; ++d) nodes[d + 1] = nodes[d] + (long long)domains[d].grid.nr * domains[d].grid.nz;
+        st = upload(b, L.off_nodes, nodes.data(), nodes.size() * sizeof(long long));
+    }
     for (int s = 0; s < axl::kBatchShapes && st == AXLBM_OK; ++s) {
         st = upload(b, L.shape[s].off_tiles, P.tiles[s].data(), P.tiles[s].size() * sizeof(axl::TileRec));
         if (st == AXLBM_OK) st = upload(b, L.shape[s].off_tstart, P.tstart[s].data(), P.tstart[s].size() * sizeof(int));
@@ -795,12 +802,7 @@ axlbm_status axlbm_batch_set_fields_all(axlbm_batch* b, const void* fields, int3
         e = cudaMemcpyAsync(tmp, fields, total * es, cudaMemcpyHostToDevice, b->stream);
         src = static_cast<const char*>(tmp);
     }
-    const BatchOps* ops = batch_ops_for(b->precision);
-    size_t off = 0;
-    for (int d = 0; d < b->n && e == cudaSuccess; ++d) {
-        e = ops->init(b, d, src + off * es, in_dtype == AXLBM_F32);
-        off += (size_t)5 * b->desc[d].grid.nr * b->desc[d].grid.nz;
-    }
+    if (e == cudaSuccess) e = batch_ops_for(b->precision)->init_all(b, src, in_dtype == AXLBM_F32);
     if (tmp && e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // the caller may reuse its array
     if (e != cudaSuccess) return bcuda(b, e, "set_fields_all");
     b->speed_valid = false;
@@ -825,13 +827,7 @@ axlbm_status axlbm_batch_moments_all(axlbm_batch* b, uint32_t mask, void* out, i
         if (e != cudaSuccess) return bfail(b, AXLBM_ENOMEM, "staging buffer");
         dst = static_cast<char*>(tmp);
     }
-    const BatchOps* ops = batch_ops_for(b->precision);
-    cudaError_t e = cudaSuccess;
-    size_t off = 0;
-    for (int d = 0; d < b->n && e == cudaSuccess; ++d) {
-        e = ops->moments(b, d, dst + off * es, mask, out_dtype == AXLBM_F32);
-        off += (size_t)nf * b->desc[d].grid.nr * b->desc[d].grid.nz;
-    }
+    cudaError_t e = batch_ops_for(b->precision)->moments_all(b, dst, mask, out_dtype == AXLBM_F32);
     if (tmp) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, total * es, cudaMemcpyDeviceToHost, b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);

@@ -546,6 +546,106 @@ static __global__ void k_batch_set_time(const DomDesc* doms, int ndom, Clock* cl
     if (threadIdx.x == 0) clock->t = t;
 }
 
+// Domain of packed node i (nodes[d] is the first node of domain d in the
+// packed order of the all-domain field calls, nodes[ndom] their total).
+__device__ __forceinline__ int batch_domain_of(const long long* nodes, int ndom, long long i) {
+    int lo = 0, hi = ndom - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (nodes[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The argument block of domain d alone, as the per-domain field calls build it.
+template <class S>
+__device__ __forceinline__ KArgs<S, float> batch_domain_kargs(const BatchArgs<S, float>& A, int d) {
+    const DomDesc& D = A.doms[d];
+    KArgs<S, float> K;
+    K.pop = A.pop;
+    K.G = dom_geom(D, A.pitch, A.plane);
+    K.C = D.cf;
+    K.az = A.dom_az + 2 * d;
+    K.g_plane = 9;
+    K.h_plane = 13;
+    return K;
+}
+
+template <class S, bool TH, class O>
+__device__ __forceinline__ void batch_node_moments(const KArgs<S, float>& K, int j, int k, long long n, long long li,
+                                                   int parity, unsigned mask, O* out) {
+    using R = float;
+    Cell<R, true, TH> c;
+    if (parity == 0) load_natural(K, j, k, c);
+    else pull_odd(K, j, k, c);
+    if (!TH)
+        for (int q = 0; q < 4; ++q) c.h[q] = R(0);
+    const R inv_r = inv_radius<R>(K.G, j);
+    const R uth = ((c.g[0] + c.g[1]) + (c.g[2] + c.g[3])) * K.C.inv_rho0;
+    const R temp = TH ? ((c.h[0] + c.h[1]) + (c.h[2] + c.h[3])) + K.C.t_ref : R(0);
+    c.collide(inv_r, K.C, R(K.az[parity]));  // sets rho, ur, uz from the pre-collision state
+    const R vals[5] = {c.rho, c.ur, c.uz, uth, temp};
+    int slotn = 0;
+    for (int f = 0; f < 5; ++f) {
+        if (mask & (1u << f)) {
+            out[slotn * n + li] = O(vals[f]);
+            ++slotn;
+        }
+    }
+}
+
+// Macroscopic fields of every domain in one launch (the per-domain moments
+// kernel's arithmetic, node by node), packed domain after domain as
+// [nf][nz][nr].
+template <class S, class O>
+__global__ void __launch_bounds__(kThreads)
+    k_moments_batch(const BatchArgs<S, float> A, const long long* nodes, int parity, unsigned mask, int nf, O* out) {
+    const long long total = nodes[A.ndom];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int d = batch_domain_of(nodes, A.ndom, i);
+        const KArgs<S, float> K = batch_domain_kargs(A, d);
+        const long long n = (long long)K.G.nr * K.G.nz, li = i - nodes[d];
+        const int j = int(li % K.G.nr), k = int(li / K.G.nr);
+        O* o = out + (long long)nf * nodes[d];
+        if (A.doms[d].temperature) batch_node_moments<S, true>(K, j, k, n, li, parity, mask, o);
+        else batch_node_moments<S, false>(K, j, k, n, li, parity, mask, o);
+    }
+}
+
+// Equilibrium state of every domain from packed fields [5][nz][nr] per
+// domain (the per-domain initialisation's arithmetic, node by node).
+template <class S, class I>
+__global__ void __launch_bounds__(kThreads) k_init_batch(const BatchArgs<S, float> A, const long long* nodes, const I* fields) {
+    using R = float;
+    const long long total = nodes[A.ndom];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int d = batch_domain_of(nodes, A.ndom, i);
+        const KArgs<S, float> K = batch_domain_kargs(A, d);
+        const Geom& G = K.G;
+        const long long n = (long long)G.nr * G.nz, li = i - nodes[d];
+        const int j = int(li % G.nr), k = int(li / G.nr);
+        const I* fd = fields + 5 * nodes[d];
+        const R rho = R(fd[li]), ur = R(fd[n + li]), uz = R(fd[2 * n + li]);
+        const R uth = R(fd[3 * n + li]), temp = R(fd[4 * n + li]);
+        const R drho = R(double(fd[li]) - (double)K.C.rho0);
+        const R usq = R(1.5) * (ur * ur + uz * uz);
+        for (int a = 0; a < 9; ++a) {
+            const R eu = R(cr9(a)) * ur + R(cz9(a)) * uz;
+            const R w = R(w9(a));
+            Codec<S>::store(slot(K.pop, G, a, j, k), w * (drho + rho * (R(3) * eu + R(4.5) * eu * eu - usq)));
+        }
+        const bool th = A.doms[d].temperature != 0;
+        for (int q = 0; q < 4; ++q) {
+            const R eu = R(cr4(q)) * ur + R(cz4(q)) * uz;
+            Codec<S>::store(slot(K.pop, G, K.g_plane + q, j, k), K.C.rho0 * uth * R(0.25) * (R(1) + R(2) * eu));
+            if (th)
+                Codec<S>::store(slot(K.pop, G, K.h_plane + q, j, k),
+                                temp * R(0.25) * (R(1) + R(2) * eu) - K.C.t_ref * R(0.25));
+        }
+    }
+}
+
 // Node-on-axis domains after an odd step: the mirror column's populations
 // into each axis column (see axis_mirror_row); one block per such domain.
 template <class S, bool SW, bool TH>

@@ -36,7 +36,7 @@ struct BatchLayout {
     int nring;
     int nring_cold;  // ring entries of domains without temperature (listed first)
     size_t off_speed, off_tilepart, off_ringpart, off_result, off_az, off_clock, off_doms, off_slots, off_ring,
-        off_rstart, off_axis, off_nee;
+        off_rstart, off_axis, off_nee, off_nodes;  // off_nodes: long long [n + 1], first packed node of each domain
     int naxis;  // domains with a node on the axis (listed at off_axis)
     int nnee;   // domains with a wet wall (listed at off_nee)
     BatchTiles shape[kBatchShapes];
@@ -102,6 +102,9 @@ struct BatchOps {
     cudaError_t (*init)(axlbm_batch* b, int d, const void* fields, int in_f32);
     cudaError_t (*gather)(axlbm_batch* b, int d, double* out);
     cudaError_t (*scatter)(axlbm_batch* b, int d, const double* in);
+    // every domain at once, in the packed layout (one launch)
+    cudaError_t (*moments_all)(axlbm_batch* b, void* out, unsigned mask, int out_f32);
+    cudaError_t (*init_all)(axlbm_batch* b, const void* fields, int in_f32);
 };
 
 extern const BatchOps batch_ops_fp32;

@@ -256,6 +256,27 @@ cudaError_t batch_scatter_impl(axlbm_batch* b, int d, const double* in) {
 }
 
 template <class S, class R>
+cudaError_t batch_moments_all_impl(axlbm_batch* b, void* out, unsigned mask, int out_f32) {
+    const BatchArgs<S, R> A = batch_args<S, R>(b);
+    const long long* nodes = reinterpret_cast<const long long*>(b->mem + b->L.off_nodes);
+    int nf = 0;
+    for (int f = 0; f < 5; ++f) nf += (mask >> f) & 1;
+    const unsigned blocks = (unsigned)(b->num_sms * 8);
+    if (out_f32) k_moments_batch<S, float><<<blocks, kThreads, 0, b->stream>>>(A, nodes, b->parity, mask, nf, (float*)out);
+    else k_moments_batch<S, double><<<blocks, kThreads, 0, b->stream>>>(A, nodes, b->parity, mask, nf, (double*)out);
+    return cudaGetLastError();
+}
+template <class S, class R>
+cudaError_t batch_init_all_impl(axlbm_batch* b, const void* fields, int in_f32) {
+    const BatchArgs<S, R> A = batch_args<S, R>(b);
+    const long long* nodes = reinterpret_cast<const long long*>(b->mem + b->L.off_nodes);
+    const unsigned blocks = (unsigned)(b->num_sms * 8);
+    if (in_f32) k_init_batch<S, float><<<blocks, kThreads, 0, b->stream>>>(A, nodes, (const float*)fields);
+    else k_init_batch<S, double><<<blocks, kThreads, 0, b->stream>>>(A, nodes, (const double*)fields);
+    return cudaGetLastError();
+}
+
+template <class S, class R>
 BatchOps make_batch_ops() {
     BatchOps o;
     o.encode = &batch_encode_impl<S>;
@@ -265,6 +286,8 @@ BatchOps make_batch_ops() {
     o.init = &batch_init_impl<S, R>;
     o.gather = &batch_gather_impl<S, R>;
     o.scatter = &batch_scatter_impl<S, R>;
+    o.moments_all = &batch_moments_all_impl<S, R>;
+    o.init_all = &batch_init_all_impl<S, R>;
     return o;
 }
 
