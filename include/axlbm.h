@@ -230,12 +230,39 @@ AXLBM_API axlbm_status axlbm_set_fields(axlbm_handle* h, const void* fields, int
 AXLBM_API axlbm_status axlbm_get_populations(axlbm_handle* h, double* f, double* g, double* t_pop);
 
 /* Replace the populations with host FP64 arrays (layout as above) and set the
- * time to `time`.  Synchronises.  Used for tests and checkpoint / resume. */
+ * time to `time`.  Synchronises.  Used by tests; a bit-exact checkpoint is
+ * axlbm_save / axlbm_load below. */
 AXLBM_API axlbm_status axlbm_set_populations(axlbm_handle* h, const double* f, const double* g,
                                    const double* t_pop, int64_t time);
 
 /* Current time level. */
 AXLBM_API axlbm_status axlbm_time(const axlbm_handle* h, int64_t* time);
+
+/* Checkpoint and resume.  A checkpoint is the handle's whole mutable device
+ * state -- the stored populations as they sit in device memory (storage type
+ * and AA layout of the current level, no conversion), the speed plane and
+ * results of the last check step, and the clock with the axial acceleration
+ * a(t) of the next step -- behind a 64-byte header that holds the time level,
+ * the layout parity, the check-step flags and a fingerprint of the grid
+ * (nr, nz, distributions, storage, device layout).  It is in host byte order.
+ * Loaded into a handle created with the same grid and storage, the run
+ * continues bit for bit as the uninterrupted run would (the populations pass
+ * through no FP64 conversion and a(t) is not recomputed, unlike
+ * axlbm_get_populations / axlbm_set_populations).  tau, forcing and walls are
+ * the loading handle's own.
+ *
+ * axlbm_save: with buf == NULL, writes the checkpoint's size in bytes to
+ * *bytes and returns.  Otherwise writes the checkpoint into the host buffer
+ * buf of cap bytes and its size to *bytes (which may then be NULL);
+ * AXLBM_EINVAL if cap is below the size, AXLBM_ETIMEOUT if a bounded wait of
+ * an earlier step gave up (the state is not valid).  Synchronises the stream.
+ *
+ * axlbm_load: replaces the state with the checkpoint buf of `bytes` bytes.
+ * AXLBM_EINVAL, with the state unchanged, if buf is not a domain checkpoint
+ * of this format or belongs to another grid, storage or layout; on
+ * AXLBM_ECUDA the state is undefined.  Synchronises the stream. */
+AXLBM_API axlbm_status axlbm_save(axlbm_handle* h, void* buf, size_t cap, size_t* bytes);
+AXLBM_API axlbm_status axlbm_load(axlbm_handle* h, const void* buf, size_t bytes);
 
 /* Runs of plain steps (all but the two check steps that end every
  * axlbm_step call) are replayed from CUDA graphs captured on first use (8
@@ -383,6 +410,15 @@ AXLBM_API axlbm_status axlbm_batch_set_time(axlbm_batch* b, int64_t t);
  * destination keeps its own parameters.  With this a caller can retire
  * converged domains by repacking the rest into a smaller batch. */
 AXLBM_API axlbm_status axlbm_batch_copy_domain(axlbm_batch* dst, int32_t dd, axlbm_batch* src, int32_t sd);
+
+/* Checkpoint and resume of a whole batch, as axlbm_save / axlbm_load: every
+ * domain's stored populations, the speed plane, check partials and results,
+ * each domain's a(t) and the clock, behind the same header (kind "batch").
+ * The loading batch must have been created with the same storage and the
+ * same domain list (grids, distributions and boundary kinds, which fix the
+ * packing); it then continues bit for bit as the uninterrupted batch. */
+AXLBM_API axlbm_status axlbm_batch_save(axlbm_batch* b, void* buf, size_t cap, size_t* bytes);
+AXLBM_API axlbm_status axlbm_batch_load(axlbm_batch* b, const void* buf, size_t bytes);
 
 /* Time level of the batch, and the bulk tile shape (rows x nodes) of its even steps. */
 AXLBM_API axlbm_status axlbm_batch_time(const axlbm_batch* b, int64_t* time);

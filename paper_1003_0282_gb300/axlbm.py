@@ -129,6 +129,11 @@ def lib() -> ctypes.CDLL:
         L.axlbm_batch_tile_shapes.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         L.axlbm_batch_use_graphs.argtypes = [H, ctypes.c_int32]
         L.axlbm_batch_set_time.argtypes = [H, ctypes.c_int64]
+        for pre in ("axlbm_", "axlbm_batch_"):
+            getattr(L, pre + "save").argtypes = [H, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+            getattr(L, pre + "save").restype = ctypes.c_int
+            getattr(L, pre + "load").argtypes = [H, ctypes.c_void_p, ctypes.c_size_t]
+            getattr(L, pre + "load").restype = ctypes.c_int
         L.axlbm_batch_copy_domain.argtypes = [H, ctypes.c_int32, H, ctypes.c_int32]
         L.axlbm_batch_graph_stats.argtypes = [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_batch_kernel_timing.argtypes = [H, ctypes.c_int32]
@@ -382,6 +387,29 @@ class Domain:
         cast = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
         axlbm_set_populations(self.handle, cast(f), cast(g), cast(h), time)
 
+    # -- checkpoint / resume
+    def save(self) -> np.ndarray:
+        """Checkpoint of the whole state (axlbm_save) as a uint8 array."""
+        return _save(lib().axlbm_save, self.handle, _check)
+
+    def load(self, checkpoint) -> None:
+        """Resume from a checkpoint of a domain with the same grid and storage (axlbm_load)."""
+        _load(lib().axlbm_load, self.handle, checkpoint, _check)
+
+
+def _save(fn, handle, check) -> np.ndarray:
+    n = ctypes.c_size_t()
+    check(fn(handle, None, 0, ctypes.byref(n)), handle)
+    out = np.empty(n.value, dtype=np.uint8)
+    check(fn(handle, out.ctypes.data, out.size, ctypes.byref(n)), handle)
+    return out
+
+
+def _load(fn, handle, checkpoint, check) -> None:
+    a = np.ascontiguousarray(np.frombuffer(checkpoint, dtype=np.uint8) if isinstance(checkpoint, (bytes, bytearray))
+                             else checkpoint, dtype=np.uint8)
+    check(fn(handle, a.ctypes.data, a.size), handle)
+
 
 # ----------------------------------------------------------------------------- batches
 
@@ -616,6 +644,15 @@ class Batch:
     def set_populations(self, d: int, f, g, h=None) -> None:
         cast = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
         axlbm_batch_set_populations(self.handle, d, cast(f), cast(g), cast(h))
+
+    # -- checkpoint / resume
+    def save(self) -> np.ndarray:
+        """Checkpoint of every domain's state (axlbm_batch_save) as a uint8 array."""
+        return _save(lib().axlbm_batch_save, self.handle, _bcheck)
+
+    def load(self, checkpoint) -> None:
+        """Resume from a checkpoint of a batch of the same domains and storage (axlbm_batch_load)."""
+        _load(lib().axlbm_batch_load, self.handle, checkpoint, _bcheck)
 
 
 # ----------------------------------------------------------------------------- warm start

@@ -642,6 +642,64 @@ axlbm_status axlbm_time(const axlbm_handle* h, int64_t* t) {
     return AXLBM_OK;
 }
 
+namespace {
+
+// What a domain checkpoint's bytes depend on: the grid's shape, the
+// distributions it carries, the storage and the device layout.
+static uint64_t domain_fingerprint(const axlbm_handle* h) {
+    uint64_t f = axl::kCkptBasis;
+    for (int64_t v : {(int64_t)axl::kCkptDomain, (int64_t)h->grid.precision, (int64_t)h->grid.nr,
+                      (int64_t)h->grid.nz, (int64_t)h->grid.with_swirl, (int64_t)h->grid.with_temperature,
+                      (int64_t)h->L.nplanes, (int64_t)h->L.pitch, (int64_t)h->L.total})
+        f = axl::ckpt_mix(f, v);
+    return f;
+}
+
+}  // namespace
+
+axlbm_status axlbm_save(axlbm_handle* h, void* buf, size_t cap, size_t* bytes) {
+    if (!h) return fail(nullptr, AXLBM_EINVAL, "handle is NULL");
+    const size_t need = sizeof(axl::CkptHeader) + h->L.total;
+    if (!buf) {
+        if (!bytes) return fail(h, AXLBM_EINVAL, "buf and bytes are both NULL");
+        *bytes = need;
+        return AXLBM_OK;
+    }
+    if (cap < need) return fail(h, AXLBM_EINVAL, "checkpoint buffer is too small");
+    char* out = static_cast<char*>(buf);
+    cudaError_t e = cudaMemcpyAsync(out + sizeof(axl::CkptHeader), h->mem, h->L.total, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "save");
+    axl::Clock clk;
+    memcpy(&clk, out + sizeof(axl::CkptHeader) + h->L.off_clock, sizeof clk);
+    if (clk.err) return fail(h, AXLBM_ETIMEOUT, "a bounded wait for a TMA copy gave up; the state is not valid");
+    const axl::CkptHeader c = axl::ckpt_header(axl::kCkptDomain, domain_fingerprint(h), h->L.total, h->t, h->parity,
+                                               h->speed_valid, h->have_check, h->last_residual_valid, h->check_parts);
+    memcpy(out, &c, sizeof c);
+    if (bytes) *bytes = need;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_load(axlbm_handle* h, const void* buf, size_t bytes) {
+    if (!h) return fail(nullptr, AXLBM_EINVAL, "handle is NULL");
+    axl::CkptHeader c;
+    const char* why = axl::ckpt_check(buf, bytes, axl::kCkptDomain, domain_fingerprint(h), h->L.total, &c);
+    if (*why) return fail(h, AXLBM_EINVAL, why);
+    cudaError_t e = cudaStreamSynchronize(h->stream);  // work queued on the old state
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->mem, static_cast<const char*>(buf) + sizeof c, h->L.total, cudaMemcpyHostToDevice,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "load");
+    h->t = c.t;
+    h->parity = c.parity;
+    h->speed_valid = (c.flags & axl::kCkptSpeedValid) != 0;
+    h->have_check = (c.flags & axl::kCkptHaveCheck) != 0;
+    h->last_residual_valid = (c.flags & axl::kCkptResidualValid) != 0;
+    h->check_parts = c.aux;
+    return AXLBM_OK;
+}
+
 axlbm_status axlbm_destroy(axlbm_handle* h) {
     if (!h) return AXLBM_EINVAL;
     cudaError_t e = cudaStreamSynchronize(h->stream);

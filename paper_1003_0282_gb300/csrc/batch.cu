@@ -925,6 +925,78 @@ axlbm_status axlbm_batch_copy_domain(axlbm_batch* dst, int32_t dd, axlbm_batch* 
     return AXLBM_OK;
 }
 
+namespace {
+
+// The mutable device bytes of a batch (everything reset_rest clears: the
+// population planes, speed plane, partials, results, a(t) per domain and the
+// clock) and what their layout depends on: the storage and every domain's
+// grid and place in the packed array.
+static size_t batch_ckpt_bytes(const axlbm_batch* b) { return b->L.off_clock + 256; }
+
+static uint64_t batch_fingerprint(const axlbm_batch* b) {
+    const BatchLayout& L = b->L;
+    uint64_t f = axl::kCkptBasis;
+    for (int64_t v : {(int64_t)axl::kCkptBatch, (int64_t)b->precision, (int64_t)b->n, (int64_t)L.nplanes,
+                      (int64_t)L.pitch, (int64_t)L.rows, (int64_t)L.nring, (int64_t)L.off_speed,
+                      (int64_t)L.off_tilepart, (int64_t)L.off_ringpart, (int64_t)L.off_result, (int64_t)L.off_az,
+                      (int64_t)L.off_clock})
+        f = axl::ckpt_mix(f, v);
+    for (int d = 0; d < b->n; ++d) {
+        const axlbm_grid& g = b->desc[d].grid;
+        for (int64_t v : {(int64_t)g.nr, (int64_t)g.nz, (int64_t)g.with_swirl, (int64_t)g.with_temperature,
+                          (int64_t)b->col0[d], (int64_t)b->row0[d]})
+            f = axl::ckpt_mix(f, v);
+    }
+    return f;
+}
+
+}  // namespace
+
+axlbm_status axlbm_batch_save(axlbm_batch* b, void* buf, size_t cap, size_t* bytes) {
+    if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
+    const size_t state = batch_ckpt_bytes(b), need = sizeof(axl::CkptHeader) + state;
+    if (!buf) {
+        if (!bytes) return bfail(b, AXLBM_EINVAL, "buf and bytes are both NULL");
+        *bytes = need;
+        return AXLBM_OK;
+    }
+    if (cap < need) return bfail(b, AXLBM_EINVAL, "checkpoint buffer is too small");
+    char* out = static_cast<char*>(buf);
+    cudaError_t e = cudaMemcpyAsync(out + sizeof(axl::CkptHeader), b->mem, state, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "save");
+    axl::Clock clk;
+    memcpy(&clk, out + sizeof(axl::CkptHeader) + b->L.off_clock, sizeof clk);
+    if (clk.err) return bfail(b, AXLBM_ETIMEOUT, "a bounded wait for a TMA copy gave up; the state is not valid");
+    const axl::CkptHeader c = axl::ckpt_header(axl::kCkptBatch, batch_fingerprint(b), state, b->t, b->parity,
+                                               b->speed_valid, b->have_check, b->last_residual_valid,
+                                               b->last_check_parity);
+    memcpy(out, &c, sizeof c);
+    if (bytes) *bytes = need;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_load(axlbm_batch* b, const void* buf, size_t bytes) {
+    if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
+    const size_t state = batch_ckpt_bytes(b);
+    axl::CkptHeader c;
+    const char* why = axl::ckpt_check(buf, bytes, axl::kCkptBatch, batch_fingerprint(b), state, &c);
+    if (*why) return bfail(b, AXLBM_EINVAL, why);
+    if (c.aux != 0 && c.aux != 1) return bfail(b, AXLBM_EINVAL, "checkpoint with a bad check parity");
+    cudaError_t e = cudaStreamSynchronize(b->stream);  // work queued on the old state
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->mem, static_cast<const char*>(buf) + sizeof c, state, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "load");
+    b->t = c.t;
+    b->parity = c.parity;
+    b->speed_valid = (c.flags & axl::kCkptSpeedValid) != 0;
+    b->have_check = (c.flags & axl::kCkptHaveCheck) != 0;
+    b->last_residual_valid = (c.flags & axl::kCkptResidualValid) != 0;
+    b->last_check_parity = c.aux;
+    return AXLBM_OK;
+}
+
 axlbm_status axlbm_batch_time(const axlbm_batch* b, int64_t* t) {
     if (!b || !t) return AXLBM_EINVAL;
     *t = b->t;

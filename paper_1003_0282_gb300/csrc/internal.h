@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <string>
 #include <vector>
@@ -143,6 +144,68 @@ cudaError_t staging(H* h, size_t bytes, void** out) {
     }
     *out = h->stage;
     return cudaSuccess;
+}
+
+// Head of a checkpoint (axlbm_save, axlbm_batch_save), in host byte order;
+// the handle's mutable device bytes follow it unchanged.
+struct CkptHeader {
+    char magic[8];          // "AXLBMCK" and a zero byte
+    uint32_t version;       // kCkptVersion
+    uint32_t kind;          // kCkptDomain or kCkptBatch
+    uint64_t fingerprint;   // grids, storage and device layout the bytes belong to
+    uint64_t state_bytes;   // device bytes after the header
+    int64_t t;              // time level
+    int32_t parity;         // AA layout parity of that level
+    uint32_t flags;         // kCkpt* flags below
+    int32_t aux;            // check partials of the last check step (domain) or its parity (batch)
+    int32_t reserved[3];
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+
+constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptDomain = 1, kCkptBatch = 2;
+constexpr uint32_t kCkptSpeedValid = 1, kCkptHaveCheck = 2, kCkptResidualValid = 4;
+
+// FNV-1a (64 bit) over the little-endian bytes of v, chained from h.
+inline uint64_t ckpt_mix(uint64_t h, int64_t v) {
+    for (int i = 0; i < 8; ++i) {
+        h ^= (uint64_t)((v >> (8 * i)) & 0xff);
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+constexpr uint64_t kCkptBasis = 14695981039346656037ull;
+
+inline CkptHeader ckpt_header(uint32_t kind, uint64_t fingerprint, uint64_t state_bytes, int64_t t, int parity,
+                              bool speed_valid, bool have_check, bool residual_valid, int aux) {
+    CkptHeader c = {};
+    memcpy(c.magic, "AXLBMCK", 8);
+    c.version = kCkptVersion;
+    c.kind = kind;
+    c.fingerprint = fingerprint;
+    c.state_bytes = state_bytes;
+    c.t = t;
+    c.parity = parity;
+    c.flags = (speed_valid ? kCkptSpeedValid : 0u) | (have_check ? kCkptHaveCheck : 0u) |
+              (residual_valid ? kCkptResidualValid : 0u);
+    c.aux = aux;
+    return c;
+}
+
+// Reads the header of checkpoint buf (bytes long) into *c; empty string if it
+// is a checkpoint of this kind, fingerprint and size, else why not.
+inline const char* ckpt_check(const void* buf, size_t bytes, uint32_t kind, uint64_t fingerprint,
+                              uint64_t state_bytes, CkptHeader* c) {
+    if (!buf || bytes < sizeof(CkptHeader)) return "not a checkpoint (too short)";
+    memcpy(c, buf, sizeof(CkptHeader));
+    if (memcmp(c->magic, "AXLBMCK", 8) != 0) return "not a checkpoint (bad magic)";
+    if (c->version != kCkptVersion) return "checkpoint of another format version";
+    if (c->kind != kind) return kind == kCkptDomain ? "a batch checkpoint, not a domain's" : "a domain checkpoint, not a batch's";
+    if (c->fingerprint != fingerprint || c->state_bytes != state_bytes)
+        return "checkpoint of another grid, storage or layout";
+    if (bytes != sizeof(CkptHeader) + state_bytes) return "checkpoint size does not match its header";
+    if (c->parity != 0 && c->parity != 1) return "checkpoint with a bad parity";
+    return "";
 }
 
 // Precision-specific launchers (one set per storage type, see ops_impl.cuh).

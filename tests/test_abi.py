@@ -73,6 +73,12 @@ def test_host_only_calls(built):
     g.nr, g.precision = 10, 9
     with pytest.raises(B.AxlbmError):
         B.axlbm_state_bytes(g)
+    # checkpoint calls without a handle are refused before any device work
+    L, n = B.lib(), ctypes.c_size_t(0)
+    for save in (L.axlbm_save, L.axlbm_batch_save):
+        assert save(None, None, 0, ctypes.byref(n)) == B.EINVAL
+    for load in (L.axlbm_load, L.axlbm_batch_load):
+        assert load(None, None, 0) == B.EINVAL
 
 
 def test_create_rejects_invalid_problems_before_any_device_work(built):
