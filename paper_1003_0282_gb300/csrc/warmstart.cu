@@ -627,7 +627,7 @@ axlbm_status axlbm_ws_create(const uint16_t* weights, size_t count, void* cuda_s
         w->boff.push_back(off);
         off += l.cout;
     }
-    const long long c = w->chunk, p1 = c * kH * kW;
+    const size_t c = (size_t)w->chunk, p1 = c * kH * kW;
     struct Buf { void** p; size_t bytes; };
     const Buf bufs[] = {{(void**)&w->w, count * 2},        {(void**)&w->x0, p1 * 8 * 2},
                         {(void**)&w->e1, p1 * 32 * 2},     {(void**)&w->p1, p1 / 4 * 32 * 2},
