@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-7, help="warmstart: per-domain residual (Eq. 57) of a steady state")
     p.add_argument("--max-steps", type=int, default=1500000, help="warmstart: give up after this many steps")
     p.add_argument("--ws-seed", type=int, default=8, help="warmstart: seed of the held-out sweep")
+    p.add_argument("--metrics-log", default=None,
+                   help="warmstart: write one JSON line per 5000 steps to PREFIX.rest.jsonl / PREFIX.warm.jsonl")
     p.add_argument("--shard", choices=["weak", "strong"], default="weak",
                    help="batch under torchrun: a sweep per rank (weak) or one sweep split over the ranks (strong)")
     return p.parse_args()
@@ -222,7 +224,8 @@ def run_warmstart(args):
     weights = np.load(path)["weights"]
     scale = args.scale if args.scale != 1.0 else 0.5
     probs = I.batch_sweep(seed=args.ws_seed, scale=scale)
-    chunk = 5000
+    from paper_1003_0282_gb300 import steady
+
     arms = {}
     for arm in ("rest", "warm"):
         batch = B.Batch(probs, "fp32")
@@ -232,22 +235,13 @@ def run_warmstart(args):
             ws = B.WarmStart(weights)
             ws.start(batch, probs)
             ws.close()
-        reached = np.full(len(probs), -1, dtype=np.int64)
-        blown = np.zeros(len(probs), dtype=bool)
-        when = np.full(len(probs), np.nan)
-        steps = 0
-        while steps < args.max_steps and np.any((reached < 0) & ~blown):
-            batch.step(chunk)
-            steps += chunk
-            res = batch.residuals(allow_nonfinite=True)[:, 0]
-            now = time.perf_counter() - t0
-            newly = (reached < 0) & (res <= args.tol) & np.isfinite(res)
-            reached[newly] = steps
-            when[newly] = now
-            blown |= ~np.isfinite(batch.residuals(allow_nonfinite=True)[:, 1])
+        log = open(f"{args.metrics_log}.{arm}.jsonl", "w") if args.metrics_log else None
+        run = steady.run_to_steady(batch, args.tol, args.max_steps, chunk=5000, log=log, t0=t0)
+        if log:
+            log.close()
         uz = [batch.moments(d, B.UZ, dtype=np.float32)[0] for d in range(len(probs))]
         batch.close()
-        arms[arm] = dict(reached=reached, when=when, uz=uz)
+        arms[arm] = dict(reached=run["reached"], when=run["when"], uz=uz)
     both = (arms["rest"]["reached"] > 0) & (arms["warm"]["reached"] > 0)
     n_ok = int(both.sum())
     out = {}

@@ -1,0 +1,81 @@
+"""Running domains to a steady state, with a JSON-lines progress log.
+
+A domain is steady when the residual of Eq. 57 (the largest change of the
+in-plane speed between two consecutive levels) is at or below a tolerance.
+run_to_steady advances a Batch (or a single Domain) in calls of `chunk`
+lattice steps.  Each call ends with the library's two check steps, which
+give every domain's residual, mass and mass budget.  The run records when
+each domain first reaches the tolerance, marks domains whose check values
+became non-finite, and stops when no domain is left to wait for or after
+max_steps.  With a log, every call appends one JSON line: time level, steps,
+wall seconds, the call's MLUPS, the largest finite residual, counts of
+converged and blown-up domains, and the summed mass and budget.
+
+Host logic only: every lattice step runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import json
+import time
+from typing import IO, Optional
+
+import numpy as np
+
+
+def check_values(solver) -> np.ndarray:
+    """[n][3] residual, mass and budget of the last check step (non-finite allowed)."""
+    if hasattr(solver, "residuals"):
+        return np.asarray(solver.residuals(allow_nonfinite=True), dtype=np.float64).reshape(-1, 3)
+    return np.asarray([solver.residual(allow_nonfinite=True)], dtype=np.float64)
+
+
+def problems_of(solver) -> list:
+    problems = getattr(solver, "problems", None)
+    return list(problems) if problems is not None else [solver.pb]
+
+
+def run_to_steady(solver, tol: float, max_steps: int, chunk: int = 5000, log: Optional[IO[str]] = None,
+                  t0: Optional[float] = None) -> dict:
+    """Step `solver` until every domain is steady (residual <= tol) or blown up, or max_steps ran.
+
+    t0 is the time.perf_counter() value the wall times count from (default:
+    the call).  Returns reached (int64 [n]: steps when the domain first met
+    tol, -1 if never), when (float [n]: seconds since t0, NaN if never),
+    blown (bool [n]: mass became non-finite) and steps (lattice steps run).
+    """
+    if chunk < 2:
+        raise ValueError("chunk must be >= 2 (each call ends with two check steps)")
+    t0 = time.perf_counter() if t0 is None else t0
+    problems = problems_of(solver)
+    n, nodes = len(problems), int(sum(p.cells for p in problems))
+    reached = np.full(n, -1, dtype=np.int64)
+    blown = np.zeros(n, dtype=bool)
+    when = np.full(n, np.nan)
+    steps = 0
+    last = time.perf_counter()
+    while steps < max_steps and np.any((reached < 0) & ~blown):
+        solver.step(chunk)
+        steps += chunk
+        vals = check_values(solver)  # synchronises
+        if vals.shape[0] != n:
+            raise ValueError(f"{vals.shape[0]} check values for {n} domains")
+        now_abs = time.perf_counter()
+        now = now_abs - t0
+        res = vals[:, 0]
+        newly = (reached < 0) & (res <= tol) & np.isfinite(res)
+        reached[newly] = steps
+        when[newly] = now
+        blown |= ~np.isfinite(vals[:, 1])
+        if log is not None:
+            finite = np.isfinite(res)
+            ok = np.isfinite(vals[:, 1])
+            log.write(json.dumps({
+                "t": int(solver.time), "steps": steps, "wall_s": now,
+                "mlups": nodes * chunk / max(now_abs - last, 1e-12) / 1e6,
+                "residual_max": float(res[finite].max()) if finite.any() else None,
+                "converged": int((reached >= 0).sum()), "blown": int(blown.sum()), "domains": n,
+                "mass": float(vals[ok, 1].sum()), "budget": float(vals[ok, 2].sum()),
+            }) + "\n")
+            log.flush()
+        last = now_abs
+    return dict(reached=reached, when=when, blown=blown, steps=steps)
