@@ -65,7 +65,7 @@ typedef enum {
     AXLBM_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
     AXLBM_ENONFINITE = 4,   /* the last check found a NaN or Inf in rho or u */
     AXLBM_ETIMEOUT = 5,     /* a bounded device wait gave up */
-    AXLBM_EUNSUPPORTED = 6  /* valid request this build does not provide */
+    AXLBM_EUNSUPPORTED = 6  /* valid request this library does not provide */
 } axlbm_status;
 
 /* Storage of the distributions.  Collision arithmetic is FP64 for AXLBM_FP64

@@ -55,7 +55,7 @@ print("cases", cases)
 
 
 def run_sanitized(tmp_path, source):
-    """Build `source` (oracle C text) with ASan and UBSan and run the driver on it."""
+    """Build `source` (oracle C text) with ASan and UBSan and run the DRIVER script on it."""
     libasan = subprocess.run(["gcc", "-print-file-name=libasan.so"], capture_output=True, text=True).stdout.strip()
     if not os.path.isabs(libasan) or not os.path.exists(libasan):
         pytest.skip("gcc has no AddressSanitizer runtime here")

@@ -1,9 +1,9 @@
-"""Host logic of the run-to-steady driver and its JSON-lines log (CPU).
+"""Host logic of steady.run_to_steady and its JSON-lines log (CPU).
 
 A scripted stand-in for a batch supplies check values as functions of the
 time level: a domain that meets the tolerance at once, one whose residual
 decays and meets it later, one that never does, and one whose check values
-become non-finite.  The driver must report, for each domain, the first
+become non-finite.  run_to_steady must report, for each domain, the first
 chunk boundary at which the tolerance holds.  It must mark the blown-up
 domain, stop once nothing is left to wait for (or at max_steps), and log one
 consistent JSON line per call.
