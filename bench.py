@@ -23,6 +23,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -147,6 +148,20 @@ def cpu_sample(workload: str):
     return I.rotating_lid_cavity(nr=64, aspect=1.5, re=1000.0), "rotating-lid cavity 64x96 (Re 1000)"
 
 
+def host_cpu() -> dict:
+    """Model name and logical core count of the host the CPU legs run on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu": model or platform.machine(), "host_cores": os.cpu_count()}
+
+
 def cpu_baseline(workload: str, inner: int, budget_s: float = 12.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload,
     advanced until ~budget_s of CPU time, single-threaded."""
@@ -161,7 +176,7 @@ def cpu_baseline(workload: str, inner: int, budget_s: float = 12.0):
         steps += inner
     dt = time.perf_counter() - t0
     return {"value": sample.cells * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle, {what}, {steps} lattice steps, {dt:.1f} s, single thread"}
+            "sample": f"FP64 oracle, {what}, {steps} lattice steps, {dt:.1f} s, single thread", **host_cpu()}
 
 
 def workload_name(args, problems):
@@ -201,7 +216,7 @@ def run_reference(args):
                                              else I.batch_sweep(scale=args.scale)),
                    "precision": "fp64 oracle", "sample": f"{what}, {inner} lattice steps per benchmark step"},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"{what} x {inner} lattice steps per benchmark step"},
+                         "sample": f"{what} x {inner} lattice steps per benchmark step", **host_cpu()},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
