@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 # at capture time.  Reported as null once the source has changed.
 NCU_TRAFFIC = {
     # profiles/k_bulk_batch_fp32_sweep320_launches.md: one even (4 x 128 tiles) and one odd (2 x 128) launch
-    "batch fp32": {"src_sha": "afda887aa152eb93", "dram_per_alg_byte": 0.9896},
+    "batch fp32": {"src_sha": "3b78c4cf84faa9ee", "dram_per_alg_byte": 0.9896},
 }
 
 
