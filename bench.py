@@ -301,6 +301,8 @@ def main():
     import torch
     import torch.distributed as dist
 
+    if not torch.cuda.is_available():
+        sys.exit("bench.py: no CUDA device; the solver runs only in the CUDA library (there is no CPU path)")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
