@@ -260,7 +260,15 @@ AXLBM_API axlbm_status axlbm_time(const axlbm_handle* h, int64_t* time);
  * axlbm_load: replaces the state with the checkpoint buf of `bytes` bytes.
  * AXLBM_EINVAL, with the state unchanged, if buf is not a domain checkpoint
  * of this format or belongs to another grid, storage or layout; on
- * AXLBM_ECUDA the state is undefined.  Synchronises the stream. */
+ * AXLBM_ECUDA the state is undefined.  Synchronises the stream.
+ *
+ * Header (byte offset: field): 0: magic "AXLBMCK" and a zero byte;
+ * 8: uint32 format version (1); 12: uint32 kind (1 domain, 2 batch);
+ * 16: uint64 fingerprint; 24: uint64 device bytes that follow the header;
+ * 32: int64 time level; 40: int32 AA layout parity; 44: uint32 flags (1: the
+ * speed plane holds the previous level, 2: a check step has run, 4: the last
+ * residual compared two consecutive levels); 48: int32 check partials of the
+ * last check step (domain) or its parity (batch); 52-63: zero. */
 AXLBM_API axlbm_status axlbm_save(axlbm_handle* h, void* buf, size_t cap, size_t* bytes);
 AXLBM_API axlbm_status axlbm_load(axlbm_handle* h, const void* buf, size_t bytes);
 

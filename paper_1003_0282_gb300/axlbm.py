@@ -397,6 +397,25 @@ class Domain:
         _load(lib().axlbm_load, self.handle, checkpoint, _check)
 
 
+# Checkpoint header fields (name, byte offset, struct format), as include/axlbm.h lays them out.
+CHECKPOINT_HEADER = (("magic", 0, "8s"), ("version", 8, "I"), ("kind", 12, "I"), ("fingerprint", 16, "Q"),
+                     ("state_bytes", 24, "Q"), ("time", 32, "q"), ("parity", 40, "i"), ("flags", 44, "I"),
+                     ("aux", 48, "i"))
+CHECKPOINT_HEADER_BYTES = 64
+
+
+def checkpoint_info(checkpoint) -> dict:
+    """The header fields of a checkpoint (axlbm_save / axlbm_batch_save), read on the host."""
+    import struct
+
+    raw = bytes(np.frombuffer(checkpoint, dtype=np.uint8)[:CHECKPOINT_HEADER_BYTES])
+    if len(raw) < CHECKPOINT_HEADER_BYTES or raw[:8] != b"AXLBMCK\0":
+        raise ValueError("not a checkpoint")
+    info = {name: struct.unpack_from("<" + fmt, raw, off)[0] for name, off, fmt in CHECKPOINT_HEADER}
+    info["kind"] = {1: "domain", 2: "batch"}.get(info["kind"], info["kind"])
+    return info
+
+
 def _save(fn, handle, check) -> np.ndarray:
     n = ctypes.c_size_t()
     check(fn(handle, None, 0, ctypes.byref(n)), handle)

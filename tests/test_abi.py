@@ -60,6 +60,32 @@ def test_binding_struct_layout_matches_header(tmp_path):
     assert got == want
 
 
+def test_checkpoint_header_layout_matches_binding(tmp_path):
+    """The library's checkpoint header (csrc/internal.h) against the binding's reader and the
+    offsets include/axlbm.h documents."""
+    from paper_1003_0282_gb300 import axlbm as B
+    from paper_1003_0282_gb300 import build
+    try:
+        cuda_include = os.path.join(os.path.dirname(os.path.dirname(build.nvcc())), "include")
+    except RuntimeError:
+        pytest.skip("no CUDA toolkit headers")
+    fields = [name for name, _, _ in B.CHECKPOINT_HEADER]
+    member = {"time": "t"}
+    prog = tmp_path / "ckpt.cpp"
+    prog.write_text(
+        '#include <cstdio>\n#include <cstddef>\n#include "internal.h"\nint main(){\n'
+        '  printf("%zu", sizeof(axl::CkptHeader));\n'
+        + "".join(f'  printf(" %zu", offsetof(axl::CkptHeader, {member.get(f, f)}));\n' for f in fields)
+        + '  printf(" %u %u %u\\n", axl::kCkptVersion, axl::kCkptDomain, axl::kCkptBatch);\n  return 0;\n}\n')
+    exe = tmp_path / "ckpt"
+    subprocess.run(["g++", "-std=c++17", "-I", os.path.join(ROOT, "paper_1003_0282_gb300", "csrc"), "-I",
+                    cuda_include, str(prog), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert got[0] == B.CHECKPOINT_HEADER_BYTES == 64
+    assert got[1:1 + len(fields)] == [off for _, off, _ in B.CHECKPOINT_HEADER]
+    assert got[1 + len(fields):] == [1, 1, 2]
+
+
 def test_host_only_calls(built):
     from paper_1003_0282_gb300 import axlbm as B
     assert B.axlbm_abi_version() == 3

@@ -59,6 +59,9 @@ def test_domain_resumes_bit_for_bit(B, name, first, precision):
     start(a, pb, seed=3)
     a.step(first)
     ck = a.save()
+    info = B.checkpoint_info(ck)
+    assert (info["kind"], info["time"], info["parity"]) == ("domain", first, first % 2)
+    assert info["state_bytes"] == ck.size - 64 == B.axlbm_state_bytes(a.grid)
     a.step(25)
     b = B.Domain(pb, precision)
     start(b, pb, seed=4)
@@ -131,6 +134,8 @@ def test_batch_resumes_bit_for_bit(B, precision):
         a.set_populations(d, st.f, st.g, st.h if pb.temperature else None)
     a.step(21)
     ck = a.save()
+    info = B.checkpoint_info(ck)
+    assert (info["kind"], info["time"], info["parity"]) == ("batch", 21, 1)
     a.step(30)
     b = B.Batch(doms, precision)
     b.step(22)  # another state, step graphs captured
