@@ -685,6 +685,7 @@ axlbm_status axlbm_load(axlbm_handle* h, const void* buf, size_t bytes) {
     axl::CkptHeader c;
     const char* why = axl::ckpt_check(buf, bytes, axl::kCkptDomain, domain_fingerprint(h), h->L.total, &c);
     if (*why) return fail(h, AXLBM_EINVAL, why);
+    if (c.aux < 0 || c.aux > h->L.nparts) return fail(h, AXLBM_EINVAL, "checkpoint with a bad partial count");
     cudaError_t e = cudaStreamSynchronize(h->stream);  // work queued on the old state
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->mem, static_cast<const char*>(buf) + sizeof c, h->L.total, cudaMemcpyHostToDevice,
