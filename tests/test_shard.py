@@ -91,3 +91,39 @@ def test_gather_rejects_overlap_and_gaps():
     with pytest.raises(ValueError):
         S.gather_per_domain(rows, [0, 1], 3)
     assert np.array_equal(S.gather_per_domain(rows, [1, 0], 2), rows)
+
+
+def _leaving_worker(rank, world, port, q):
+    import datetime
+    import time
+
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)  # leaves between steps, with nothing in flight and without a word
+    t0 = time.time()
+    try:
+        S.max_over_ranks(1.0)
+        q.put(("no error", time.time() - t0))
+    except Exception as e:  # the collective must end with an error, not wait forever
+        q.put((type(e).__name__, time.time() - t0))
+    os._exit(0)
+
+
+def test_a_rank_that_leaves_ends_the_next_collective_with_an_error():
+    """Failure detection on the host: a rank that exits between steps makes
+    the survivors' next reduction raise within the process group's timeout."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_leaving_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    what, waited = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert what != "no error", what
+    assert waited < 60.0
+    assert procs[1].exitcode == 3 and procs[0].exitcode == 0
