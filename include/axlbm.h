@@ -16,7 +16,15 @@
  *     periodic ends;
  *   - the paper's node-on-axis grid (Sec. IV A) as an alternative inner face:
  *     node 0 on the axis, every term in 1/r zero there, specular reflection
- *     by a mirror column at r = -1.
+ *     by a mirror column at r = -1;
+ *   - the MRT collision with the axisymmetric momentum correction
+ *     (Sec. III B, Eqs. 37-51) in place of BGK;
+ *   - wet walls by non-equilibrium extrapolation (Sec. IV B) and a Zou-He
+ *     pipe wall (Sec. IV A).
+ * Around the update: batches of uneven domains advanced by one persistent
+ * launch per lattice step, bit-exact checkpoints of a domain or a batch, and
+ * a learned warm start (a convolutional network that predicts initial fields,
+ * with its training step).
  *
  * Conventions used by every call:
  *   - Lattice units: dx = dt = 1, c_s^2 = 1/3 (Eq. 6).
