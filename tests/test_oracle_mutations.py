@@ -89,6 +89,17 @@ MUTATIONS = {
         ("const double mz = -0.5 * force_at(p, t);", "const double mz = 0.0 * force_at(p, t);"),
     "sign of the buoyancy force":
         ("fz += p->rho0 * p->gbeta * (temp - p->t_ref);", "fz -= p->rho0 * p->gbeta * (temp - p->t_ref);"),
+    "lid speed taken at the outer wall instead of at the crossing column":
+        ("default: return p->omega_w[face] * node_r(p, j);", "default: return p->omega_w[face] * (p->r0 + p->nr);"),
+    "g equilibrium with half its advection term (Eq. 54)":
+        ("const double geq = p->rho0 * uth / 4.0 * (1.0 + 2.0 * eu);",
+         "const double geq = p->rho0 * uth / 4.0 * (1.0 + 1.0 * eu);"),
+    "temperature equilibrium with half its advection term":
+        ("const double heq = temp / 4.0 * (1.0 + 2.0 * eu);", "const double heq = temp / 4.0 * (1.0 + 1.0 * eu);"),
+    "periodic wrap off by one row":
+        ("s.k = ((s.k % p->nz) + p->nz) % p->nz;", "s.k = ((s.k % p->nz) + p->nz - 1) % p->nz;"),
+    "Dirichlet temperature wall bounced back with the wrong sign":
+        ("p->t_dirichlet[s.face] ? -v + 0.5 * p->t_w[s.face] : v;", "p->t_dirichlet[s.face] ? v + 0.5 * p->t_w[s.face] : v;"),
 }
 
 
