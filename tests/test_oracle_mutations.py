@@ -98,6 +98,11 @@ MUTATIONS = {
         ("const double heq = temp / 4.0 * (1.0 + 2.0 * eu);", "const double heq = temp / 4.0 * (1.0 + 1.0 * eu);"),
     "periodic wrap off by one row":
         ("s.k = ((s.k % p->nz) + p->nz) % p->nz;", "s.k = ((s.k % p->nz) + p->nz - 1) % p->nz;"),
+    "force taken one step late (after the collision's time)":
+        ("return p->az0 * cos(p->omega_t * (double)t);", "return p->az0 * cos(p->omega_t * (double)(t + 1));"),
+    "free surface without the flip of e_z":
+        ("s.k = s.k < 0 ? -1 - s.k : 2 * p->nz - 1 - s.k;\n            s.fz = 1;",
+         "s.k = s.k < 0 ? -1 - s.k : 2 * p->nz - 1 - s.k;\n            s.fz = 0;"),
     "Dirichlet temperature wall bounced back with the wrong sign":
         ("p->t_dirichlet[s.face] ? -v + 0.5 * p->t_w[s.face] : v;", "p->t_dirichlet[s.face] ? v + 0.5 * p->t_w[s.face] : v;"),
 }

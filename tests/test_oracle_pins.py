@@ -180,6 +180,22 @@ def test_momentum_gain_far_from_axis_is_the_force(orc):
         assert (E9[:, 0] @ fo) - (E9[:, 0] @ f) == pytest.approx(0.0, abs=1e-14)
 
 
+def test_force_is_taken_at_the_pre_collision_time(orc):
+    """The axial force of step n is a(n) = az0 cos(omega_t n), at the
+    pre-collision time.  One step from rest at time t0 adds exactly a(t0) to
+    sum e_z f of a node whose neighbours are fluid at rest too (far from the
+    axis, where the 1/r terms vanish), and not a(t0 + 1)."""
+    az0, om, t0 = 2e-5, 0.3, 5
+    pb = I.Problem(nr=5, nz=4, tau=0.8, inner="wall", r0=1e12, z_lo="periodic", z_hi="periodic",
+                   az0=az0, omega_t=om)
+    st = orc.rest_state(pb)
+    st.t = t0
+    orc.step(st, 1)
+    gain = E9[:, 1] @ st.f[:, :, 2]  # middle column, every row
+    assert np.allclose(gain, az0 * np.cos(om * t0), rtol=1e-9, atol=0)
+    assert not np.allclose(gain, az0 * np.cos(om * (t0 + 1)), rtol=1e-3, atol=0)
+
+
 # ----------------------------------------------------------------------------- streaming
 
 BOUNDARY_MIXES = [
