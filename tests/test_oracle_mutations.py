@@ -98,6 +98,10 @@ MUTATIONS = {
         ("const double heq = temp / 4.0 * (1.0 + 2.0 * eu);", "const double heq = temp / 4.0 * (1.0 + 1.0 * eu);"),
     "periodic wrap off by one row":
         ("s.k = ((s.k % p->nz) + p->nz) % p->nz;", "s.k = ((s.k % p->nz) + p->nz - 1) % p->nz;"),
+    "MRT: q_x relaxed at the epsilon rate":
+        ("    L[4] = sq;\n", "    L[4] = seps;\n"),
+    "MRT: p_xy relaxed at the epsilon rate":
+        ("    L[8] = sv;\n", "    L[8] = seps;\n"),
     "force taken one step late (after the collision's time)":
         ("return p->az0 * cos(p->omega_t * (double)t);", "return p->az0 * cos(p->omega_t * (double)(t + 1));"),
     "free surface without the flip of e_z":
