@@ -64,7 +64,7 @@
 extern "C" {
 #endif
 
-#define AXLBM_ABI_VERSION 3
+#define AXLBM_ABI_VERSION 4
 
 typedef enum {
     AXLBM_OK = 0,
@@ -315,6 +315,13 @@ AXLBM_API axlbm_status axlbm_kernel_times(axlbm_handle* h, int64_t* bulk_launche
  * rho u_r / r (budget), out[3] = number of nodes with a non-finite rho or u
  * -- for one time level given by the caller, where s = sqrt(u_r^2 + u_z^2)
  * from Eqs. 16-17 at force a_z.
+ *   bc: the domain's boundary, or NULL for the half-spacing grid.  Only
+ *     bc->inner is read: it fixes the radius of column j, r0 + j + 1/2
+ *     (AXLBM_INNER_AXIS, AXLBM_INNER_WALL) or j with every 1/r term zero at
+ *     r = 0 (AXLBM_INNER_AXIS_NODE, Sec. IV A), as in axlbm_step's check.
+ *     Wet-wall nodes (AXLBM_*_NEE) count with the moments of their stored
+ *     state, as in that check step.  An unknown inner kind, or an axis with
+ *     r0 != 0, returns AXLBM_EINVAL.
  *   f, g, t_pop: device, FP64 populations [9|4|4][nz][nr] (g / t_pop exactly
  *     when the grid enables them); the grid's precision field is ignored.
  *   speed_prev: device [nz][nr] speeds of the previous level, or NULL.
@@ -327,9 +334,9 @@ AXLBM_API axlbm_status axlbm_kernel_times(axlbm_handle* h, int64_t* bulk_launche
  * array: calls that overlap on the GPU race.  Errors are read with
  * axlbm_last_error(NULL). */
 AXLBM_API axlbm_status axlbm_check_static(const axlbm_grid* grid, double tau, const axlbm_forcing* forcing,
-                                          const double* f, const double* g, const double* t_pop, double a_z,
-                                          const double* speed_prev, double* speed_out, double* out,
-                                          void* cuda_stream);
+                                          const axlbm_boundary* bc, const double* f, const double* g,
+                                          const double* t_pop, double a_z, const double* speed_prev,
+                                          double* speed_out, double* out, void* cuda_stream);
 
 /* Self-test of the error path of the bounded device waits (every wait of the
  * bulk kernels on a TMA copy gives up after a cycle budget, and the call then

@@ -103,7 +103,8 @@ def lib() -> ctypes.CDLL:
         L.axlbm_graph_stats.argtypes = [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_kernel_times.argtypes = [H, ctypes.POINTER(ctypes.c_int64), dp, dp, ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_check_static.argtypes = [ctypes.POINTER(axlbm_grid), ctypes.c_double,
-                                         ctypes.POINTER(axlbm_forcing), ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.POINTER(axlbm_forcing), ctypes.POINTER(axlbm_boundary),
+                                         ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p]
         L.axlbm_last_error.restype = ctypes.c_char_p
@@ -262,12 +263,14 @@ def axlbm_kernel_times(h):
     return int(nb.value), ms.value, by.value, int(na.value)
 
 
-def axlbm_check_static(grid: axlbm_grid, tau: float, forcing: axlbm_forcing, f_ptr: int, g_ptr: int,
+def axlbm_check_static(grid: axlbm_grid, tau: float, forcing: axlbm_forcing, bc, f_ptr: int, g_ptr: int,
                        t_ptr: int, a_z: float, speed_prev_ptr: int, speed_out_ptr: int, out_ptr: int,
                        stream: int = 0) -> None:
-    """Check-step statistics over caller device buffers, without allocating."""
+    """Check-step statistics over caller device buffers, without allocating
+    (bc: an axlbm_boundary, or None for the half-spacing grid)."""
     vp = lambda p: ctypes.c_void_p(p or None)
-    _check(lib().axlbm_check_static(ctypes.byref(grid), float(tau), ctypes.byref(forcing), vp(f_ptr), vp(g_ptr),
+    bcp = ctypes.byref(bc) if bc is not None else None
+    _check(lib().axlbm_check_static(ctypes.byref(grid), float(tau), ctypes.byref(forcing), bcp, vp(f_ptr), vp(g_ptr),
                                     vp(t_ptr), float(a_z), vp(speed_prev_ptr), vp(speed_out_ptr), vp(out_ptr),
                                     vp(stream)))
 

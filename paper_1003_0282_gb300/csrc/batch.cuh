@@ -139,8 +139,8 @@ __device__ __forceinline__ void warp_slot_store(RedR<R> v, int q, const SlotDesc
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const R rm = __shfl_up_sync(full, v.rmax, off);
-        const R dm = __shfl_up_sync(full, v.dmass, off);
-        const R bu = __shfl_up_sync(full, v.budget, off);
+        const double dm = __shfl_up_sync(full, v.dmass, off);
+        const double bu = __shfl_up_sync(full, v.budget, off);
         const int bd = __shfl_up_sync(full, v.bad, off);
         const int ct = __shfl_up_sync(full, v.count, off);
         const int qo = __shfl_up_sync(full, q, off);
@@ -309,8 +309,8 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
             const R sp = sqrt(vur * vur + vuz * vuz);
             if (A.residual) red.rmax = max(red.rmax, (R)fabs(sp - sp_old[l]));
             A.speed[x] = sp;
-            red.dmass += Lanes<RC>::get(c.ds0, l);
-            red.budget += vrho * vur * inv_r;
+            red.dmass += (double)Lanes<RC>::get(c.ds0, l);
+            red.budget += (double)vrho * (double)vur * (double)inv_r;
             red.bad += (isfinite(vrho) && isfinite(vur) && isfinite(vuz)) ? 0 : 1;
             red.count += 1;
         }
@@ -448,7 +448,7 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
                 const double rj = D.r0 + (double)jl + (D.axis_node ? 0.0 : 0.5);
                 const R inv_r = rj > 0.0 ? rcp(R(rj)) : R(0);
                 const S* st = sm + s * STAGE;
-                RedR<R> red{R(0), R(0), R(0), 0, 0};
+                RedR<R> red{R(0), 0.0, 0.0, 0, 0};
                 const bool dth = TH && M.r.th;
                 // one node pair per thread: rows rr0 and rr0 + TK/2 of column jj
                 if (dth)

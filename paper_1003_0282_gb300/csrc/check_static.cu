@@ -54,11 +54,15 @@ cudaError_t scratch_address(double** out) {
 }
 
 // One node per thread: moments of the pre-collision state (Eqs. 16-17), its
-// speed sqrt(u_r^2 + u_z^2), and the block's partial reductions.
+// speed sqrt(u_r^2 + u_z^2), and the block's partial reductions.  The radius
+// of column j is r0 + j + 1/2 on the half-spacing grid and j with a node on
+// the axis (Sec. IV A), where every term in 1/r is zero at r = 0 -- the
+// radius the library's own check step uses.  Wet-wall nodes count like every
+// node, with the moments of their stored state, as in that check step.
 template <bool SW, bool TH>
 __global__ void __launch_bounds__(kThreads)
-k_check_static(const double* f, const double* g, const double* h, int nr, int nz, double r0, Coef<double> C,
-               double az, const double* speed_prev, double* speed_out, double* partials) {
+k_check_static(const double* f, const double* g, const double* h, int nr, int nz, double r0, int axis_node,
+               Coef<double> C, double az, const double* speed_prev, double* speed_out, double* partials) {
     const long long n = (long long)nr * nz;
     const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
     Red red{0.0, 0.0, 0.0, 0.0};
@@ -72,7 +76,8 @@ k_check_static(const double* f, const double* g, const double* h, int nr, int nz
             c.g[q] = SW ? g[q * n + i] : 0.0;
             c.h[q] = TH ? h[q * n + i] - 0.25 * C.t_ref : 0.0;
         }
-        const double inv_r = 1.0 / (r0 + (double)j + 0.5);
+        const double rj = r0 + (double)j + (axis_node ? 0.0 : 0.5);
+        const double inv_r = rj > 0.0 ? 1.0 / rj : 0.0;
         c.collide(inv_r, C, az);
         const double sp = sqrt(c.ur * c.ur + c.uz * c.uz);
         if (speed_prev) red.rmax = fabs(sp - speed_prev[i]);
@@ -93,7 +98,8 @@ axlbm_status reject(axlbm_status st, const char* msg) {
 }  // namespace axl
 
 extern "C" AXLBM_API axlbm_status axlbm_check_static(const axlbm_grid* grid, double tau,
-                                                     const axlbm_forcing* forcing, const double* f,
+                                                     const axlbm_forcing* forcing, const axlbm_boundary* bc,
+                                                     const double* f,
                                                      const double* g, const double* t_pop, double a_z,
                                                      const double* speed_prev, double* speed_out, double* out,
                                                      void* cuda_stream) {
@@ -109,6 +115,12 @@ extern "C" AXLBM_API axlbm_status axlbm_check_static(const axlbm_grid* grid, dou
     if (!(tau > 0.5) || !(forcing->rho0 > 0.0) || (grid->with_temperature && !(forcing->tau_t > 0.5)))
         return reject(AXLBM_EINVAL, "tau, tau_t must be > 1/2 and rho0 > 0");
     if (!(grid->r0 >= 0.0)) return reject(AXLBM_EINVAL, "r0 must be >= 0");
+    const int inner = bc ? bc->inner : AXLBM_INNER_AXIS;
+    if (inner != AXLBM_INNER_AXIS && inner != AXLBM_INNER_AXIS_NODE && inner != AXLBM_INNER_WALL)
+        return reject(AXLBM_EINVAL, "bc->inner is not an AXLBM_INNER_* kind");
+    if (inner != AXLBM_INNER_WALL && grid->r0 != 0.0)
+        return reject(AXLBM_EINVAL, "an inner face on the axis needs r0 == 0");
+    const int axis_node = inner == AXLBM_INNER_AXIS_NODE;
 
     double* scratch = nullptr;
     cudaError_t e = scratch_address(&scratch);
@@ -136,18 +148,20 @@ extern "C" AXLBM_API axlbm_status axlbm_check_static(const axlbm_grid* grid, dou
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     const int blocks = int((n + kThreads - 1) / kThreads);
     const bool sw = grid->with_swirl, th = grid->with_temperature;
+    const int nr = grid->nr, nz = grid->nz;
+    const double r0 = grid->r0;
     if (sw && th)
-        k_check_static<true, true><<<blocks, kThreads, 0, stream>>>(f, g, t_pop, grid->nr, grid->nz, grid->r0, C, a_z,
+        k_check_static<true, true><<<blocks, kThreads, 0, stream>>>(f, g, t_pop, nr, nz, r0, axis_node, C, a_z,
                                                                     speed_prev, speed_out, scratch);
     else if (sw)
-        k_check_static<true, false><<<blocks, kThreads, 0, stream>>>(f, g, t_pop, grid->nr, grid->nz, grid->r0, C, a_z,
+        k_check_static<true, false><<<blocks, kThreads, 0, stream>>>(f, g, t_pop, nr, nz, r0, axis_node, C, a_z,
                                                                      speed_prev, speed_out, scratch);
     else if (th)
-        k_check_static<false, true><<<blocks, kThreads, 0, stream>>>(f, g, t_pop, grid->nr, grid->nz, grid->r0, C, a_z,
+        k_check_static<false, true><<<blocks, kThreads, 0, stream>>>(f, g, t_pop, nr, nz, r0, axis_node, C, a_z,
                                                                      speed_prev, speed_out, scratch);
     else
-        k_check_static<false, false><<<blocks, kThreads, 0, stream>>>(f, g, t_pop, grid->nr, grid->nz, grid->r0, C,
-                                                                      a_z, speed_prev, speed_out, scratch);
+        k_check_static<false, false><<<blocks, kThreads, 0, stream>>>(f, g, t_pop, nr, nz, r0, axis_node, C, a_z,
+                                                                      speed_prev, speed_out, scratch);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_finalize(scratch, blocks, out, stream);
     if (e != cudaSuccess) return reject(AXLBM_ECUDA, "axlbm_check_static: kernel launch failed");

@@ -580,12 +580,13 @@ struct Lanes<F2> {
     __device__ static __forceinline__ float get(F2 v, int l) { return l ? v.v.y : v.v.x; }
 };
 
-// Per-thread check accumulators in the arithmetic type (FP32 in FP32 mode:
-// the mass is kept as the deviation sum, so FP32 partial sums lose nothing
-// that matters), folded to FP64 per warp and per block.
+// Per-thread check accumulators: the residual maximum in the arithmetic type
+// (a maximum rounds nothing), the mass deviation and the budget in FP64 from
+// the first addition on, then folded per warp and per block in FP64.
 template <class R>
 struct RedR {
-    R rmax, dmass, budget;
+    R rmax;
+    double dmass, budget;
     int bad, count;
 };
 
@@ -694,7 +695,7 @@ k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
     }
     __syncthreads();
 
-    RedR<R> red{R(0), R(0), R(0), 0, 0};
+    RedR<R> red{R(0), 0.0, 0.0, 0, 0};
     if (warp == kConsumerWarps) {
         // ---------------- producer
         if (lane == 0) {
@@ -837,8 +838,8 @@ k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
                         const R sp = sqrt(vur * vur + vuz * vuz);
                         if (A.residual) red.rmax = max(red.rmax, (R)fabs(sp - sp_old[(rr - tid / kTileJ) / 2 + l]));
                         A.speed[x] = sp;
-                        red.dmass += Lanes<RC>::get(c.ds0, l);
-                        red.budget += vrho * vur * inv_r;
+                        red.dmass += (double)Lanes<RC>::get(c.ds0, l);
+                        red.budget += (double)vrho * (double)vur * (double)inv_r;
                         red.bad += (isfinite(vrho) && isfinite(vur) && isfinite(vuz)) ? 0 : 1;
                         red.count += 1;
                     }

@@ -142,7 +142,7 @@ def test_full_sweep_sampled_domains(B, precision):
     doms = I.batch_sweep()
     batch = B.Batch(doms, precision)
     picks = [0, 7, 255, 256, 300, 319]
-    small = sorted(picks, key=lambda d: doms[d].cells)[:4]
+    small = sorted(set(sorted(picks, key=lambda d: doms[d].cells)[:4]) | {300})  # 300: a Wheeler cell (h)
     states = {}
     for d in small:
         st = seeded_state(doms[d], 500 + d)
@@ -155,8 +155,11 @@ def test_full_sweep_sampled_domains(B, precision):
     tol = POP_TOL.get(precision, 5e-3)
     for d in small:
         oracle.step(states[d], 6)
-        f, g, _ = batch.get_populations(d)
+        f, g, h = batch.get_populations(d)
         assert rel_err(f, states[d].f) <= tol and rel_err(g, states[d].g) <= max(tol, 1e-4 if precision == "fp16" else tol), d
+        if doms[d].temperature:
+            assert rel_err(h, states[d].h) <= tol, d
+    assert any(doms[d].temperature for d in small)
     # mass budget M(6) = M(5) - B(5) in every domain (storage rounding only)
     mtol = 1e-9 if precision == "fp32" else 1e-5
     assert np.all(np.abs(r6[:, 1] - (r5[:, 1] - r5[:, 2])) <= mtol * np.abs(r5[:, 1]))

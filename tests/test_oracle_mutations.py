@@ -107,6 +107,10 @@ MUTATIONS = {
     "free surface without the flip of e_z":
         ("s.k = s.k < 0 ? -1 - s.k : 2 * p->nz - 1 - s.k;\n            s.fz = 1;",
          "s.k = s.k < 0 ? -1 - s.k : 2 * p->nz - 1 - s.k;\n            s.fz = 0;"),
+    "Eq. 57 speed including the azimuthal velocity":
+        ("speed[x] = sqrt(m[1] * m[1] + m[2] * m[2]);", "speed[x] = sqrt(m[1] * m[1] + m[2] * m[2] + m[3] * m[3]);"),
+    "Eq. 57 speed from the axial velocity alone":
+        ("speed[x] = sqrt(m[1] * m[1] + m[2] * m[2]);", "speed[x] = fabs(m[2]);"),
     "Dirichlet temperature wall bounced back with the wrong sign":
         ("p->t_dirichlet[s.face] ? -v + 0.5 * p->t_w[s.face] : v;", "p->t_dirichlet[s.face] ? v + 0.5 * p->t_w[s.face] : v;"),
 }

@@ -469,3 +469,24 @@ def test_equilibrium_reproduces_its_fields(orc):
     got = orc.moments(st)
     for q in range(5):
         assert np.max(np.abs(got[q] - fields[q])) <= 1e-12 * max(1.0, np.max(np.abs(fields[q]))), q
+
+
+def test_residual_speed_is_the_meridional_speed(orc):
+    """Eq. 57 measures |u_p| = sqrt(u_z^2 + u_r^2): the azimuthal velocity is
+    not part of it.  Far from the axis (where the 1/r terms of Eqs. 15-16 are
+    negligible) an equilibrium built from fields (u_r, u_z, u_theta) must give
+    the speed hypot(u_r, u_z) -- and 0 when only u_theta is non-zero, where a
+    speed that included u_theta would be |u_theta|."""
+    pb = I.Problem(nr=6, nz=5, tau=0.8, r0=1e6, inner="wall", swirl=True)
+    fields = np.zeros((5, 5, 6))
+    fields[0] = 1.0
+    fields[4] = pb.t_ref
+    rng = np.random.default_rng(57)
+    fields[1] = rng.uniform(-0.03, 0.03, (5, 6))
+    fields[2] = rng.uniform(-0.03, 0.03, (5, 6))
+    fields[3] = rng.uniform(0.02, 0.05, (5, 6))
+    _, _, speed = orc.stats(orc.equilibrium(pb, fields))
+    assert np.max(np.abs(speed - np.hypot(fields[1], fields[2]))) <= 1e-8
+    fields[1] = fields[2] = 0.0
+    _, _, speed = orc.stats(orc.equilibrium(pb, fields))
+    assert np.max(speed) <= 1e-8
