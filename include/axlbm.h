@@ -100,10 +100,14 @@ enum {
     AXLBM_Z_FREE = 2,     /* free surface: mirror in z (zero normal gradient) */
     AXLBM_Z_MIXED = 3,    /* "hi" only: wall where the link crosses at r < r_split
                              (crystal disk), free surface beyond */
-    AXLBM_Z_NEE = 4       /* wet wall: node row 0 (lo) or nz - 1 (hi) lies on the wall and is
+    AXLBM_Z_NEE = 4,      /* wet wall: node row 0 (lo) or nz - 1 (hi) lies on the wall and is
                              rebuilt after every step by non-equilibrium extrapolation from the
                              next rows inwards (see AXLBM_OUTER_NEE); needs nz >= 3, nz >= 4
                              when both axial faces are wet */
+    AXLBM_Z_HALO = 5      /* a cut through one larger domain (z-slab decomposition): the
+                             populations that cross the face go to and come from the
+                             neighbouring slab through axlbm_halo_send / axlbm_halo_recv
+                             after every step (single domains only; see there) */
 };
 /* Outer face (axlbm_boundary.outer).  AXLBM_OUTER_BB: half-way bounce-back
  * wall at r_{nr-1} + 1/2.  AXLBM_OUTER_NEE: wet wall on column nr - 1 (the
@@ -223,6 +227,21 @@ AXLBM_API axlbm_status axlbm_moments(axlbm_handle* h, uint32_t field_mask, void*
  * before the first step. */
 AXLBM_API axlbm_status axlbm_residual(axlbm_handle* h, double* residual, double* mass, double* budget);
 
+/* Which residual the check steps record (Eq. 57, Sec. IV B).  lag 1 (the
+ * default) is Eq. 57 as printed: max |s^(t+1) - s^t| between consecutive
+ * levels, s = sqrt(u_r^2 + u_z^2).  lag 2 records max |s^(t+1) - s^(t-1)| / 2,
+ * the same per-step change measured across two levels: an axlbm_step call
+ * then ends with a check step, a plain step and a check step, and a residual
+ * needs n >= 3 (else +Inf).  For a flow that approaches its steady state
+ * without a period-2 part both agree to first order.  The lattice carries
+ * quantities that alternate in sign from one level to the next --
+ * sum (-1)^(k+t) rho u_z, sum (-1)^(j+t) rho u_r and sum (-1)^(j+k+t) sum g --
+ * that streaming leaves unchanged and the collision conserves up to its
+ * sources and the walls; FP32 rounding keeps them excited, and in FP32
+ * storage they hold the lag-1 residual near 1e-6 while the lag-2 residual
+ * keeps falling.  AXLBM_EINVAL for another lag. */
+AXLBM_API axlbm_status axlbm_set_residual_lag(axlbm_handle* h, int32_t lag);
+
 /* Reset the state to the equilibria of given macroscopic fields
  * [5][nz][nr] (rho, u_r, u_z, u_theta, T) of element type in_dtype, on the
  * device (on_device = 1, read asynchronously) or the host (copied before the
@@ -245,6 +264,38 @@ AXLBM_API axlbm_status axlbm_set_populations(axlbm_handle* h, const double* f, c
 
 /* Current time level. */
 AXLBM_API axlbm_status axlbm_time(const axlbm_handle* h, int64_t* time);
+
+/* z-slab decomposition of one domain (the periodic pipes of Sec. IV A, one
+ * slab per GPU).  A domain is cut across z into slabs, each its own handle
+ * whose cut faces are AXLBM_Z_HALO; the slabs run the same time levels, and
+ * after every step (axlbm_step with n = 1) each cut face hands the
+ * populations that cross it to the neighbouring slab:
+ *     A.send(lo) -> B.recv(hi)  and  B.send(hi) -> A.recv(lo)
+ * for slab A above slab B (for a periodic domain the top slab's hi face
+ * pairs with the bottom slab's lo face).  Under the in-place (AA) layout
+ * the exchange alternates: after an in-place step the message is the
+ * boundary row's stored values that the next (neighbour-to-neighbour) step
+ * pulls across the cut, and after that step it is what the step pushed
+ * across the cut, which the receiver stores into its boundary row.  A face
+ * message is the 3 D2Q9 populations crossing the cut (+1 of g, +1 of h when
+ * enabled) x nr nodes, in the storage type, bit for bit, so the slabs
+ * together advance exactly the undivided domain.
+ * axlbm_halo_bytes: bytes of one face message.
+ * axlbm_halo_send(h, face, out, on_device): face AXLBM_FACE_LO or _HI (an
+ *   AXLBM_Z_HALO face); `out` receives the message, caller-owned, on the
+ *   device (queued on the handle's stream) or on the host (synchronises).
+ * axlbm_halo_recv(h, face, in, on_device): stores the neighbour's message.
+ * Both return AXLBM_EINVAL for a face that is not a cut, and before the
+ * first step or after a reset (nothing to exchange).  axlbm_step returns
+ * AXLBM_EINVAL when n > 1, or when a cut face has not received its message
+ * since the last step.  Cut faces need the half-spacing axis or an inner
+ * wall, the bounce-back outer wall and no wet axial wall (the post-step
+ * passes of those faces read the nodes next to the cut before the exchange),
+ * and nz >= 2.  Moments and populations of a slab at a level after an
+ * in-place step read the received message. */
+AXLBM_API axlbm_status axlbm_halo_bytes(const axlbm_handle* h, size_t* bytes);
+AXLBM_API axlbm_status axlbm_halo_send(axlbm_handle* h, int32_t face, void* out, int32_t out_on_device);
+AXLBM_API axlbm_status axlbm_halo_recv(axlbm_handle* h, int32_t face, const void* in, int32_t in_on_device);
 
 /* Checkpoint and resume.  A checkpoint is the handle's whole mutable device
  * state -- the stored populations as they sit in device memory (storage type
@@ -390,6 +441,9 @@ AXLBM_API axlbm_status axlbm_batch_step(axlbm_batch* b, int64_t n);
  * AXLBM_ENONFINITE (values still written) if any domain saw a NaN or Inf. */
 AXLBM_API axlbm_status axlbm_batch_residuals(axlbm_batch* b, double* out);
 
+/* The residual the batch's check steps record, as axlbm_set_residual_lag. */
+AXLBM_API axlbm_status axlbm_batch_set_residual_lag(axlbm_batch* b, int32_t lag);
+
 /* Macroscopic fields of domain d, as axlbm_moments. */
 AXLBM_API axlbm_status axlbm_batch_moments(axlbm_batch* b, int32_t d, uint32_t field_mask, void* out,
                                            int32_t out_dtype, int32_t out_on_device);
@@ -496,8 +550,9 @@ AXLBM_API axlbm_status axlbm_destroy(axlbm_handle* h);
 AXLBM_API const char* axlbm_last_error(const axlbm_handle* h);
 
 /* ------------------------------------------------------------------ warm start
- * Learned warm start of a batch (not in the paper).  A small U-Net (weights
- * in BF16, FP32 accumulation; architecture fixed, see csrc/warmstart.cu) maps
+ * Learned warm start of a batch (not in the paper).  A four-level U-Net
+ * (weights in BF16, FP32 accumulation on the tensor cores; channels 32, 64,
+ * 96, 128; architecture fixed, listed in csrc/warmstart.cu) maps
  * each domain's feature vector, broadcast on a 256 (z) x 128 (r) canvas with
  * the normalised coordinates, to u_r, u_z, u_theta (in units of the lid
  * speed) and T - T_ref.  The predicted fields are resampled onto each domain
@@ -507,7 +562,7 @@ AXLBM_API const char* axlbm_last_error(const axlbm_handle* h);
  * Features (AXLBM_WS_FEATURES floats per domain): kind (0 rotating-lid
  * cavity, 1 Wheeler-type cell), H/R / 3.5, log10(Re) - 3 (Re = Omega_lid
  * R^2 / nu), log10(1 + Gr) / 6, log10(Pr) / 2 (0 without temperature),
- * Omega_side / Omega_lid.  Weights: for each of the 11 layers in order, the
+ * Omega_side / Omega_lid.  Weights: for each of the 15 layers in order, the
  * kernel [Cout][ky][kx][Cin] then the bias [Cout], BF16 bit patterns;
  * axlbm_ws_weight_count() values in all. */
 #define AXLBM_WS_FEATURES 6

@@ -4,8 +4,9 @@ infrastructure: only tests/ use it; the product path runs the CUDA kernels).
 Plain numpy in float64 with the BF16 weights widened exactly: every 3x3
 convolution is written as nine shifted matrix products over the zero-padded
 input, the pooling and upsampling as array reshapes, so that each layer can
-be read against the architecture the library documents (a U-Net 8 -> 32 -> 32
-| pool | 32 -> 64 -> 64 | pool | 64 -> 128 -> 128 | up, concat | 192 -> 64 ->
+be read against the architecture the library documents (a four-level U-Net
+8 -> 32 -> 32 | pool | 32 -> 64 -> 64 | pool | 64 -> 96 -> 96 | pool |
+96 -> 128 -> 128 | up, concat | 224 -> 96 -> 96 | up, concat | 160 -> 64 ->
 64 | up, concat | 96 -> 32 -> 32 | 1x1 32 -> 4, ReLU after every 3x3
 convolution, canvas 256 (z) x 128 (r)).
 """
@@ -14,8 +15,11 @@ from __future__ import annotations
 import numpy as np
 
 H, W = 256, 128
-LAYERS = [(8, 32, 3), (32, 32, 3), (32, 64, 3), (64, 64, 3), (64, 128, 3), (128, 128, 3), (192, 64, 3),
-          (64, 64, 3), (96, 32, 3), (32, 32, 3), (32, 4, 1)]
+CHANNELS = (32, 64, 96, 128)  # per level
+# encoder levels 0-3 (two 3x3 layers each), decoder levels 2, 1, 0 (two each), the 1x1 head
+LAYERS = [(8, 32, 3), (32, 32, 3), (32, 64, 3), (64, 64, 3), (64, 96, 3), (96, 96, 3), (96, 128, 3),
+          (128, 128, 3), (224, 96, 3), (96, 96, 3), (160, 64, 3), (64, 64, 3), (96, 32, 3), (32, 32, 3),
+          (32, 4, 1)]
 
 
 def weight_count() -> int:
@@ -88,13 +92,18 @@ def forward(bits, features) -> np.ndarray:
     """Canvases [n][4][H][W] of the network with weights `bits` (uint16)."""
     L = unpack(bits)
     x = input_canvas(features)
-    e1 = relu_bf16(conv3(relu_bf16(conv3(x, *L[0])), *L[1]))
-    e2 = relu_bf16(conv3(relu_bf16(conv3(pool(e1), *L[2])), *L[3]))
-    e3 = relu_bf16(conv3(relu_bf16(conv3(pool(e2), *L[4])), *L[5]))
-    d2 = relu_bf16(conv3(relu_bf16(conv3(up_concat(e3, e2), *L[6])), *L[7]))
-    d1 = relu_bf16(conv3(relu_bf16(conv3(up_concat(d2, e1), *L[8])), *L[9]))
-    wh, bh = L[10]
-    y = d1 @ wh.T + bh
+    levels = len(CHANNELS)
+    skips = []
+    for lev in range(levels):  # encoder
+        if lev:
+            x = pool(x)
+        x = relu_bf16(conv3(relu_bf16(conv3(x, *L[2 * lev])), *L[2 * lev + 1]))
+        skips.append(x)
+    for j, lev in enumerate(range(levels - 2, -1, -1)):  # decoder, from the bottom up
+        first = 2 * levels + 2 * j
+        x = relu_bf16(conv3(relu_bf16(conv3(up_concat(x, skips[lev]), *L[first])), *L[first + 1]))
+    wh, bh = L[-1]
+    y = x @ wh.T + bh
     return np.transpose(y, (0, 3, 1, 2))
 
 

@@ -23,12 +23,13 @@ OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED = range(7)
 FP64, FP32, FP16_DEV, BF16_DEV = range(4)
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP16_DEV, "bf16": BF16_DEV}
 INNER_AXIS, INNER_WALL, INNER_AXIS_NODE = 0, 1, 2
-Z_PERIODIC, Z_WALL, Z_FREE, Z_MIXED, Z_NEE = range(5)
+Z_PERIODIC, Z_WALL, Z_FREE, Z_MIXED, Z_NEE, Z_HALO = range(6)
+FACE_INNER, FACE_OUTER, FACE_LO, FACE_HI = range(4)
 OUTER_BB, OUTER_NEE, OUTER_ZOUHE = 0, 1, 2
 RHO, UR, UZ, UTH, T = 1, 2, 4, 8, 16
 F64, F32 = 0, 1
 BGK, MRT = 0, 1
-_ZKIND = {"periodic": Z_PERIODIC, "wall": Z_WALL, "free": Z_FREE, "mixed": Z_MIXED, "nee": Z_NEE}
+_ZKIND = {"periodic": Z_PERIODIC, "wall": Z_WALL, "free": Z_FREE, "mixed": Z_MIXED, "nee": Z_NEE, "halo": Z_HALO}
 _OUTER = {"wall": OUTER_BB, "nee": OUTER_NEE, "zou_he": OUTER_ZOUHE}
 _INNER = {"axis": INNER_AXIS, "wall": INNER_WALL, "axis_node": INNER_AXIS_NODE}
 
@@ -100,6 +101,11 @@ def lib() -> ctypes.CDLL:
         L.axlbm_destroy.argtypes = [H]
         L.axlbm_kernel_timing.argtypes = [H, ctypes.c_int32]
         L.axlbm_use_graphs.argtypes = [H, ctypes.c_int32]
+        L.axlbm_set_residual_lag.argtypes = [H, ctypes.c_int32]
+        L.axlbm_halo_bytes.argtypes = [H, ctypes.POINTER(ctypes.c_size_t)]
+        L.axlbm_halo_send.argtypes = [H, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32]
+        L.axlbm_halo_recv.argtypes = [H, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32]
+        L.axlbm_batch_set_residual_lag.argtypes = [H, ctypes.c_int32]
         L.axlbm_graph_stats.argtypes = [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_kernel_times.argtypes = [H, ctypes.POINTER(ctypes.c_int64), dp, dp, ctypes.POINTER(ctypes.c_int64)]
         L.axlbm_check_static.argtypes = [ctypes.POINTER(axlbm_grid), ctypes.c_double,
@@ -165,7 +171,7 @@ def lib() -> ctypes.CDLL:
                      "axlbm_batch_moments", "axlbm_batch_set_fields", "axlbm_batch_get_populations",
                      "axlbm_batch_set_populations", "axlbm_batch_time", "axlbm_batch_tile_shape",
                      "axlbm_batch_set_tile_shape", "axlbm_batch_tile_shapes", "axlbm_batch_use_graphs", "axlbm_batch_graph_stats",
-                     "axlbm_batch_set_time", "axlbm_batch_copy_domain",
+                     "axlbm_batch_set_time", "axlbm_batch_copy_domain", "axlbm_batch_set_residual_lag",
                      "axlbm_batch_kernel_timing", "axlbm_batch_kernel_times", "axlbm_batch_kernel_times_by_parity",
                      "axlbm_batch_destroy",
                      "axlbm_batch_set_fields_all", "axlbm_batch_moments_all"):
@@ -173,7 +179,8 @@ def lib() -> ctypes.CDLL:
         for name in ("axlbm_state_bytes", "axlbm_create", "axlbm_step", "axlbm_moments", "axlbm_residual",
                      "axlbm_set_fields", "axlbm_get_populations", "axlbm_set_populations", "axlbm_time",
                      "axlbm_destroy", "axlbm_kernel_timing", "axlbm_kernel_times", "axlbm_check_static",
-                     "axlbm_use_graphs", "axlbm_graph_stats",
+                     "axlbm_use_graphs", "axlbm_graph_stats", "axlbm_set_residual_lag",
+                     "axlbm_halo_bytes", "axlbm_halo_send", "axlbm_halo_recv",
                      "axlbm_selftest_bounded_wait"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -339,6 +346,32 @@ class Domain:
     def use_graphs(self, enable: bool) -> None:
         """Replay runs of plain steps from captured CUDA graphs (default) or launch every kernel."""
         _check(lib().axlbm_use_graphs(self.handle, int(bool(enable))), self.handle)
+
+    def set_residual_lag(self, lag: int) -> None:
+        """1: Eq. 57 between consecutive levels (default); 2: half the change over two levels."""
+        _check(lib().axlbm_set_residual_lag(self.handle, int(lag)), self.handle)
+
+    # -- cut faces (z-slab decomposition)
+    def halo_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().axlbm_halo_bytes(self.handle, ctypes.byref(n)), self.handle)
+        return int(n.value)
+
+    def halo_send(self, face: int, out) -> None:
+        """Message of cut face `face` (FACE_LO / FACE_HI) into `out`: a uint8
+        numpy array (host, synchronises) or a uint8 CUDA tensor (queued)."""
+        if isinstance(out, np.ndarray):
+            _check(lib().axlbm_halo_send(self.handle, int(face), out.ctypes.data, 0), self.handle)
+        else:
+            _check(lib().axlbm_halo_send(self.handle, int(face), out.data_ptr(), 1), self.handle)
+
+    def halo_recv(self, face: int, msg) -> None:
+        """Store the neighbouring slab's message for cut face `face`."""
+        if isinstance(msg, np.ndarray):
+            m = np.ascontiguousarray(msg)
+            _check(lib().axlbm_halo_recv(self.handle, int(face), m.ctypes.data, 0), self.handle)
+        else:
+            _check(lib().axlbm_halo_recv(self.handle, int(face), msg.data_ptr(), 1), self.handle)
 
     def graph_stats(self):
         """(captures, launches) of the step graphs since creation."""
@@ -599,6 +632,10 @@ class Batch:
     def use_graphs(self, enable: bool) -> None:
         """Replay runs of plain steps from captured CUDA graphs (default) or launch every kernel."""
         _bcheck(lib().axlbm_batch_use_graphs(self.handle, int(bool(enable))), self.handle)
+
+    def set_residual_lag(self, lag: int) -> None:
+        """1: Eq. 57 between consecutive levels (default); 2: half the change over two levels."""
+        _bcheck(lib().axlbm_batch_set_residual_lag(self.handle, int(lag)), self.handle)
 
     def set_time(self, t: int) -> None:
         """Move the batch (at an even level) to the even time level t."""

@@ -65,6 +65,9 @@ Layout make_layout(const axlbm_grid* g) {
     L.pitch = (long long)align_up((size_t)g->nr, row_align);
     L.plane = L.pitch * g->nz;
     L.pop_bytes = align_up((size_t)L.nplanes * (size_t)L.plane * L.elem, 256);
+    // one row per population plane and axial face for the neighbour's values
+    // across a cut face (AXLBM_Z_HALO): [face lo, hi][plane][pitch]
+    L.halo_bytes = align_up(2 * (size_t)L.nplanes * (size_t)L.pitch * L.elem, 256);
     const size_t rbytes = g->precision == AXLBM_FP64 ? 8 : 4;
     L.speed_bytes = align_up((size_t)L.plane * rbytes, 256);
     // bulk tiles of kTileK x kTileJ nodes, persistent CTAs
@@ -74,7 +77,8 @@ Layout make_layout(const axlbm_grid* g) {
     L.frame_blocks = (L.nframe + 255) / 256;
     L.nparts = axl::kMaxBulkBlocks + L.frame_blocks;
     L.part_bytes = align_up((size_t)L.nparts * 4 * sizeof(double), 256);
-    L.off_speed = L.pop_bytes;
+    L.off_halo = L.pop_bytes;
+    L.off_speed = L.off_halo + L.halo_bytes;
     L.off_part = L.off_speed + L.speed_bytes;
     L.off_result = L.off_part + L.part_bytes;
     L.off_clock = L.off_result + 256;
@@ -176,8 +180,15 @@ bool validate_problem(const axlbm_grid* grid, double tau, const axlbm_forcing* f
         return no("bad inner face kind");
     if (bc->inner != AXLBM_INNER_WALL && grid->r0 != 0.0) return no("the axis needs r0 == 0");
     if (bc->inner == AXLBM_INNER_AXIS_NODE && grid->nr < 2) return no("a node on the axis needs nr >= 2");
-    if (bc->z_lo < 0 || bc->z_lo > AXLBM_Z_NEE || bc->z_lo == AXLBM_Z_MIXED || bc->z_hi < 0 || bc->z_hi > AXLBM_Z_NEE)
+    if (bc->z_lo < 0 || bc->z_lo > AXLBM_Z_HALO || bc->z_lo == AXLBM_Z_MIXED || bc->z_hi < 0 || bc->z_hi > AXLBM_Z_HALO)
         return no("bad axial face kind (the bottom face cannot be mixed)");
+    if (bc->z_lo == AXLBM_Z_HALO || bc->z_hi == AXLBM_Z_HALO) {
+        if (bc->inner == AXLBM_INNER_AXIS_NODE || bc->outer != AXLBM_OUTER_BB || bc->z_lo == AXLBM_Z_NEE ||
+            bc->z_hi == AXLBM_Z_NEE)
+            return no("a cut face (AXLBM_Z_HALO) needs the half-spacing axis or an inner wall, the bounce-back "
+                      "outer wall and no wet axial wall");
+        if (grid->nz < 2) return no("a cut face (AXLBM_Z_HALO) needs nz >= 2");
+    }
     if ((bc->z_lo == AXLBM_Z_PERIODIC) != (bc->z_hi == AXLBM_Z_PERIODIC)) return no("periodic needs both axial faces periodic");
     if (bc->outer != AXLBM_OUTER_BB && bc->outer != AXLBM_OUTER_NEE && bc->outer != AXLBM_OUTER_ZOUHE)
         return no("bad outer face kind");
@@ -259,11 +270,20 @@ axlbm_status axlbm_create(const axlbm_grid* grid, double tau, const axlbm_forcin
     h->G.r_split = bc->r_split;
     h->G.col0 = 0;
     h->G.row0 = 0;
+    {
+        const double off = bc->inner == AXLBM_INNER_AXIS_NODE ? 0.0 : 0.5;
+        h->G.rb = (float)(grid->r0 + off);
+        h->G.rb_exact = (double)h->G.rb == grid->r0 + off;
+        for (int j = 0; j < grid->nr && h->G.rb_exact; ++j)
+            h->G.rb_exact = (double)(h->G.rb + (float)j) == grid->r0 + off + j;
+    }
     h->parity = 0;
     h->t = 0;
     h->speed_valid = false;
     h->have_check = false;
     h->last_residual_valid = false;
+    h->residual_lag = 1;
+    h->last_residual_lag = 1;
     h->timing = false;
     h->use_graphs = true;
     h->graphs_ready = false;
@@ -273,6 +293,8 @@ axlbm_status axlbm_create(const axlbm_grid* grid, double tau, const axlbm_forcin
     h->stage = nullptr;
     h->stage_bytes = 0;
     h->check_parts = 0;
+    h->halo_phase = 0;
+    h->halo_recv = 0;
     h->bulk_grid[0][0] = h->bulk_grid[0][1] = h->bulk_grid[1][0] = h->bulk_grid[1][1] = 0;
     {
         int dev = 0;
@@ -408,14 +430,18 @@ axlbm_status graph_pairs(axlbm_handle* h, const Ops* ops, int64_t pairs) {
 axlbm_status axlbm_step(axlbm_handle* h, int64_t n) {
     if (!h) return fail(nullptr, AXLBM_EINVAL, "handle is NULL");
     if (n < 0) return fail(h, AXLBM_EINVAL, "n must be >= 0");
+    const axlbm_status hs = axl::halo_before_step(h, n);
+    if (hs != AXLBM_OK) return hs;
     const Ops* ops = ops_for(h->grid.precision);
     int64_t s = 0;
-    // every step but the last two (the check steps) is plain: with timing
-    // off, whole (even, odd) pairs of them replay captured graphs once the
-    // plain bulk kernels have been sized by earlier launches
+    // every step but the tail is plain: the tail is the two check steps (lag
+    // 1), or a check step, a plain step and a check step (lag 2); with timing
+    // off, whole (even, odd) pairs of plain steps replay captured graphs once
+    // the plain bulk kernels have been sized by earlier launches
+    const int tail = h->residual_lag == 2 ? 3 : 2;
     const bool odd_bulk = h->G.nr > 2 && h->G.nz > 2;
     const bool sized = h->bulk_grid[0][0] > 0 && (h->bulk_grid[1][0] > 0 || !odd_bulk);
-    if (h->use_graphs && !h->timing && sized && n - 2 - h->parity >= 2 * kMinGraphPairs) {
+    if (h->use_graphs && !h->timing && sized && n - tail - h->parity >= 2 * kMinGraphPairs) {
         if (h->parity == 1) {
             int nl = 0;
             const cudaError_t e = ops->step(h, 0, 0, nullptr, nullptr, &nl);
@@ -425,16 +451,16 @@ axlbm_status axlbm_step(axlbm_handle* h, int64_t n) {
             h->t += 1;
             s = 1;
         }
-        const int64_t pairs = (n - 2 - s) / 2;
+        const int64_t pairs = (n - tail - s) / 2;
         const axlbm_status st = graph_pairs(h, ops, pairs);
         if (st != AXLBM_OK) return st;
         s += 2 * pairs;
     }
     for (; s < n; ++s) {
         const bool last = s == n - 1;
-        const bool before_last = s == n - 2;
-        const int check = (last || before_last) ? 1 : 0;
-        const int residual = (last && (n >= 2 || h->speed_valid)) ? 1 : 0;
+        const bool first_check = s == n - tail;
+        const int check = (last || first_check) ? 1 : 0;
+        const int residual = (last && (n >= tail || (tail == 2 && h->speed_valid))) ? 1 : 0;
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         if (h->timing) {
             axlbm_status st = timing_slot(h, &ev0, &ev1);
@@ -456,12 +482,21 @@ axlbm_status axlbm_step(axlbm_handle* h, int64_t n) {
             h->have_check = true;
             h->speed_valid = true;
             h->last_residual_valid = residual != 0;
+            h->last_residual_lag = tail - 1;
         } else {
             h->speed_valid = check != 0;
         }
         h->parity ^= 1;
         h->t += 1;
     }
+    if (n > 0) axl::halo_after_step(h);
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_set_residual_lag(axlbm_handle* h, int32_t lag) {
+    if (!h) return fail(nullptr, AXLBM_EINVAL, "handle is NULL");
+    if (lag != 1 && lag != 2) return fail(h, AXLBM_EINVAL, "lag must be 1 or 2");
+    h->residual_lag = lag;
     return AXLBM_OK;
 }
 
@@ -512,7 +547,7 @@ axlbm_status axlbm_residual(axlbm_handle* h, double* residual, double* mass, dou
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "residual read");
     if (clk.err) return fail(h, AXLBM_ETIMEOUT, "a bounded wait for a TMA copy gave up; the state is not valid");
-    if (residual) *residual = h->last_residual_valid ? r[0] : INFINITY;
+    if (residual) *residual = h->last_residual_valid ? r[0] / h->last_residual_lag : INFINITY;
     if (mass) *mass = r[1];
     if (budget) *budget = r[2];
     if (r[3] != 0.0) return fail(h, AXLBM_ENONFINITE, "non-finite density or velocity in the last check step");
@@ -563,6 +598,7 @@ axlbm_status axlbm_set_fields(axlbm_handle* h, const void* fields, int32_t in_dt
     if (e != cudaSuccess) return cuda_fail(h, e, "set_fields");
     h->parity = 0;
     h->speed_valid = false;
+    h->halo_phase = 0;
     return upload_clock(h);
 }
 
@@ -633,6 +669,7 @@ axlbm_status axlbm_set_populations(axlbm_handle* h, const double* f, const doubl
     h->parity = 0;
     h->t = time;
     h->speed_valid = false;
+    h->halo_phase = 0;
     return upload_clock(h);
 }
 
@@ -673,8 +710,9 @@ axlbm_status axlbm_save(axlbm_handle* h, void* buf, size_t cap, size_t* bytes) {
     axl::Clock clk;
     memcpy(&clk, out + sizeof(axl::CkptHeader) + h->L.off_clock, sizeof clk);
     if (clk.err) return fail(h, AXLBM_ETIMEOUT, "a bounded wait for a TMA copy gave up; the state is not valid");
-    const axl::CkptHeader c = axl::ckpt_header(axl::kCkptDomain, domain_fingerprint(h), h->L.total, h->t, h->parity,
-                                               h->speed_valid, h->have_check, h->last_residual_valid, h->check_parts);
+    axl::CkptHeader c = axl::ckpt_header(axl::kCkptDomain, domain_fingerprint(h), h->L.total, h->t, h->parity,
+                                         h->speed_valid, h->have_check, h->last_residual_valid, h->check_parts);
+    if (h->last_residual_lag == 2) c.flags |= axl::kCkptResidualLag2;
     memcpy(out, &c, sizeof c);
     if (bytes) *bytes = need;
     return AXLBM_OK;
@@ -697,7 +735,9 @@ axlbm_status axlbm_load(axlbm_handle* h, const void* buf, size_t bytes) {
     h->speed_valid = (c.flags & axl::kCkptSpeedValid) != 0;
     h->have_check = (c.flags & axl::kCkptHaveCheck) != 0;
     h->last_residual_valid = (c.flags & axl::kCkptResidualValid) != 0;
+    h->last_residual_lag = (c.flags & axl::kCkptResidualLag2) ? 2 : 1;
     h->check_parts = c.aux;
+    h->halo_phase = 0;  // a checkpoint of a slab is taken after its exchange
     return AXLBM_OK;
 }
 

@@ -83,6 +83,10 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
             return false;
         }
         if (!dom[d].grid.with_swirl) { *why = "domain " + std::to_string(d) + ": batches need with_swirl = 1"; return false; }
+        if (dom[d].boundary.z_lo == AXLBM_Z_HALO || dom[d].boundary.z_hi == AXLBM_Z_HALO) {
+            *why = "domain " + std::to_string(d) + ": cut faces (AXLBM_Z_HALO) are for single domains";
+            return false;
+        }
         if ((long long)dom[d].grid.nr * dom[d].grid.nz > (1ll << 28)) { *why = "domain too large for a batch"; return false; }
         P->thmax |= dom[d].grid.with_temperature;
     }
@@ -277,9 +281,11 @@ axlbm_status reset_rest(axlbm_batch* b) {
     cudaError_t e = cudaMemsetAsync(b->mem, 0, L.off_clock + 256, b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "memset");
     std::vector<double> az(6 * b->n, 0.0);
-    for (int d = 0; d < b->n; ++d) {  // a(0) = az0 cos(0)
+    for (int d = 0; d < b->n; ++d) {  // a(0) = az0 cos(0); the bulk kernel's word also holds it in FP32
         az[2 * d] = b->desc[d].forcing.az0;
         az[2 * b->n + 4 * d] = b->desc[d].forcing.az0;
+        const float f = (float)b->desc[d].forcing.az0;
+        memcpy(&az[2 * b->n + 4 * d + 1], &f, sizeof f);
     }
     axlbm_status st = upload(b, L.off_az, az.data(), az.size() * sizeof(double));
     if (st != AXLBM_OK) return st;
@@ -304,6 +310,7 @@ axlbm_status reset_rest(axlbm_batch* b) {
     b->parity = 0;
     b->t = 0;
     b->speed_valid = b->have_check = b->last_residual_valid = false;
+    b->residual_lag = b->last_residual_lag = 1;
     return AXLBM_OK;
 }
 
@@ -431,11 +438,13 @@ axlbm_status batch_graph_pairs(axlbm_batch* b, const BatchOps* ops, int64_t pair
 axlbm_status batch_step_n(axlbm_batch* b, int64_t n) {
     const BatchOps* ops = batch_ops_for(b->precision);
     int64_t s = 0;
-    // every step but the last two (the check steps) is plain: with timing off,
-    // whole (even, odd) pairs of them replay captured graphs once the plain
-    // kernels of the shapes in use have been sized by earlier launches
+    // every step but the tail is plain: the tail is the two check steps (lag
+    // 1), or a check step, a plain step and a check step (lag 2); with timing
+    // off, whole (even, odd) pairs of plain steps replay captured graphs once
+    // the plain kernels of the shapes in use have been sized by earlier launches
+    const int tail = b->residual_lag == 2 ? 3 : 2;
     const bool sized = b->grid[b->shape[0]][0][0] > 0 && b->grid[b->shape[1]][1][0] > 0;
-    if (b->use_graphs && !b->timing && sized && n - 2 - b->parity >= 2 * kMinGraphPairs) {
+    if (b->use_graphs && !b->timing && sized && n - tail - b->parity >= 2 * kMinGraphPairs) {
         if (b->parity == 1) {
             int nl = 0;
             const cudaError_t e = ops->step(b, 0, 0, nullptr, nullptr, &nl);
@@ -445,15 +454,15 @@ axlbm_status batch_step_n(axlbm_batch* b, int64_t n) {
             b->t += 1;
             s = 1;
         }
-        const int64_t pairs = (n - 2 - s) / 2;
+        const int64_t pairs = (n - tail - s) / 2;
         const axlbm_status st = batch_graph_pairs(b, ops, pairs);
         if (st != AXLBM_OK) return st;
         s += 2 * pairs;
     }
     for (; s < n; ++s) {
-        const bool last = s == n - 1, before_last = s == n - 2;
-        const int check = (last || before_last) ? 1 : 0;
-        const int residual = (last && (n >= 2 || b->speed_valid)) ? 1 : 0;
+        const bool last = s == n - 1, first_check = s == n - tail;
+        const int check = (last || first_check) ? 1 : 0;
+        const int residual = (last && (n >= tail || (tail == 2 && b->speed_valid))) ? 1 : 0;
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         if (b->timing) {
             axlbm_status st = batch_timing_slot(b, &ev0, &ev1);
@@ -476,6 +485,7 @@ axlbm_status batch_step_n(axlbm_batch* b, int64_t n) {
             b->have_check = true;
             b->speed_valid = true;
             b->last_residual_valid = residual != 0;
+            b->last_residual_lag = tail - 1;
             b->last_check_parity = b->parity;
         } else {
             b->speed_valid = check != 0;
@@ -668,6 +678,12 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
         y.r0 = x.r0;
         y.rho0 = D.forcing.rho0;
         y.c = x.cf;
+        // FP32 radius base of the atlas columns, used when exact for every column
+        const double off = D.boundary.inner == AXLBM_INNER_AXIS_NODE ? 0.0 : 0.5;
+        y.rb = (float)(x.r0 + off - x.col0);
+        y.rb_exact = (double)y.rb == x.r0 + off - x.col0;
+        for (int jl = 0; jl < x.nr && y.rb_exact; ++jl)
+            y.rb_exact = (double)(y.rb + (float)(x.col0 + jl)) == x.r0 + off + jl;
     }
     const BatchLayout& L = b->L;
     if (st == AXLBM_OK) st = upload(b, L.off_doms, dd.data(), dd.size() * sizeof(axl::DomDesc));
@@ -729,7 +745,7 @@ axlbm_status axlbm_batch_residuals(axlbm_batch* b, double* out) {
     if (clk.err) return bfail(b, AXLBM_ETIMEOUT, "a bounded wait for a TMA copy gave up; the state is not valid");
     bool bad = false;
     for (int d = 0; d < b->n; ++d) {
-        out[3 * d + 0] = b->last_residual_valid ? r[4 * d] : INFINITY;
+        out[3 * d + 0] = b->last_residual_valid ? r[4 * d] / b->last_residual_lag : INFINITY;
         out[3 * d + 1] = r[4 * d + 1];
         out[3 * d + 2] = r[4 * d + 2];
         bad = bad || r[4 * d + 3] != 0.0;
@@ -968,9 +984,9 @@ axlbm_status axlbm_batch_save(axlbm_batch* b, void* buf, size_t cap, size_t* byt
     axl::Clock clk;
     memcpy(&clk, out + sizeof(axl::CkptHeader) + b->L.off_clock, sizeof clk);
     if (clk.err) return bfail(b, AXLBM_ETIMEOUT, "a bounded wait for a TMA copy gave up; the state is not valid");
-    const axl::CkptHeader c = axl::ckpt_header(axl::kCkptBatch, batch_fingerprint(b), state, b->t, b->parity,
-                                               b->speed_valid, b->have_check, b->last_residual_valid,
-                                               b->last_check_parity);
+    axl::CkptHeader c = axl::ckpt_header(axl::kCkptBatch, batch_fingerprint(b), state, b->t, b->parity,
+                                         b->speed_valid, b->have_check, b->last_residual_valid, b->last_check_parity);
+    if (b->last_residual_lag == 2) c.flags |= axl::kCkptResidualLag2;
     memcpy(out, &c, sizeof c);
     if (bytes) *bytes = need;
     return AXLBM_OK;
@@ -993,6 +1009,7 @@ axlbm_status axlbm_batch_load(axlbm_batch* b, const void* buf, size_t bytes) {
     b->speed_valid = (c.flags & axl::kCkptSpeedValid) != 0;
     b->have_check = (c.flags & axl::kCkptHaveCheck) != 0;
     b->last_residual_valid = (c.flags & axl::kCkptResidualValid) != 0;
+    b->last_residual_lag = (c.flags & axl::kCkptResidualLag2) ? 2 : 1;
     b->last_check_parity = c.aux;
     return AXLBM_OK;
 }
@@ -1035,6 +1052,13 @@ axlbm_status axlbm_batch_tile_shapes(const axlbm_batch* b, int32_t* rows, int32_
         rows[par] = axl::kShapeTK[b->shape[par]];
         nodes[par] = axl::kShapeTJ[b->shape[par]];
     }
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_set_residual_lag(axlbm_batch* b, int32_t lag) {
+    if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
+    if (lag != 1 && lag != 2) return bfail(b, AXLBM_EINVAL, "lag must be 1 or 2");
+    b->residual_lag = lag;
     return AXLBM_OK;
 }
 

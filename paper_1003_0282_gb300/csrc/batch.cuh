@@ -47,9 +47,12 @@ struct DomDesc {
 // shared memory by a bulk copy next to the tile's data (16-byte multiple).
 struct __align__(16) SlotDesc {
     int nr, nz, col0, row0;
-    int temperature, axis_node, wet, pad2;  // axis_node: node 0 on the axis (r_j = j); wet: 1 outer, 2 lo, 4 hi
+    int temperature, axis_node, wet, rb_exact;  // axis_node: node 0 on the axis (r_j = j); wet: 1 outer, 2 lo, 4 hi
     double r0, rho0;
     CoefCore<float> c;
+    // radius of atlas column x: rb + x, exact in FP32 for every column of the
+    // domain when rb_exact (else it is formed in FP64 from r0)
+    float rb, pad[3];
 };
 static_assert(sizeof(SlotDesc) % 16 == 0, "bulk copies move 16-byte multiples");
 
@@ -94,6 +97,8 @@ __device__ __forceinline__ Geom dom_geom(const DomDesc& D, long long pitch, long
     G.r_split = D.r_split;
     G.col0 = D.col0;
     G.row0 = D.row0;
+    G.rb = 0.0f;
+    G.rb_exact = 0;  // (the per-domain kernels take the radius in FP64)
     return G;
 }
 
@@ -117,6 +122,15 @@ struct BatchArgs {
     int residual;
 };
 
+// a(t) of domain d for AA parity par in the bulk kernel's 16-byte word: the
+// value, then its FP32 rounding (what the FP32 arithmetic of the bulk kernel
+// uses, so that the kernel converts nothing per tile).
+__device__ __forceinline__ void store_az16(double* az16, int d, int par, double a) {
+    az16[4 * d + 2 * par] = a;
+    *reinterpret_cast<float*>(az16 + 4 * d + 2 * par + 1) = (float)a;
+}
+__device__ __forceinline__ float az16_f32(const double (&w)[2]) { return *reinterpret_cast<const float*>(&w[1]); }
+
 // Global -> shared bulk copy completing on an mbarrier (16-byte aligned
 // addresses, size a multiple of 16).
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -139,15 +153,15 @@ __device__ __forceinline__ void warp_slot_store(RedR<R> v, int q, const SlotDesc
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const R rm = __shfl_up_sync(full, v.rmax, off);
-        const double dm = __shfl_up_sync(full, v.dmass, off);
-        const double bu = __shfl_up_sync(full, v.budget, off);
+        const CSum<R> dm = v.dmass.shfl_up(off);
+        const CSum<R> bu = v.budget.shfl_up(off);
         const int bd = __shfl_up_sync(full, v.bad, off);
         const int ct = __shfl_up_sync(full, v.count, off);
         const int qo = __shfl_up_sync(full, q, off);
         if (lane >= off && qo == q) {
             v.rmax = max(v.rmax, rm);
-            v.dmass += dm;
-            v.budget += bu;
+            v.dmass.add(dm);
+            v.budget.add(bu);
             v.bad += bd;
             v.count += ct;
         }
@@ -156,8 +170,8 @@ __device__ __forceinline__ void warp_slot_store(RedR<R> v, int q, const SlotDesc
     if (lane == 31 || qn != q) {
         double* o = out + 4ll * (q * kBatchMaxWarps + warp);
         o[0] = (double)v.rmax;
-        o[1] = (double)v.count * sl[q].rho0 + (double)v.dmass;
-        o[2] = (double)v.budget;
+        o[1] = (double)v.count * sl[q].rho0 + v.dmass.value();
+        o[2] = v.budget.value();
         o[3] = (double)v.bad;
     }
 }
@@ -309,8 +323,8 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
             const R sp = sqrt(vur * vur + vuz * vuz);
             if (A.residual) red.rmax = max(red.rmax, (R)fabs(sp - sp_old[l]));
             A.speed[x] = sp;
-            red.dmass += (double)Lanes<RC>::get(c.ds0, l);
-            red.budget += (double)vrho * (double)vur * (double)inv_r;
+            red.dmass.add(Lanes<RC>::get(c.ds0, l));
+            red.budget.add(vrho * vur * inv_r);
             red.bad += (isfinite(vrho) && isfinite(vur) && isfinite(vuz)) ? 0 : 1;
             red.count += 1;
         }
@@ -443,12 +457,17 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
 #pragma unroll
                 for (int u = 1; u < kSlots; ++u) q += (u < nseg && jj >= M.r.start[u]) ? 1 : 0;
                 const SlotDesc& D = slots[s * kSlots + q];
-                const R az = R(M.az[q][0]);
-                const int jl = j0 + jj - D.col0;
-                const double rj = D.r0 + (double)jl + (D.axis_node ? 0.0 : 0.5);
-                const R inv_r = rj > 0.0 ? rcp(R(rj)) : R(0);
+                const R az = az16_f32(M.az[q]);
+                R inv_r;
+                if (D.rb_exact) {  // the common case: no FP64 instruction in the loop over tiles
+                    const float rj = D.rb + (float)(j0 + jj);
+                    inv_r = rj > 0.0f ? rcp(rj) : R(0);
+                } else {
+                    const double rj = D.r0 + (double)(j0 + jj - D.col0) + (D.axis_node ? 0.0 : 0.5);
+                    inv_r = rj > 0.0 ? rcp(R(rj)) : R(0);
+                }
                 const S* st = sm + s * STAGE;
-                RedR<R> red{R(0), 0.0, 0.0, 0, 0};
+                RedR<R> red;
                 const bool dth = TH && M.r.th;
                 // one node pair per thread: rows rr0 and rr0 + TK/2 of column jj
                 if (dth)
@@ -478,7 +497,7 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
         for (int d = tid; d < A.ndom; d += blockDim.x) {
             const double a = A.doms[d].az0 * cos(A.doms[d].omega_t * (double)t1);
             A.dom_az[2 * d + 1] = a;
-            A.dom_az16[4 * d + 2] = a;
+            store_az16(A.dom_az16, d, 1, a);
         }
         __syncthreads();
         if (tid == 0) A.clock->t = t1;
@@ -502,6 +521,8 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_batch(const BatchArgs<S, 
         if ((D.temperature != 0) == THD) {
             KArgs<S, R> K;
             K.pop = A.pop;
+            K.halo = nullptr;  // batch domains have no cut faces
+            K.nplanes = 0;
             K.G = dom_geom(D, A.pitch, A.plane);
             K.C = dom_coef<R>(D);
             K.g_plane = 9;
@@ -528,7 +549,7 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_batch(const BatchArgs<S, 
         for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) {
             const double a = A.doms[d].az0 * cos(A.doms[d].omega_t * (double)t1);
             A.dom_az[2 * d] = a;
-            A.dom_az16[4 * d] = a;
+            store_az16(A.dom_az16, d, 0, a);
         }
         __syncthreads();
         if (threadIdx.x == 0) A.clock->t = t1;
@@ -541,7 +562,7 @@ static __global__ void k_batch_set_time(const DomDesc* doms, int ndom, Clock* cl
     for (int d = threadIdx.x; d < ndom; d += blockDim.x) {
         const double a = doms[d].az0 * cos(doms[d].omega_t * (double)t);
         az[2 * d] = a;
-        az16[4 * d] = a;
+        store_az16(az16, d, 0, a);
     }
     if (threadIdx.x == 0) clock->t = t;
 }

@@ -66,6 +66,7 @@ struct axlbm_batch {
     int parity;
     int64_t t;
     bool speed_valid, have_check, last_residual_valid;
+    int residual_lag, last_residual_lag;  // 1: Eq. 57 between consecutive levels; 2: half the change over two levels
     int last_check_parity;
     // timing
     bool timing;

@@ -38,6 +38,8 @@ KArgs<S, R> domain_args(axlbm_batch* b, int d) {
     const axlbm_domain& D = b->desc[d];
     KArgs<S, R> K;
     K.pop = reinterpret_cast<S*>(b->mem);
+    K.halo = nullptr;  // batch domains have no cut faces
+    K.nplanes = 0;
     K.speed = reinterpret_cast<R*>(b->mem + L.off_speed);
     K.partials = nullptr;
     K.part_offset = 0;
@@ -57,6 +59,8 @@ KArgs<S, R> domain_args(axlbm_batch* b, int d) {
     K.G.r_split = D.boundary.r_split;
     K.G.col0 = b->col0[d];
     K.G.row0 = b->row0[d];
+    K.G.rb = 0.0f;
+    K.G.rb_exact = 0;
     K.C = make_coef<R>(D.tau, D.forcing, D.boundary);
     K.C.mrt = D.grid.collision == AXLBM_MRT;
     K.g_plane = 9;

@@ -29,6 +29,8 @@ struct Geom {
     int outer;        // AXLBM_OUTER_BB or AXLBM_OUTER_NEE
     double r_split;
     int col0, row0;   // position of node (0, 0) in the array (non-zero for a domain of a batch)
+    float rb;         // radius of column j is rb + j, exact in FP32 for every column when rb_exact
+    int rb_exact;
 };
 
 // Per-step forcing state on the device.  Kernels of a step with AA parity p
@@ -73,8 +75,8 @@ struct Layout {
     int h_plane;      // first h plane (or -1)
     size_t elem;      // bytes per stored value
     long long pitch, plane;
-    size_t pop_bytes, speed_bytes, part_bytes;
-    size_t off_speed, off_part, off_result, off_clock, total;
+    size_t pop_bytes, halo_bytes, speed_bytes, part_bytes;
+    size_t off_halo, off_speed, off_part, off_result, off_clock, total;
     int tiles_j, tiles_k;  // bulk tiles
     int nframe, frame_blocks;
     int nparts;           // reduction slots (bulk blocks of any launch + frame blocks)
@@ -97,10 +99,17 @@ struct axlbm_handle {
     int64_t t;          // time level
     bool speed_valid;   // the speed buffer holds |u| of time t - 1 (last step was a check step)
     bool have_check;    // a check step has run
-    bool last_residual_valid;  // the last check step compared two consecutive levels
+    bool last_residual_valid;  // the last check step compared two levels (residual_lag apart)
+    int residual_lag;          // 1: Eq. 57 between consecutive levels; 2: half the change over two levels
+    int last_residual_lag;     // the lag of the last check step's residual
     int num_sms;
     int bulk_grid[2][2];  // persistent grid per (parity, check), from the occupancy API
     int check_parts;      // partials written by the last check step
+    // cut faces (AXLBM_Z_HALO): 0 nothing to exchange, 1 after an in-place
+    // step (rows -> neighbour's halo), 2 after a neighbour-to-neighbour step
+    // (halo -> neighbour's rows); bit f of halo_recv: face f received since
+    int halo_phase;
+    unsigned halo_recv;
     // bulk-kernel timing
     bool timing;
     std::vector<cudaEvent_t> ev;     // event pairs of launches not yet folded into the totals
@@ -121,6 +130,11 @@ struct axlbm_handle {
 };
 
 namespace axl {
+
+// Cut faces (halo.cu): checks before a step of a domain with AXLBM_Z_HALO
+// faces, and the exchange that is due after it.
+axlbm_status halo_before_step(axlbm_handle* h, int64_t n);
+void halo_after_step(axlbm_handle* h);
 
 // A device staging buffer of at least `bytes` for host-side I/O of handle h
 // (an axlbm_handle or an axlbm_batch), kept between calls and grown on demand.
@@ -164,7 +178,7 @@ static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
 
 constexpr uint32_t kCkptVersion = 1;
 constexpr uint32_t kCkptDomain = 1, kCkptBatch = 2;
-constexpr uint32_t kCkptSpeedValid = 1, kCkptHaveCheck = 2, kCkptResidualValid = 4;
+constexpr uint32_t kCkptSpeedValid = 1, kCkptHaveCheck = 2, kCkptResidualValid = 4, kCkptResidualLag2 = 8;
 
 // FNV-1a (64 bit) over the little-endian bytes of v, chained from h.
 inline uint64_t ckpt_mix(uint64_t h, int64_t v) {

@@ -41,6 +41,7 @@ constexpr int kThreads = 256;
 template <class S, class R>
 struct KArgs {
     S* pop;
+    S* halo;           // cut faces (AXLBM_Z_HALO): [face lo, hi][plane][pitch] neighbour rows, else unused
     R* speed;
     double* partials;
     int part_offset;
@@ -50,6 +51,7 @@ struct KArgs {
     Geom G;
     Coef<R> C;
     int g_plane, h_plane;
+    int nplanes;       // population planes (halo row stride per face)
     int nframe;
     int residual;  // 1: compare |u| with the stored previous level
     int tiles_j, tiles_k;  // bulk tiles (kTileJ x kTileK nodes) along r and z
@@ -284,6 +286,9 @@ __device__ __forceinline__ Site classify(const Geom& G, int j, int k, int ex, in
         if (kind == AXLBM_Z_MIXED) kind = (node_radius(G, j) + 0.5 * ex < G.r_split) ? AXLBM_Z_WALL : AXLBM_Z_FREE;
         if (kind == AXLBM_Z_PERIODIC) {
             s.k += s.k < 0 ? G.nz : -G.nz;
+        } else if (kind == AXLBM_Z_HALO) {
+            // a cut: the site is the neighbouring slab's boundary row, row -1
+            // or nz here, held in the halo rows (see site_slot)
         } else if (kind == AXLBM_Z_WALL || kind == AXLBM_Z_NEE) {  // (a wet row is rebuilt after the step)
             s.solid = 1;
             s.face = face;
@@ -342,6 +347,16 @@ __device__ __forceinline__ S* slot(S* pop, const Geom& G, int plane, int j, int 
     return pop + (long long)plane * G.plane + (long long)(G.row0 + k) * G.pitch + (G.col0 + j);
 }
 
+// Where the population of plane `plane` at a fluid site (j, k) lives: in the
+// domain, or -- row -1 or nz, beyond a cut face -- in that face's halo row.
+template <class S, class R>
+__device__ __forceinline__ S* site_slot(const KArgs<S, R>& A, int plane, int j, int k) {
+    const Geom& G = A.G;
+    if (k < 0) return A.halo + (long long)plane * G.pitch + j;
+    if (k >= G.nz) return A.halo + (long long)(A.nplanes + plane) * G.pitch + j;
+    return slot(A.pop, G, plane, j, k);
+}
+
 // Pull the odd-step populations of node (j, k) with boundary rules.
 template <class S, class R, bool SW, bool TH>
 __device__ __forceinline__ void pull_odd(const KArgs<S, R>& A, int j, int k, Cell<R, SW, TH>& c) {
@@ -353,7 +368,7 @@ __device__ __forceinline__ void pull_odd(const KArgs<S, R>& A, int j, int k, Cel
             c.d[a] = Codec<S>::load(slot(A.pop, G, a, j, k));
         } else {
             const int b = idx9(s.fr ? -cr9(a) : cr9(a), s.fz ? -cz9(a) : cz9(a));
-            c.d[a] = Codec<S>::load(slot(A.pop, G, opp9(b), s.j, s.k));
+            c.d[a] = Codec<S>::load(site_slot(A, opp9(b), s.j, s.k));
         }
     }
     if (SW) {
@@ -364,7 +379,7 @@ __device__ __forceinline__ void pull_odd(const KArgs<S, R>& A, int j, int k, Cel
                 c.g[q] = bounce_g(G, A.C, s.face, j, Codec<S>::load(slot(A.pop, G, A.g_plane + q, j, k)));
             } else {
                 const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
-                const R v = Codec<S>::load(slot(A.pop, G, A.g_plane + opp4(b), s.j, s.k));
+                const R v = Codec<S>::load(site_slot(A, A.g_plane + opp4(b), s.j, s.k));
                 c.g[q] = s.fr ? -v : v;
             }
         }
@@ -377,7 +392,7 @@ __device__ __forceinline__ void pull_odd(const KArgs<S, R>& A, int j, int k, Cel
                 c.h[q] = bounce_h(A.C, s.face, R(Codec<S>::load(slot(A.pop, G, A.h_plane + q, j, k))));
             } else {
                 const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
-                c.h[q] = Codec<S>::load(slot(A.pop, G, A.h_plane + opp4(b), s.j, s.k));
+                c.h[q] = Codec<S>::load(site_slot(A, A.h_plane + opp4(b), s.j, s.k));
             }
         }
     }
@@ -396,7 +411,7 @@ __device__ __forceinline__ void push_odd(const KArgs<S, R>& A, int j, int k, con
             // leaves through the axis into the mirror column
         } else {
             const int b = idx9(s.fr ? -cr9(a) : cr9(a), s.fz ? -cz9(a) : cz9(a));
-            Codec<S>::store(slot(A.pop, G, b, s.j, s.k), c.d[a]);
+            Codec<S>::store(site_slot(A, b, s.j, s.k), c.d[a]);
         }
     }
     if (SW) {
@@ -409,7 +424,7 @@ __device__ __forceinline__ void push_odd(const KArgs<S, R>& A, int j, int k, con
                 // leaves through the axis into the mirror column
             } else {
                 const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
-                Codec<S>::store(slot(A.pop, G, A.g_plane + b, s.j, s.k), s.fr ? -c.g[q] : c.g[q]);
+                Codec<S>::store(site_slot(A, A.g_plane + b, s.j, s.k), s.fr ? -c.g[q] : c.g[q]);
             }
         }
     }
@@ -423,7 +438,7 @@ __device__ __forceinline__ void push_odd(const KArgs<S, R>& A, int j, int k, con
                 // leaves through the axis into the mirror column
             } else {
                 const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
-                Codec<S>::store(slot(A.pop, G, A.h_plane + b, s.j, s.k), c.h[q]);
+                Codec<S>::store(site_slot(A, A.h_plane + b, s.j, s.k), c.h[q]);
             }
         }
     }
@@ -580,14 +595,66 @@ struct Lanes<F2> {
     __device__ static __forceinline__ float get(F2 v, int l) { return l ? v.v.y : v.v.x; }
 };
 
+// A sum for the check step's mass deviation and budget.  With FP64
+// arithmetic it is a double.  With FP32 arithmetic it is an unevaluated pair
+// hi + lo of floats kept by error-free transformations (Knuth's TwoSum):
+// every addition returns the exact rounding error into lo, so the pair
+// carries about 48 bits -- the accuracy of FP64 for these sums at FP32
+// instruction cost (GB300 issues FP64 at a small fraction of the FP32 rate,
+// and FP64 adds at every node cost ~2 % of a batch step).  Warp folds add
+// pairs; the per-warp result is converted to FP64 and folded in FP64.
+template <class R>
+struct CSum {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ void add(const CSum& o) { v += o.v; }
+    __device__ __forceinline__ double value() const { return v; }
+    __device__ __forceinline__ CSum shfl_down(int off) const {
+        CSum r;
+        r.v = __shfl_down_sync(0xffffffffu, v, off);
+        return r;
+    }
+    __device__ __forceinline__ CSum shfl_up(int off) const {
+        CSum r;
+        r.v = __shfl_up_sync(0xffffffffu, v, off);
+        return r;
+    }
+};
+template <>
+struct CSum<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float s = hi + x, bv = s - hi;
+        const float e = (hi - (s - bv)) + (x - bv);  // hi + x = s + e exactly
+        lo += e;
+        hi = s;
+    }
+    __device__ __forceinline__ void add(const CSum& o) {
+        add(o.hi);
+        lo += o.lo;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+    __device__ __forceinline__ CSum shfl_down(int off) const {
+        CSum r;
+        r.hi = __shfl_down_sync(0xffffffffu, hi, off);
+        r.lo = __shfl_down_sync(0xffffffffu, lo, off);
+        return r;
+    }
+    __device__ __forceinline__ CSum shfl_up(int off) const {
+        CSum r;
+        r.hi = __shfl_up_sync(0xffffffffu, hi, off);
+        r.lo = __shfl_up_sync(0xffffffffu, lo, off);
+        return r;
+    }
+};
+
 // Per-thread check accumulators: the residual maximum in the arithmetic type
-// (a maximum rounds nothing), the mass deviation and the budget in FP64 from
-// the first addition on, then folded per warp and per block in FP64.
+// (a maximum rounds nothing), the mass deviation and the budget as CSum.
 template <class R>
 struct RedR {
-    R rmax;
-    double dmass, budget;
-    int bad, count;
+    R rmax = R(0);
+    CSum<R> dmass, budget;
+    int bad = 0, count = 0;
 };
 
 template <class R>
@@ -595,12 +662,12 @@ __device__ __forceinline__ void block_reduce_store_r(RedR<R> v, double rho0, dou
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         v.rmax = max(v.rmax, __shfl_down_sync(0xffffffffu, v.rmax, off));
-        v.dmass += __shfl_down_sync(0xffffffffu, v.dmass, off);
-        v.budget += __shfl_down_sync(0xffffffffu, v.budget, off);
+        v.dmass.add(v.dmass.shfl_down(off));
+        v.budget.add(v.budget.shfl_down(off));
         v.bad += __shfl_down_sync(0xffffffffu, v.bad, off);
         v.count += __shfl_down_sync(0xffffffffu, v.count, off);
     }
-    Red w{(double)v.rmax, (double)v.count * rho0 + (double)v.dmass, (double)v.budget, (double)v.bad};
+    Red w{(double)v.rmax, (double)v.count * rho0 + v.dmass.value(), v.budget.value(), (double)v.bad};
     __shared__ double sh[4][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = (blockDim.x + 31) >> 5;
@@ -695,7 +762,7 @@ k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
     }
     __syncthreads();
 
-    RedR<R> red{R(0), 0.0, 0.0, 0, 0};
+    RedR<R> red;
     if (warp == kConsumerWarps) {
         // ---------------- producer
         if (lane == 0) {
@@ -747,8 +814,14 @@ k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
             // together below (its lanes meet in __syncwarp)
             const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((it / NS) & 1), kWaitCycles);
             const S* st = sm + s * STAGE;
-            const double rj = node_radius(G, j);
-            const Sc inv_r = rj > 0.0 ? rcp(Sc(rj)) : Sc(0);
+            Sc inv_r;
+            if (sizeof(Sc) == 4 && G.rb_exact) {  // FP32: no FP64 instruction in the loop over tiles
+                const float rj = G.rb + (float)j;
+                inv_r = rj > 0.0f ? rcp(Sc(rj)) : Sc(0);
+            } else {
+                const double rj = node_radius(G, j);
+                inv_r = rj > 0.0 ? rcp(Sc(rj)) : Sc(0);
+            }
 #pragma unroll
             for (int rr = tid / kTileJ; ok && rr < kTileK / NL; rr += kBulkThreads / kTileJ) {
                 bool act[NL];
@@ -838,8 +911,8 @@ k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
                         const R sp = sqrt(vur * vur + vuz * vuz);
                         if (A.residual) red.rmax = max(red.rmax, (R)fabs(sp - sp_old[(rr - tid / kTileJ) / 2 + l]));
                         A.speed[x] = sp;
-                        red.dmass += (double)Lanes<RC>::get(c.ds0, l);
-                        red.budget += (double)vrho * (double)vur * (double)inv_r;
+                        red.dmass.add(Lanes<RC>::get(c.ds0, l));
+                        red.budget.add(vrho * vur * inv_r);
                         red.bad += (isfinite(vrho) && isfinite(vur) && isfinite(vuz)) ? 0 : 1;
                         red.count += 1;
                     }
@@ -967,7 +1040,7 @@ __device__ __forceinline__ void store_pull(const KArgs<S, R>& A, int j, int k, c
             Codec<S>::store(slot(A.pop, G, a, j, k), c.d[a]);
         } else if (!(mirror_col && s.fr)) {
             const int b = idx9(s.fr ? -cr9(a) : cr9(a), s.fz ? -cz9(a) : cz9(a));
-            Codec<S>::store(slot(A.pop, G, opp9(b), s.j, s.k), c.d[a]);
+            Codec<S>::store(site_slot(A, opp9(b), s.j, s.k), c.d[a]);
         }
     }
     if (SW) {
@@ -978,7 +1051,7 @@ __device__ __forceinline__ void store_pull(const KArgs<S, R>& A, int j, int k, c
                 Codec<S>::store(slot(A.pop, G, A.g_plane + q, j, k), bounce_g(G, A.C, s.face, j, c.g[q]));
             } else if (!(mirror_col && s.fr)) {
                 const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
-                Codec<S>::store(slot(A.pop, G, A.g_plane + opp4(b), s.j, s.k), s.fr ? -c.g[q] : c.g[q]);
+                Codec<S>::store(site_slot(A, A.g_plane + opp4(b), s.j, s.k), s.fr ? -c.g[q] : c.g[q]);
             }
         }
     }
@@ -990,7 +1063,7 @@ __device__ __forceinline__ void store_pull(const KArgs<S, R>& A, int j, int k, c
                 Codec<S>::store(slot(A.pop, G, A.h_plane + q, j, k), bounce_h(A.C, s.face, c.h[q]));
             } else if (!(mirror_col && s.fr)) {
                 const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
-                Codec<S>::store(slot(A.pop, G, A.h_plane + opp4(b), s.j, s.k), c.h[q]);
+                Codec<S>::store(site_slot(A, A.h_plane + opp4(b), s.j, s.k), c.h[q]);
             }
         }
     }
@@ -1302,6 +1375,8 @@ template <class S, class R>
 KArgs<S, R> make_args(axlbm_handle* h) {
     KArgs<S, R> A;
     A.pop = reinterpret_cast<S*>(h->mem);
+    A.halo = reinterpret_cast<S*>(h->mem + h->L.off_halo);
+    A.nplanes = h->L.nplanes;
     A.speed = reinterpret_cast<R*>(h->mem + h->L.off_speed);
     A.partials = reinterpret_cast<double*>(h->mem + h->L.off_part);
     A.part_offset = 0;

@@ -1,25 +1,26 @@
 // warmstart.cu -- learned warm start of a batch (initial fields from a CNN).
 //
 // Time to a steady state is set by how far the initial fields are from it.
-// A small convolutional network maps each domain's parameters (kind, aspect
-// ratio, Reynolds, Grashof and Prandtl numbers, rotation ratio), broadcast
-// on a 256 (z) x 128 (r) canvas together with the normalised coordinates, to
-// the steady fields u_r, u_z, u_theta (in units of the lid speed) and T.
-// The canvases are resampled onto every domain's grid and the batch starts
-// from the equilibria of those fields (the same initialisation as
+// A convolutional network maps each domain's parameters (kind, aspect ratio,
+// Reynolds, Grashof and Prandtl numbers, rotation ratio), broadcast on a
+// 256 (z) x 128 (r) canvas together with the normalised coordinates, to the
+// steady fields u_r, u_z, u_theta (in units of the lid speed) and T.  The
+// canvases are resampled onto every domain's grid and the batch starts from
+// the equilibria of those fields (the same initialisation as
 // axlbm_batch_set_fields_all).
 //
-// Network (weights in BF16, accumulation in FP32): a U-Net of 3x3
-// convolutions with ReLU -- 8 -> 32 -> 32 at 256 x 128, 2x2 average pool,
-// 32 -> 64 -> 64 at 128 x 64, pool, 64 -> 128 -> 128 at 64 x 32, nearest
-// upsampling and concatenation with the skip, 192 -> 64 -> 64, upsample,
-// concatenation, 96 -> 32 -> 32, and a 1x1 head 32 -> 4 without activation.
-// Activations are NHWC in BF16.  Each 3x3 convolution is an im2col into a
-// [pixels][9 Cin] matrix followed by one cuBLAS BF16 GEMM with FP32
-// accumulation (a plain library GEMM on the tensor cores) and a fused
-// bias + ReLU + BF16 epilogue; canvases are processed in chunks so that the
-// im2col buffer stays below ~0.5 GB.
-#include <cublas_v2.h>
+// Network (weights in BF16, accumulation in FP32): a four-level U-Net of 3x3
+// convolutions with ReLU, channels 32, 64, 96, 128 at 256 x 128, 128 x 64,
+// 64 x 32 and 32 x 16 -- per level two convolutions (8 -> 32 -> 32 first),
+// 2x2 average pooling between levels -- then, from the bottom up, nearest
+// upsampling and concatenation with the level's skip (deep channels first),
+// two convolutions per level (224 -> 96 -> 96, 160 -> 64 -> 64,
+// 96 -> 32 -> 32), and a 1x1 head 32 -> 4 without activation: 0.91 M weights.
+// Activations are NHWC in BF16.  Every 3x3 convolution -- forward, and in
+// training the input and weight gradients -- is an implicit GEMM of this
+// library on the tensor cores (ws_conv.cuh: mma.sync BF16 with FP32
+// accumulation, operands gathered straight from the activations); no im2col
+// matrix is formed and no GEMM library is called.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -30,18 +31,33 @@
 
 #include "batch_internal.h"
 #include "internal.h"
+#include "ws_conv.cuh"
 
 struct axlbm_ws_train;  // training state (warmstart.cu, below)
 
+namespace {
+
+constexpr int kLevels = 4;
+constexpr int kCh[kLevels] = {32, 64, 96, 128};
+
+// The activations of one pass over n canvases: x0 the input canvas; per
+// encoder level the outputs of its two convolutions (a, e) and the pooled e
+// (p); per decoder level the upsampled deeper output concatenated with the
+// skip (u) and the outputs of its two convolutions (b, d).
+struct Acts {
+    __nv_bfloat16 *x0 = nullptr;
+    __nv_bfloat16 *a[kLevels] = {}, *e[kLevels] = {}, *p[kLevels - 1] = {};
+    __nv_bfloat16 *u[kLevels - 1] = {}, *b[kLevels - 1] = {}, *d[kLevels - 1] = {};
+};
+
+}  // namespace
+
 struct axlbm_ws {
     cudaStream_t stream;
-    cublasHandle_t blas;
     __nv_bfloat16* w;  // all layers, packed as in include/axlbm.h
     std::vector<size_t> woff, boff;
     int chunk;
-    // work buffers for one chunk of canvases
-    __nv_bfloat16 *x0, *e1, *p1, *e2, *p2, *e3, *u2, *d2, *u1, *d1, *tmp, *col;
-    float* y;
+    Acts act;  // one chunk of canvases
     axlbm_ws_train* train;  // allocated by the first training call
     std::string err;
 };
@@ -57,10 +73,14 @@ constexpr int kFeat = AXLBM_WS_FEATURES;
 struct Layer {
     int cin, cout, k;  // k: 3 (3x3, padding 1) or 1
 };
-constexpr int kLayers = 11;
-constexpr Layer kNet[kLayers] = {{8, 32, 3},   {32, 32, 3},  {32, 64, 3},  {64, 64, 3},
-                                 {64, 128, 3}, {128, 128, 3}, {192, 64, 3}, {64, 64, 3},
-                                 {96, 32, 3},  {32, 32, 3},  {32, 4, 1}};
+// encoder levels 0-3 (two layers each), decoder levels 2, 1, 0 (two each), head
+constexpr int kLayers = 15;
+constexpr Layer kNet[kLayers] = {{8, 32, 3},   {32, 32, 3},  {32, 64, 3},  {64, 64, 3},  {64, 96, 3},
+                                 {96, 96, 3},  {96, 128, 3}, {128, 128, 3}, {224, 96, 3}, {96, 96, 3},
+                                 {160, 64, 3}, {64, 64, 3},  {96, 32, 3},  {32, 32, 3},  {32, 4, 1}};
+constexpr int enc_layer(int l) { return 2 * l; }            // first layer of encoder level l
+constexpr int dec_layer(int l) { return 8 + 2 * (2 - l); }  // first layer of decoder level l (0..2)
+constexpr int kHead = 14;
 
 size_t net_values() {
     size_t n = 0;
@@ -86,30 +106,6 @@ __global__ void k_ws_input(const float* feat, int n, bf16* x) {
     for (int f = 0; f < kFeat; ++f) o[f] = __float2bfloat16(feat[b * kFeat + f]);
     o[6] = __float2bfloat16((c + 0.5f) / kW);
     o[7] = __float2bfloat16((r + 0.5f) / kH);
-}
-
-// im2col of a 3x3, padding-1 convolution: col[p][(ky * 3 + kx) * cin + c].
-__global__ void k_ws_im2col(const bf16* x, int n, int h, int w, int cin, bf16* col) {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long k9 = 9ll * cin;
-    const long long total = (long long)n * h * w * k9;
-    if (i >= total) return;
-    const int kk = int(i % k9);
-    const long long p = i / k9;
-    const int c = kk % cin, tap = kk / cin, ky = tap / 3, kx = tap % 3;
-    const int xw = int(p % w), yh = int((p / w) % h), b = int(p / ((long long)h * w));
-    const int yy = yh + ky - 1, xx = xw + kx - 1;
-    bf16 v = __float2bfloat16(0.0f);
-    if (yy >= 0 && yy < h && xx >= 0 && xx < w) v = x[(((long long)b * h + yy) * w + xx) * cin + c];
-    col[i] = v;
-}
-
-// y [p][cout] (FP32) + bias, ReLU, to BF16 NHWC.
-__global__ void k_ws_bias_relu(const float* y, const bf16* bias, long long pixels, int cout, bf16* out) {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= pixels * cout) return;
-    const float v = y[i] + __bfloat162float(bias[i % cout]);
-    out[i] = __float2bfloat16(v > 0.0f ? v : 0.0f);
 }
 
 // 2x2 average pool, NHWC.
@@ -201,58 +197,123 @@ __global__ void k_ws_to_canvas(const float* m, axlbm_ws_domain D, float* canvas)
 
 unsigned blocks_for(long long n) { return (unsigned)((n + 255) / 256); }
 
-cudaError_t conv3(axlbm_ws* w, int layer, const bf16* in, int n, int h, int wd, bf16* out, bf16* col, float* y) {
+// Output channels per block column of the implicit GEMM: 64 where they
+// divide, else 32 (every channel count here is a multiple of 32).
+int conv_bn(int cout) { return cout % 64 == 0 ? 64 : 32; }
+
+// 3x3 convolution of layer `layer` over n canvases of h x wd, with bias,
+// ReLU and BF16 output (the forward pass).
+cudaError_t conv3(axlbm_ws* w, int layer, const bf16* in, int n, int h, int wd, bf16* out) {
+    using namespace axl::wsconv;
     const Layer& L = kNet[layer];
     const long long pixels = (long long)n * h * wd;
-    const long long k9 = 9ll * L.cin;
-    k_ws_im2col<<<blocks_for(pixels * k9), 256, 0, w->stream>>>(in, n, h, wd, L.cin, col);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // y^T (cout x pixels, column-major) = W (cout x k9; stored row-major) * col^T
-    const float one = 1.0f, zero = 0.0f;
-    cublasStatus_t s = cublasGemmEx(w->blas, CUBLAS_OP_T, CUBLAS_OP_N, L.cout, (int)pixels, (int)k9, &one,
-                                    w->w + w->woff[layer], CUDA_R_16BF, (int)k9, col, CUDA_R_16BF, (int)k9, &zero,
-                                    y, CUDA_R_32F, L.cout, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-    if (s != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    k_ws_bias_relu<<<blocks_for(pixels * L.cout), 256, 0, w->stream>>>(y, w->w + w->boff[layer], pixels, L.cout,
-                                                                         out);
+    const int bn = conv_bn(L.cout);
+    const dim3 grid((unsigned)((pixels + kBM - 1) / kBM), (unsigned)(L.cout / bn));
+    const bf16* wt = w->w + w->woff[layer];
+    const bf16* bias = w->w + w->boff[layer];
+    if (bn == 64) k_conv_igemm<64, 0><<<grid, kThreads, 0, w->stream>>>(in, n, h, wd, L.cin, 0, wt, L.cout, bias, out);
+    else k_conv_igemm<32, 0><<<grid, kThreads, 0, w->stream>>>(in, n, h, wd, L.cin, 0, wt, L.cout, bias, out);
     return cudaGetLastError();
 }
 
-cudaError_t forward_chunk(axlbm_ws* w, const float* feat_dev, int n, float* canvas) {
+// Forward pass of n canvases through the network into the activations A,
+// the output canvases into `canvas` (FP32 [n][4][kH][kW]).
+cudaError_t forward_acts(axlbm_ws* w, const float* feat_dev, int n, Acts& A, float* canvas) {
     cudaError_t e;
-    const long long p1 = (long long)n * kH * kW;
-    k_ws_input<<<blocks_for(p1), 256, 0, w->stream>>>(feat_dev, n, w->x0);
+    k_ws_input<<<blocks_for((long long)n * kH * kW), 256, 0, w->stream>>>(feat_dev, n, A.x0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = conv3(w, 0, w->x0, n, kH, kW, w->tmp, w->col, w->y)) != cudaSuccess) return e;
-    if ((e = conv3(w, 1, w->tmp, n, kH, kW, w->e1, w->col, w->y)) != cudaSuccess) return e;
-    k_ws_pool<<<blocks_for(p1 / 4 * 32), 256, 0, w->stream>>>(w->e1, n, kH, kW, 32, w->p1);
-    if ((e = conv3(w, 2, w->p1, n, kH / 2, kW / 2, w->tmp, w->col, w->y)) != cudaSuccess) return e;
-    if ((e = conv3(w, 3, w->tmp, n, kH / 2, kW / 2, w->e2, w->col, w->y)) != cudaSuccess) return e;
-    k_ws_pool<<<blocks_for(p1 / 16 * 64), 256, 0, w->stream>>>(w->e2, n, kH / 2, kW / 2, 64, w->p2);
-    if ((e = conv3(w, 4, w->p2, n, kH / 4, kW / 4, w->tmp, w->col, w->y)) != cudaSuccess) return e;
-    if ((e = conv3(w, 5, w->tmp, n, kH / 4, kW / 4, w->e3, w->col, w->y)) != cudaSuccess) return e;
-    k_ws_up_concat<<<blocks_for(p1 / 4 * 192), 256, 0, w->stream>>>(w->e3, w->e2, n, kH / 2, kW / 2, 128, 64, w->u2);
-    if ((e = conv3(w, 6, w->u2, n, kH / 2, kW / 2, w->tmp, w->col, w->y)) != cudaSuccess) return e;
-    if ((e = conv3(w, 7, w->tmp, n, kH / 2, kW / 2, w->d2, w->col, w->y)) != cudaSuccess) return e;
-    k_ws_up_concat<<<blocks_for(p1 * 96), 256, 0, w->stream>>>(w->d2, w->e1, n, kH, kW, 64, 32, w->u1);
-    if ((e = conv3(w, 8, w->u1, n, kH, kW, w->tmp, w->col, w->y)) != cudaSuccess) return e;
-    if ((e = conv3(w, 9, w->tmp, n, kH, kW, w->d1, w->col, w->y)) != cudaSuccess) return e;
-    k_ws_head<<<blocks_for(p1), 256, 0, w->stream>>>(w->d1, w->w + w->woff[10], w->w + w->boff[10], n, canvas);
+    const bf16* in = A.x0;
+    for (int l = 0; l < kLevels; ++l) {  // encoder
+        const int h = kH >> l, wd = kW >> l;
+        if ((e = conv3(w, enc_layer(l), in, n, h, wd, A.a[l])) != cudaSuccess) return e;
+        if ((e = conv3(w, enc_layer(l) + 1, A.a[l], n, h, wd, A.e[l])) != cudaSuccess) return e;
+        if (l + 1 < kLevels) {
+            k_ws_pool<<<blocks_for((long long)n * (h / 2) * (wd / 2) * kCh[l]), 256, 0, w->stream>>>(
+                A.e[l], n, h, wd, kCh[l], A.p[l]);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            in = A.p[l];
+        }
+    }
+    const bf16* deep = A.e[kLevels - 1];
+    for (int l = kLevels - 2; l >= 0; --l) {  // decoder
+        const int h = kH >> l, wd = kW >> l, cd = kCh[l + 1], cs = kCh[l];
+        k_ws_up_concat<<<blocks_for((long long)n * h * wd * (cd + cs)), 256, 0, w->stream>>>(deep, A.e[l], n, h, wd, cd,
+                                                                                           cs, A.u[l]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = conv3(w, dec_layer(l), A.u[l], n, h, wd, A.b[l])) != cudaSuccess) return e;
+        if ((e = conv3(w, dec_layer(l) + 1, A.b[l], n, h, wd, A.d[l])) != cudaSuccess) return e;
+        deep = A.d[l];
+    }
+    k_ws_head<<<blocks_for((long long)n * kH * kW), 256, 0, w->stream>>>(A.d[0], w->w + w->woff[kHead],
+                                                                          w->w + w->boff[kHead], n, canvas);
     return cudaGetLastError();
+}
+
+// Sizes (values) of the activations of n canvases, in the order acts_ptrs lists them.
+std::vector<size_t> acts_sizes(int n) {
+    const size_t P0 = (size_t)n * kH * kW;
+    std::vector<size_t> v;
+    v.push_back(P0 * 8);
+    for (int l = 0; l < kLevels; ++l) {
+        const size_t P = P0 >> (2 * l);
+        v.push_back(P * kCh[l]);                   // a
+        v.push_back(P * kCh[l]);                   // e
+        if (l + 1 < kLevels) v.push_back(P / 4 * kCh[l]);  // p
+    }
+    for (int l = 0; l + 1 < kLevels; ++l) {
+        const size_t P = P0 >> (2 * l);
+        v.push_back(P * (kCh[l] + kCh[l + 1]));    // u
+        v.push_back(P * kCh[l]);                   // b
+        v.push_back(P * kCh[l]);                   // d
+    }
+    return v;
+}
+std::vector<bf16**> acts_ptrs(Acts& A) {
+    std::vector<bf16**> v;
+    v.push_back(&A.x0);
+    for (int l = 0; l < kLevels; ++l) {
+        v.push_back(&A.a[l]);
+        v.push_back(&A.e[l]);
+        if (l + 1 < kLevels) v.push_back(&A.p[l]);
+    }
+    for (int l = 0; l + 1 < kLevels; ++l) {
+        v.push_back(&A.u[l]);
+        v.push_back(&A.b[l]);
+        v.push_back(&A.d[l]);
+    }
+    return v;
+}
+bool acts_alloc(Acts& A, int n) {
+    const std::vector<size_t> sz = acts_sizes(n);
+    const std::vector<bf16**> ps = acts_ptrs(A);
+    for (size_t i = 0; i < ps.size(); ++i) {
+        if (cudaMalloc(ps[i], sz[i] * sizeof(bf16)) != cudaSuccess) {
+            cudaGetLastError();
+            *ps[i] = nullptr;
+            return false;
+        }
+    }
+    return true;
+}
+void acts_free(Acts& A) {
+    for (bf16** p : acts_ptrs(A)) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
 }
 
 // ---------------------------------------------------------------- training
 //
 // One training step on up to kTrainMax canvases: the forward pass keeps every
 // layer's output; the loss is the mean squared error over the canvases; the
-// backward pass runs through the head, the ReLU masks, the convolutions
-// (weight gradient dW = col^T dY and input gradient col2im(dY W), both cuBLAS
-// BF16 GEMMs with FP32 accumulation, the im2col recomputed from the kept
-// input), the concatenations and the pools; Adam then updates FP32 master
-// weights and rewrites the BF16 weights the forward pass uses.  Reductions
-// (loss, biases, head) go through per-block partials summed in a fixed order,
-// so a step is deterministic.
+// backward pass runs through the head, the ReLU masks, the convolutions (the
+// weight gradient dW[o][k] = sum_p dY[p][o] A[p][k] and the input gradient,
+// a convolution of dY with the mirrored taps, both implicit GEMMs of
+// ws_conv.cuh with FP32 accumulation), the concatenations and the pools; Adam
+// then updates FP32 master weights and rewrites the BF16 weights the forward
+// pass uses.  Reductions (loss, biases, head, weight gradients over pixel
+// ranges) go through partials summed in a fixed order, so a step is
+// deterministic.
 
 constexpr int kTrainMax = 16;      // canvases per training step
 constexpr int kRowsPerBlock = 2048;  // rows of one reduction block
@@ -286,15 +347,17 @@ __global__ void k_ws_sum_double(const double* part, int n, double* out) {
     }
 }
 
-// Column sums of x [rows][cols] (cols divides 256): per-block partials
+// Column sums of x [rows][cols] (cols <= 256): per-block partials
 // part[block][cols] over rows [block * kRowsPerBlock, ...).
 __global__ void k_ws_colsum(const bf16* x, long long rows, int cols, float* part) {
     __shared__ float sh[256];
-    const int c = threadIdx.x % cols, ph = threadIdx.x / cols, nph = blockDim.x / cols;
+    const int nph = blockDim.x / cols;
+    const int c = threadIdx.x % cols, ph = threadIdx.x / cols;
     const long long r0 = (long long)blockIdx.x * kRowsPerBlock;
     const long long r1 = r0 + kRowsPerBlock < rows ? r0 + kRowsPerBlock : rows;
     float s = 0.0f;
-    for (long long r = r0 + ph; r < r1; r += nph) s += __bfloat162float(x[r * cols + c]);
+    if (ph < nph)
+        for (long long r = r0 + ph; r < r1; r += nph) s += __bfloat162float(x[r * cols + c]);
     sh[threadIdx.x] = s;
     __syncthreads();
     if (ph == 0) {
@@ -349,29 +412,6 @@ __global__ void k_ws_mask(const float* g, const float* g2, const bf16* act, long
     if (i >= count) return;
     const float v = g[i] + (g2 ? g2[i] : 0.0f);
     dy[i] = __float2bfloat16(__bfloat162float(act[i]) > 0.0f ? v : 0.0f);
-}
-
-// Input gradient of a 3x3 convolution from the gradient of its im2col
-// matrix: gx[b][y][x][c] = sum over taps of dcol at the output pixel that
-// read (y, x) through that tap.
-__global__ void k_ws_col2im(const bf16* dcol, int n, int h, int w, int cin, float* gx) {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= (long long)n * h * w * cin) return;
-    const int c = int(i % cin);
-    const long long p = i / cin;
-    const int xw = int(p % w), yh = int((p / w) % h), b = int(p / ((long long)h * w));
-    const long long k9 = 9ll * cin;
-    float s = 0.0f;
-    for (int ky = 0; ky < 3; ++ky) {
-        const int yy = yh - ky + 1;
-        if (yy < 0 || yy >= h) continue;
-        for (int kx = 0; kx < 3; ++kx) {
-            const int xx = xw - kx + 1;
-            if (xx < 0 || xx >= w) continue;
-            s += __bfloat162float(dcol[(((long long)b * h + yy) * w + xx) * k9 + (ky * 3 + kx) * cin + c]);
-        }
-    }
-    gx[i] = s;
 }
 
 // Backward of the nearest upsampling + concatenation (h x w output, deep
@@ -432,26 +472,42 @@ __global__ void k_bf16_to_f32(const bf16* x, size_t count, float* y) {
 // Training state: FP32 master weights, their gradients and Adam moments, and
 // every activation of one step's forward pass (sized for kTrainMax canvases).
 struct axlbm_ws_train {
-    float *master, *grad, *m, *v;
-    int64_t step;
-    bf16 *x0, *a0, *e1, *p1, *a2, *e2, *p2, *a4, *e3, *u2, *a6, *d2, *u1, *a8, *d1;
-    bf16 *col, *dcol, *dy;
-    float *y, *out, *dout, *gx, *gx2, *gs1, *gs2, *part;
-    double *dpart, *loss;
+    float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    int64_t step = 0;
+    Acts act;            // every activation of the kept forward pass
+    bf16* dy = nullptr;  // gradient of a layer's pre-activation output (BF16, the GEMM operand)
+    bf16* wtt = nullptr; // the mirrored-tap weights of the input gradient of one layer
+    float *out = nullptr, *dout = nullptr, *gx = nullptr, *gx2 = nullptr, *part = nullptr, *wpart = nullptr;
+    float* gs[kLevels - 1] = {};  // gradients reaching the skips
+    double *dpart = nullptr, *loss = nullptr;
 };
 
 namespace {
 
 constexpr int kLossBlocks = 1024;
+constexpr int kSplitPixels = 2048;  // pixels per partial of a weight gradient
 
 void train_free(axlbm_ws_train* t) {
     if (!t) return;
-    void* ps[] = {t->master, t->grad, t->m, t->v, t->x0, t->a0, t->e1, t->p1, t->a2, t->e2, t->p2, t->a4, t->e3,
-                  t->u2, t->a6, t->d2, t->u1, t->a8, t->d1, t->col, t->dcol, t->dy, t->y, t->out, t->dout,
-                  t->gx, t->gx2, t->gs1, t->gs2, t->part, t->dpart, t->loss};
+    acts_free(t->act);
+    void* ps[] = {t->master, t->grad, t->m, t->v, t->dy, t->wtt, t->out, t->dout, t->gx, t->gx2, t->part, t->wpart,
+                  t->gs[0], t->gs[1], t->gs[2], t->dpart, t->loss};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete t;
+}
+
+// Values of the largest weight-gradient partial buffer of a training step.
+size_t wpart_values() {
+    size_t best = 0;
+    for (int l = 0; l < kHead; ++l) {
+        const int lev = l < 8 ? l / 2 : 2 - (l - 8) / 2;  // level of layer l
+        const size_t P = (size_t)kTrainMax * (kH >> lev) * (kW >> lev);
+        const size_t nsplit = (P + kSplitPixels - 1) / kSplitPixels;
+        const size_t v = nsplit * kNet[l].cout * 9 * kNet[l].cin;
+        if (v > best) best = v;
+    }
+    return best;
 }
 
 // Allocate the training state; the master weights start from the BF16 weights.
@@ -460,27 +516,29 @@ axlbm_status train_ensure(axlbm_ws* w) {
     axlbm_ws_train* t = new (std::nothrow) axlbm_ws_train();
     if (!t) return wfail(w, AXLBM_ENOMEM, "host allocation failed");
     const size_t count = net_values();
-    const size_t P = (size_t)kTrainMax * kH * kW;  // level-1 pixels
+    const size_t P = (size_t)kTrainMax * kH * kW;  // level-0 pixels
+    size_t wtt = 0;
+    for (int l = 0; l < kHead; ++l) wtt = std::max(wtt, (size_t)9 * kNet[l].cin * kNet[l].cout);
     struct Buf { void** p; size_t bytes; };
     const Buf bufs[] = {
         {(void**)&t->master, count * 4}, {(void**)&t->grad, count * 4}, {(void**)&t->m, count * 4},
-        {(void**)&t->v, count * 4},      {(void**)&t->x0, P * 8 * 2},   {(void**)&t->a0, P * 32 * 2},
-        {(void**)&t->e1, P * 32 * 2},    {(void**)&t->p1, P / 4 * 32 * 2}, {(void**)&t->a2, P / 4 * 64 * 2},
-        {(void**)&t->e2, P / 4 * 64 * 2}, {(void**)&t->p2, P / 16 * 64 * 2}, {(void**)&t->a4, P / 16 * 128 * 2},
-        {(void**)&t->e3, P / 16 * 128 * 2}, {(void**)&t->u2, P / 4 * 192 * 2}, {(void**)&t->a6, P / 4 * 64 * 2},
-        {(void**)&t->d2, P / 4 * 64 * 2}, {(void**)&t->u1, P * 96 * 2},  {(void**)&t->a8, P * 32 * 2},
-        {(void**)&t->d1, P * 32 * 2},    {(void**)&t->col, P * 864 * 2}, {(void**)&t->dcol, P * 864 * 2},
-        {(void**)&t->dy, P * 32 * 2},    {(void**)&t->y, P * 32 * 4},   {(void**)&t->out, P * 4 * 4},
-        {(void**)&t->dout, P * 4 * 4},   {(void**)&t->gx, P * 96 * 4},  {(void**)&t->gx2, P * 32 * 4},
-        {(void**)&t->gs1, P * 32 * 4},   {(void**)&t->gs2, P / 4 * 64 * 4},
-        {(void**)&t->part, (P / kRowsPerBlock + 1) * 132 * 4}, {(void**)&t->dpart, kLossBlocks * 8},
-        {(void**)&t->loss, 8}};
+        {(void**)&t->v, count * 4},      {(void**)&t->dy, P * 32 * 2},  {(void**)&t->wtt, wtt * 2},
+        {(void**)&t->out, P * 4 * 4},    {(void**)&t->dout, P * 4 * 4}, {(void**)&t->gx, P * 96 * 4},
+        {(void**)&t->gx2, P * 32 * 4},   {(void**)&t->part, (P / kRowsPerBlock + 1) * 132 * 4},
+        {(void**)&t->wpart, wpart_values() * 4},
+        {(void**)&t->gs[0], P * kCh[0] * 4}, {(void**)&t->gs[1], P / 4 * kCh[1] * 4},
+        {(void**)&t->gs[2], P / 16 * kCh[2] * 4}, {(void**)&t->dpart, kLossBlocks * 8}, {(void**)&t->loss, 8}};
     for (const Buf& b : bufs) {
         if (cudaMalloc(b.p, b.bytes) != cudaSuccess) {
             cudaGetLastError();
+            *b.p = nullptr;
             train_free(t);
             return wfail(w, AXLBM_ENOMEM, "training buffers");
         }
+    }
+    if (!acts_alloc(t->act, kTrainMax)) {
+        train_free(t);
+        return wfail(w, AXLBM_ENOMEM, "training activations");
     }
     cudaError_t e = cudaMemsetAsync(t->m, 0, count * 4, w->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(t->v, 0, count * 4, w->stream);
@@ -499,27 +557,7 @@ axlbm_status train_ensure(axlbm_ws* w) {
 
 // Forward pass of n <= kTrainMax canvases keeping every layer's output.
 cudaError_t train_forward(axlbm_ws* w, const float* feat, int n) {
-    axlbm_ws_train* t = w->train;
-    cudaError_t e;
-    const long long p1 = (long long)n * kH * kW;
-    k_ws_input<<<blocks_for(p1), 256, 0, w->stream>>>(feat, n, t->x0);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = conv3(w, 0, t->x0, n, kH, kW, t->a0, t->col, t->y)) != cudaSuccess) return e;
-    if ((e = conv3(w, 1, t->a0, n, kH, kW, t->e1, t->col, t->y)) != cudaSuccess) return e;
-    k_ws_pool<<<blocks_for(p1 / 4 * 32), 256, 0, w->stream>>>(t->e1, n, kH, kW, 32, t->p1);
-    if ((e = conv3(w, 2, t->p1, n, kH / 2, kW / 2, t->a2, t->col, t->y)) != cudaSuccess) return e;
-    if ((e = conv3(w, 3, t->a2, n, kH / 2, kW / 2, t->e2, t->col, t->y)) != cudaSuccess) return e;
-    k_ws_pool<<<blocks_for(p1 / 16 * 64), 256, 0, w->stream>>>(t->e2, n, kH / 2, kW / 2, 64, t->p2);
-    if ((e = conv3(w, 4, t->p2, n, kH / 4, kW / 4, t->a4, t->col, t->y)) != cudaSuccess) return e;
-    if ((e = conv3(w, 5, t->a4, n, kH / 4, kW / 4, t->e3, t->col, t->y)) != cudaSuccess) return e;
-    k_ws_up_concat<<<blocks_for(p1 / 4 * 192), 256, 0, w->stream>>>(t->e3, t->e2, n, kH / 2, kW / 2, 128, 64, t->u2);
-    if ((e = conv3(w, 6, t->u2, n, kH / 2, kW / 2, t->a6, t->col, t->y)) != cudaSuccess) return e;
-    if ((e = conv3(w, 7, t->a6, n, kH / 2, kW / 2, t->d2, t->col, t->y)) != cudaSuccess) return e;
-    k_ws_up_concat<<<blocks_for(p1 * 96), 256, 0, w->stream>>>(t->d2, t->e1, n, kH, kW, 64, 32, t->u1);
-    if ((e = conv3(w, 8, t->u1, n, kH, kW, t->a8, t->col, t->y)) != cudaSuccess) return e;
-    if ((e = conv3(w, 9, t->a8, n, kH, kW, t->d1, t->col, t->y)) != cudaSuccess) return e;
-    k_ws_head<<<blocks_for(p1), 256, 0, w->stream>>>(t->d1, w->w + w->woff[10], w->w + w->boff[10], n, t->out);
-    return cudaGetLastError();
+    return forward_acts(w, feat, n, w->train->act, w->train->out);
 }
 
 // Sum of squared errors of the kept prediction against target into t->loss
@@ -536,74 +574,70 @@ cudaError_t train_loss(axlbm_ws* w, const float* target, int n, bool grad) {
 // gradient of its pre-activation output in t->dy: bias and weight gradients
 // into t->grad, and the input gradient into gx (FP32) unless gx is null.
 cudaError_t conv_bwd(axlbm_ws* w, int l, const bf16* in, int n, int h, int wd, float* gx) {
+    using namespace axl::wsconv;
     axlbm_ws_train* t = w->train;
     const Layer& L = kNet[l];
-    const long long P = (long long)n * h * wd, k9 = 9ll * L.cin;
-    k_ws_im2col<<<blocks_for(P * k9), 256, 0, w->stream>>>(in, n, h, wd, L.cin, t->col);
+    cudaStream_t st = w->stream;
+    const long long P = (long long)n * h * wd;
+    const int K = 9 * L.cin;
     const int nb = (int)((P + kRowsPerBlock - 1) / kRowsPerBlock);
-    k_ws_colsum<<<nb, 256, 0, w->stream>>>(t->dy, P, L.cout, t->part);
-    k_ws_fold<<<1, 128, 0, w->stream>>>(t->part, nb, L.cout, t->grad + w->boff[l]);
+    k_ws_colsum<<<nb, 256, 0, st>>>(t->dy, P, L.cout, t->part);
+    k_ws_fold<<<1, 128, 0, st>>>(t->part, nb, L.cout, t->grad + w->boff[l]);
+    const int nsplit = (int)((P + kSplitPixels - 1) / kSplitPixels);
+    const dim3 gw((unsigned)((K + kWgN - 1) / kWgN), (unsigned)(L.cout / 32), (unsigned)nsplit);
+    k_conv_wgrad<<<gw, kThreads, 0, st>>>(t->dy, in, n, h, wd, L.cin, L.cout, kSplitPixels, t->wpart);
+    const long long cnt = (long long)L.cout * K;
+    k_fold_splits<<<blocks_for(cnt), 256, 0, st>>>(t->wpart, nsplit, cnt, t->grad + w->woff[l]);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const float one = 1.0f, zero = 0.0f;
-    // dW (k9 x cout, column-major = the [cout][k9] packing) = col (k9 x P) dy^T
-    cublasStatus_t s = cublasGemmEx(w->blas, CUBLAS_OP_N, CUBLAS_OP_T, (int)k9, L.cout, (int)P, &one, t->col,
-                                    CUDA_R_16BF, (int)k9, t->dy, CUDA_R_16BF, L.cout, &zero, t->grad + w->woff[l],
-                                    CUDA_R_32F, (int)k9, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-    if (s != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    if (!gx) return cudaSuccess;
-    // dcol (k9 x P) = W (k9 x cout) dy (cout x P), then back onto the input pixels
-    s = cublasGemmEx(w->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)k9, (int)P, L.cout, &one, w->w + w->woff[l],
-                     CUDA_R_16BF, (int)k9, t->dy, CUDA_R_16BF, L.cout, &zero, t->dcol, CUDA_R_16BF, (int)k9,
-                     CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-    if (s != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    k_ws_col2im<<<blocks_for(P * L.cin), 256, 0, w->stream>>>(t->dcol, n, h, wd, L.cin, gx);
+    if (e != cudaSuccess || !gx) return e;
+    // the input gradient: dy convolved with the mirrored taps of Wt[c][tap][o]
+    k_transpose_taps<<<blocks_for(cnt), 256, 0, st>>>(w->w + w->woff[l], L.cout, L.cin, t->wtt);
+    const int bn = conv_bn(L.cin);
+    const dim3 gi((unsigned)((P + kBM - 1) / kBM), (unsigned)(L.cin / bn));
+    if (bn == 64) k_conv_igemm<64, 1><<<gi, kThreads, 0, st>>>(t->dy, n, h, wd, L.cout, 1, t->wtt, L.cin, nullptr, gx);
+    else k_conv_igemm<32, 1><<<gi, kThreads, 0, st>>>(t->dy, n, h, wd, L.cout, 1, t->wtt, L.cin, nullptr, gx);
     return cudaGetLastError();
 }
 
 // Backward pass of the kept forward pass from t->dout, gradients into t->grad.
 cudaError_t train_backward(axlbm_ws* w, int n) {
     axlbm_ws_train* t = w->train;
-    const int H = kH, W = kW;
-    const long long P1 = (long long)n * H * W, P2 = P1 / 4, P3 = P1 / 16;
+    Acts& A = t->act;
     cudaStream_t st = w->stream;
     cudaError_t e;
+    const long long P0 = (long long)n * kH * kW;
     // head (packed kernel then bias: 132 contiguous values)
-    const int nb = (int)((P1 + kRowsPerBlock - 1) / kRowsPerBlock);
-    k_ws_head_wgrad<<<nb, 160, 0, st>>>(t->dout, t->d1, n, t->part);
-    k_ws_fold<<<1, 160, 0, st>>>(t->part, nb, 132, t->grad + w->woff[10]);
-    k_ws_head_dx<<<blocks_for(P1 * 32), 256, 0, st>>>(t->dout, w->w + w->woff[10], t->d1, n, t->dy);
+    const int nb = (int)((P0 + kRowsPerBlock - 1) / kRowsPerBlock);
+    k_ws_head_wgrad<<<nb, 160, 0, st>>>(t->dout, A.d[0], n, t->part);
+    k_ws_fold<<<1, 160, 0, st>>>(t->part, nb, 132, t->grad + w->woff[kHead]);
+    k_ws_head_dx<<<blocks_for(P0 * 32), 256, 0, st>>>(t->dout, w->w + w->woff[kHead], A.d[0], n, t->dy);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // decoder, level 1
-    if ((e = conv_bwd(w, 9, t->a8, n, H, W, t->gx)) != cudaSuccess) return e;
-    k_ws_mask<<<blocks_for(P1 * 32), 256, 0, st>>>(t->gx, nullptr, t->a8, P1 * 32, t->dy);
-    if ((e = conv_bwd(w, 8, t->u1, n, H, W, t->gx)) != cudaSuccess) return e;
-    k_ws_upcat_bwd_deep<<<blocks_for(P2 * 64), 256, 0, st>>>(t->gx, n, H, W, 64, 32, t->gx2);
-    k_ws_upcat_bwd_skip<<<blocks_for(P1 * 32), 256, 0, st>>>(t->gx, P1, 64, 32, t->gs1);
-    // decoder, level 2
-    k_ws_mask<<<blocks_for(P2 * 64), 256, 0, st>>>(t->gx2, nullptr, t->d2, P2 * 64, t->dy);
-    if ((e = conv_bwd(w, 7, t->a6, n, H / 2, W / 2, t->gx)) != cudaSuccess) return e;
-    k_ws_mask<<<blocks_for(P2 * 64), 256, 0, st>>>(t->gx, nullptr, t->a6, P2 * 64, t->dy);
-    if ((e = conv_bwd(w, 6, t->u2, n, H / 2, W / 2, t->gx)) != cudaSuccess) return e;
-    k_ws_upcat_bwd_deep<<<blocks_for(P3 * 128), 256, 0, st>>>(t->gx, n, H / 2, W / 2, 128, 64, t->gx2);
-    k_ws_upcat_bwd_skip<<<blocks_for(P2 * 64), 256, 0, st>>>(t->gx, P2, 128, 64, t->gs2);
-    // bottom, level 3
-    k_ws_mask<<<blocks_for(P3 * 128), 256, 0, st>>>(t->gx2, nullptr, t->e3, P3 * 128, t->dy);
-    if ((e = conv_bwd(w, 5, t->a4, n, H / 4, W / 4, t->gx)) != cudaSuccess) return e;
-    k_ws_mask<<<blocks_for(P3 * 128), 256, 0, st>>>(t->gx, nullptr, t->a4, P3 * 128, t->dy);
-    if ((e = conv_bwd(w, 4, t->p2, n, H / 4, W / 4, t->gx)) != cudaSuccess) return e;
-    // encoder, level 2 (e2 feeds the pool and the skip)
-    k_ws_pool_bwd<<<blocks_for(P2 * 64), 256, 0, st>>>(t->gx, n, H / 2, W / 2, 64, t->gx2);
-    k_ws_mask<<<blocks_for(P2 * 64), 256, 0, st>>>(t->gx2, t->gs2, t->e2, P2 * 64, t->dy);
-    if ((e = conv_bwd(w, 3, t->a2, n, H / 2, W / 2, t->gx)) != cudaSuccess) return e;
-    k_ws_mask<<<blocks_for(P2 * 64), 256, 0, st>>>(t->gx, nullptr, t->a2, P2 * 64, t->dy);
-    if ((e = conv_bwd(w, 2, t->p1, n, H / 2, W / 2, t->gx)) != cudaSuccess) return e;
-    // encoder, level 1 (e1 feeds the pool and the skip)
-    k_ws_pool_bwd<<<blocks_for(P1 * 32), 256, 0, st>>>(t->gx, n, H, W, 32, t->gx2);
-    k_ws_mask<<<blocks_for(P1 * 32), 256, 0, st>>>(t->gx2, t->gs1, t->e1, P1 * 32, t->dy);
-    if ((e = conv_bwd(w, 1, t->a0, n, H, W, t->gx)) != cudaSuccess) return e;
-    k_ws_mask<<<blocks_for(P1 * 32), 256, 0, st>>>(t->gx, nullptr, t->a0, P1 * 32, t->dy);
-    if ((e = conv_bwd(w, 0, t->x0, n, H, W, nullptr)) != cudaSuccess) return e;
+    // decoder levels 0, 1, 2; t->dy holds the gradient of the level's second convolution
+    for (int l = 0; l + 1 < kLevels; ++l) {
+        const int h = kH >> l, wd = kW >> l, cd = kCh[l + 1], cs = kCh[l];
+        const long long P = P0 >> (2 * l);
+        if ((e = conv_bwd(w, dec_layer(l) + 1, A.b[l], n, h, wd, t->gx)) != cudaSuccess) return e;
+        k_ws_mask<<<blocks_for(P * cs), 256, 0, st>>>(t->gx, nullptr, A.b[l], P * cs, t->dy);
+        if ((e = conv_bwd(w, dec_layer(l), A.u[l], n, h, wd, t->gx)) != cudaSuccess) return e;
+        k_ws_upcat_bwd_deep<<<blocks_for(P / 4 * cd), 256, 0, st>>>(t->gx, n, h, wd, cd, cs, t->gx2);
+        k_ws_upcat_bwd_skip<<<blocks_for(P * cs), 256, 0, st>>>(t->gx, P, cd, cs, t->gs[l]);
+        const bf16* deep = l + 2 < kLevels ? A.d[l + 1] : A.e[kLevels - 1];
+        k_ws_mask<<<blocks_for(P / 4 * cd), 256, 0, st>>>(t->gx2, nullptr, deep, P / 4 * cd, t->dy);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // encoder levels 3 .. 0; t->gx holds the gradient of the pooled output of the level
+    for (int l = kLevels - 1; l >= 0; --l) {
+        const int h = kH >> l, wd = kW >> l, c = kCh[l];
+        const long long P = P0 >> (2 * l);
+        if (l + 1 < kLevels) {  // e[l] feeds the pool and the skip
+            k_ws_pool_bwd<<<blocks_for(P * c), 256, 0, st>>>(t->gx, n, h, wd, c, t->gx2);
+            k_ws_mask<<<blocks_for(P * c), 256, 0, st>>>(t->gx2, t->gs[l], A.e[l], P * c, t->dy);
+        }
+        if ((e = conv_bwd(w, enc_layer(l) + 1, A.a[l], n, h, wd, t->gx)) != cudaSuccess) return e;
+        k_ws_mask<<<blocks_for(P * c), 256, 0, st>>>(t->gx, nullptr, A.a[l], P * c, t->dy);
+        if ((e = conv_bwd(w, enc_layer(l), l ? A.p[l - 1] : A.x0, n, h, wd, l ? t->gx : nullptr)) != cudaSuccess)
+            return e;
+    }
     return cudaGetLastError();
 }
 
@@ -617,6 +651,10 @@ axlbm_status axlbm_ws_create(const uint16_t* weights, size_t count, void* cuda_s
     if (!out || !weights) return wfail(nullptr, AXLBM_EINVAL, "weights and out are required");
     if (count != net_values()) return wfail(nullptr, AXLBM_EINVAL, "weight count does not match the network");
     axlbm_ws* w = new (std::nothrow) axlbm_ws();
+    if (w) {
+        w->w = nullptr;
+        w->train = nullptr;
+    }
     if (!w) return wfail(nullptr, AXLBM_ENOMEM, "host allocation failed");
     w->stream = static_cast<cudaStream_t>(cuda_stream);
     w->chunk = 8;
@@ -627,30 +665,16 @@ axlbm_status axlbm_ws_create(const uint16_t* weights, size_t count, void* cuda_s
         w->boff.push_back(off);
         off += l.cout;
     }
-    const size_t c = (size_t)w->chunk, p1 = c * kH * kW;
-    struct Buf { void** p; size_t bytes; };
-    const Buf bufs[] = {{(void**)&w->w, count * 2},        {(void**)&w->x0, p1 * 8 * 2},
-                        {(void**)&w->e1, p1 * 32 * 2},     {(void**)&w->p1, p1 / 4 * 32 * 2},
-                        {(void**)&w->e2, p1 / 4 * 64 * 2}, {(void**)&w->p2, p1 / 16 * 64 * 2},
-                        {(void**)&w->e3, p1 / 16 * 128 * 2}, {(void**)&w->u2, p1 / 4 * 192 * 2},
-                        {(void**)&w->d2, p1 / 4 * 64 * 2}, {(void**)&w->u1, p1 * 96 * 2},
-                        {(void**)&w->d1, p1 * 32 * 2},     {(void**)&w->tmp, p1 * 32 * 2},
-                        {(void**)&w->col, p1 * 96 * 9 * 2}, {(void**)&w->y, p1 * 32 * 4}};
-    for (const Buf& b : bufs) {
-        if (cudaMalloc(b.p, b.bytes) != cudaSuccess) {
-            cudaGetLastError();
-            axlbm_ws_destroy(w);
-            return wfail(nullptr, AXLBM_ENOMEM, "device allocation failed");
-        }
+    if (cudaMalloc(&w->w, count * 2) != cudaSuccess || !acts_alloc(w->act, w->chunk)) {
+        cudaGetLastError();
+        axlbm_ws_destroy(w);
+        return wfail(nullptr, AXLBM_ENOMEM, "device allocation failed");
     }
-    // the widest intermediate of a level must fit `tmp` (64 x 128 x 64 channels
-    // at level 2, 128 channels at level 3): all are <= p1 * 32 values
     cudaError_t e = cudaMemcpyAsync(w->w, weights, count * 2, cudaMemcpyHostToDevice, w->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
-    if (e != cudaSuccess || cublasCreate(&w->blas) != CUBLAS_STATUS_SUCCESS ||
-        cublasSetStream(w->blas, w->stream) != CUBLAS_STATUS_SUCCESS) {
+    if (e != cudaSuccess) {
         axlbm_ws_destroy(w);
-        return wfail(nullptr, AXLBM_ECUDA, "weights upload or cuBLAS set-up failed");
+        return wfail(nullptr, AXLBM_ECUDA, "weights upload failed");
     }
     *out = w;
     return AXLBM_OK;
@@ -668,7 +692,7 @@ axlbm_status axlbm_ws_predict(axlbm_ws* w, const float* features, int32_t n, flo
     e = cudaMemcpyAsync(fd, features, (size_t)n * kFeat * sizeof(float), cudaMemcpyHostToDevice, w->stream);
     for (int b0 = 0; b0 < n && e == cudaSuccess; b0 += w->chunk) {
         const int m = n - b0 < w->chunk ? n - b0 : w->chunk;
-        e = forward_chunk(w, fd + (size_t)b0 * kFeat, m, canvas + (size_t)b0 * 4 * kH * kW);
+        e = forward_acts(w, fd + (size_t)b0 * kFeat, m, w->act, canvas + (size_t)b0 * 4 * kH * kW);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
     cudaFree(fd);
@@ -776,10 +800,8 @@ axlbm_status axlbm_ws_to_canvas(axlbm_ws* w, const float* moments, int32_t n, co
 axlbm_status axlbm_ws_destroy(axlbm_ws* w) {
     if (!w) return AXLBM_EINVAL;
     train_free(w->train);
-    if (w->blas) cublasDestroy(w->blas);
-    void* ps[] = {w->w, w->x0, w->e1, w->p1, w->e2, w->p2, w->e3, w->u2, w->d2, w->u1, w->d1, w->tmp, w->col, w->y};
-    for (void* p : ps)
-        if (p) cudaFree(p);
+    acts_free(w->act);
+    if (w->w) cudaFree(w->w);
     delete w;
     return AXLBM_OK;
 }

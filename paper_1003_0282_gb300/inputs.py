@@ -34,6 +34,7 @@ PERIODIC = "periodic"
 FREE = "free"
 MIXED = "mixed"  # top only: wall for r < r_split, free surface beyond
 ZOU_HE = "zou_he"  # outer face only: Zou-He wall through the last column (pipes)
+HALO = "halo"    # a cut through a larger domain (z-slab decomposition): populations cross to the neighbour slab
 NEE = "nee"      # wet wall: the node row (or, as ``outer``, the last column) lies on the wall and is
                  # rebuilt by non-equilibrium extrapolation from its inner neighbour
 

@@ -1,7 +1,8 @@
 """Running domains to a steady state, with a JSON-lines progress log.
 
 A domain is steady when the residual of Eq. 57 (the largest change of the
-in-plane speed between two consecutive levels) is at or below a tolerance.
+in-plane speed per step, between two consecutive levels or, with the
+solver's residual lag 2, across two levels) is at or below a tolerance.
 run_to_steady advances a Batch (or a single Domain) in calls of `chunk`
 lattice steps.  Each call ends with the library's two check steps, which
 give every domain's residual, mass and mass budget.  The run records when
@@ -43,8 +44,8 @@ def run_to_steady(solver, tol: float, max_steps: int, chunk: int = 5000, log: Op
     tol, -1 if never), when (float [n]: seconds since t0, NaN if never),
     blown (bool [n]: mass became non-finite) and steps (lattice steps run).
     """
-    if chunk < 2:
-        raise ValueError("chunk must be >= 2 (each call ends with two check steps)")
+    if chunk < 3:
+        raise ValueError("chunk must be >= 3 (each call ends with its check steps)")
     t0 = time.perf_counter() if t0 is None else t0
     problems = problems_of(solver)
     n, nodes = len(problems), int(sum(p.cells for p in problems))

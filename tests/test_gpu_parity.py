@@ -128,6 +128,60 @@ def test_moments_residual_mass_budget(B, precision):
     dom.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [3, 4, 21])
+def test_residual_over_two_levels(B, precision, n):
+    """With residual lag 2 a call of n steps from level t0 records
+    max |s(t0 + n - 1) - s(t0 + n - 3)| / 2 (s = sqrt(u_r^2 + u_z^2), Eq. 57
+    measured across two levels) and the mass and budget of level t0 + n - 1;
+    the single domain and a batch holding the same domain agree with the
+    oracle, from both AA parities."""
+    pb = problem(70, 41, "crystal")
+    for t0 in (6, 7):
+        st = seeded_state(pb, 23)
+        dom = B.Domain(pb, precision)
+        upload(dom, st)
+        dom.step(t0)
+        dom.set_residual_lag(2)
+        dom.step(n)
+        res, mass, budget = dom.residual()
+        dom.close()
+        oracle.step(st, t0 + n - 3)
+        _, _, sp_a = oracle.stats(st)
+        oracle.step(st, 2)
+        m_b, b_b, sp_b = oracle.stats(st)
+        want = float(np.max(np.abs(sp_b - sp_a))) / 2
+        fp64 = precision == "fp64"
+        assert res == pytest.approx(want, rel=1e-9 if fp64 else 2e-3, abs=1e-13), (t0, n)
+        assert mass == pytest.approx(m_b, rel=1e-12 if fp64 else 1e-7)
+        assert budget == pytest.approx(b_b, rel=1e-9 if fp64 else 1e-3, abs=1e-12 if fp64 else 1e-9)
+        if precision == "fp32":
+            batch = B.Batch([pb], "fp32")
+            st0 = seeded_state(pb, 23)
+            batch.set_populations(0, st0.f, st0.g, st0.h)
+            batch.step(t0)
+            batch.set_residual_lag(2)
+            batch.step(n)
+            r = batch.residuals()
+            batch.close()
+            assert r[0, 0] == pytest.approx(want, rel=2e-3, abs=1e-13), (t0, n)
+            assert r[0, 1] == pytest.approx(m_b, rel=1e-7)
+
+
+def test_residual_lag_two_needs_three_steps(B):
+    pb = problem(40, 30, "closed")
+    dom = B.Domain(pb, "fp64")
+    upload(dom, seeded_state(pb, 3))
+    dom.set_residual_lag(2)
+    dom.step(2)
+    assert math.isinf(dom.residual()[0])
+    dom.step(3)
+    assert math.isfinite(dom.residual()[0])
+    with pytest.raises(B.AxlbmError):
+        dom.set_residual_lag(3)
+    dom.close()
+
+
 def test_residual_single_steps_and_first_call(B):
     pb = problem(40, 30, "closed")
     dom = B.Domain(pb, "fp64")

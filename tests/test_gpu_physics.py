@@ -126,21 +126,27 @@ def _record(name, got):
 def test_cavity_128x192_to_steady_state(B):
     """The rotating-lid cylinder at the smallest grid of the benchmark's
     cavity family (128 x 192, A = 1.5, Re = 990, lid speed 0.1): FP64 storage
-    reaches the Eq. 57 residual 1e-8 (2.95 M steps) and Table 2's axial peak;
-    FP32 and FP16 deviation storage, run as many steps, stop at their rounding
-    floors of the residual, with their fields within the stated bounds of the
-    FP64 ones."""
+    reaches the Eq. 57 residual 1e-8 (2.95 M steps) and Table 2's axial peak.
+    FP32 and FP16 deviation storage, run as many steps, stop at floors of the
+    consecutive-level residual: the period-2 (staggered) modes of the lattice,
+    which streaming and the collision do not damp, are kept excited by their
+    rounding.  Measured across two levels (residual lag 2) the period-2 part
+    cancels and FP32 gets to 1e-8 (in fewer steps than FP64 needs for Eq. 57
+    between consecutive levels); its fields stay within the stated bound of
+    FP64's after as many steps."""
     pb = I.rotating_lid_cavity(nr=128, aspect=1.5, re=990.0)
     mask = B.RHO | B.UR | B.UZ | B.UTH
     dom = B.Domain(pb, "fp64")
     steps, res = 0, 1.0
     trace = []
+    snap = {}  # FP64 fields every 50,000 steps
     while res > 1e-8 and steps < 3_000_000:
         dom.step(50_000)
         steps += 50_000
         res = dom.residual()[0]
         trace.append(res)
-    m64 = dom.moments(mask)
+        snap[steps] = dom.moments(mask)
+    m64 = snap[steps]
     dom.close()
     assert res <= 1e-8, (steps, trace[::5])
     umax, h = axis_peak(pb, m64)
@@ -148,16 +154,36 @@ def test_cavity_128x192_to_steady_state(B):
     assert abs(umax - want_u) <= 0.05 * want_u and abs(h - want_h) <= 0.02, (umax, h)
     lid = pb.omega_of("hi") * pb.wall_radius
     out = {"steps_to_1e-8_fp64": steps, "uz_max": umax, "h_over_H": h, "fp64_residual_every_250k": trace[4::5]}
-    # residual floor, field error over the lid speed (measured: FP32 1.4e-6, 6e-5; FP16 4.7e-4, 4.9e-2 -- the
-    # interior's per-step changes are below the resolution of 16-bit deviations)
+    # consecutive-level floor, field error over the lid speed (measured: FP32 1.4e-6, 6e-5; FP16 4.7e-4,
+    # 4.9e-2 -- the interior's per-step changes are below the resolution of 16-bit deviations)
     bounds = {"fp32": (1e-5, 2e-4), "fp16": (2e-3, 1e-1)}
     for precision in bounds:
         d = B.Domain(pb, precision)
         d.step(steps)
         r = d.residual()[0]
         m = d.moments(mask)
+        d.set_residual_lag(2)
+        d.step(3)
+        r2 = d.residual()[0]
         d.close()
-        out[precision] = {"residual": r, "max_velocity_error_over_lid": float(np.max(np.abs(m[1:] - m64[1:]))) / lid}
+        out[precision] = {"residual": r, "residual_lag2": r2,
+                          "max_velocity_error_over_lid": float(np.max(np.abs(m[1:] - m64[1:]))) / lid}
+    # FP32 from rest with the two-level residual: steps to 1e-8, and its fields against FP64's after as many
+    # steps (the 1e-8 criterion stops both while the slowest mode still drifts by ~1e-3 of the lid speed)
+    d = B.Domain(pb, "fp32")
+    d.set_residual_lag(2)
+    s32, r32 = 0, 1.0
+    while r32 > 1e-8 and s32 < steps:
+        d.step(50_000)
+        s32 += 50_000
+        r32 = d.residual()[0]
+    m32 = d.moments(mask)
+    d.close()
+    out["fp32_lag2"] = {"steps_to_1e-8": s32, "residual": r32,
+                        "max_velocity_error_over_lid_same_steps": float(np.max(np.abs(m32[1:] - snap[s32][1:]))) / lid,
+                        "max_velocity_difference_over_lid_from_fp64_at_1e-8":
+                            float(np.max(np.abs(m32[1:] - m64[1:]))) / lid}
     record("tables.json", "cavity_128x192", out)
     for precision, (floor, tol) in bounds.items():
         assert out[precision]["residual"] <= floor and out[precision]["max_velocity_error_over_lid"] <= tol, out
+    assert r32 <= 1e-8 and out["fp32_lag2"]["max_velocity_error_over_lid_same_steps"] <= 2e-4, out

@@ -66,7 +66,7 @@ def test_zero_kernels_give_the_head_bias():
 
 def test_weight_count_matches_the_library():
     from paper_1003_0282_gb300 import axlbm as B
-    assert B.lib().axlbm_ws_weight_count() == WS.weight_count() == 473092
+    assert B.lib().axlbm_ws_weight_count() == WS.weight_count() == 906628
 
 
 @pytest.fixture(scope="module")
@@ -160,12 +160,18 @@ def torch_reference(bits, feats):
     x[:, 7] = ((torch.arange(WS.H, device="cuda") + 0.5) / WS.H)[None, :, None]
     x = x.to(torch.bfloat16).float()
     c = lambda i, t: F.conv2d(t, params[2 * i], params[2 * i + 1], padding=1 if WS.LAYERS[i][2] == 3 else 0)
-    e1 = F.relu(c(1, F.relu(c(0, x))))
-    e2 = F.relu(c(3, F.relu(c(2, F.avg_pool2d(e1, 2)))))
-    e3 = F.relu(c(5, F.relu(c(4, F.avg_pool2d(e2, 2)))))
-    d2 = F.relu(c(7, F.relu(c(6, torch.cat([F.interpolate(e3, scale_factor=2, mode="nearest"), e2], 1)))))
-    d1 = F.relu(c(9, F.relu(c(8, torch.cat([F.interpolate(d2, scale_factor=2, mode="nearest"), e1], 1)))))
-    return c(10, d1), params
+    levels = len(WS.CHANNELS)
+    skips = []
+    for lev in range(levels):
+        if lev:
+            x = F.avg_pool2d(x, 2)
+        x = F.relu(c(2 * lev + 1, F.relu(c(2 * lev, x))))
+        skips.append(x)
+    for j, lev in enumerate(range(levels - 2, -1, -1)):
+        first = 2 * levels + 2 * j
+        x = F.relu(c(first + 1, F.relu(c(first, torch.cat([F.interpolate(x, scale_factor=2, mode="nearest"),
+                                                            skips[lev]], 1)))))
+    return c(len(WS.LAYERS) - 1, x), params
 
 
 def packed_grad(params):
