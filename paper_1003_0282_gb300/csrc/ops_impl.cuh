@@ -349,16 +349,19 @@ __device__ __forceinline__ S* slot(S* pop, const Geom& G, int plane, int j, int 
 
 // Where the population of plane `plane` at a fluid site (j, k) lives: in the
 // domain, or -- row -1 or nz, beyond a cut face -- in that face's halo row.
-template <class S, class R>
+// HALO: the kernel may meet cut faces (else the check is compiled out).
+template <bool HALO, class S, class R>
 __device__ __forceinline__ S* site_slot(const KArgs<S, R>& A, int plane, int j, int k) {
     const Geom& G = A.G;
-    if (k < 0) return A.halo + (long long)plane * G.pitch + j;
-    if (k >= G.nz) return A.halo + (long long)(A.nplanes + plane) * G.pitch + j;
+    if (HALO) {
+        if (k < 0) return A.halo + (long long)plane * G.pitch + j;
+        if (k >= G.nz) return A.halo + (long long)(A.nplanes + plane) * G.pitch + j;
+    }
     return slot(A.pop, G, plane, j, k);
 }
 
 // Pull the odd-step populations of node (j, k) with boundary rules.
-template <class S, class R, bool SW, bool TH>
+template <class S, class R, bool SW, bool TH, bool HALO = false>
 __device__ __forceinline__ void pull_odd(const KArgs<S, R>& A, int j, int k, Cell<R, SW, TH>& c) {
     const Geom& G = A.G;
 #pragma unroll
@@ -368,7 +371,7 @@ __device__ __forceinline__ void pull_odd(const KArgs<S, R>& A, int j, int k, Cel
             c.d[a] = Codec<S>::load(slot(A.pop, G, a, j, k));
         } else {
             const int b = idx9(s.fr ? -cr9(a) : cr9(a), s.fz ? -cz9(a) : cz9(a));
-            c.d[a] = Codec<S>::load(site_slot(A, opp9(b), s.j, s.k));
+            c.d[a] = Codec<S>::load(site_slot<HALO>(A, opp9(b), s.j, s.k));
         }
     }
     if (SW) {
@@ -379,7 +382,7 @@ __device__ __forceinline__ void pull_odd(const KArgs<S, R>& A, int j, int k, Cel
                 c.g[q] = bounce_g(G, A.C, s.face, j, Codec<S>::load(slot(A.pop, G, A.g_plane + q, j, k)));
             } else {
                 const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
-                const R v = Codec<S>::load(site_slot(A, A.g_plane + opp4(b), s.j, s.k));
+                const R v = Codec<S>::load(site_slot<HALO>(A, A.g_plane + opp4(b), s.j, s.k));
                 c.g[q] = s.fr ? -v : v;
             }
         }
@@ -392,14 +395,14 @@ __device__ __forceinline__ void pull_odd(const KArgs<S, R>& A, int j, int k, Cel
                 c.h[q] = bounce_h(A.C, s.face, R(Codec<S>::load(slot(A.pop, G, A.h_plane + q, j, k))));
             } else {
                 const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
-                c.h[q] = Codec<S>::load(site_slot(A, A.h_plane + opp4(b), s.j, s.k));
+                c.h[q] = Codec<S>::load(site_slot<HALO>(A, A.h_plane + opp4(b), s.j, s.k));
             }
         }
     }
 }
 
 // Push the odd-step post-collision populations of node (j, k) with boundary rules.
-template <class S, class R, bool SW, bool TH>
+template <class S, class R, bool SW, bool TH, bool HALO = false>
 __device__ __forceinline__ void push_odd(const KArgs<S, R>& A, int j, int k, const Cell<R, SW, TH>& c) {
     const Geom& G = A.G;
 #pragma unroll
@@ -411,7 +414,7 @@ __device__ __forceinline__ void push_odd(const KArgs<S, R>& A, int j, int k, con
             // leaves through the axis into the mirror column
         } else {
             const int b = idx9(s.fr ? -cr9(a) : cr9(a), s.fz ? -cz9(a) : cz9(a));
-            Codec<S>::store(site_slot(A, b, s.j, s.k), c.d[a]);
+            Codec<S>::store(site_slot<HALO>(A, b, s.j, s.k), c.d[a]);
         }
     }
     if (SW) {
@@ -424,7 +427,7 @@ __device__ __forceinline__ void push_odd(const KArgs<S, R>& A, int j, int k, con
                 // leaves through the axis into the mirror column
             } else {
                 const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
-                Codec<S>::store(site_slot(A, A.g_plane + b, s.j, s.k), s.fr ? -c.g[q] : c.g[q]);
+                Codec<S>::store(site_slot<HALO>(A, A.g_plane + b, s.j, s.k), s.fr ? -c.g[q] : c.g[q]);
             }
         }
     }
@@ -438,7 +441,7 @@ __device__ __forceinline__ void push_odd(const KArgs<S, R>& A, int j, int k, con
                 // leaves through the axis into the mirror column
             } else {
                 const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
-                Codec<S>::store(site_slot(A, A.h_plane + b, s.j, s.k), c.h[q]);
+                Codec<S>::store(site_slot<HALO>(A, A.h_plane + b, s.j, s.k), c.h[q]);
             }
         }
     }
@@ -965,26 +968,26 @@ __device__ __forceinline__ void frame_coord(const Geom& G, int i, int& j, int& k
 // Odd-step update of one outer-ring node (j, k): pull with the boundary
 // rules, collide, push, check values.  Shared by the single-domain and batch
 // ring kernels, each of which instantiates it for one cell type only.
-template <class S, class R, bool SW, bool TH, bool CHK>
+template <class S, class R, bool SW, bool TH, bool CHK, bool HALO = false>
 __device__ __forceinline__ void ring_node(const KArgs<S, R>& A, int j, int k, R az, Red& red) {
     Cell<R, SW, TH> c;
-    pull_odd(A, j, k, c);
+    pull_odd<S, R, SW, TH, HALO>(A, j, k, c);
     const R inv_r = inv_radius<R>(A.G, j);
     if (on_wet_wall(A.G, j, k)) {
         // a wet-wall node holds its post-collision state: stream it as it is
         Cell<R, SW, TH> m = c;
         m.collide(inv_r, A.C, az);  // moments for the check values
-        push_odd(A, j, k, c);
+        push_odd<S, R, SW, TH, HALO>(A, j, k, c);
         if (CHK) check_cell(A, j, k, inv_r, m, red);
         return;
     }
     c.collide(inv_r, A.C, az);
-    push_odd(A, j, k, c);
+    push_odd<S, R, SW, TH, HALO>(A, j, k, c);
     if (CHK) check_cell(A, j, k, inv_r, c, red);
 }
 
 // Odd-step update of the outer ring with the boundary rules.
-template <class S, class R, bool SW, bool TH, bool CHK>
+template <class S, class R, bool SW, bool TH, bool CHK, bool HALO>
 __global__ void __launch_bounds__(kThreads) k_frame(const KArgs<S, R> A) {
     const Geom& G = A.G;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -992,7 +995,7 @@ __global__ void __launch_bounds__(kThreads) k_frame(const KArgs<S, R> A) {
     if (i < A.nframe) {
         int j, k;
         frame_coord(G, i, j, k);
-        ring_node<S, R, SW, TH, CHK>(A, j, k, R(A.az[1]), red);
+        ring_node<S, R, SW, TH, CHK, HALO>(A, j, k, R(A.az[1]), red);
     }
     if (CHK) block_reduce_store(red, A.partials + 4ll * (A.part_offset + blockIdx.x));
     if (blockIdx.x == 0 && threadIdx.x == 0) advance_clock(A.clock, 1, A.az0, A.omega_t);
@@ -1040,7 +1043,7 @@ __device__ __forceinline__ void store_pull(const KArgs<S, R>& A, int j, int k, c
             Codec<S>::store(slot(A.pop, G, a, j, k), c.d[a]);
         } else if (!(mirror_col && s.fr)) {
             const int b = idx9(s.fr ? -cr9(a) : cr9(a), s.fz ? -cz9(a) : cz9(a));
-            Codec<S>::store(site_slot(A, opp9(b), s.j, s.k), c.d[a]);
+            Codec<S>::store(site_slot<false>(A, opp9(b), s.j, s.k), c.d[a]);
         }
     }
     if (SW) {
@@ -1051,7 +1054,7 @@ __device__ __forceinline__ void store_pull(const KArgs<S, R>& A, int j, int k, c
                 Codec<S>::store(slot(A.pop, G, A.g_plane + q, j, k), bounce_g(G, A.C, s.face, j, c.g[q]));
             } else if (!(mirror_col && s.fr)) {
                 const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
-                Codec<S>::store(site_slot(A, A.g_plane + opp4(b), s.j, s.k), s.fr ? -c.g[q] : c.g[q]);
+                Codec<S>::store(site_slot<false>(A, A.g_plane + opp4(b), s.j, s.k), s.fr ? -c.g[q] : c.g[q]);
             }
         }
     }
@@ -1063,7 +1066,7 @@ __device__ __forceinline__ void store_pull(const KArgs<S, R>& A, int j, int k, c
                 Codec<S>::store(slot(A.pop, G, A.h_plane + q, j, k), bounce_h(A.C, s.face, c.h[q]));
             } else if (!(mirror_col && s.fr)) {
                 const int b = idx4(s.fr ? -cr4(q) : cr4(q), s.fz ? -cz4(q) : cz4(q));
-                Codec<S>::store(site_slot(A, A.h_plane + opp4(b), s.j, s.k), c.h[q]);
+                Codec<S>::store(site_slot<false>(A, A.h_plane + opp4(b), s.j, s.k), c.h[q]);
             }
         }
     }
@@ -1230,7 +1233,7 @@ __global__ void __launch_bounds__(kThreads) k_moments(const KArgs<S, R> A, int p
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int j = int(i % G.nr), k = int(i / G.nr);
         Cell<R, SW, TH> c;
-        if (parity == 0) load_natural(A, j, k, c); else pull_odd(A, j, k, c);
+        if (parity == 0) load_natural(A, j, k, c); else pull_odd<S, R, SW, TH, true>(A, j, k, c);
         for (int q = 0; q < 4; ++q) {
             if (!SW) c.g[q] = R(0);
             if (!TH) c.h[q] = R(0);
@@ -1258,7 +1261,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(const KArgs<S, R> A, int pa
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int j = int(i % G.nr), k = int(i / G.nr);
         Cell<R, SW, TH> c;
-        if (parity == 0) load_natural(A, j, k, c); else pull_odd(A, j, k, c);
+        if (parity == 0) load_natural(A, j, k, c); else pull_odd<S, R, SW, TH, true>(A, j, k, c);
         for (int a = 0; a < 9; ++a) out[a * n + i] = (double)c.d[a] + w9(a) * (double)A.C.rho0;
         int p = 9;
         if (SW) {
@@ -1477,8 +1480,14 @@ cudaError_t step_sw(axlbm_handle* h, int check, int residual, cudaEvent_t ev0, c
         if (ev1) cudaEventRecord(ev1, h->stream);
         if (e != cudaSuccess) return e;
         A.part_offset = blocks;  // the frame blocks follow the bulk blocks
-        if (check) k_frame<S, R, SW, TH, true><<<L.frame_blocks, kThreads, 0, h->stream>>>(A);
-        else k_frame<S, R, SW, TH, false><<<L.frame_blocks, kThreads, 0, h->stream>>>(A);
+        const bool cut = h->bc.z_lo == AXLBM_Z_HALO || h->bc.z_hi == AXLBM_Z_HALO;
+        if (cut) {
+            if (check) k_frame<S, R, SW, TH, true, true><<<L.frame_blocks, kThreads, 0, h->stream>>>(A);
+            else k_frame<S, R, SW, TH, false, true><<<L.frame_blocks, kThreads, 0, h->stream>>>(A);
+        } else {
+            if (check) k_frame<S, R, SW, TH, true, false><<<L.frame_blocks, kThreads, 0, h->stream>>>(A);
+            else k_frame<S, R, SW, TH, false, false><<<L.frame_blocks, kThreads, 0, h->stream>>>(A);
+        }
         *nlaunch += 1;
         if (check) h->check_parts = blocks + L.frame_blocks;
         e = cudaGetLastError();

@@ -1,0 +1,128 @@
+"""The pipe and cavity configurations of the benchmark on the GPU.
+
+Womersley pipe (Sec. IV A, Eq. 56): N_r = 64 x N_z = 4, periodic, axial force
+a0 cos(omega t) with the period derived from (alpha, tau_s, R = N_r):
+(alpha, tau_s) = (2, 1.0), (5, 1.0), (10, 0.8), (10, 0.6), i.e. T = 38604,
+6177, 2574 and 7721 steps.  From rest the start-up transient decays by
+exp(-j0^2 2 pi / alpha^2) per period, so the comparison runs over period
+P = max(3, 1 + ceil(6.91 alpha^2 / (2 pi j0^2))) (3, 6, 21, 21): sixteen
+samples of u_z across it against the Bessel-function profile (<xi> of
+Sec. IV A) and against the FP64 oracle run alongside on the CPU.
+
+Rotating-lid cylinder (Sec. IV B) at the larger grids of the benchmark's
+cavity family, A = H/R = 2.5: 256 x 640 at Re = 1492 and 512 x 1280 at
+Re = 2494.  Their steady states lie ~R^2/nu = 3.8 M and 12.8 M steps away,
+more than a test can run in FP64; FP64, FP32 and FP16 storage run the same
+number of steps from rest and the reduced storage is compared with FP64 field
+by field (the per-field error the benchmark states), with finite fields and
+the mass budget checked.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import analytic as A
+from paper_1003_0282_gb300 import inputs as I
+from parity_util import record
+
+pytestmark = pytest.mark.gpu
+
+J0_ROOT = 2.404825557695773
+WOMERSLEY = [(2.0, 1.0), (5.0, 1.0), (10.0, 0.8), (10.0, 0.6)]
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1003_0282_gb300 import build
+    build.build()
+    from paper_1003_0282_gb300 import axlbm
+    return axlbm
+
+
+_ORACLE = {}
+
+
+def womersley_schedule(alpha, tau):
+    pb = I.womersley(nr=64, nz=4, tau=tau, alpha=alpha)
+    periods = max(3, 1 + math.ceil(6.91 * alpha ** 2 / (2 * math.pi * J0_ROOT ** 2)))
+    times = [(periods - 1) * pb.period + n * pb.period // 16 for n in range(16)]
+    return pb, times
+
+
+def oracle_samples(alpha, tau):
+    """u_z [16][nz][nr] of the FP64 oracle at the sample times (computed once)."""
+    if (alpha, tau) not in _ORACLE:
+        pb, times = womersley_schedule(alpha, tau)
+        st = oracle.rest_state(pb)
+        out = []
+        for t in times:
+            oracle.step(st, t - st.t)
+            out.append(oracle.moments(st)[2])
+        _ORACLE[(alpha, tau)] = np.array(out)
+    return _ORACLE[(alpha, tau)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("alpha,tau", WOMERSLEY)
+def test_womersley_pipe(B, alpha, tau, precision):
+    pb, times = womersley_schedule(alpha, tau)
+    mu = pb.rho0 * (tau - 0.5) / 3.0
+    want = oracle_samples(alpha, tau)
+    dom = B.Domain(pb, precision)
+    r = pb.node_radius(np.arange(pb.nr))
+    xis, dev = [], 0.0
+    for n, t in enumerate(times):
+        dom.step(t - dom.time)
+        uz = dom.moments(B.UZ)[0]
+        ua = A.womersley(r, t, float(pb.nr), pb.az0, pb.rho0, pb.omega_t, mu)
+        xis.append(A.xi(uz.mean(axis=0), ua))
+        dev = max(dev, float(np.max(np.abs(uz - want[n]))) / float(np.max(np.abs(want[n]))))
+    dom.close()
+    record("configs.json", f"womersley alpha={alpha:g} tau={tau:g} {precision}",
+           {"period": pb.period, "mean_xi": float(np.mean(xis)), "max_xi": float(np.max(xis)),
+            "max_rel_dev_from_oracle": dev})
+    assert np.mean(xis) <= 0.005, xis  # the oracle's own <xi>: 0.05 % .. 0.14 %
+    assert dev <= (1e-10 if precision == "fp64" else 2e-4), dev
+
+
+CAVITIES = [(256, 2.5, 1492.0, 400_000), (512, 2.5, 2494.0, 200_000)]
+
+
+@pytest.mark.parametrize("nr,aspect,re,steps", CAVITIES)
+def test_large_cavity_storage_error_against_fp64(B, nr, aspect, re, steps):
+    pb = I.rotating_lid_cavity(nr=nr, aspect=aspect, re=re, collision="mrt")
+    lid = pb.omega_of("hi") * pb.wall_radius
+    mask = B.RHO | B.UR | B.UZ | B.UTH
+    fields, checks = {}, {}
+    for precision in ("fp64", "fp32", "fp16"):
+        d = B.Domain(pb, precision)
+        d.step(steps - 3)
+        _, m0, b0 = d.residual()
+        d.set_residual_lag(2)
+        d.step(3)
+        r, m1, _ = d.residual()
+        fields[precision] = d.moments(mask)
+        checks[precision] = (r, m0, b0, m1)
+        d.close()
+        assert np.all(np.isfinite(fields[precision])), precision
+    out = {"steps": steps, "lid_speed": lid}
+    for precision in ("fp32", "fp16"):
+        err = {name: float(np.max(np.abs(fields[precision][q] - fields["fp64"][q]))) / (lid if q else 1.0)
+               for q, name in enumerate(("rho", "u_r", "u_z", "u_theta"))}
+        out[precision] = {"max_error_over_lid_speed": err, "residual_lag2": checks[precision][0]}
+    out["fp64"] = {"residual_lag2": checks["fp64"][0]}
+    record("configs.json", f"cavity {nr}x{int(round(aspect * nr))} Re={re:g}", out)
+    # FP32 storage stays within 1e-4 of the lid speed of FP64, FP16 within 5e-2 (its deviations carry
+    # ~11 bits); the density within 1e-5 / 1e-3
+    for precision, (tu, tr) in (("fp32", (1e-4, 1e-5)), ("fp16", (5e-2, 1e-3))):
+        e = out[precision]["max_error_over_lid_speed"]
+        assert max(e["u_r"], e["u_z"], e["u_theta"]) <= tu and e["rho"] <= tr, out
+    # mass moves only by the budget: over three steps the change is three budgets to within rounding
+    for precision in ("fp64", "fp32"):
+        r, m0, b0, m1 = checks[precision]
+        assert abs(m1 - m0) <= 10 * abs(b0) + (1e-12 if precision == "fp64" else 1e-8) * m0, (precision, m0, m1, b0)
