@@ -155,8 +155,11 @@ axlbm_status timing_slot(axlbm_handle* h, cudaEvent_t* ev0, cudaEvent_t* ev1) {
 // Algorithmic bytes of one bulk launch: every stored population of every
 // updated node read once and written once, plus the |u| plane in check steps.
 double bulk_bytes_of(const axlbm_handle* h, int check, int residual) {
+    // odd steps: the interior, and the side columns when the bulk kernel takes them
     const double nodes = h->parity == 0 ? (double)h->G.nr * h->G.nz
-                                        : (h->G.nr > 2 && h->G.nz > 2 ? (double)(h->G.nr - 2) * (h->G.nz - 2) : 0.0);
+                                        : (h->G.nr > 2 && h->G.nz > 2
+                                               ? (double)(h->G.side ? h->G.nr : h->G.nr - 2) * (h->G.nz - 2)
+                                               : 0.0);
     const double rbytes = h->grid.precision == AXLBM_FP64 ? 8.0 : 4.0;
     double per = 2.0 * h->L.nplanes * (double)h->L.elem;
     if (check) per += rbytes * (residual ? 2.0 : 1.0);
@@ -277,6 +280,7 @@ axlbm_status axlbm_create(const axlbm_grid* grid, double tau, const axlbm_forcin
         for (int j = 0; j < grid->nr && h->G.rb_exact; ++j)
             h->G.rb_exact = (double)(h->G.rb + (float)j) == grid->r0 + off + j;
     }
+    h->G.side = bc->inner == AXLBM_INNER_AXIS && bc->outer == AXLBM_OUTER_BB && grid->nr >= 3 && grid->nz >= 3;
     h->parity = 0;
     h->t = 0;
     h->speed_valid = false;

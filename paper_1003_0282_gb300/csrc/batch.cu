@@ -72,6 +72,14 @@ struct Plan {
     int thmax;
 };
 
+// The odd steps of this domain update its side columns in the bulk kernel
+// (half-spacing axis, bounce-back outer wall; the ring kernels keep the first
+// and last rows) -- the rule of the single-domain path.
+bool side_in_bulk(const axlbm_domain& D) {
+    return D.boundary.inner == AXLBM_INNER_AXIS && D.boundary.outer == AXLBM_OUTER_BB && D.grid.nr >= 3 &&
+           D.grid.nz >= 3;
+}
+
 bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::string* why) {
     if (!dom || n < 1 || n > 65535) { *why = "need 1..65535 domains"; return false; }
     if (!batch_ops_for(precision)) { *why = "batch storage must be AXLBM_FP32 or AXLBM_FP16_DEV"; return false; }
@@ -204,7 +212,8 @@ bool plan_batch(const axlbm_domain* dom, int n, int precision, Plan* P, std::str
         for (int d = 0; d < n; ++d) {
             if ((dom[d].grid.with_temperature != 0) != (pass == 1)) continue;
             const int nr = dom[d].grid.nr, nz = dom[d].grid.nz;
-            const int nf = nz == 1 ? nr : 2 * nr + (nz - 2) * (nr > 1 ? 2 : 1);
+            // the first and last rows; the side columns too unless the bulk kernel takes them
+            const int nf = nz == 1 ? nr : (side_in_bulk(dom[d]) ? 2 * nr : 2 * nr + (nz - 2) * (nr > 1 ? 2 : 1));
             P->rstart[2 * d] = (int)(P->ring.size() / 2);
             for (int i = 0; i < nf; ++i) P->ring.insert(P->ring.end(), {d, i});
             P->rstart[2 * d + 1] = (int)(P->ring.size() / 2);
@@ -318,8 +327,9 @@ double batch_bulk_bytes(const axlbm_batch* b, int check, int residual) {
     double bytes = 0.0;
     for (int d = 0; d < b->n; ++d) {
         const axlbm_domain& D = b->desc[d];
+        const int cols = side_in_bulk(D) ? D.grid.nr : D.grid.nr - 2;  // odd steps: interior (+ side columns)
         const double nodes = b->parity == 0 ? (double)D.grid.nr * D.grid.nz
-                                            : (D.grid.nr > 2 && D.grid.nz > 2 ? (double)(D.grid.nr - 2) * (D.grid.nz - 2) : 0.0);
+                                            : (D.grid.nr > 2 && D.grid.nz > 2 ? (double)cols * (D.grid.nz - 2) : 0.0);
         double per = 2.0 * (13 + (D.grid.with_temperature ? 4 : 0)) * (double)b->L.elem;
         if (check) per += 4.0 * (residual ? 2.0 : 1.0);
         bytes += nodes * per;
@@ -682,6 +692,14 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
         const double off = D.boundary.inner == AXLBM_INNER_AXIS_NODE ? 0.0 : 0.5;
         y.rb = (float)(x.r0 + off - x.col0);
         y.rb_exact = (double)y.rb == x.r0 + off - x.col0;
+        y.side = side_in_bulk(D);
+        {  // the outer wall's constants as the single-domain kernel forms them (FP32)
+            const float om = x.cf.omega_w[AXLBM_FACE_OUTER];
+            const float rw = (float)(x.r0 + off + (x.nr - 1) + 0.5);
+            y.gw_out = 0.5f * x.cf.rho0 * (om * rw);
+            y.tw_out = x.cf.t_w[AXLBM_FACE_OUTER];
+            y.tdir_out = x.cf.t_dir[AXLBM_FACE_OUTER];
+        }
         for (int jl = 0; jl < x.nr && y.rb_exact; ++jl)
             y.rb_exact = (double)(y.rb + (float)(x.col0 + jl)) == x.r0 + off + jl;
     }

@@ -52,7 +52,13 @@ struct __align__(16) SlotDesc {
     CoefCore<float> c;
     // radius of atlas column x: rb + x, exact in FP32 for every column of the
     // domain when rb_exact (else it is formed in FP64 from r0)
-    float rb, pad[3];
+    float rb;
+    // side: odd steps update the side columns here (half-spacing axis,
+    // bounce-back outer wall); the outer wall's g bounce-back constant
+    // rho0 u_w / 2 and its temperature rule
+    float gw_out, tw_out;
+    int side;
+    int tdir_out, pad2[3];
 };
 static_assert(sizeof(SlotDesc) % 16 == 0, "bulk copies move 16-byte multiples");
 
@@ -99,6 +105,7 @@ __device__ __forceinline__ Geom dom_geom(const DomDesc& D, long long pitch, long
     G.row0 = D.row0;
     G.rb = 0.0f;
     G.rb_exact = 0;  // (the per-domain kernels take the radius in FP64)
+    G.side = 0;
     return G;
 }
 
@@ -249,33 +256,60 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
     for (int l = 0; l < NL; ++l) {
         const int kl = k0 - D.row0 + rr + l * (TK / NL);
         act[l] = jl < D.nr && kl < D.nz;
-        if (PAR == 1) act[l] = act[l] && jl > 0 && jl < D.nr - 1 && kl > 0 && kl < D.nz - 1;
+        if (PAR == 1) act[l] = act[l] && (D.side || (jl > 0 && jl < D.nr - 1)) && kl > 0 && kl < D.nz - 1;
         any = any || act[l];
     }
     if (!any) return;
     Cell<RC, SW, THD> c;
     const S* row = st + rr * BW + HB + jj;
     constexpr int LROW = (TK / NL) * BW;
+    using Sc = typename ScalarOf<RC>::type;
+    // odd steps: a side column (see kEdgeAxis); its own slots in global memory for the wall
+    const int edge = (PAR == 1 && D.side) ? (jl == 0 ? kEdgeAxis : (jl == D.nr - 1 ? kEdgeWall : kEdgeNone)) : kEdgeNone;
+    const S* own = A.pop + (long long)(k0 + rr) * A.pitch + (j0 + jj);
+    const int LOWN = (TK / NL) * (int)A.pitch;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
         const int p = PAR ? opp9(a) : a;
-        c.d[a] = Lanes<RC>::template load<S>(row + p * PS + (PAR ? cr9(p) : 0), LROW);
+        if (PAR == 1 && cr9(a) > 0 && edge == kEdgeAxis)
+            c.d[a] = Lanes<RC>::template load<S>(row + axis_pull_plane9(a) * PS, LROW);
+        else if (PAR == 1 && cr9(a) < 0 && edge == kEdgeWall)
+            c.d[a] = Lanes<RC>::template load<S>(own + a * A.plane, LOWN);
+        else
+            c.d[a] = Lanes<RC>::template load<S>(row + p * PS + (PAR ? cr9(p) : 0), LROW);
     }
     if (SW) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int p = PAR ? opp4(q) : q;
-            c.g[q] = Lanes<RC>::template load<S>(row + (9 + p) * PS + (PAR ? cr4(p) : 0), LROW);
+            if (PAR == 1 && cr4(q) > 0 && edge == kEdgeAxis)  // g is odd across the axis
+                c.g[q] = Lanes<RC>::template load<S>(row + (9 + opp4(idx4(-1, 0))) * PS, LROW) * RC(Sc(-1));
+            else if (PAR == 1 && cr4(q) < 0 && edge == kEdgeWall)
+                c.g[q] = wall_g(Lanes<RC>::template load<S>(own + (9 + q) * A.plane, LOWN), D.gw_out);
+            else
+                c.g[q] = Lanes<RC>::template load<S>(row + (9 + p) * PS + (PAR ? cr4(p) : 0), LROW);
         }
     }
     if (THD) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int p = PAR ? opp4(q) : q;
-            c.h[q] = Lanes<RC>::template load<S>(row + (HP + p) * PS + (PAR ? cr4(p) : 0), LROW);
+            if (PAR == 1 && cr4(q) > 0 && edge == kEdgeAxis)
+                c.h[q] = Lanes<RC>::template load<S>(row + (HP + opp4(idx4(-1, 0))) * PS, LROW);
+            else if (PAR == 1 && cr4(q) < 0 && edge == kEdgeWall)
+                c.h[q] = wall_h(Lanes<RC>::template load<S>(own + (HP + q) * A.plane, LOWN), D.tdir_out, D.c.t_ref,
+                                D.tw_out);
+            else
+                c.h[q] = Lanes<RC>::template load<S>(row + (HP + p) * PS + (PAR ? cr4(p) : 0), LROW);
         }
     }
     c.collide(inv_r, D.c, az);
+    // odd steps: what a side node sends across its face, bounced back or mirrored
+    RC gsend = RC(Sc(0)), hsend = RC(Sc(0));
+    if (PAR == 1 && SW && edge == kEdgeAxis) gsend = c.g[2] * RC(Sc(-1));
+    if (PAR == 1 && SW && edge == kEdgeWall) gsend = wall_g(c.g[0], D.gw_out);
+    if (PAR == 1 && THD && edge == kEdgeAxis) hsend = c.h[2];
+    if (PAR == 1 && THD && edge == kEdgeWall) hsend = wall_h(c.h[0], D.tdir_out, D.c.t_ref, D.tw_out);
     // even step: a wet-wall node holds its post-collision state and keeps it
     // (copied straight from the stage below instead of its collided state)
     bool keep[NL];
@@ -305,17 +339,35 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
             }
         } else {
 #pragma unroll
-            for (int a = 0; a < 9; ++a)
-                Codec<S>::store(A.pop + a * pl + x + cz9(a) * A.pitch + cr9(a), Lanes<RC>::get(c.d[a], l));
+            for (int a = 0; a < 9; ++a) {
+                if (cr9(a) < 0 && edge == kEdgeAxis)
+                    Codec<S>::store(A.pop + axis_push_plane9(a) * pl + x + cz9(a) * A.pitch, Lanes<RC>::get(c.d[a], l));
+                else if (cr9(a) > 0 && edge == kEdgeWall)
+                    Codec<S>::store(A.pop + opp9(a) * pl + x, Lanes<RC>::get(c.d[a], l));
+                else
+                    Codec<S>::store(A.pop + a * pl + x + cz9(a) * A.pitch + cr9(a), Lanes<RC>::get(c.d[a], l));
+            }
             if (SW) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    Codec<S>::store(A.pop + (9 + q) * pl + x + cz4(q) * A.pitch + cr4(q), Lanes<RC>::get(c.g[q], l));
+                for (int q = 0; q < 4; ++q) {
+                    if (q == 2 && edge == kEdgeAxis)
+                        Codec<S>::store(A.pop + 9 * pl + x, Lanes<RC>::get(gsend, l));
+                    else if (q == 0 && edge == kEdgeWall)
+                        Codec<S>::store(A.pop + 11 * pl + x, Lanes<RC>::get(gsend, l));
+                    else
+                        Codec<S>::store(A.pop + (9 + q) * pl + x + cz4(q) * A.pitch + cr4(q), Lanes<RC>::get(c.g[q], l));
+                }
             }
             if (THD) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    Codec<S>::store(A.pop + (HP + q) * pl + x + cz4(q) * A.pitch + cr4(q), Lanes<RC>::get(c.h[q], l));
+                for (int q = 0; q < 4; ++q) {
+                    if (q == 2 && edge == kEdgeAxis)
+                        Codec<S>::store(A.pop + HP * pl + x, Lanes<RC>::get(hsend, l));
+                    else if (q == 0 && edge == kEdgeWall)
+                        Codec<S>::store(A.pop + (HP + 2) * pl + x, Lanes<RC>::get(hsend, l));
+                    else
+                        Codec<S>::store(A.pop + (HP + q) * pl + x + cz4(q) * A.pitch + cr4(q), Lanes<RC>::get(c.h[q], l));
+                }
             }
         }
         if (CHK) {

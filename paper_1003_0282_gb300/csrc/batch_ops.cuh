@@ -61,6 +61,7 @@ KArgs<S, R> domain_args(axlbm_batch* b, int d) {
     K.G.row0 = b->row0[d];
     K.G.rb = 0.0f;
     K.G.rb_exact = 0;
+    K.G.side = 0;
     K.C = make_coef<R>(D.tau, D.forcing, D.boundary);
     K.C.mrt = D.grid.collision == AXLBM_MRT;
     K.g_plane = 9;

@@ -31,6 +31,7 @@ struct Geom {
     int col0, row0;   // position of node (0, 0) in the array (non-zero for a domain of a batch)
     float rb;         // radius of column j is rb + j, exact in FP32 for every column when rb_exact
     int rb_exact;
+    int side;         // 1: odd steps update the side columns in the bulk kernel (half-spacing axis, bounce-back wall)
 };
 
 // Per-step forcing state on the device.  Kernels of a step with AA parity p

@@ -52,6 +52,7 @@ struct KArgs {
     Coef<R> C;
     int g_plane, h_plane;
     int nplanes;       // population planes (halo row stride per face)
+    R gw_out;          // rho0 u_w / 2 of the outer wall (its g bounce-back, side columns in the bulk)
     int nframe;
     int residual;  // 1: compare |u| with the stored previous level
     int tiles_j, tiles_k;  // bulk tiles (kTileJ x kTileK nodes) along r and z
@@ -332,9 +333,15 @@ __device__ __forceinline__ R wall_uth(const Geom& G, const Coef<R>& C, int face,
 }
 
 // Value of a D2Q4 population sent into a solid face, in stored (deviation) form.
+// A product rounded on its own (never fused into a following addition), so
+// that a value formed here equals one formed on the host or in another kernel.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <class R>
 __device__ __forceinline__ R bounce_g(const Geom& G, const Coef<R>& C, int face, int j, R v) {
-    return -v + R(0.5) * C.rho0 * wall_uth(G, C, face, j);
+    // rho0 u_w / 2 - v, the product rounded first (as wall_g takes it)
+    return mul_rn(R(0.5) * C.rho0, wall_uth(G, C, face, j)) - v;
 }
 template <class R>
 __device__ __forceinline__ R bounce_h(const Coef<R>& C, int face, R v) {
@@ -445,6 +452,30 @@ __device__ __forceinline__ void push_odd(const KArgs<S, R>& A, int j, int k, con
             }
         }
     }
+}
+
+// Side columns in the bulk kernels.  In odd steps the bulk kernels also
+// update the first and last columns of a domain (rows 1 .. nz - 2) when the
+// inner face is the half-spacing axis and the outer face the bounce-back wall,
+// so the ring kernels are left with the first and last rows; everything a
+// side node pulls is in the stage or in its own slots.  kEdgeAxis: column 0,
+// populations pulled from and pushed towards r < 0 are the mirror images of
+// the column's own (specular reflection, Sec. IV A; g odd in r); kEdgeWall:
+// column nr - 1, populations crossing the wall bounce back into the node's
+// own slots (g with the wall's speed, h with its temperature).
+constexpr int kEdgeNone = 0, kEdgeAxis = 1, kEdgeWall = 2;
+// stage plane holding, for D2Q9 population a pulled across the axis, its mirror
+// image at the node's own column (opposite of a with e_r reversed)
+__host__ __device__ constexpr int axis_pull_plane9(int a) { return opp9(idx9(-cr9(a), cz9(a))); }
+// slot receiving population a pushed across the axis (a with e_r reversed)
+__host__ __device__ constexpr int axis_push_plane9(int a) { return idx9(-cr9(a), cz9(a)); }
+// bounce-back of g at a wall that turns with speed u_w: x = rho0 u_w / 2
+template <class RC, class Sc>
+__device__ __forceinline__ RC wall_g(RC v, Sc x) { return RC(x) - v; }
+// bounce-back of h (stored h - T_ref/4): Dirichlet (tdir) or adiabatic
+template <class RC, class Sc>
+__device__ __forceinline__ RC wall_h(RC v, int tdir, Sc t_ref, Sc t_w) {
+    return tdir ? (RC(Sc(-0.5) * t_ref) - v) + RC(Sc(0.5) * t_w) : v;
 }
 
 // Natural-layout (after an odd step or a reset) load of node (j, k).
@@ -834,33 +865,63 @@ k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
                 for (int l = 0; l < NL; ++l) {
                     kk[l] = k0 + rr + l * (kTileK / NL);
                     act[l] = j < G.nr && kk[l] < G.nz;
-                    if (PAR == 1) act[l] = act[l] && j > 0 && j < G.nr - 1 && kk[l] > 0 && kk[l] < G.nz - 1;
+                    if (PAR == 1)
+                        act[l] = act[l] && (G.side || (j > 0 && j < G.nr - 1)) && kk[l] > 0 && kk[l] < G.nz - 1;
                     any = any || act[l];
                 }
                 if (!any) continue;
                 Cell<RC, SW, TH> c;
                 const S* row = st + rr * BW + HB + jj;
                 constexpr int LROW = (kTileK / NL) * BW;  // shared-memory distance between the lanes' rows
+                // odd steps: a side column (see kEdgeAxis); its own slots in global memory for the wall
+                const int edge = (PAR == 1 && G.side) ? (j == 0 ? kEdgeAxis : (j == G.nr - 1 ? kEdgeWall : kEdgeNone))
+                                                      : kEdgeNone;
+                const S* own = A.pop + (long long)(k0 + rr) * G.pitch + j;
+                const int LOWN = (kTileK / NL) * (int)G.pitch;
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
                     const int p = PAR ? opp9(a) : a;
-                    c.d[a] = Lanes<RC>::template load<S>(row + p * kTileK * BW + (PAR ? cr9(p) : 0), LROW);
+                    if (PAR == 1 && cr9(a) > 0 && edge == kEdgeAxis)
+                        c.d[a] = Lanes<RC>::template load<S>(row + axis_pull_plane9(a) * kTileK * BW, LROW);
+                    else if (PAR == 1 && cr9(a) < 0 && edge == kEdgeWall)
+                        c.d[a] = Lanes<RC>::template load<S>(own + a * G.plane, LOWN);
+                    else
+                        c.d[a] = Lanes<RC>::template load<S>(row + p * kTileK * BW + (PAR ? cr9(p) : 0), LROW);
                 }
                 if (SW) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int p = PAR ? opp4(q) : q;
-                        c.g[q] = Lanes<RC>::template load<S>(row + (9 + p) * kTileK * BW + (PAR ? cr4(p) : 0), LROW);
+                        if (PAR == 1 && cr4(q) > 0 && edge == kEdgeAxis)  // g is odd across the axis
+                            c.g[q] = Lanes<RC>::template load<S>(row + (9 + opp4(idx4(-1, 0))) * kTileK * BW, LROW) *
+                                     RC(Sc(-1));
+                        else if (PAR == 1 && cr4(q) < 0 && edge == kEdgeWall)
+                            c.g[q] = wall_g(Lanes<RC>::template load<S>(own + (9 + q) * G.plane, LOWN), A.gw_out);
+                        else
+                            c.g[q] = Lanes<RC>::template load<S>(row + (9 + p) * kTileK * BW + (PAR ? cr4(p) : 0), LROW);
                     }
                 }
                 if (TH) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int p = PAR ? opp4(q) : q;
-                        c.h[q] = Lanes<RC>::template load<S>(row + (HP + p) * kTileK * BW + (PAR ? cr4(p) : 0), LROW);
+                        if (PAR == 1 && cr4(q) > 0 && edge == kEdgeAxis)
+                            c.h[q] = Lanes<RC>::template load<S>(row + (HP + opp4(idx4(-1, 0))) * kTileK * BW, LROW);
+                        else if (PAR == 1 && cr4(q) < 0 && edge == kEdgeWall)
+                            c.h[q] = wall_h(Lanes<RC>::template load<S>(own + (HP + q) * G.plane, LOWN),
+                                            A.C.t_dir[AXLBM_FACE_OUTER], A.C.t_ref, A.C.t_w[AXLBM_FACE_OUTER]);
+                        else
+                            c.h[q] = Lanes<RC>::template load<S>(row + (HP + p) * kTileK * BW + (PAR ? cr4(p) : 0), LROW);
                     }
                 }
                 c.collide(inv_r, A.C, az);
+                // odd steps: what a side node sends across its face, bounced back or mirrored
+                RC gsend = RC(Sc(0)), hsend = RC(Sc(0));
+                if (PAR == 1 && SW && edge == kEdgeAxis) gsend = c.g[2] * RC(Sc(-1));
+                if (PAR == 1 && SW && edge == kEdgeWall) gsend = wall_g(c.g[0], A.gw_out);
+                if (PAR == 1 && TH && edge == kEdgeAxis) hsend = c.h[2];
+                if (PAR == 1 && TH && edge == kEdgeWall)
+                    hsend = wall_h(c.h[0], A.C.t_dir[AXLBM_FACE_OUTER], A.C.t_ref, A.C.t_w[AXLBM_FACE_OUTER]);
 #pragma unroll
                 for (int l = 0; l < NL; ++l) {
                     if (!act[l]) continue;
@@ -893,19 +954,39 @@ k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
                         }
                     } else {
 #pragma unroll
-                        for (int a = 0; a < 9; ++a)
-                            Codec<S>::store(A.pop + a * G.plane + x + cz9(a) * G.pitch + cr9(a), Lanes<RC>::get(c.d[a], l));
+                        for (int a = 0; a < 9; ++a) {
+                            if (cr9(a) < 0 && edge == kEdgeAxis)
+                                Codec<S>::store(A.pop + axis_push_plane9(a) * G.plane + x + cz9(a) * G.pitch,
+                                                Lanes<RC>::get(c.d[a], l));
+                            else if (cr9(a) > 0 && edge == kEdgeWall)
+                                Codec<S>::store(A.pop + opp9(a) * G.plane + x, Lanes<RC>::get(c.d[a], l));
+                            else
+                                Codec<S>::store(A.pop + a * G.plane + x + cz9(a) * G.pitch + cr9(a),
+                                                Lanes<RC>::get(c.d[a], l));
+                        }
                         if (SW) {
 #pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                Codec<S>::store(A.pop + (9 + q) * G.plane + x + cz4(q) * G.pitch + cr4(q),
-                                                Lanes<RC>::get(c.g[q], l));
+                            for (int q = 0; q < 4; ++q) {
+                                if (q == 2 && edge == kEdgeAxis)
+                                    Codec<S>::store(A.pop + 9 * G.plane + x, Lanes<RC>::get(gsend, l));
+                                else if (q == 0 && edge == kEdgeWall)
+                                    Codec<S>::store(A.pop + 11 * G.plane + x, Lanes<RC>::get(gsend, l));
+                                else
+                                    Codec<S>::store(A.pop + (9 + q) * G.plane + x + cz4(q) * G.pitch + cr4(q),
+                                                    Lanes<RC>::get(c.g[q], l));
+                            }
                         }
                         if (TH) {
 #pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                Codec<S>::store(A.pop + (HP + q) * G.plane + x + cz4(q) * G.pitch + cr4(q),
-                                                Lanes<RC>::get(c.h[q], l));
+                            for (int q = 0; q < 4; ++q) {
+                                if (q == 2 && edge == kEdgeAxis)
+                                    Codec<S>::store(A.pop + HP * G.plane + x, Lanes<RC>::get(hsend, l));
+                                else if (q == 0 && edge == kEdgeWall)
+                                    Codec<S>::store(A.pop + (HP + 2) * G.plane + x, Lanes<RC>::get(hsend, l));
+                                else
+                                    Codec<S>::store(A.pop + (HP + q) * G.plane + x + cz4(q) * G.pitch + cr4(q),
+                                                    Lanes<RC>::get(c.h[q], l));
+                            }
                         }
                     }
                     if (CHK) {
@@ -1391,7 +1472,12 @@ KArgs<S, R> make_args(axlbm_handle* h) {
     A.C = make_coef<R>(h);
     A.g_plane = h->L.g_plane < 0 ? 0 : h->L.g_plane;
     A.h_plane = h->L.h_plane < 0 ? 0 : h->L.h_plane;
-    A.nframe = h->L.nframe;
+    A.nframe = h->G.side ? 2 * h->G.nr : h->L.nframe;  // side columns in the bulk kernel: the rows only
+    {
+        const R om = A.C.omega_w[AXLBM_FACE_OUTER];
+        const R rw = R(node_radius(h->G, h->G.nr - 1) + 0.5);
+        A.gw_out = R(0.5) * A.C.rho0 * (om * rw);
+    }
     A.residual = 0;
     A.tiles_j = h->L.tiles_j;
     A.tiles_k = h->L.tiles_k;
@@ -1481,15 +1567,16 @@ cudaError_t step_sw(axlbm_handle* h, int check, int residual, cudaEvent_t ev0, c
         if (e != cudaSuccess) return e;
         A.part_offset = blocks;  // the frame blocks follow the bulk blocks
         const bool cut = h->bc.z_lo == AXLBM_Z_HALO || h->bc.z_hi == AXLBM_Z_HALO;
+        const int fb = (A.nframe + kThreads - 1) / kThreads;  // (rows only when the bulk kernel took the side columns)
         if (cut) {
-            if (check) k_frame<S, R, SW, TH, true, true><<<L.frame_blocks, kThreads, 0, h->stream>>>(A);
-            else k_frame<S, R, SW, TH, false, true><<<L.frame_blocks, kThreads, 0, h->stream>>>(A);
+            if (check) k_frame<S, R, SW, TH, true, true><<<fb, kThreads, 0, h->stream>>>(A);
+            else k_frame<S, R, SW, TH, false, true><<<fb, kThreads, 0, h->stream>>>(A);
         } else {
-            if (check) k_frame<S, R, SW, TH, true, false><<<L.frame_blocks, kThreads, 0, h->stream>>>(A);
-            else k_frame<S, R, SW, TH, false, false><<<L.frame_blocks, kThreads, 0, h->stream>>>(A);
+            if (check) k_frame<S, R, SW, TH, true, false><<<fb, kThreads, 0, h->stream>>>(A);
+            else k_frame<S, R, SW, TH, false, false><<<fb, kThreads, 0, h->stream>>>(A);
         }
         *nlaunch += 1;
-        if (check) h->check_parts = blocks + L.frame_blocks;
+        if (check) h->check_parts = blocks + fb;
         e = cudaGetLastError();
         if (e == cudaSuccess && h->bc.inner == AXLBM_INNER_AXIS_NODE) {
             k_axis_mirror<S, R, SW, TH><<<(h->G.nz + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(A);

@@ -9,10 +9,11 @@ without heat, 100 x 100, crystal beta = 0.4, Re_x = 100 (Re_c = -25) and
 in units of nu R_c.  The paper does not state either normalisation; these
 are the ones its numbers follow.
 
-All eight domains run as one batch of 800,000 steps (the flows are then
-steady to ~1e-6 per step).  The build's walls differ from the paper's
-(half-way bounce-back, or the wet non-equilibrium-extrapolation walls the
-paper uses, with the node on the axis), so the bounds are a few per cent.
+All eight domains run as one batch until each reaches the paper's
+convergence criterion (Eq. 57 residual <= 1e-8); the fields are taken there.
+The build's walls differ from the paper's (half-way bounce-back), or follow
+them (the wet non-equilibrium-extrapolation walls the paper uses, with the
+node on the axis), so the bounds are a few per cent.
 """
 import dataclasses
 
@@ -56,11 +57,33 @@ def cases():
 
 @pytest.fixture(scope="module")
 def steady(B):
+    """Every case run to the paper's convergence criterion (Eq. 57 residual
+    <= 1e-8, Sec. IV B; measured across two levels, which FP32 storage can
+    reach), its fields taken when it first gets there.  The wet walls do not
+    conserve mass: past that point their cells slowly gain mass and the
+    secondary vortex fades (after 800,000 steps psi_min of the wet Wheeler
+    cell is -0.032 instead of -0.043), so the paper's numbers belong to the
+    first steady level."""
     cs = cases()
     batch = B.Batch([c[3] for c in cs], "fp32")
-    batch.step(800000)
-    res = batch.residuals()
-    fields = [batch.moments(d, B.RHO | B.UR | B.UZ | B.UTH) for d in range(len(cs))]
+    batch.set_residual_lag(2)
+    mask = B.RHO | B.UR | B.UZ | B.UTH
+    fields, res = [None] * len(cs), np.full((len(cs), 3), np.nan)
+    steps = 0
+    while any(f is None for f in fields) and steps < 800000:
+        batch.step(5000)
+        steps += 5000
+        r = batch.residuals()
+        for d in range(len(cs)):
+            if fields[d] is None and r[d, 0] <= 1e-8:
+                fields[d] = batch.moments(d, mask)
+                res[d] = r[d]
+                res[d, 2] = steps
+    for d in range(len(cs)):  # a case that never got there is compared as it ends
+        if fields[d] is None:
+            fields[d] = batch.moments(d, mask)
+            res[d] = batch.residuals()[d]
+            res[d, 2] = steps
     batch.close()
     return cs, res, fields
 
@@ -112,9 +135,15 @@ def test_table1_wheeler_stream_function(steady):
         # next to the axis) comes out ~35 % weaker and psi_max ~20 % (the same
         # grid without wet walls does the same in the oracle, so it is the axis
         # rule of Sec. IV A -- every 1/r term zero on the axis -- not the walls)
-        tol_min, tol_max = (0.06, 0.06) if re_x < 500 else (0.10, 0.10)
-        if walls == "wet":
-            tol_min, tol_max = 0.5, 0.25
+        # half-spacing grid, bounce-back walls: the table within 6 % (10 % at Re_x = 1000).  With the node
+        # on the axis the secondary vortex next to the axis (psi_min) comes out ~13 % weaker at Re_x = 100
+        # whichever walls (the FP64 oracle at 100 x 100: -0.0429 with bounce-back, -0.0430 with wet walls
+        # at the 1e-8 criterion), so it is the axis rule of Sec. IV A -- every 1/r term zero on the axis,
+        # u_r / r included, whose limit is d u_r / dr -- not the walls; pinned there within 4 %.
+        if walls == "wet" and re_x < 500:
+            want_min, tol_min, tol_max = -0.0430, 0.04, 0.03
+        else:
+            tol_min, tol_max = (0.06, 0.06) if re_x < 500 else (0.10, 0.10)
         assert abs(pmin - want_min) <= tol_min * abs(want_min), (re_x, walls, pmin)
         assert abs(pmax - want_max) <= tol_max * abs(want_max), (re_x, walls, pmax)
 
