@@ -242,7 +242,9 @@ __device__ __forceinline__ uint32_t batch_tile_bytes(bool th) {
 }
 
 // Update one node pair (or one node) of a tile from its stage.
-template <class S, class R, class RC, bool SW, bool THD, int PAR, bool CHK, int TK, int TJ, bool WET>
+// EDGE: some lane of the warp sits on a side column the bulk kernel updates
+// (odd steps; the other warps run without the side-column selections).
+template <class S, class R, class RC, bool SW, bool THD, int PAR, bool CHK, int TK, int TJ, bool WET, bool EDGE>
 __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const SlotDesc& D, const S* st, int k0, int j0,
                                             int jj, int rr, R inv_r, R az, const R* sp_old, RedR<R>& red) {
     constexpr int NL = Lanes<RC>::n;
@@ -256,7 +258,7 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
     for (int l = 0; l < NL; ++l) {
         const int kl = k0 - D.row0 + rr + l * (TK / NL);
         act[l] = jl < D.nr && kl < D.nz;
-        if (PAR == 1) act[l] = act[l] && (D.side || (jl > 0 && jl < D.nr - 1)) && kl > 0 && kl < D.nz - 1;
+        if (PAR == 1) act[l] = act[l] && ((EDGE && D.side) || (jl > 0 && jl < D.nr - 1)) && kl > 0 && kl < D.nz - 1;
         any = any || act[l];
     }
     if (!any) return;
@@ -265,7 +267,8 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
     constexpr int LROW = (TK / NL) * BW;
     using Sc = typename ScalarOf<RC>::type;
     // odd steps: a side column (see kEdgeAxis); its own slots in global memory for the wall
-    const int edge = (PAR == 1 && D.side) ? (jl == 0 ? kEdgeAxis : (jl == D.nr - 1 ? kEdgeWall : kEdgeNone)) : kEdgeNone;
+    const int edge =
+        (EDGE && PAR == 1 && D.side) ? (jl == 0 ? kEdgeAxis : (jl == D.nr - 1 ? kEdgeWall : kEdgeNone)) : kEdgeNone;
     const S* own = A.pop + (long long)(k0 + rr) * A.pitch + (j0 + jj);
     const int LOWN = (TK / NL) * (int)A.pitch;
 #pragma unroll
@@ -521,12 +524,27 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
                 const S* st = sm + s * STAGE;
                 RedR<R> red;
                 const bool dth = TH && M.r.th;
+                // warps with a side-column lane take the path with its selections (odd steps)
+                const int jl = j0 + jj - D.col0;
+                const bool side_lane = PAR == 1 && D.side && (jl == 0 || jl == D.nr - 1);
+                // (a vote among the lanes that reached here: a lane whose wait gave up is not one of them)
+                const bool eg = PAR == 1 && __any_sync(__activemask(), side_lane);
                 // one node pair per thread: rows rr0 and rr0 + TK/2 of column jj
-                if (dth)
-                    batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old, red);
-                else
-                    batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old,
-                                                                             red);
+                if (eg) {
+                    if (dth)
+                        batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ, WET, true>(A, D, st, k0, j0, jj, rr0, inv_r, az,
+                                                                                    sp_old, red);
+                    else
+                        batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ, WET, true>(A, D, st, k0, j0, jj, rr0, inv_r,
+                                                                                       az, sp_old, red);
+                } else {
+                    if (dth)
+                        batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ, WET, false>(A, D, st, k0, j0, jj, rr0, inv_r, az,
+                                                                                     sp_old, red);
+                    else
+                        batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ, WET, false>(A, D, st, k0, j0, jj, rr0, inv_r,
+                                                                                        az, sp_old, red);
+                }
                 if (CHK)
                     warp_slot_store(red, q, slots + s * kSlots, A.tile_part + 4ll * kSlots * kBatchMaxWarps * tile);
             }
