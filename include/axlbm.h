@@ -464,6 +464,23 @@ AXLBM_API axlbm_status axlbm_batch_set_fields_all(axlbm_batch* b, const void* fi
 AXLBM_API axlbm_status axlbm_batch_moments_all(axlbm_batch* b, uint32_t field_mask, void* out, int32_t out_dtype,
                                                int32_t out_on_device);
 
+/* Asynchronous host I/O of every domain's fields, for a run that sets fields
+ * from and reads results into host memory each call: the copies run on a
+ * stream of the library's own, through two staging buffers each way (kept,
+ * grown as needed, until the batch is destroyed), so one call's copies run
+ * beside the previous or the next call's steps.  Same layouts, dtypes and
+ * rules as axlbm_batch_set_fields_all / axlbm_batch_moments_all with host
+ * arrays; the order of the calls on the batch is kept (fields set before a
+ * step are the ones it starts from, moments are those of the level at the
+ * call).  host_fields must stay untouched and host_out is filled only when
+ * axlbm_batch_sync returns; page-locked host memory lets the copies overlap
+ * (pageable memory works, without overlap). */
+AXLBM_API axlbm_status axlbm_batch_set_fields_all_async(axlbm_batch* b, const void* host_fields, int32_t in_dtype);
+AXLBM_API axlbm_status axlbm_batch_moments_all_async(axlbm_batch* b, uint32_t field_mask, void* host_out,
+                                                     int32_t out_dtype);
+/* Wait for the batch's work and every asynchronous copy. */
+AXLBM_API axlbm_status axlbm_batch_sync(axlbm_batch* b);
+
 /* Populations of domain d at the current level (host FP64, layout as
  * axlbm_get_populations).  Synchronises. */
 AXLBM_API axlbm_status axlbm_batch_get_populations(axlbm_batch* b, int32_t d, double* f, double* g,

@@ -134,6 +134,9 @@ def lib() -> ctypes.CDLL:
                                                   ctypes.POINTER(ctypes.c_uint32)]
         L.axlbm_batch_set_tile_shape.argtypes = [H, ctypes.c_int32, ctypes.c_int32]
         L.axlbm_batch_tile_shapes.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+        L.axlbm_batch_set_fields_all_async.argtypes = [H, ctypes.c_void_p, ctypes.c_int32]
+        L.axlbm_batch_moments_all_async.argtypes = [H, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int32]
+        L.axlbm_batch_sync.argtypes = [H]
         L.axlbm_batch_use_graphs.argtypes = [H, ctypes.c_int32]
         L.axlbm_batch_set_time.argtypes = [H, ctypes.c_int64]
         for pre in ("axlbm_", "axlbm_batch_"):
@@ -172,6 +175,7 @@ def lib() -> ctypes.CDLL:
                      "axlbm_batch_set_populations", "axlbm_batch_time", "axlbm_batch_tile_shape",
                      "axlbm_batch_set_tile_shape", "axlbm_batch_tile_shapes", "axlbm_batch_use_graphs", "axlbm_batch_graph_stats",
                      "axlbm_batch_set_time", "axlbm_batch_copy_domain", "axlbm_batch_set_residual_lag",
+                     "axlbm_batch_set_fields_all_async", "axlbm_batch_moments_all_async", "axlbm_batch_sync",
                      "axlbm_batch_kernel_timing", "axlbm_batch_kernel_times", "axlbm_batch_kernel_times_by_parity",
                      "axlbm_batch_destroy",
                      "axlbm_batch_set_fields_all", "axlbm_batch_moments_all"):
@@ -527,6 +531,18 @@ def axlbm_batch_set_fields_all(b, ptr: int, in_dtype: int, on_device: int) -> No
 def axlbm_batch_moments_all(b, mask: int, out_ptr: int, out_dtype: int, out_on_device: int) -> None:
     _bcheck(lib().axlbm_batch_moments_all(b, int(mask), ctypes.c_void_p(out_ptr), int(out_dtype),
                                           int(out_on_device)), b)
+
+
+def axlbm_batch_set_fields_all_async(b, host_ptr: int, in_dtype: int) -> None:
+    _bcheck(lib().axlbm_batch_set_fields_all_async(b, ctypes.c_void_p(host_ptr), int(in_dtype)), b)
+
+
+def axlbm_batch_moments_all_async(b, mask: int, host_ptr: int, out_dtype: int) -> None:
+    _bcheck(lib().axlbm_batch_moments_all_async(b, int(mask), ctypes.c_void_p(host_ptr), int(out_dtype)), b)
+
+
+def axlbm_batch_sync(b) -> None:
+    _bcheck(lib().axlbm_batch_sync(b), b)
 
 
 def axlbm_batch_get_populations(b, d: int, f, g, t_pop) -> None:

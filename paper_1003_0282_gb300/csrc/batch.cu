@@ -869,6 +869,107 @@ axlbm_status axlbm_batch_moments_all(axlbm_batch* b, uint32_t mask, void* out, i
     return e == cudaSuccess ? AXLBM_OK : bcuda(b, e, "moments_all");
 }
 
+}  // extern "C"
+
+namespace {
+
+// The copy stream and the events of the asynchronous host I/O (created once).
+cudaError_t io_setup(axlbm_batch* b) {
+    if (b->io) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->io, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        cudaEvent_t* evs[] = {&b->ev_in_ready[k], &b->ev_in_free[k], &b->ev_out_ready[k], &b->ev_out_free[k]};
+        for (cudaEvent_t* ev : evs) {
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(*ev, b->stream);  // nothing to wait for yet
+        }
+    }
+    return e;
+}
+
+// Staging buffer `buf` of at least `bytes` (grown after both streams are idle).
+cudaError_t io_buffer(axlbm_batch* b, void** buf, size_t* have, size_t bytes) {
+    if (*have >= bytes) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(b->io);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return e;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    e = cudaMalloc(buf, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return e;
+    }
+    *have = bytes;
+    return cudaSuccess;
+}
+
+size_t all_values(const axlbm_batch* b, int per_node) {
+    size_t total = 0;
+    for (int d = 0; d < b->n; ++d) total += (size_t)per_node * b->desc[d].grid.nr * b->desc[d].grid.nz;
+    return total;
+}
+
+}  // namespace
+
+extern "C" {
+
+axlbm_status axlbm_batch_set_fields_all_async(axlbm_batch* b, const void* host_fields, int32_t in_dtype) {
+    if (!b || !host_fields || (in_dtype != AXLBM_F64 && in_dtype != AXLBM_F32))
+        return bfail(b, AXLBM_EINVAL, "bad batch or fields");
+    if (b->parity != 0) return bfail(b, AXLBM_EINVAL, "set_fields needs an even time level");
+    const size_t bytes = all_values(b, 5) * (in_dtype == AXLBM_F32 ? 4 : 8);
+    cudaError_t e = io_setup(b);
+    const int k = b->io_in_next;
+    if (e == cudaSuccess) e = io_buffer(b, &b->io_in[k], &b->io_in_bytes[k], bytes);
+    if (e != cudaSuccess) return bfail(b, AXLBM_ENOMEM, "asynchronous staging buffer");
+    // the copy waits until the kernel that last read this buffer is done
+    e = cudaStreamWaitEvent(b->io, b->ev_in_free[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->io_in[k], host_fields, bytes, cudaMemcpyHostToDevice, b->io);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_in_ready[k], b->io);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_in_ready[k], 0);
+    if (e == cudaSuccess) e = batch_ops_for(b->precision)->init_all(b, b->io_in[k], in_dtype == AXLBM_F32);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_in_free[k], b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "set_fields_all_async");
+    b->io_in_next ^= 1;
+    b->speed_valid = false;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_moments_all_async(axlbm_batch* b, uint32_t mask, void* host_out, int32_t out_dtype) {
+    if (!b || !host_out || mask == 0 || (mask & ~31u)) return bfail(b, AXLBM_EINVAL, "bad batch, output or field mask");
+    if (out_dtype != AXLBM_F64 && out_dtype != AXLBM_F32) return bfail(b, AXLBM_EINVAL, "bad out_dtype");
+    if (mask & AXLBM_T)
+        for (int d = 0; d < b->n; ++d)
+            if (!b->desc[d].grid.with_temperature) return bfail(b, AXLBM_EINVAL, "T needs with_temperature in every domain");
+    int nf = 0;
+    for (int f = 0; f < 5; ++f) nf += (mask >> f) & 1;
+    const size_t bytes = all_values(b, nf) * (out_dtype == AXLBM_F32 ? 4 : 8);
+    cudaError_t e = io_setup(b);
+    const int k = b->io_out_next;
+    if (e == cudaSuccess) e = io_buffer(b, &b->io_out[k], &b->io_out_bytes[k], bytes);
+    if (e != cudaSuccess) return bfail(b, AXLBM_ENOMEM, "asynchronous staging buffer");
+    // the kernel waits until the copy that last read this buffer is done
+    e = cudaStreamWaitEvent(b->stream, b->ev_out_free[k], 0);
+    if (e == cudaSuccess) e = batch_ops_for(b->precision)->moments_all(b, b->io_out[k], mask, out_dtype == AXLBM_F32);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_out_ready[k], b->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->io, b->ev_out_ready[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, b->io_out[k], bytes, cudaMemcpyDeviceToHost, b->io);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_out_free[k], b->io);
+    if (e != cudaSuccess) return bcuda(b, e, "moments_all_async");
+    b->io_out_next ^= 1;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_sync(axlbm_batch* b) {
+    if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess && b->io) e = cudaStreamSynchronize(b->io);
+    return e == cudaSuccess ? AXLBM_OK : bcuda(b, e, "sync");
+}
+
 axlbm_status axlbm_batch_get_populations(axlbm_batch* b, int32_t d, double* f, double* g, double* tp) {
     if (!domain_ok(b, d) || !f) return bfail(b, AXLBM_EINVAL, "bad batch, domain index or arrays");
     const axlbm_domain& D = b->desc[d];
@@ -1145,6 +1246,18 @@ axlbm_status axlbm_batch_destroy(axlbm_batch* b) {
     batch_drop_graphs(b);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->stage) cudaFree(b->stage);
+    if (b->io) {
+        cudaError_t e2 = cudaStreamSynchronize(b->io);
+        if (e == cudaSuccess) e = e2;
+        cudaStreamDestroy(b->io);
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (b->io_in[k]) cudaFree(b->io_in[k]);
+        if (b->io_out[k]) cudaFree(b->io_out[k]);
+        cudaEvent_t evs[] = {b->ev_in_ready[k], b->ev_in_free[k], b->ev_out_ready[k], b->ev_out_free[k]};
+        for (cudaEvent_t ev : evs)
+            if (ev) cudaEventDestroy(ev);
+    }
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->join) cudaEventDestroy(b->join);
     for (auto ev : b->ev)

@@ -242,11 +242,12 @@ __device__ __forceinline__ uint32_t batch_tile_bytes(bool th) {
 }
 
 // Update one node pair (or one node) of a tile from its stage.
-// EDGE: some lane of the warp sits on a side column the bulk kernel updates
-// (odd steps; the other warps run without the side-column selections).
-template <class S, class R, class RC, bool SW, bool THD, int PAR, bool CHK, int TK, int TJ, bool WET, bool EDGE>
+// eg: some lane of the warp sits on a side column the bulk kernel updates
+// (odd steps; the other warps load and store without the side-column
+// selections -- only those sections exist twice, the collision once).
+template <class S, class R, class RC, bool SW, bool THD, int PAR, bool CHK, int TK, int TJ, bool WET>
 __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const SlotDesc& D, const S* st, int k0, int j0,
-                                            int jj, int rr, R inv_r, R az, const R* sp_old, RedR<R>& red) {
+                                            int jj, int rr, R inv_r, R az, const R* sp_old, RedR<R>& red, bool eg) {
     constexpr int NL = Lanes<RC>::n;
     constexpr int BW = batch_box_w<S, TK, TJ>(), HB = 16 / (int)sizeof(S);
     constexpr int PS = batch_plane_elems<S, TK, TJ>();
@@ -258,7 +259,7 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
     for (int l = 0; l < NL; ++l) {
         const int kl = k0 - D.row0 + rr + l * (TK / NL);
         act[l] = jl < D.nr && kl < D.nz;
-        if (PAR == 1) act[l] = act[l] && ((EDGE && D.side) || (jl > 0 && jl < D.nr - 1)) && kl > 0 && kl < D.nz - 1;
+        if (PAR == 1) act[l] = act[l] && ((eg && D.side) || (jl > 0 && jl < D.nr - 1)) && kl > 0 && kl < D.nz - 1;
         any = any || act[l];
     }
     if (!any) return;
@@ -267,17 +268,21 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
     constexpr int LROW = (TK / NL) * BW;
     using Sc = typename ScalarOf<RC>::type;
     // odd steps: a side column (see kEdgeAxis); its own slots in global memory for the wall
-    const int edge =
-        (EDGE && PAR == 1 && D.side) ? (jl == 0 ? kEdgeAxis : (jl == D.nr - 1 ? kEdgeWall : kEdgeNone)) : kEdgeNone;
+    const int edge_rt =
+        (PAR == 1 && eg && D.side) ? (jl == 0 ? kEdgeAxis : (jl == D.nr - 1 ? kEdgeWall : kEdgeNone)) : kEdgeNone;
     const S* own = A.pop + (long long)(k0 + rr) * A.pitch + (j0 + jj);
     const int LOWN = (TK / NL) * (int)A.pitch;
+    auto load_node = [&](auto edge_tag) {
+    constexpr bool EDGE = decltype(edge_tag)::value;
+    const int edge = EDGE ? edge_rt : kEdgeNone;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
         const int p = PAR ? opp9(a) : a;
         if (PAR == 1 && cr9(a) > 0 && edge == kEdgeAxis)
             c.d[a] = Lanes<RC>::template load<S>(row + axis_pull_plane9(a) * PS, LROW);
-        else if (PAR == 1 && cr9(a) < 0 && edge == kEdgeWall)
-            c.d[a] = Lanes<RC>::template load<S>(own + a * A.plane, LOWN);
+        else if (PAR == 1 && cr9(a) < 0 && edge == kEdgeWall)  // own slot: in the stage for a = 3 (no row shift)
+            c.d[a] = a == 3 ? Lanes<RC>::template load<S>(row + 3 * PS, LROW)
+                            : Lanes<RC>::template load<S>(own + a * A.plane, LOWN);
         else
             c.d[a] = Lanes<RC>::template load<S>(row + p * PS + (PAR ? cr9(p) : 0), LROW);
     }
@@ -288,7 +293,7 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
             if (PAR == 1 && cr4(q) > 0 && edge == kEdgeAxis)  // g is odd across the axis
                 c.g[q] = Lanes<RC>::template load<S>(row + (9 + opp4(idx4(-1, 0))) * PS, LROW) * RC(Sc(-1));
             else if (PAR == 1 && cr4(q) < 0 && edge == kEdgeWall)
-                c.g[q] = wall_g(Lanes<RC>::template load<S>(own + (9 + q) * A.plane, LOWN), D.gw_out);
+                c.g[q] = wall_g(Lanes<RC>::template load<S>(row + (9 + q) * PS, LROW), D.gw_out);  // own slot, in the stage
             else
                 c.g[q] = Lanes<RC>::template load<S>(row + (9 + p) * PS + (PAR ? cr4(p) : 0), LROW);
         }
@@ -300,12 +305,16 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
             if (PAR == 1 && cr4(q) > 0 && edge == kEdgeAxis)
                 c.h[q] = Lanes<RC>::template load<S>(row + (HP + opp4(idx4(-1, 0))) * PS, LROW);
             else if (PAR == 1 && cr4(q) < 0 && edge == kEdgeWall)
-                c.h[q] = wall_h(Lanes<RC>::template load<S>(own + (HP + q) * A.plane, LOWN), D.tdir_out, D.c.t_ref,
-                                D.tw_out);
+                c.h[q] = wall_h(Lanes<RC>::template load<S>(row + (HP + q) * PS, LROW), D.tdir_out, D.c.t_ref,
+                                D.tw_out);  // own slot, in the stage
             else
                 c.h[q] = Lanes<RC>::template load<S>(row + (HP + p) * PS + (PAR ? cr4(p) : 0), LROW);
         }
     }
+    };
+    if (PAR == 1 && eg) load_node(std::true_type{});
+    else load_node(std::false_type{});
+    const int edge = edge_rt;
     c.collide(inv_r, D.c, az);
     // odd steps: what a side node sends across its face, bounced back or mirrored
     RC gsend = RC(Sc(0)), hsend = RC(Sc(0));
@@ -341,6 +350,9 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
                 for (int q = 0; q < 4; ++q) Codec<S>::store(A.pop + (HP + opp4(q)) * pl + x, Lanes<RC>::get(c.h[q], l));
             }
         } else {
+            auto store_node = [&](auto edge_tag) {
+            constexpr bool EDGE = decltype(edge_tag)::value;
+            const int edge = EDGE ? edge_rt : kEdgeNone;
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
                 if (cr9(a) < 0 && edge == kEdgeAxis)
@@ -372,6 +384,9 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
                         Codec<S>::store(A.pop + (HP + q) * pl + x + cz4(q) * A.pitch + cr4(q), Lanes<RC>::get(c.h[q], l));
                 }
             }
+            };
+            if (eg) store_node(std::true_type{});
+            else store_node(std::false_type{});
         }
         if (CHK) {
             const R vur = Lanes<RC>::get(c.ur, l), vuz = Lanes<RC>::get(c.uz, l), vrho = Lanes<RC>::get(c.rho, l);
@@ -530,21 +545,12 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
                 // (a vote among the lanes that reached here: a lane whose wait gave up is not one of them)
                 const bool eg = PAR == 1 && __any_sync(__activemask(), side_lane);
                 // one node pair per thread: rows rr0 and rr0 + TK/2 of column jj
-                if (eg) {
-                    if (dth)
-                        batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ, WET, true>(A, D, st, k0, j0, jj, rr0, inv_r, az,
-                                                                                    sp_old, red);
-                    else
-                        batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ, WET, true>(A, D, st, k0, j0, jj, rr0, inv_r,
-                                                                                       az, sp_old, red);
-                } else {
-                    if (dth)
-                        batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ, WET, false>(A, D, st, k0, j0, jj, rr0, inv_r, az,
-                                                                                     sp_old, red);
-                    else
-                        batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ, WET, false>(A, D, st, k0, j0, jj, rr0, inv_r,
-                                                                                        az, sp_old, red);
-                }
+                if (dth)
+                    batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old, red,
+                                                                          eg);
+                else
+                    batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old,
+                                                                             red, eg);
                 if (CHK)
                     warp_slot_store(red, q, slots + s * kSlots, A.tile_part + 4ll * kSlots * kBatchMaxWarps * tile);
             }

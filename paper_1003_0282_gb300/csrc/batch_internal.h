@@ -89,6 +89,15 @@ struct axlbm_batch {
     int64_t graph_captures, graph_launches;
     void* stage;  // device staging buffer of host-side field I/O, kept between calls
     size_t stage_bytes;
+    // asynchronous all-domain host I/O (axlbm_batch_*_all_async): a copy
+    // stream of the library's own and two staging buffers each way, so that
+    // one call's copies run beside the previous or next call's steps
+    cudaStream_t io = nullptr;
+    void* io_in[2] = {nullptr, nullptr};
+    void* io_out[2] = {nullptr, nullptr};
+    size_t io_in_bytes[2] = {0, 0}, io_out_bytes[2] = {0, 0};
+    cudaEvent_t ev_in_ready[2] = {}, ev_in_free[2] = {}, ev_out_ready[2] = {}, ev_out_free[2] = {};
+    int io_in_next = 0, io_out_next = 0;
     std::string err;
 };
 

@@ -856,161 +856,173 @@ k_bulk(const __grid_constant__ CUtensorMap map, const KArgs<S, R> A) {
                 const double rj = node_radius(G, j);
                 inv_r = rj > 0.0 ? rcp(Sc(rj)) : Sc(0);
             }
-            // the node rows of this thread in the tile; EDGE: some lane of the warp sits on a side
-            // column the bulk kernel updates (odd steps; other warps run without those selections)
-            auto tile_rows = [&](auto edge_tag) {
-                constexpr bool EDGE = decltype(edge_tag)::value;
-    #pragma unroll
-                for (int rr = tid / kTileJ; ok && rr < kTileK / NL; rr += kBulkThreads / kTileJ) {
-                    bool act[NL];
-                    int kk[NL];
-                    bool any = false;
-    #pragma unroll
-                    for (int l = 0; l < NL; ++l) {
-                        kk[l] = k0 + rr + l * (kTileK / NL);
-                        act[l] = j < G.nr && kk[l] < G.nz;
-                        if (PAR == 1)
-                            act[l] = act[l] && ((EDGE && G.side) || (j > 0 && j < G.nr - 1)) && kk[l] > 0 && kk[l] < G.nz - 1;
-                        any = any || act[l];
-                    }
-                    if (!any) continue;
-                    Cell<RC, SW, TH> c;
-                    const S* row = st + rr * BW + HB + jj;
-                    constexpr int LROW = (kTileK / NL) * BW;  // shared-memory distance between the lanes' rows
-                    // odd steps: a side column (see kEdgeAxis); its own slots in global memory for the wall
-                    const int edge = (EDGE && PAR == 1 && G.side) ? (j == 0 ? kEdgeAxis : (j == G.nr - 1 ? kEdgeWall : kEdgeNone))
-                                                          : kEdgeNone;
-                    const S* own = A.pop + (long long)(k0 + rr) * G.pitch + j;
-                    const int LOWN = (kTileK / NL) * (int)G.pitch;
-    #pragma unroll
-                    for (int a = 0; a < 9; ++a) {
-                        const int p = PAR ? opp9(a) : a;
-                        if (PAR == 1 && cr9(a) > 0 && edge == kEdgeAxis)
-                            c.d[a] = Lanes<RC>::template load<S>(row + axis_pull_plane9(a) * kTileK * BW, LROW);
-                        else if (PAR == 1 && cr9(a) < 0 && edge == kEdgeWall)
-                            c.d[a] = Lanes<RC>::template load<S>(own + a * G.plane, LOWN);
-                        else
-                            c.d[a] = Lanes<RC>::template load<S>(row + p * kTileK * BW + (PAR ? cr9(p) : 0), LROW);
-                    }
-                    if (SW) {
-    #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int p = PAR ? opp4(q) : q;
-                            if (PAR == 1 && cr4(q) > 0 && edge == kEdgeAxis)  // g is odd across the axis
-                                c.g[q] = Lanes<RC>::template load<S>(row + (9 + opp4(idx4(-1, 0))) * kTileK * BW, LROW) *
-                                         RC(Sc(-1));
-                            else if (PAR == 1 && cr4(q) < 0 && edge == kEdgeWall)
-                                c.g[q] = wall_g(Lanes<RC>::template load<S>(own + (9 + q) * G.plane, LOWN), A.gw_out);
-                            else
-                                c.g[q] = Lanes<RC>::template load<S>(row + (9 + p) * kTileK * BW + (PAR ? cr4(p) : 0), LROW);
-                        }
-                    }
-                    if (TH) {
-    #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int p = PAR ? opp4(q) : q;
-                            if (PAR == 1 && cr4(q) > 0 && edge == kEdgeAxis)
-                                c.h[q] = Lanes<RC>::template load<S>(row + (HP + opp4(idx4(-1, 0))) * kTileK * BW, LROW);
-                            else if (PAR == 1 && cr4(q) < 0 && edge == kEdgeWall)
-                                c.h[q] = wall_h(Lanes<RC>::template load<S>(own + (HP + q) * G.plane, LOWN),
-                                                A.C.t_dir[AXLBM_FACE_OUTER], A.C.t_ref, A.C.t_w[AXLBM_FACE_OUTER]);
-                            else
-                                c.h[q] = Lanes<RC>::template load<S>(row + (HP + p) * kTileK * BW + (PAR ? cr4(p) : 0), LROW);
-                        }
-                    }
-                    c.collide(inv_r, A.C, az);
-                    // odd steps: what a side node sends across its face, bounced back or mirrored
-                    RC gsend = RC(Sc(0)), hsend = RC(Sc(0));
-                    if (PAR == 1 && SW && edge == kEdgeAxis) gsend = c.g[2] * RC(Sc(-1));
-                    if (PAR == 1 && SW && edge == kEdgeWall) gsend = wall_g(c.g[0], A.gw_out);
-                    if (PAR == 1 && TH && edge == kEdgeAxis) hsend = c.h[2];
-                    if (PAR == 1 && TH && edge == kEdgeWall)
-                        hsend = wall_h(c.h[0], A.C.t_dir[AXLBM_FACE_OUTER], A.C.t_ref, A.C.t_w[AXLBM_FACE_OUTER]);
-    #pragma unroll
-                    for (int l = 0; l < NL; ++l) {
-                        if (!act[l]) continue;
-                        const long long x = (long long)kk[l] * G.pitch + j;
-                        if (PAR == 0 && has_wet_wall(G) && on_wet_wall(G, j, kk[l])) {
-                            // a wet-wall node holds its post-collision state and keeps it
-                            const S* src = row + l * LROW;
-    #pragma unroll
-                            for (int a = 0; a < 9; ++a) A.pop[opp9(a) * G.plane + x] = src[a * kTileK * BW];
-                            if (SW) {
-    #pragma unroll
-                                for (int q = 0; q < 4; ++q) A.pop[(9 + opp4(q)) * G.plane + x] = src[(9 + q) * kTileK * BW];
-                            }
-                            if (TH) {
-    #pragma unroll
-                                for (int q = 0; q < 4; ++q) A.pop[(HP + opp4(q)) * G.plane + x] = src[(HP + q) * kTileK * BW];
-                            }
-                        } else if (PAR == 0) {
-    #pragma unroll
-                            for (int a = 0; a < 9; ++a) Codec<S>::store(A.pop + opp9(a) * G.plane + x, Lanes<RC>::get(c.d[a], l));
-                            if (SW) {
-    #pragma unroll
-                                for (int q = 0; q < 4; ++q)
-                                    Codec<S>::store(A.pop + (9 + opp4(q)) * G.plane + x, Lanes<RC>::get(c.g[q], l));
-                            }
-                            if (TH) {
-    #pragma unroll
-                                for (int q = 0; q < 4; ++q)
-                                    Codec<S>::store(A.pop + (HP + opp4(q)) * G.plane + x, Lanes<RC>::get(c.h[q], l));
-                            }
-                        } else {
-    #pragma unroll
-                            for (int a = 0; a < 9; ++a) {
-                                if (cr9(a) < 0 && edge == kEdgeAxis)
-                                    Codec<S>::store(A.pop + axis_push_plane9(a) * G.plane + x + cz9(a) * G.pitch,
-                                                    Lanes<RC>::get(c.d[a], l));
-                                else if (cr9(a) > 0 && edge == kEdgeWall)
-                                    Codec<S>::store(A.pop + opp9(a) * G.plane + x, Lanes<RC>::get(c.d[a], l));
-                                else
-                                    Codec<S>::store(A.pop + a * G.plane + x + cz9(a) * G.pitch + cr9(a),
-                                                    Lanes<RC>::get(c.d[a], l));
-                            }
-                            if (SW) {
-    #pragma unroll
-                                for (int q = 0; q < 4; ++q) {
-                                    if (q == 2 && edge == kEdgeAxis)
-                                        Codec<S>::store(A.pop + 9 * G.plane + x, Lanes<RC>::get(gsend, l));
-                                    else if (q == 0 && edge == kEdgeWall)
-                                        Codec<S>::store(A.pop + 11 * G.plane + x, Lanes<RC>::get(gsend, l));
-                                    else
-                                        Codec<S>::store(A.pop + (9 + q) * G.plane + x + cz4(q) * G.pitch + cr4(q),
-                                                        Lanes<RC>::get(c.g[q], l));
-                                }
-                            }
-                            if (TH) {
-    #pragma unroll
-                                for (int q = 0; q < 4; ++q) {
-                                    if (q == 2 && edge == kEdgeAxis)
-                                        Codec<S>::store(A.pop + HP * G.plane + x, Lanes<RC>::get(hsend, l));
-                                    else if (q == 0 && edge == kEdgeWall)
-                                        Codec<S>::store(A.pop + (HP + 2) * G.plane + x, Lanes<RC>::get(hsend, l));
-                                    else
-                                        Codec<S>::store(A.pop + (HP + q) * G.plane + x + cz4(q) * G.pitch + cr4(q),
-                                                        Lanes<RC>::get(c.h[q], l));
-                                }
-                            }
-                        }
-                        if (CHK) {
-                            const R vur = Lanes<RC>::get(c.ur, l), vuz = Lanes<RC>::get(c.uz, l);
-                            const R vrho = Lanes<RC>::get(c.rho, l);
-                            const R sp = sqrt(vur * vur + vuz * vuz);
-                            if (A.residual) red.rmax = max(red.rmax, (R)fabs(sp - sp_old[(rr - tid / kTileJ) / 2 + l]));
-                            A.speed[x] = sp;
-                            red.dmass.add(Lanes<RC>::get(c.ds0, l));
-                            red.budget.add(vrho * vur * inv_r);
-                            red.bad += (isfinite(vrho) && isfinite(vur) && isfinite(vuz)) ? 0 : 1;
-                            red.count += 1;
-                        }
-                    }
-                }
-            };
+            // warps with a side-column lane load and store with the side-column
+            // selections (odd steps); the others without them
             const bool side_lane = PAR == 1 && G.side && (j == 0 || j == G.nr - 1);
             // (a vote among the lanes that reached here: a lane whose wait gave up is not one of them)
-            if (PAR == 1 && __any_sync(__activemask(), side_lane)) tile_rows(std::true_type{});
-            else tile_rows(std::false_type{});
+            const bool eg = PAR == 1 && __any_sync(__activemask(), side_lane);
+#pragma unroll
+            for (int rr = tid / kTileJ; ok && rr < kTileK / NL; rr += kBulkThreads / kTileJ) {
+                bool act[NL];
+                int kk[NL];
+                bool any = false;
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    kk[l] = k0 + rr + l * (kTileK / NL);
+                    act[l] = j < G.nr && kk[l] < G.nz;
+                    if (PAR == 1)
+                        act[l] = act[l] && ((eg && G.side) || (j > 0 && j < G.nr - 1)) && kk[l] > 0 && kk[l] < G.nz - 1;
+                    any = any || act[l];
+                }
+                if (!any) continue;
+                Cell<RC, SW, TH> c;
+                const S* row = st + rr * BW + HB + jj;
+                constexpr int LROW = (kTileK / NL) * BW;  // shared-memory distance between the lanes' rows
+                // odd steps: a side column (see kEdgeAxis); its own slots in global memory for the wall
+                const int edge_rt =
+                    (eg && PAR == 1 && G.side) ? (j == 0 ? kEdgeAxis : (j == G.nr - 1 ? kEdgeWall : kEdgeNone)) : kEdgeNone;
+                const S* own = A.pop + (long long)(k0 + rr) * G.pitch + j;
+                const int LOWN = (kTileK / NL) * (int)G.pitch;
+                auto load_node = [&](auto edge_tag) {
+                constexpr bool EDGE = decltype(edge_tag)::value;
+                const int edge = EDGE ? edge_rt : kEdgeNone;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    const int p = PAR ? opp9(a) : a;
+                    if (PAR == 1 && cr9(a) > 0 && edge == kEdgeAxis)
+                        c.d[a] = Lanes<RC>::template load<S>(row + axis_pull_plane9(a) * kTileK * BW, LROW);
+                    else if (PAR == 1 && cr9(a) < 0 && edge == kEdgeWall)  // own slot: in the stage for a = 3 (no row shift)
+                        c.d[a] = a == 3 ? Lanes<RC>::template load<S>(row + 3 * kTileK * BW, LROW)
+                                        : Lanes<RC>::template load<S>(own + a * G.plane, LOWN);
+                    else
+                        c.d[a] = Lanes<RC>::template load<S>(row + p * kTileK * BW + (PAR ? cr9(p) : 0), LROW);
+                }
+                if (SW) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int p = PAR ? opp4(q) : q;
+                        if (PAR == 1 && cr4(q) > 0 && edge == kEdgeAxis)  // g is odd across the axis
+                            c.g[q] = Lanes<RC>::template load<S>(row + (9 + opp4(idx4(-1, 0))) * kTileK * BW, LROW) *
+                                     RC(Sc(-1));
+                        else if (PAR == 1 && cr4(q) < 0 && edge == kEdgeWall)
+                            c.g[q] = wall_g(Lanes<RC>::template load<S>(row + (9 + q) * kTileK * BW, LROW),
+                                            A.gw_out);  // own slot, in the stage
+                        else
+                            c.g[q] = Lanes<RC>::template load<S>(row + (9 + p) * kTileK * BW + (PAR ? cr4(p) : 0), LROW);
+                    }
+                }
+                if (TH) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int p = PAR ? opp4(q) : q;
+                        if (PAR == 1 && cr4(q) > 0 && edge == kEdgeAxis)
+                            c.h[q] = Lanes<RC>::template load<S>(row + (HP + opp4(idx4(-1, 0))) * kTileK * BW, LROW);
+                        else if (PAR == 1 && cr4(q) < 0 && edge == kEdgeWall)
+                            c.h[q] = wall_h(Lanes<RC>::template load<S>(row + (HP + q) * kTileK * BW, LROW),
+                                            A.C.t_dir[AXLBM_FACE_OUTER], A.C.t_ref,
+                                            A.C.t_w[AXLBM_FACE_OUTER]);  // own slot, in the stage
+                        else
+                            c.h[q] = Lanes<RC>::template load<S>(row + (HP + p) * kTileK * BW + (PAR ? cr4(p) : 0), LROW);
+                    }
+                }
+                };
+                if (PAR == 1 && eg) load_node(std::true_type{});
+                else load_node(std::false_type{});
+                const int edge = edge_rt;
+                c.collide(inv_r, A.C, az);
+                // odd steps: what a side node sends across its face, bounced back or mirrored
+                RC gsend = RC(Sc(0)), hsend = RC(Sc(0));
+                if (PAR == 1 && SW && edge == kEdgeAxis) gsend = c.g[2] * RC(Sc(-1));
+                if (PAR == 1 && SW && edge == kEdgeWall) gsend = wall_g(c.g[0], A.gw_out);
+                if (PAR == 1 && TH && edge == kEdgeAxis) hsend = c.h[2];
+                if (PAR == 1 && TH && edge == kEdgeWall)
+                    hsend = wall_h(c.h[0], A.C.t_dir[AXLBM_FACE_OUTER], A.C.t_ref, A.C.t_w[AXLBM_FACE_OUTER]);
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    if (!act[l]) continue;
+                    const long long x = (long long)kk[l] * G.pitch + j;
+                    if (PAR == 0 && has_wet_wall(G) && on_wet_wall(G, j, kk[l])) {
+                        // a wet-wall node holds its post-collision state and keeps it
+                        const S* src = row + l * LROW;
+#pragma unroll
+                        for (int a = 0; a < 9; ++a) A.pop[opp9(a) * G.plane + x] = src[a * kTileK * BW];
+                        if (SW) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) A.pop[(9 + opp4(q)) * G.plane + x] = src[(9 + q) * kTileK * BW];
+                        }
+                        if (TH) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) A.pop[(HP + opp4(q)) * G.plane + x] = src[(HP + q) * kTileK * BW];
+                        }
+                    } else if (PAR == 0) {
+#pragma unroll
+                        for (int a = 0; a < 9; ++a) Codec<S>::store(A.pop + opp9(a) * G.plane + x, Lanes<RC>::get(c.d[a], l));
+                        if (SW) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                Codec<S>::store(A.pop + (9 + opp4(q)) * G.plane + x, Lanes<RC>::get(c.g[q], l));
+                        }
+                        if (TH) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                Codec<S>::store(A.pop + (HP + opp4(q)) * G.plane + x, Lanes<RC>::get(c.h[q], l));
+                        }
+                    } else {
+                        auto store_node = [&](auto edge_tag) {
+                        constexpr bool EDGE = decltype(edge_tag)::value;
+                        const int edge = EDGE ? edge_rt : kEdgeNone;
+#pragma unroll
+                        for (int a = 0; a < 9; ++a) {
+                            if (cr9(a) < 0 && edge == kEdgeAxis)
+                                Codec<S>::store(A.pop + axis_push_plane9(a) * G.plane + x + cz9(a) * G.pitch,
+                                                Lanes<RC>::get(c.d[a], l));
+                            else if (cr9(a) > 0 && edge == kEdgeWall)
+                                Codec<S>::store(A.pop + opp9(a) * G.plane + x, Lanes<RC>::get(c.d[a], l));
+                            else
+                                Codec<S>::store(A.pop + a * G.plane + x + cz9(a) * G.pitch + cr9(a),
+                                                Lanes<RC>::get(c.d[a], l));
+                        }
+                        if (SW) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                if (q == 2 && edge == kEdgeAxis)
+                                    Codec<S>::store(A.pop + 9 * G.plane + x, Lanes<RC>::get(gsend, l));
+                                else if (q == 0 && edge == kEdgeWall)
+                                    Codec<S>::store(A.pop + 11 * G.plane + x, Lanes<RC>::get(gsend, l));
+                                else
+                                    Codec<S>::store(A.pop + (9 + q) * G.plane + x + cz4(q) * G.pitch + cr4(q),
+                                                    Lanes<RC>::get(c.g[q], l));
+                            }
+                        }
+                        if (TH) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                if (q == 2 && edge == kEdgeAxis)
+                                    Codec<S>::store(A.pop + HP * G.plane + x, Lanes<RC>::get(hsend, l));
+                                else if (q == 0 && edge == kEdgeWall)
+                                    Codec<S>::store(A.pop + (HP + 2) * G.plane + x, Lanes<RC>::get(hsend, l));
+                                else
+                                    Codec<S>::store(A.pop + (HP + q) * G.plane + x + cz4(q) * G.pitch + cr4(q),
+                                                    Lanes<RC>::get(c.h[q], l));
+                            }
+                        }
+                        };
+                        if (eg) store_node(std::true_type{});
+                        else store_node(std::false_type{});
+                    }
+                    if (CHK) {
+                        const R vur = Lanes<RC>::get(c.ur, l), vuz = Lanes<RC>::get(c.uz, l);
+                        const R vrho = Lanes<RC>::get(c.rho, l);
+                        const R sp = sqrt(vur * vur + vuz * vuz);
+                        if (A.residual) red.rmax = max(red.rmax, (R)fabs(sp - sp_old[(rr - tid / kTileJ) / 2 + l]));
+                        A.speed[x] = sp;
+                        red.dmass.add(Lanes<RC>::get(c.ds0, l));
+                        red.budget.add(vrho * vur * inv_r);
+                        red.bad += (isfinite(vrho) && isfinite(vur) && isfinite(vuz)) ? 0 : 1;
+                        red.count += 1;
+                    }
+                }
+            }
             __syncwarp();
             if (!__all_sync(0xffffffffu, ok && !abort_flag)) {
                 abort_flag = 1;
