@@ -533,6 +533,19 @@ def axlbm_batch_moments_all(b, mask: int, out_ptr: int, out_dtype: int, out_on_d
                                           int(out_on_device)), b)
 
 
+def _host_array(a):
+    """(dtype code, address) of a contiguous FP32/FP64 host array (numpy or CPU tensor)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous or a.dtype not in (np.float32, np.float64):
+            raise ValueError("a contiguous float32 or float64 array is needed")
+        return (F32 if a.dtype == np.float32 else F64), a.ctypes.data
+    import torch
+
+    if a.device.type != "cpu" or not a.is_contiguous() or a.dtype not in (torch.float32, torch.float64):
+        raise ValueError("a contiguous float32 or float64 CPU tensor is needed")
+    return (F32 if a.dtype == torch.float32 else F64), a.data_ptr()
+
+
 def axlbm_batch_set_fields_all_async(b, host_ptr: int, in_dtype: int) -> None:
     _bcheck(lib().axlbm_batch_set_fields_all_async(b, ctypes.c_void_p(host_ptr), int(in_dtype)), b)
 
@@ -608,13 +621,15 @@ class Batch:
         nbytes = axlbm_batch_state_bytes(self.domains, self.precision)
         self._mem = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._in_flight = []  # host arrays of queued asynchronous copies, kept alive until sync()
         self.handle = axlbm_batch_create(self.domains, self.precision, stream=self.stream.cuda_stream,
                                          state_mem=self._mem.data_ptr(), state_bytes=nbytes)
 
     def close(self) -> None:
         if getattr(self, "handle", None) is not None:
-            axlbm_batch_destroy(self.handle)
+            axlbm_batch_destroy(self.handle)  # waits for the copies in flight
             self.handle = None
+            self._in_flight = []
 
     def __del__(self):
         try:
@@ -707,6 +722,24 @@ class Batch:
 
             axlbm_batch_moments_all(self.handle, mask, out.data_ptr(), F32 if out.dtype == torch.float32 else F64,
                                     0 if out.device.type == "cpu" else 1)
+
+    def set_fields_all_async(self, fields) -> None:
+        """As set_fields_all from host memory (numpy or CPU tensor, FP32 or FP64), the copy queued on the
+        batch's copy stream; the array is kept alive, and must stay unchanged, until sync()."""
+        dt, ptr = _host_array(fields)
+        axlbm_batch_set_fields_all_async(self.handle, ptr, dt)
+        self._in_flight.append(fields)
+
+    def moments_all_async(self, mask: int, out) -> None:
+        """As moments_all into host memory (numpy or CPU tensor); `out` is filled when sync() returns."""
+        dt, ptr = _host_array(out)
+        axlbm_batch_moments_all_async(self.handle, mask, ptr, dt)
+        self._in_flight.append(out)
+
+    def sync(self) -> None:
+        """Wait for the batch's steps and every asynchronous copy."""
+        axlbm_batch_sync(self.handle)
+        self._in_flight.clear()
 
     def get_populations(self, d: int):
         pb = self.problems[d]

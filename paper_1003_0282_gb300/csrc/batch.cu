@@ -874,16 +874,20 @@ axlbm_status axlbm_batch_moments_all(axlbm_batch* b, uint32_t mask, void* out, i
 namespace {
 
 // The copy stream and the events of the asynchronous host I/O (created once).
+// A failed setup is retried by the next call (what was created is kept and
+// freed with the batch).
 cudaError_t io_setup(axlbm_batch* b) {
-    if (b->io) return cudaSuccess;
-    cudaError_t e = cudaStreamCreateWithFlags(&b->io, cudaStreamNonBlocking);
+    if (b->io_ready) return cudaSuccess;
+    cudaError_t e = b->io ? cudaSuccess : cudaStreamCreateWithFlags(&b->io, cudaStreamNonBlocking);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
         cudaEvent_t* evs[] = {&b->ev_in_ready[k], &b->ev_in_free[k], &b->ev_out_ready[k], &b->ev_out_free[k]};
         for (cudaEvent_t* ev : evs) {
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+            if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventRecord(*ev, b->stream);  // nothing to wait for yet
         }
     }
+    if (e != cudaSuccess) cudaGetLastError();
+    b->io_ready = e == cudaSuccess;
     return e;
 }
 
@@ -922,9 +926,10 @@ axlbm_status axlbm_batch_set_fields_all_async(axlbm_batch* b, const void* host_f
     if (b->parity != 0) return bfail(b, AXLBM_EINVAL, "set_fields needs an even time level");
     const size_t bytes = all_values(b, 5) * (in_dtype == AXLBM_F32 ? 4 : 8);
     cudaError_t e = io_setup(b);
+    if (e != cudaSuccess) return bcuda(b, e, "asynchronous copy stream");
     const int k = b->io_in_next;
-    if (e == cudaSuccess) e = io_buffer(b, &b->io_in[k], &b->io_in_bytes[k], bytes);
-    if (e != cudaSuccess) return bfail(b, AXLBM_ENOMEM, "asynchronous staging buffer");
+    if (io_buffer(b, &b->io_in[k], &b->io_in_bytes[k], bytes) != cudaSuccess)
+        return bfail(b, AXLBM_ENOMEM, "asynchronous staging buffer");
     // the copy waits until the kernel that last read this buffer is done
     e = cudaStreamWaitEvent(b->io, b->ev_in_free[k], 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->io_in[k], host_fields, bytes, cudaMemcpyHostToDevice, b->io);
@@ -948,9 +953,10 @@ axlbm_status axlbm_batch_moments_all_async(axlbm_batch* b, uint32_t mask, void* 
     for (int f = 0; f < 5; ++f) nf += (mask >> f) & 1;
     const size_t bytes = all_values(b, nf) * (out_dtype == AXLBM_F32 ? 4 : 8);
     cudaError_t e = io_setup(b);
+    if (e != cudaSuccess) return bcuda(b, e, "asynchronous copy stream");
     const int k = b->io_out_next;
-    if (e == cudaSuccess) e = io_buffer(b, &b->io_out[k], &b->io_out_bytes[k], bytes);
-    if (e != cudaSuccess) return bfail(b, AXLBM_ENOMEM, "asynchronous staging buffer");
+    if (io_buffer(b, &b->io_out[k], &b->io_out_bytes[k], bytes) != cudaSuccess)
+        return bfail(b, AXLBM_ENOMEM, "asynchronous staging buffer");
     // the kernel waits until the copy that last read this buffer is done
     e = cudaStreamWaitEvent(b->stream, b->ev_out_free[k], 0);
     if (e == cudaSuccess) e = batch_ops_for(b->precision)->moments_all(b, b->io_out[k], mask, out_dtype == AXLBM_F32);

@@ -98,6 +98,7 @@ struct axlbm_batch {
     size_t io_in_bytes[2] = {0, 0}, io_out_bytes[2] = {0, 0};
     cudaEvent_t ev_in_ready[2] = {}, ev_in_free[2] = {}, ev_out_ready[2] = {}, ev_out_free[2] = {};
     int io_in_next = 0, io_out_next = 0;
+    bool io_ready = false;
     std::string err;
 };
 

@@ -80,3 +80,59 @@ def run_to_steady(solver, tol: float, max_steps: int, chunk: int = 5000, log: Op
             log.flush()
         last = now_abs
     return dict(reached=reached, when=when, blown=blown, steps=steps)
+
+
+def _main(argv=None) -> int:
+    """Run one rotating-lid cavity (Sec. IV B) from rest to the Eq. 57
+    criterion and save its fields; with --against, print the per-field
+    difference from a saved run (the FP64 one) over the lid speed."""
+    import argparse
+
+    from . import axlbm as B
+    from . import inputs as I
+
+    p = argparse.ArgumentParser(prog="python -m paper_1003_0282_gb300.steady")
+    p.add_argument("--cavity", nargs=3, type=float, metavar=("NR", "ASPECT", "RE"), required=True)
+    p.add_argument("--collision", default="mrt", choices=["bgk", "mrt"])
+    p.add_argument("--precision", default="fp32", choices=sorted(B.PRECISIONS))
+    p.add_argument("--tol", type=float, default=1e-8)
+    p.add_argument("--lag", type=int, default=2, choices=[1, 2])
+    p.add_argument("--max-steps", type=int, default=10_000_000)
+    p.add_argument("--chunk", type=int, default=20_000)
+    p.add_argument("--log", default=None, help="JSON-lines progress log")
+    p.add_argument("--save", default=None, help=".npz of rho, u_r, u_z, u_theta and the run's record")
+    p.add_argument("--against", default=None, help="a saved run to compare with")
+    a = p.parse_args(argv)
+    nr = int(a.cavity[0])
+    pb = I.rotating_lid_cavity(nr=nr, aspect=a.cavity[1], re=a.cavity[2], collision=a.collision)
+    lid = pb.omega_of("hi") * pb.wall_radius
+    dom = B.Domain(pb, a.precision)
+    dom.set_residual_lag(a.lag)
+    log = open(a.log, "a") if a.log else None
+    try:
+        out = run_to_steady(dom, a.tol, a.max_steps, chunk=a.chunk, log=log)
+    finally:
+        if log:
+            log.close()
+    res, mass, budget = dom.residual(allow_nonfinite=True)
+    fields = dom.moments(B.RHO | B.UR | B.UZ | B.UTH)
+    dom.close()
+    rec = {"problem": pb.name, "precision": a.precision, "collision": a.collision, "tol": a.tol, "lag": a.lag,
+           "steps": int(out["steps"]), "reached": int(out["reached"][0]), "wall_s": float(out["when"][0]),
+           "residual": float(res), "mass": float(mass), "lid_speed": float(lid)}
+    if a.against:
+        ref = np.load(a.against)
+        want = ref["fields"]
+        rec["against"] = {"run": str(ref["precision"]), "steps": int(ref["steps"]),
+                          "max_error_over_lid_speed": {
+                              name: float(np.max(np.abs(fields[q] - want[q]))) / (lid if q else 1.0)
+                              for q, name in enumerate(("rho", "u_r", "u_z", "u_theta"))}}
+    if a.save:
+        np.savez_compressed(a.save, fields=fields, precision=a.precision, steps=out["steps"],
+                            record=json.dumps(rec))
+    print(json.dumps(rec), flush=True)
+    return 0 if out["reached"][0] >= 0 else 1
+
+
+if __name__ == "__main__":
+    raise SystemExit(_main())

@@ -189,6 +189,48 @@ def test_batch_packed_fields_match_per_domain_calls(B):
     batch.close()
 
 
+def test_batch_async_host_io_matches_the_synchronous_calls(B):
+    """Fields in and moments out through the copy stream, three rounds queued
+    before one sync (the two staging buffers each way are reused), against the
+    same sequence of synchronous calls, bit for bit: FP32 from pinned memory,
+    FP64 from pageable memory, results into pinned and pageable memory."""
+    import torch
+
+    doms = mixed_batch()
+    cells = sum(pb.cells for pb in doms)
+    mask = B.RHO | B.UR | B.UZ
+    fin = []
+    for n in range(3):
+        a = np.concatenate([I.random_fields(pb.nr, pb.nz, seed=90 + 7 * n + d).ravel() for d, pb in enumerate(doms)])
+        fin.append(a if n == 1 else torch.from_numpy(a.astype(np.float32)).pin_memory())
+    want = []
+    ref = B.Batch(doms, "fp32")
+    for n in range(3):
+        ref.set_fields_all(fin[n])
+        ref.step(4)
+        out = np.empty(3 * cells, dtype=np.float32)
+        ref.moments_all(mask, out)
+        want.append(out)
+    ref.close()
+    batch = B.Batch(doms, "fp32")
+    outs = [torch.empty(3 * cells, dtype=torch.float32).pin_memory(), np.empty(3 * cells, dtype=np.float32),
+            torch.empty(3 * cells, dtype=torch.float32).pin_memory()]
+    for n in range(3):
+        batch.set_fields_all_async(fin[n])
+        batch.step(4)
+        batch.moments_all_async(mask, outs[n])
+    batch.sync()
+    for n in range(3):
+        got = outs[n].numpy() if isinstance(outs[n], torch.Tensor) else outs[n]
+        assert np.array_equal(got, want[n]), n
+    with pytest.raises(ValueError):
+        batch.moments_all_async(mask, np.empty((3, cells), dtype=np.float32)[:, ::2])
+    batch.step(1)
+    with pytest.raises(B.AxlbmError):
+        batch.set_fields_all_async(np.zeros(5 * cells))  # fields are set at an even level
+    batch.close()
+
+
 def test_batch_mixes_bgk_and_mrt_domains(B):
     doms = mixed_batch()
     doms = [dataclasses.replace(pb, collision="mrt") if i % 2 else pb for i, pb in enumerate(doms)]

@@ -127,3 +127,26 @@ def test_large_cavity_storage_error_against_fp64(B, nr, aspect, re, steps):
     for precision in ("fp64", "fp32"):
         r, m0, b0, m1 = checks[precision]
         assert abs(m1 - m0) <= 10 * abs(b0) + (1e-12 if precision == "fp64" else 1e-8) * m0, (precision, m0, m1, b0)
+
+
+def test_steady_cli_saves_and_compares(B, tmp_path):
+    """The run-to-steady command: a small cavity to the Eq. 57 criterion in
+    FP64, saved, then FP32 compared with it field by field."""
+    import json
+    import subprocess
+    import sys
+
+    ref = tmp_path / "fp64.npz"
+    cmd = [sys.executable, "-m", "paper_1003_0282_gb300.steady", "--cavity", "16", "1.5", "100",
+           "--tol", "1e-7", "--chunk", "2000", "--max-steps", "400000"]
+    r64 = subprocess.run(cmd + ["--precision", "fp64", "--save", str(ref)], capture_output=True, text=True)
+    assert r64.returncode == 0, r64.stderr
+    rec64 = json.loads(r64.stdout.strip().splitlines()[-1])
+    assert 0 < rec64["reached"] == rec64["steps"] and rec64["residual"] <= 1e-7
+    r32 = subprocess.run(cmd + ["--precision", "fp32", "--against", str(ref), "--log", str(tmp_path / "p.jsonl")],
+                         capture_output=True, text=True)
+    assert r32.returncode == 0, r32.stderr
+    rec32 = json.loads(r32.stdout.strip().splitlines()[-1])
+    err = rec32["against"]["max_error_over_lid_speed"]
+    assert max(err["u_r"], err["u_z"], err["u_theta"]) <= 1e-3 and err["rho"] <= 1e-4, rec32
+    assert (tmp_path / "p.jsonl").read_text().count("\n") == rec32["steps"] // 2000

@@ -93,21 +93,34 @@ def test_gather_rejects_overlap_and_gaps():
     assert np.array_equal(S.gather_per_domain(rows, [1, 0], 2), rows)
 
 
+def _say(q, msg):
+    """Put msg and wait for the queue's feeder thread to write it (os._exit follows)."""
+    q.put(msg)
+    q.close()
+    q.join_thread()
+
+
 def _leaving_worker(rank, world, port, q):
     import datetime
     import time
 
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
-    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    try:
+        dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+        S.max_over_ranks(float(rank))  # one whole step together: the group is fully connected
+    except Exception as e:
+        _say(q, (f"setup failed on rank {rank}: {type(e).__name__}", -1.0))
+        os._exit(4)
     if rank == 1:
         os._exit(3)  # leaves between steps, with nothing in flight and without a word
+    time.sleep(0.5)
     t0 = time.time()
     try:
         S.max_over_ranks(1.0)
-        q.put(("no error", time.time() - t0))
+        _say(q, ("no error", time.time() - t0))
     except Exception as e:  # the collective must end with an error, not wait forever
-        q.put((type(e).__name__, time.time() - t0))
+        _say(q, (type(e).__name__, time.time() - t0))
     os._exit(0)
 
 
@@ -124,6 +137,6 @@ def test_a_rank_that_leaves_ends_the_next_collective_with_an_error():
     what, waited = q.get(timeout=120)
     for p in procs:
         p.join(timeout=60)
-    assert what != "no error", what
-    assert waited < 60.0
+    assert what != "no error" and not what.startswith("setup failed"), what
+    assert 0.0 <= waited < 60.0
     assert procs[1].exitcode == 3 and procs[0].exitcode == 0
