@@ -431,7 +431,7 @@ def main():
     host_out = torch.empty(3 * nodes, dtype=torch.float32, pin_memory=True)
     if solver.time % 2:
         solver.step(1)  # fields are set at an even level
-    if args.workload != "pipe":  # the copy stream and its staging buffers are made by the first call
+    if args.workload != "pipe":  # the copy streams and their staging buffers are made by the first call
         B.axlbm_batch_set_fields_all_async(solver.handle, host_in.data_ptr(), B.F32)
         B.axlbm_batch_moments_all_async(solver.handle, B.RHO | B.UR | B.UZ, host_out.data_ptr(), B.F32)
         B.axlbm_batch_set_fields_all_async(solver.handle, host_in.data_ptr(), B.F32)
@@ -445,7 +445,7 @@ def main():
             solver.step(args.inner)
             B.axlbm_moments(solver.handle, B.RHO | B.UR | B.UZ, host_out.data_ptr(), B.F32, 0)
         else:
-            # copies on the batch's copy stream: this step's upload runs beside the previous step's
+            # copies on the batch's copy streams: this step's upload runs beside the previous step's
             # lattice steps, its download beside the next one's
             B.axlbm_batch_set_fields_all_async(solver.handle, host_in.data_ptr(), B.F32)
             solver.step(args.inner)
@@ -490,7 +490,7 @@ def main():
                     "h2d_bytes_per_step": 5 * 4 * all_nodes, "d2h_bytes_per_step": 3 * 4 * all_nodes,
                     "steps": args.e2e_steps,
                     "copies": ("synchronous, pinned host buffers" if args.workload == "pipe" else
-                               "asynchronous on the batch's copy stream, pinned host buffers, one sync at the end")},
+                               "asynchronous on the batch's copy streams, pinned host buffers, one sync at the end")},
             "gpu_launches": all_launches,
             "clocks": clk.summary(),
             "check": {"residual": res, "mass": mass},

@@ -399,6 +399,13 @@ AXLBM_API axlbm_status axlbm_check_static(const axlbm_grid* grid, double tau, co
  * AXLBM_EINVAL for a budget out of range or NULL outputs. */
 AXLBM_API axlbm_status axlbm_selftest_bounded_wait(int64_t max_cycles, int32_t* gave_up, uint32_t* err_word);
 
+/* Self-test of the FP32 reciprocal of the collision (the 1/rho-type factors
+ * of Eqs. 16-17 and 1/r): evaluates it on the device for n host values x
+ * (1 <= n <= 2^26), scalar into out[0 .. n) and in the paired-lane form into
+ * out[n .. 2n) (host arrays, float).  Synchronises; AXLBM_EINVAL for NULL
+ * arrays or n out of range. */
+AXLBM_API axlbm_status axlbm_selftest_rcp(const float* x, int64_t n, float* out);
+
 /* ------------------------------------------------------------------ batches
  * Many independent domains of uneven size advanced together: every step is
  * one persistent launch over a packed tile list of all domains (plus one
@@ -465,10 +472,11 @@ AXLBM_API axlbm_status axlbm_batch_moments_all(axlbm_batch* b, uint32_t field_ma
                                                int32_t out_on_device);
 
 /* Asynchronous host I/O of every domain's fields, for a run that sets fields
- * from and reads results into host memory each call: the copies run on a
- * stream of the library's own, through two staging buffers each way (kept,
- * grown as needed, until the batch is destroyed), so one call's copies run
- * beside the previous or the next call's steps.  Same layouts, dtypes and
+ * from and reads results into host memory each call: the copies run on two
+ * streams of the library's own (one per direction), through two staging
+ * buffers each way (kept, grown as needed, until the batch is destroyed), so
+ * that one call's upload runs beside the previous call's steps and its
+ * download beside the next call's.  Same layouts, dtypes and
  * rules as axlbm_batch_set_fields_all / axlbm_batch_moments_all with host
  * arrays; the order of the calls on the batch is kept (fields set before a
  * step are the ones it starts from, moments are those of the level at the

@@ -132,6 +132,7 @@ def lib() -> ctypes.CDLL:
         L.axlbm_batch_tile_shape.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         L.axlbm_selftest_bounded_wait.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
                                                   ctypes.POINTER(ctypes.c_uint32)]
+        L.axlbm_selftest_rcp.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         L.axlbm_batch_set_tile_shape.argtypes = [H, ctypes.c_int32, ctypes.c_int32]
         L.axlbm_batch_tile_shapes.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         L.axlbm_batch_set_fields_all_async.argtypes = [H, ctypes.c_void_p, ctypes.c_int32]
@@ -185,7 +186,7 @@ def lib() -> ctypes.CDLL:
                      "axlbm_destroy", "axlbm_kernel_timing", "axlbm_kernel_times", "axlbm_check_static",
                      "axlbm_use_graphs", "axlbm_graph_stats", "axlbm_set_residual_lag",
                      "axlbm_halo_bytes", "axlbm_halo_send", "axlbm_halo_recv",
-                     "axlbm_selftest_bounded_wait"):
+                     "axlbm_selftest_bounded_wait", "axlbm_selftest_rcp"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -596,6 +597,14 @@ def axlbm_batch_kernel_times_by_parity(b):
     ms, by = (ctypes.c_double * 2)(), (ctypes.c_double * 2)()
     _bcheck(lib().axlbm_batch_kernel_times_by_parity(b, nb, ms, by), b)
     return list(nb), list(ms), list(by)
+
+
+def axlbm_selftest_rcp(x) -> tuple:
+    """(scalar, paired) FP32 reciprocals of the collision evaluated on the device for the values x."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.empty(2 * x.size, dtype=np.float32)
+    _check(lib().axlbm_selftest_rcp(x.ctypes.data, x.size, out.ctypes.data), None)
+    return out[:x.size], out[x.size:]
 
 
 def axlbm_selftest_bounded_wait(max_cycles: int):

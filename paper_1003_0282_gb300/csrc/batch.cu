@@ -873,12 +873,14 @@ axlbm_status axlbm_batch_moments_all(axlbm_batch* b, uint32_t mask, void* out, i
 
 namespace {
 
-// The copy stream and the events of the asynchronous host I/O (created once).
+// The copy streams (host to device: io, device to host: io_back) and the
+// events of the asynchronous host I/O (created once).
 // A failed setup is retried by the next call (what was created is kept and
 // freed with the batch).
 cudaError_t io_setup(axlbm_batch* b) {
     if (b->io_ready) return cudaSuccess;
     cudaError_t e = b->io ? cudaSuccess : cudaStreamCreateWithFlags(&b->io, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !b->io_back) e = cudaStreamCreateWithFlags(&b->io_back, cudaStreamNonBlocking);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
         cudaEvent_t* evs[] = {&b->ev_in_ready[k], &b->ev_in_free[k], &b->ev_out_ready[k], &b->ev_out_free[k]};
         for (cudaEvent_t* ev : evs) {
@@ -895,6 +897,7 @@ cudaError_t io_setup(axlbm_batch* b) {
 cudaError_t io_buffer(axlbm_batch* b, void** buf, size_t* have, size_t bytes) {
     if (*have >= bytes) return cudaSuccess;
     cudaError_t e = cudaStreamSynchronize(b->io);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->io_back);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return e;
     if (*buf) cudaFree(*buf);
@@ -961,9 +964,9 @@ axlbm_status axlbm_batch_moments_all_async(axlbm_batch* b, uint32_t mask, void* 
     e = cudaStreamWaitEvent(b->stream, b->ev_out_free[k], 0);
     if (e == cudaSuccess) e = batch_ops_for(b->precision)->moments_all(b, b->io_out[k], mask, out_dtype == AXLBM_F32);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_out_ready[k], b->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->io, b->ev_out_ready[k], 0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, b->io_out[k], bytes, cudaMemcpyDeviceToHost, b->io);
-    if (e == cudaSuccess) e = cudaEventRecord(b->ev_out_free[k], b->io);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->io_back, b->ev_out_ready[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, b->io_out[k], bytes, cudaMemcpyDeviceToHost, b->io_back);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_out_free[k], b->io_back);
     if (e != cudaSuccess) return bcuda(b, e, "moments_all_async");
     b->io_out_next ^= 1;
     return AXLBM_OK;
@@ -973,6 +976,7 @@ axlbm_status axlbm_batch_sync(axlbm_batch* b) {
     if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e == cudaSuccess && b->io) e = cudaStreamSynchronize(b->io);
+    if (e == cudaSuccess && b->io_back) e = cudaStreamSynchronize(b->io_back);
     return e == cudaSuccess ? AXLBM_OK : bcuda(b, e, "sync");
 }
 
@@ -1252,6 +1256,11 @@ axlbm_status axlbm_batch_destroy(axlbm_batch* b) {
     batch_drop_graphs(b);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->stage) cudaFree(b->stage);
+    if (b->io_back) {
+        cudaError_t e2 = cudaStreamSynchronize(b->io_back);
+        if (e == cudaSuccess) e = e2;
+        cudaStreamDestroy(b->io_back);
+    }
     if (b->io) {
         cudaError_t e2 = cudaStreamSynchronize(b->io);
         if (e == cudaSuccess) e = e2;

@@ -90,9 +90,10 @@ struct axlbm_batch {
     void* stage;  // device staging buffer of host-side field I/O, kept between calls
     size_t stage_bytes;
     // asynchronous all-domain host I/O (axlbm_batch_*_all_async): a copy
-    // stream of the library's own and two staging buffers each way, so that
-    // one call's copies run beside the previous or next call's steps
-    cudaStream_t io = nullptr;
+    // stream of the library's own per direction and two staging buffers each
+    // way, so that one call's upload runs beside the previous call's steps and
+    // its download beside the next call's
+    cudaStream_t io = nullptr, io_back = nullptr;
     void* io_in[2] = {nullptr, nullptr};
     void* io_out[2] = {nullptr, nullptr};
     size_t io_in_bytes[2] = {0, 0}, io_out_bytes[2] = {0, 0};

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "pair.cuh"
 #include "tma.cuh"
 
 namespace axl {
@@ -28,6 +29,20 @@ __global__ void __launch_bounds__(32) k_wait_selftest(long long max_cycles, int*
     if (!ok) atomicAdd(gave_up, 1);
     __syncwarp();
     if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) atomicOr(err, 1u);
+}
+
+// The collision's FP32 reciprocal, scalar (out[i]) and paired (out[n + i]).
+__global__ void __launch_bounds__(256) k_rcp_selftest(const float* x, long long n, float* out) {
+    const long long i = blockIdx.x * 256ll + threadIdx.x;
+    if (2 * i >= n) return;
+    const float a = x[2 * i], b = 2 * i + 1 < n ? x[2 * i + 1] : 1.0f;
+    out[2 * i] = rcp(a);
+    const F2 p = rcp(F2(a, b));
+    out[n + 2 * i] = p.v.x;
+    if (2 * i + 1 < n) {
+        out[2 * i + 1] = rcp(b);
+        out[n + 2 * i + 1] = p.v.y;
+    }
 }
 
 axlbm_status selftest_fail(axlbm_status st, const char* msg) {
@@ -62,4 +77,24 @@ extern "C" AXLBM_API axlbm_status axlbm_selftest_bounded_wait(int64_t max_cycles
     *gave_up = host[0];
     *err_word = (uint32_t)host[1];
     return AXLBM_OK;
+}
+
+extern "C" AXLBM_API axlbm_status axlbm_selftest_rcp(const float* x, int64_t n, float* out) {
+    using namespace axl;
+    if (!x || !out || n < 1 || n > (1ll << 26)) return selftest_fail(AXLBM_EINVAL, "x and out are required, 1 <= n <= 2^26");
+    float* dev = nullptr;
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&dev, 3 * n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dev, x, n * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const long long pairs = (n + 1) / 2;
+        k_rcp_selftest<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(dev, n, dev + n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dev + n, 2 * n * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (dev) cudaFree(dev);
+    if (s) cudaStreamDestroy(s);
+    return e == cudaSuccess ? AXLBM_OK : selftest_fail(AXLBM_ECUDA, cudaGetErrorString(e));
 }
