@@ -40,7 +40,11 @@ sys.path.insert(0, ROOT)
 # at capture time.  Reported as null once the source has changed.
 NCU_TRAFFIC = {
     # profiles/k_bulk_batch_fp32_sweep320_launches.md: one even (4 x 128 tiles) and one odd (2 x 128) launch
-    "batch fp32": {"src_sha": "3b78c4cf84faa9ee", "dram_per_alg_byte": 0.9896},
+    "batch fp32": {"src_sha": "c5f3d3afebca1cef", "dram_per_alg_byte": 0.9886},
+    # profiles/k_bulk_batch_fp16_sweep_half_full.md: full-size DRAM capture, one even and one odd launch (4 x 128)
+    "batch fp16": {"src_sha": "c5f3d3afebca1cef", "dram_per_alg_byte": 0.9620},
+    # profiles/k_bulk_fp32_pipe4096x8192_launches.md: one even and one odd launch (4 x 128 tiles)
+    "pipe fp32": {"src_sha": "c5f3d3afebca1cef", "dram_per_alg_byte": 1.0419},
 }
 
 
