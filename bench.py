@@ -39,12 +39,12 @@ sys.path.insert(0, ROOT)
 # captured launch, keyed by kernel and the SHA-256 prefix of the kernel source
 # at capture time.  Reported as null once the source has changed.
 NCU_TRAFFIC = {
-    # profiles/k_bulk_batch_fp32_sweep320_launches.md: one even (4 x 128 tiles) and one odd (2 x 128) launch
-    "batch fp32": {"src_sha": "c5f3d3afebca1cef", "dram_per_alg_byte": 0.9886},
+    # profiles/k_bulk_batch_fp32_sweep320_launches.md: one even and one odd launch (4 x 128 tiles)
+    "batch fp32": {"src_sha": "ec082870e1ae52bd", "dram_per_alg_byte": 0.9890},
     # profiles/k_bulk_batch_fp16_sweep_half_full.md: full-size DRAM capture, one even and one odd launch (4 x 128)
-    "batch fp16": {"src_sha": "c5f3d3afebca1cef", "dram_per_alg_byte": 0.9620},
+    "batch fp16": {"src_sha": "ec082870e1ae52bd", "dram_per_alg_byte": 0.9618},
     # profiles/k_bulk_fp32_pipe4096x8192_launches.md: one even and one odd launch (4 x 128 tiles)
-    "pipe fp32": {"src_sha": "c5f3d3afebca1cef", "dram_per_alg_byte": 1.0419},
+    "pipe fp32": {"src_sha": "ec082870e1ae52bd", "dram_per_alg_byte": 1.0369},
 }
 
 
@@ -59,8 +59,8 @@ def parse():
                    help="warmstart: time to a steady state from rest and from the warm-start network")
     p.add_argument("--scale", type=float, default=1.0, help="batch: shrink every domain (small profiling cases)")
     p.add_argument("--tile", default=None,
-                   help="batch: bulk tile shapes RxN[,RxN] instead of the timed ones (even steps 4x128 or 8x64; "
-                        "odd steps with FP32 storage 2x128 or 4x64)")
+                   help="batch: bulk tile shape RxN for both steps, or RxN,RxN for even and odd steps, instead "
+                        "of the timed ones (4x128 or 8x64)")
     p.add_argument("--nr", type=int, default=4096)
     p.add_argument("--nz", type=int, default=8192)
     p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
@@ -90,7 +90,8 @@ def peaks():
 def kernel_source_sha():
     import hashlib
     h = hashlib.sha256()
-    for name in ("ops_impl.cuh", "lattice.cuh", "pair.cuh", "tma.cuh", "batch.cuh", "batch.cu"):
+    for name in ("ops_impl.cuh", "lattice.cuh", "pair.cuh", "tma.cuh", "batch.cuh", "batch.cu", "batch_ops.cuh",
+                 "batch_internal.h"):
         with open(os.path.join(ROOT, "paper_1003_0282_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -379,8 +380,8 @@ def main():
         kernel_times = lambda: B.axlbm_batch_kernel_times(solver.handle)
         parity_times = lambda: B.axlbm_batch_kernel_times_by_parity(solver.handle)
         if args.tile:
-            for t in args.tile.split(","):
-                solver.tile_shape = tuple(int(v) for v in t.split("x"))
+            shapes = [tuple(int(v) for v in t.split("x")) for t in args.tile.split(",")]
+            solver.tile_shapes = (shapes[0], shapes[-1])
         tile = solver.tile_shapes
         workload = workload_name(args, problems)
     nodes = sum(p.cells for p in problems)

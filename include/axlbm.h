@@ -64,7 +64,7 @@
 extern "C" {
 #endif
 
-#define AXLBM_ABI_VERSION 4
+#define AXLBM_ABI_VERSION 5
 
 typedef enum {
     AXLBM_OK = 0,
@@ -538,13 +538,15 @@ AXLBM_API axlbm_status axlbm_batch_use_graphs(axlbm_batch* b, int32_t enable);
  * (either pointer may be NULL). */
 AXLBM_API axlbm_status axlbm_batch_graph_stats(const axlbm_batch* b, int64_t* captures, int64_t* launches);
 
-/* Use the bulk tile shape rows x nodes from the next step on, instead of the
- * one timed at creation (for profiling a given shape; results do not depend
- * on it), for the steps whose candidates include it: 512-node tiles (4 x 128,
- * 8 x 64) run CTAs of eight computing warps and serve every step except the
- * odd steps with FP32 storage, which run 256-node tiles (2 x 128, 4 x 64) in
- * CTAs of four.  AXLBM_EINVAL for a shape no step of this batch uses. */
+/* Use the bulk tile shape rows x nodes in both steps of a pair from the next
+ * step on, instead of the ones timed at creation (for profiling a given
+ * shape; results do not depend on it).  The candidates are 4 x 128 and 8 x 64
+ * (512-node tiles in CTAs of eight computing warps).  AXLBM_EINVAL for any
+ * other shape. */
 AXLBM_API axlbm_status axlbm_batch_set_tile_shape(axlbm_batch* b, int32_t rows, int32_t nodes);
+/* The same per parity: rows[0] x nodes[0] for even steps, rows[1] x nodes[1]
+ * for odd steps (arrays of two). */
+AXLBM_API axlbm_status axlbm_batch_set_tile_shapes(axlbm_batch* b, const int32_t* rows, const int32_t* nodes);
 /* The tile shapes of even ([0]) and odd ([1]) steps (arrays of two). */
 AXLBM_API axlbm_status axlbm_batch_tile_shapes(const axlbm_batch* b, int32_t* rows, int32_t* nodes);
 

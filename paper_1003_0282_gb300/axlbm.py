@@ -134,6 +134,7 @@ def lib() -> ctypes.CDLL:
                                                   ctypes.POINTER(ctypes.c_uint32)]
         L.axlbm_selftest_rcp.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         L.axlbm_batch_set_tile_shape.argtypes = [H, ctypes.c_int32, ctypes.c_int32]
+        L.axlbm_batch_set_tile_shapes.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         L.axlbm_batch_tile_shapes.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         L.axlbm_batch_set_fields_all_async.argtypes = [H, ctypes.c_void_p, ctypes.c_int32]
         L.axlbm_batch_moments_all_async.argtypes = [H, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int32]
@@ -174,7 +175,7 @@ def lib() -> ctypes.CDLL:
         for name in ("axlbm_batch_state_bytes", "axlbm_batch_create", "axlbm_batch_step", "axlbm_batch_residuals",
                      "axlbm_batch_moments", "axlbm_batch_set_fields", "axlbm_batch_get_populations",
                      "axlbm_batch_set_populations", "axlbm_batch_time", "axlbm_batch_tile_shape",
-                     "axlbm_batch_set_tile_shape", "axlbm_batch_tile_shapes", "axlbm_batch_use_graphs", "axlbm_batch_graph_stats",
+                     "axlbm_batch_set_tile_shape", "axlbm_batch_set_tile_shapes", "axlbm_batch_tile_shapes", "axlbm_batch_use_graphs", "axlbm_batch_graph_stats",
                      "axlbm_batch_set_time", "axlbm_batch_copy_domain", "axlbm_batch_set_residual_lag",
                      "axlbm_batch_set_fields_all_async", "axlbm_batch_moments_all_async", "axlbm_batch_sync",
                      "axlbm_batch_kernel_timing", "axlbm_batch_kernel_times", "axlbm_batch_kernel_times_by_parity",
@@ -659,7 +660,7 @@ class Batch:
 
     @tile_shape.setter
     def tile_shape(self, shape):
-        """Use this tile shape for the steps whose candidates include it."""
+        """Use this tile shape (rows, nodes) in even and odd steps."""
         _bcheck(lib().axlbm_batch_set_tile_shape(self.handle, int(shape[0]), int(shape[1])), self.handle)
 
     @property
@@ -668,6 +669,13 @@ class Batch:
         r, n = (ctypes.c_int32 * 2)(), (ctypes.c_int32 * 2)()
         _bcheck(lib().axlbm_batch_tile_shapes(self.handle, r, n), self.handle)
         return (int(r[0]), int(n[0])), (int(r[1]), int(n[1]))
+
+    @tile_shapes.setter
+    def tile_shapes(self, shapes):
+        """Use shapes[0] in even steps and shapes[1] in odd steps."""
+        r = (ctypes.c_int32 * 2)(int(shapes[0][0]), int(shapes[1][0]))
+        n = (ctypes.c_int32 * 2)(int(shapes[0][1]), int(shapes[1][1]))
+        _bcheck(lib().axlbm_batch_set_tile_shapes(self.handle, r, n), self.handle)
 
     def use_graphs(self, enable: bool) -> None:
         """Replay runs of plain steps from captured CUDA graphs (default) or launch every kernel."""

@@ -530,9 +530,8 @@ axlbm_status tune(axlbm_batch* b) {
     int best_shape = 0;
     axlbm_status st = AXLBM_OK;
     // every pair of an even-step and an odd-step candidate shape
-    const int e0s = axl::shape_first(b->L.elem, 0), o0s = axl::shape_first(b->L.elem, 1);
     for (int c = 0; c < 4 && st == AXLBM_OK; ++c) {
-        const int s = 4 * (e0s + c / 2) + (o0s + c % 2);
+        const int s = 4 * (c / 2) + c % 2;
         b->shape[0] = s / 4;
         b->shape[1] = s % 4;
         // warm-up: every kernel variant of the shapes (plain and check steps
@@ -550,7 +549,7 @@ axlbm_status tune(axlbm_batch* b) {
             }
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
-            // another pair must beat the first (the wide / narrow 128-node pair) by 1 %
+            // another pair must beat the first (4 x 128 tiles in both steps) by 1 %
             if (c == 0 ? ms < best : ms < 0.99f * best) {
                 best = ms;
                 best_shape = s;
@@ -604,7 +603,7 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
     b->fork = b->join = nullptr;
     b->L = P.L;
     b->shape[0] = 0;
-    b->shape[1] = axl::shape_first(b->L.elem, 1);
+    b->shape[1] = 0;
     memset(b->grid, 0, sizeof b->grid);
     b->timing = false;
     b->ev_used = 0;
@@ -1156,22 +1155,30 @@ axlbm_status axlbm_batch_tile_shape(const axlbm_batch* b, int32_t* rows, int32_t
     return AXLBM_OK;
 }
 
+namespace {
+
+int shape_index(int32_t rows, int32_t nodes) {
+    for (int s = 0; s < axl::kBatchShapes; ++s)
+        if (axl::kShapeTK[s] == rows && axl::kShapeTJ[s] == nodes) return s;
+    return -1;
+}
+
+}  // namespace
+
 axlbm_status axlbm_batch_set_tile_shape(axlbm_batch* b, int32_t rows, int32_t nodes) {
     if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
-    bool any = false;
-    for (int s = 0; s < axl::kBatchShapes; ++s) {
-        if (axl::kShapeTK[s] != rows || axl::kShapeTJ[s] != nodes) continue;
-        for (int par = 0; par < 2; ++par) {  // every parity whose candidates include the shape
-            const int first = axl::shape_first(b->L.elem, par);
-            if (s == first || s == first + 1) {
-                b->shape[par] = s;
-                any = true;
-            }
-        }
-    }
-    if (!any)
-        return bfail(b, AXLBM_EINVAL, "no bulk tile shape " + std::to_string(rows) + " x " + std::to_string(nodes) +
-                                          " for this storage");
+    const int s = shape_index(rows, nodes);
+    if (s < 0) return bfail(b, AXLBM_EINVAL, "no bulk tile shape " + std::to_string(rows) + " x " + std::to_string(nodes));
+    b->shape[0] = b->shape[1] = s;
+    return AXLBM_OK;
+}
+
+axlbm_status axlbm_batch_set_tile_shapes(axlbm_batch* b, const int32_t* rows, const int32_t* nodes) {
+    if (!b || !rows || !nodes) return bfail(b, AXLBM_EINVAL, "batch, rows and nodes are required");
+    const int s0 = shape_index(rows[0], nodes[0]), s1 = shape_index(rows[1], nodes[1]);
+    if (s0 < 0 || s1 < 0) return bfail(b, AXLBM_EINVAL, "no such bulk tile shape");
+    b->shape[0] = s0;
+    b->shape[1] = s1;
     return AXLBM_OK;
 }
 

@@ -8,18 +8,12 @@
 
 namespace axl {
 
-// Candidate bulk tile shapes (rows x nodes): 512-node tiles for CTAs of
-// eight computing warps (shapes 0, 1) and 256-node tiles for CTAs of four
-// (shapes 2, 3).
-constexpr int kBatchShapes = 4;
-constexpr int kShapeTK[kBatchShapes] = {4, 8, 2, 4};
-constexpr int kShapeTJ[kBatchShapes] = {128, 64, 128, 64};
-
-// The two candidate shapes of a step of parity par with storage of elem bytes
-// are shape_first(...) and the one after it.  The odd step with FP32 storage
-// runs the narrow CTAs (its shifted stores keep more addresses live: at 96
-// registers per thread they spilled); every other step runs the wide ones.
-inline int shape_first(size_t elem, int par) { return (elem == 4 && par == 1) ? 2 : 0; }
+// Candidate bulk tile shapes (rows x nodes) of both parities: 512-node tiles
+// for CTAs of eight computing warps and the producer warp, two CTAs per SM.
+// Each parity's shape is timed at creation (axlbm_batch_create).
+constexpr int kBatchShapes = 2;
+constexpr int kShapeTK[kBatchShapes] = {4, 8};
+constexpr int kShapeTJ[kBatchShapes] = {128, 64};
 
 struct BatchTiles {
     int ntiles;

@@ -96,10 +96,8 @@ cudaError_t launch_bulk_batch(axlbm_batch* b, const BatchArgs<S, R>& A) {
 
 template <class S, class R, bool TH, int PAR, bool CHK, bool WET>
 cudaError_t launch_bulk_batch_wet(axlbm_batch* b, const BatchArgs<S, R>& A) {
-    // the odd step with FP32 storage runs the narrow CTAs (shapes 2, 3), every other step the wide ones (0, 1)
-    constexpr int first = (PAR == 1 && sizeof(S) == 4) ? 2 : 0;
-    return b->shape[PAR] == first ? launch_bulk_batch<S, R, TH, PAR, CHK, first, WET>(b, A)
-                                  : launch_bulk_batch<S, R, TH, PAR, CHK, first + 1, WET>(b, A);
+    return b->shape[PAR] == 0 ? launch_bulk_batch<S, R, TH, PAR, CHK, 0, WET>(b, A)
+                              : launch_bulk_batch<S, R, TH, PAR, CHK, 1, WET>(b, A);
 }
 
 template <class S, class R, bool TH, int PAR, bool CHK>

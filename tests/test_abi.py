@@ -88,7 +88,7 @@ def test_checkpoint_header_layout_matches_binding(tmp_path):
 
 def test_host_only_calls(built):
     from paper_1003_0282_gb300 import axlbm as B
-    assert B.axlbm_abi_version() == 4
+    assert B.axlbm_abi_version() == 5
     g = B.axlbm_grid(nr=100, nz=37, precision=B.FP32, with_swirl=1, with_temperature=0, collision=0, r0=0.0)
     n = B.axlbm_state_bytes(g)
     assert n >= 13 * 37 * 128 * 4  # 13 planes, rows padded to 128 floats

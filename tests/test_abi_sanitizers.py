@@ -46,7 +46,7 @@ for name in names:
         continue
     got = fn(*[t() for t in fn.argtypes])
     if name == "axlbm_abi_version":
-        assert got == 4
+        assert got == 5
     elif name == "axlbm_ws_weight_count":
         assert got > 0
     elif fn.restype is ctypes.c_char_p:

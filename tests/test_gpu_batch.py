@@ -308,19 +308,24 @@ def test_results_do_not_depend_on_the_tile_shape(B):
     their summation order.  An unknown shape is refused."""
     doms = mixed_batch()
     runs = []
-    # (even-step shape, odd-step shape) per call: FP32 odd steps run 256-node tiles
-    for shapes in ([((4, 128), (2, 128))] * 2, [((8, 64), (4, 64))] * 2, [((8, 64), (2, 128)), ((4, 128), (4, 64))]):
+    # (even-step shape, odd-step shape) per call
+    for shapes in ([((4, 128), (4, 128))] * 2, [((8, 64), (8, 64))] * 2, [((8, 64), (4, 128)), ((4, 128), (8, 64))]):
         batch = B.Batch(doms, "fp32")
         for d, pb in enumerate(doms):
             st = seeded_state(pb, seed=70 + d)
             batch.set_populations(d, st.f, st.g, st.h if pb.temperature else None)
         for even, odd in shapes:
-            batch.tile_shape = even
-            batch.tile_shape = odd
+            if even == odd:
+                batch.tile_shape = even
+            else:
+                batch.tile_shapes = (even, odd)
             assert batch.tile_shapes == (even, odd) and batch.tile_shape == even
             batch.step(3)
+        for bad in ((4, 32), (2, 128)):
+            with pytest.raises(B.AxlbmError):
+                batch.tile_shape = bad
         with pytest.raises(B.AxlbmError):
-            batch.tile_shape = (4, 32)
+            batch.tile_shapes = ((4, 128), (4, 64))
         runs.append(([batch.get_populations(d) for d in range(len(doms))], batch.residuals()))
         batch.close()
     pops0, res0 = runs[0]
