@@ -40,11 +40,11 @@ sys.path.insert(0, ROOT)
 # at capture time.  Reported as null once the source has changed.
 NCU_TRAFFIC = {
     # profiles/k_bulk_batch_fp32_sweep320_launches.md: one even and one odd launch (4 x 128 tiles)
-    "batch fp32": {"src_sha": "ec082870e1ae52bd", "dram_per_alg_byte": 0.9890},
+    "batch fp32": {"src_sha": "bb850171a9ef0d27", "dram_per_alg_byte": 0.9867},
     # profiles/k_bulk_batch_fp16_sweep_half_full.md: full-size DRAM capture, one even and one odd launch (4 x 128)
-    "batch fp16": {"src_sha": "ec082870e1ae52bd", "dram_per_alg_byte": 0.9618},
+    "batch fp16": {"src_sha": "bb850171a9ef0d27", "dram_per_alg_byte": 0.9621},
     # profiles/k_bulk_fp32_pipe4096x8192_launches.md: one even and one odd launch (4 x 128 tiles)
-    "pipe fp32": {"src_sha": "ec082870e1ae52bd", "dram_per_alg_byte": 1.0369},
+    "pipe fp32": {"src_sha": "bb850171a9ef0d27", "dram_per_alg_byte": 1.0349},
 }
 
 

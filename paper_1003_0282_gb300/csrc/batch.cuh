@@ -702,8 +702,9 @@ __global__ void __launch_bounds__(kThreads)
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         const int d = batch_domain_of(nodes, A.ndom, i);
         const KArgs<S, float> K = batch_domain_kargs(A, d);
-        const long long n = (long long)K.G.nr * K.G.nz, li = i - nodes[d];
-        const int j = int(li % K.G.nr), k = int(li / K.G.nr);
+        // a batch domain holds at most 2^28 nodes: 32-bit index arithmetic
+        const int lid = int(i - nodes[d]), k = lid / K.G.nr, j = lid - k * K.G.nr;
+        const long long n = (long long)K.G.nr * K.G.nz, li = lid;
         O* o = out + (long long)nf * nodes[d];
         if (A.doms[d].temperature) batch_node_moments<S, true>(K, j, k, n, li, parity, mask, o);
         else batch_node_moments<S, false>(K, j, k, n, li, parity, mask, o);
@@ -720,12 +721,18 @@ __global__ void __launch_bounds__(kThreads) k_init_batch(const BatchArgs<S, floa
         const int d = batch_domain_of(nodes, A.ndom, i);
         const KArgs<S, float> K = batch_domain_kargs(A, d);
         const Geom& G = K.G;
-        const long long n = (long long)G.nr * G.nz, li = i - nodes[d];
-        const int j = int(li % G.nr), k = int(li / G.nr);
+        // a batch domain holds at most 2^28 nodes: 32-bit index arithmetic
+        const int lid = int(i - nodes[d]), k = lid / G.nr, j = lid - k * G.nr;
+        const long long n = (long long)G.nr * G.nz, li = lid;
         const I* fd = fields + 5 * nodes[d];
         const R rho = R(fd[li]), ur = R(fd[n + li]), uz = R(fd[2 * n + li]);
         const R uth = R(fd[3 * n + li]), temp = R(fd[4 * n + li]);
-        const R drho = R(double(fd[li]) - (double)K.C.rho0);
+        // rho - rho0 rounded once to FP32: for FP32 inputs the FP32 subtraction does that directly
+        // (the FP64 difference of two FP32 values within a factor 2^29 of each other is exact, so
+        // rounding it gives the same value), for FP64 inputs the difference is taken in FP64
+        R drho;
+        if constexpr (sizeof(I) == 4) drho = fd[li] - K.C.rho0;
+        else drho = R(double(fd[li]) - (double)K.C.rho0);
         const R usq = R(1.5) * (ur * ur + uz * uz);
         for (int a = 0; a < 9; ++a) {
             const R eu = R(cr9(a)) * ur + R(cz9(a)) * uz;

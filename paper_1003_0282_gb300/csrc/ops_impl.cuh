@@ -1327,13 +1327,27 @@ __global__ void __launch_bounds__(kThreads) k_nee(const KArgs<S, R> A, int level
     nee_node<S, R, SW, TH>(A, level, j, k);
 }
 
+// Column j and row k of node i of a row-major [nz][nr] array; 32-bit
+// division where the index allows (the 64-bit one costs many times more).
+__device__ __forceinline__ void node_jk(long long i, int nr, int& j, int& k) {
+    if (i <= 0x7fffffffll) {
+        const int i32 = int(i);
+        k = i32 / nr;
+        j = i32 - k * nr;
+    } else {
+        k = int(i / nr);
+        j = int(i - (long long)k * nr);
+    }
+}
+
 // Macroscopic fields (Eqs. 16-17) at the current level, in either layout.
 template <class S, class R, bool SW, bool TH, class O>
 __global__ void __launch_bounds__(kThreads) k_moments(const KArgs<S, R> A, int parity, unsigned mask, O* out) {
     const Geom& G = A.G;
     const long long n = (long long)G.nr * G.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int j = int(i % G.nr), k = int(i / G.nr);
+        int j, k;
+        node_jk(i, G.nr, j, k);
         Cell<R, SW, TH> c;
         if (parity == 0) load_natural(A, j, k, c); else pull_odd<S, R, SW, TH, true>(A, j, k, c);
         for (int q = 0; q < 4; ++q) {
@@ -1361,7 +1375,8 @@ __global__ void __launch_bounds__(kThreads) k_gather(const KArgs<S, R> A, int pa
     const Geom& G = A.G;
     const long long n = (long long)G.nr * G.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int j = int(i % G.nr), k = int(i / G.nr);
+        int j, k;
+        node_jk(i, G.nr, j, k);
         Cell<R, SW, TH> c;
         if (parity == 0) load_natural(A, j, k, c); else pull_odd<S, R, SW, TH, true>(A, j, k, c);
         for (int a = 0; a < 9; ++a) out[a * n + i] = (double)c.d[a] + w9(a) * (double)A.C.rho0;
@@ -1382,7 +1397,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const KArgs<S, R> A, const
     const Geom& G = A.G;
     const long long n = (long long)G.nr * G.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int j = int(i % G.nr), k = int(i / G.nr);
+        int j, k;
+        node_jk(i, G.nr, j, k);
         for (int a = 0; a < 9; ++a)
             Codec<S>::store(slot(A.pop, G, a, j, k), R(in[a * n + i] - w9(a) * (double)A.C.rho0));
         int p = 9;
@@ -1403,10 +1419,15 @@ __global__ void __launch_bounds__(kThreads) k_init(const KArgs<S, R> A, const I*
     const Geom& G = A.G;
     const long long n = (long long)G.nr * G.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int j = int(i % G.nr), k = int(i / G.nr);
+        int j, k;
+        node_jk(i, G.nr, j, k);
         const R rho = R(fields[i]), ur = R(fields[n + i]), uz = R(fields[2 * n + i]);
         const R uth = R(fields[3 * n + i]), temp = R(fields[4 * n + i]);
-        const R drho = R(double(fields[i]) - (double)A.C.rho0);
+        // rho - rho0 rounded once: with FP32 inputs and arithmetic the FP32 subtraction gives the
+        // same value as rounding the (exact) FP64 difference; otherwise the difference is in FP64
+        R drho;
+        if constexpr (sizeof(I) == 4 && sizeof(R) == 4) drho = fields[i] - A.C.rho0;
+        else drho = R(double(fields[i]) - (double)A.C.rho0);
         const R usq = R(1.5) * (ur * ur + uz * uz);
         for (int a = 0; a < 9; ++a) {
             const R eu = R(cr9(a)) * ur + R(cz9(a)) * uz;
