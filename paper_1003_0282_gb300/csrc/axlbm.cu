@@ -273,13 +273,7 @@ axlbm_status axlbm_create(const axlbm_grid* grid, double tau, const axlbm_forcin
     h->G.r_split = bc->r_split;
     h->G.col0 = 0;
     h->G.row0 = 0;
-    {
-        const double off = bc->inner == AXLBM_INNER_AXIS_NODE ? 0.0 : 0.5;
-        h->G.rb = (float)(grid->r0 + off);
-        h->G.rb_exact = (double)h->G.rb == grid->r0 + off;
-        for (int j = 0; j < grid->nr && h->G.rb_exact; ++j)
-            h->G.rb_exact = (double)(h->G.rb + (float)j) == grid->r0 + off + j;
-    }
+    axl::radius_base(grid->r0 + (bc->inner == AXLBM_INNER_AXIS_NODE ? 0.0 : 0.5), grid->nr, &h->G.rb, &h->G.rb_exact);
     h->G.side = bc->inner == AXLBM_INNER_AXIS && bc->outer == AXLBM_OUTER_BB && grid->nr >= 3 && grid->nz >= 3;
     h->parity = 0;
     h->t = 0;

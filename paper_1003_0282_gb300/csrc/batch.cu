@@ -674,6 +674,7 @@ axlbm_status axlbm_batch_create(const axlbm_domain* domains, int32_t n, int32_t 
         x.cf = axl::make_coef<float>(D.tau, D.forcing, D.boundary);
         x.cd = axl::make_coef<double>(D.tau, D.forcing, D.boundary);
         x.cf.mrt = x.cd.mrt = D.grid.collision == AXLBM_MRT;
+        axl::radius_base(x.r0 + (D.boundary.inner == AXLBM_INNER_AXIS_NODE ? 0.0 : 0.5), x.nr, &x.rb, &x.rb_exact);
         axl::SlotDesc& y = sd[d];
         memset(&y, 0, sizeof y);
         y.nr = x.nr;

@@ -36,7 +36,9 @@ __host__ __device__ constexpr int batch_min_blocks() { return TK * TJ >= 512 ? 2
 struct DomDesc {
     int nr, nz, col0, row0;
     int inner, z_lo, z_hi, swirl;
-    int temperature, outer, pad1, pad2;
+    int temperature, outer;
+    int rb_exact;  // radius of local column j is rb + j, exact in FP32 for every column
+    float rb;
     double r0, r_split;
     double az0, omega_t;
     Coef<float> cf;
@@ -103,8 +105,8 @@ __device__ __forceinline__ Geom dom_geom(const DomDesc& D, long long pitch, long
     G.r_split = D.r_split;
     G.col0 = D.col0;
     G.row0 = D.row0;
-    G.rb = 0.0f;
-    G.rb_exact = 0;  // (the per-domain kernels take the radius in FP64)
+    G.rb = D.rb;
+    G.rb_exact = D.rb_exact;
     G.side = 0;
     return G;
 }

@@ -59,8 +59,8 @@ KArgs<S, R> domain_args(axlbm_batch* b, int d) {
     K.G.r_split = D.boundary.r_split;
     K.G.col0 = b->col0[d];
     K.G.row0 = b->row0[d];
-    K.G.rb = 0.0f;
-    K.G.rb_exact = 0;
+    radius_base(D.grid.r0 + (D.boundary.inner == AXLBM_INNER_AXIS_NODE ? 0.0 : 0.5), D.grid.nr, &K.G.rb,
+                &K.G.rb_exact);
     K.G.side = 0;
     K.C = make_coef<R>(D.tau, D.forcing, D.boundary);
     K.C.mrt = D.grid.collision == AXLBM_MRT;

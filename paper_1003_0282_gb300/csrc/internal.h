@@ -19,6 +19,16 @@ constexpr int kTileJ = 128;
 constexpr int kTileK = 4;
 constexpr int kMaxBulkBlocks = 4096;
 
+// FP32 radius base of columns 0 .. nr-1 whose radii are roff + j: *rb =
+// roff in FP32, *exact = 1 when rb + j equals roff + j exactly for every
+// column (then the kernels take 1/r in FP32 without FP64 instructions).
+inline void radius_base(double roff, int nr, float* rb, int* exact) {
+    *rb = (float)roff;
+    int ok = (double)*rb == roff;
+    for (int j = 0; j < nr && ok; ++j) ok = (double)(*rb + (float)j) == roff + j;
+    *exact = ok;
+}
+
 // Problem geometry and boundary description as the kernels see it.
 struct Geom {
     int nr, nz;

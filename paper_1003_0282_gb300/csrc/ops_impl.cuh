@@ -565,6 +565,10 @@ __device__ __forceinline__ void advance_clock(Clock* clk, int parity, double az0
 
 template <class R>
 __device__ __forceinline__ R inv_radius(const Geom& G, int j) {
+    if (sizeof(R) == 4 && G.rb_exact) {  // the FP32 radius is exact: the same value, no FP64 instruction
+        const float r = G.rb + (float)j;
+        return r > 0.0f ? R(1) / R(r) : R(0);
+    }
     return inv_of<R>(node_radius(G, j));
 }
 
