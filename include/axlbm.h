@@ -541,8 +541,9 @@ AXLBM_API axlbm_status axlbm_batch_graph_stats(const axlbm_batch* b, int64_t* ca
 /* Use the bulk tile shape rows x nodes in both steps of a pair from the next
  * step on, instead of the ones timed at creation (for profiling a given
  * shape; results do not depend on it).  The candidates are 4 x 128 and 8 x 64
- * (512-node tiles in CTAs of eight computing warps).  AXLBM_EINVAL for any
- * other shape. */
+ * (512-node tiles: each computing thread updates two nodes) and, with 16-bit
+ * storage, 8 x 128 (each thread updates four nodes of its column); all run
+ * CTAs of eight computing warps.  AXLBM_EINVAL for any other shape. */
 AXLBM_API axlbm_status axlbm_batch_set_tile_shape(axlbm_batch* b, int32_t rows, int32_t nodes);
 /* The same per parity: rows[0] x nodes[0] for even steps, rows[1] x nodes[1]
  * for odd steps (arrays of two). */

@@ -530,8 +530,9 @@ axlbm_status tune(axlbm_batch* b) {
     int best_shape = 0;
     axlbm_status st = AXLBM_OK;
     // every pair of an even-step and an odd-step candidate shape
-    for (int c = 0; c < 4 && st == AXLBM_OK; ++c) {
-        const int s = 4 * (c / 2) + c % 2;
+    const int nc = axl::batch_shape_count(b->L.elem);
+    for (int c = 0; c < nc * nc && st == AXLBM_OK; ++c) {
+        const int s = 4 * (c / nc) + c % nc;
         b->shape[0] = s / 4;
         b->shape[1] = s % 4;
         // warm-up: every kernel variant of the shapes (plain and check steps
@@ -1158,8 +1159,9 @@ axlbm_status axlbm_batch_tile_shape(const axlbm_batch* b, int32_t* rows, int32_t
 
 namespace {
 
-int shape_index(int32_t rows, int32_t nodes) {
-    for (int s = 0; s < axl::kBatchShapes; ++s)
+// Index of the candidate shape rows x nodes for this batch's storage, or -1.
+int shape_index(const axlbm_batch* b, int32_t rows, int32_t nodes) {
+    for (int s = 0; s < axl::batch_shape_count(b->L.elem); ++s)
         if (axl::kShapeTK[s] == rows && axl::kShapeTJ[s] == nodes) return s;
     return -1;
 }
@@ -1168,16 +1170,18 @@ int shape_index(int32_t rows, int32_t nodes) {
 
 axlbm_status axlbm_batch_set_tile_shape(axlbm_batch* b, int32_t rows, int32_t nodes) {
     if (!b) return bfail(nullptr, AXLBM_EINVAL, "batch is NULL");
-    const int s = shape_index(rows, nodes);
-    if (s < 0) return bfail(b, AXLBM_EINVAL, "no bulk tile shape " + std::to_string(rows) + " x " + std::to_string(nodes));
+    const int s = shape_index(b, rows, nodes);
+    if (s < 0)
+        return bfail(b, AXLBM_EINVAL, "no bulk tile shape " + std::to_string(rows) + " x " + std::to_string(nodes) +
+                                          " for this storage");
     b->shape[0] = b->shape[1] = s;
     return AXLBM_OK;
 }
 
 axlbm_status axlbm_batch_set_tile_shapes(axlbm_batch* b, const int32_t* rows, const int32_t* nodes) {
     if (!b || !rows || !nodes) return bfail(b, AXLBM_EINVAL, "batch, rows and nodes are required");
-    const int s0 = shape_index(rows[0], nodes[0]), s1 = shape_index(rows[1], nodes[1]);
-    if (s0 < 0 || s1 < 0) return bfail(b, AXLBM_EINVAL, "no such bulk tile shape");
+    const int s0 = shape_index(b, rows[0], nodes[0]), s1 = shape_index(b, rows[1], nodes[1]);
+    if (s0 < 0 || s1 < 0) return bfail(b, AXLBM_EINVAL, "no such bulk tile shape for this storage");
     b->shape[0] = s0;
     b->shape[1] = s1;
     return AXLBM_OK;

@@ -20,14 +20,20 @@ constexpr int kSlots = 4;     // domains a tile may meet
 constexpr int kRowAlign = 8;  // shelf rows start on multiples of this (>= every tile height)
 constexpr int kBatchMaxWarps = 8;  // computing warps of the widest bulk CTA (stride of the check partials)
 
-// A bulk CTA of a TK x TJ tile: TK TJ / 2 computing threads (two nodes of one
-// column each) plus one producer warp.  512-node tiles run eight computing
-// warps, two CTAs per SM (96 registers per thread); 256-node tiles run four,
-// three CTAs per SM (128 registers per thread).
+// A bulk CTA of a TK x TJ tile: computing threads that each update
+// batch_pairs() pairs of nodes of one column, plus one producer warp.
+// 512-node tiles give each thread one pair (eight computing warps, two CTAs
+// per SM, 96 registers per thread); 1024-node tiles (16-bit storage) give it
+// two pairs of its column, which share the per-tile work of a thread (slot,
+// coefficients, radius, votes, barrier waits), with as many warps.
+__host__ __device__ constexpr int batch_pairs_of(int tk, int tj) { return tk * tj >= 1024 ? 2 : 1; }
+__host__ __device__ constexpr int batch_nwarps_of(int tk, int tj) { return tk * tj / (64 * batch_pairs_of(tk, tj)); }
 template <int TK, int TJ>
-__host__ __device__ constexpr int batch_nthreads() { return TK * TJ / 2; }
+__host__ __device__ constexpr int batch_pairs() { return batch_pairs_of(TK, TJ); }
 template <int TK, int TJ>
-__host__ __device__ constexpr int batch_nwarps() { return TK * TJ / 64; }
+__host__ __device__ constexpr int batch_nthreads() { return 32 * batch_nwarps_of(TK, TJ); }
+template <int TK, int TJ>
+__host__ __device__ constexpr int batch_nwarps() { return batch_nwarps_of(TK, TJ); }
 template <int TK, int TJ>
 __host__ __device__ constexpr int batch_min_blocks() { return TK * TJ >= 512 ? 2 : 3; }
 
@@ -435,9 +441,11 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
     constexpr int NS = batch_nstages<S, SW, TH, TK, TJ>();
     constexpr int STAGE = batch_stage_elems<S, SW, TH, TK, TJ>();
     constexpr int NW = batch_nwarps<TK, TJ>();  // computing warps; warp NW is the producer
+    constexpr int NP = batch_pairs<TK, TJ>();   // node pairs per computing thread
+    constexpr int TPC = TK / (2 * NP);          // computing threads per column
     using RC = typename std::conditional<std::is_same<R, float>::value, F2, R>::type;
     static_assert(std::is_same<R, float>::value, "batch arithmetic is FP32");
-    static_assert(NW <= kBatchMaxWarps && NW * 32 / TJ == TK / 2, "two nodes of one column per computing thread");
+    static_assert(NW <= kBatchMaxWarps && TPC >= 1 && NW * 32 == TJ * TPC, "NP node pairs of one column per thread");
     static_assert(TK <= kRowAlign && kRowAlign % TK == 0, "a tile row band stays inside one shelf");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -499,17 +507,19 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
         }
     } else {
         const int jj = tid % TJ;
-        const int rr0 = tid / TJ;
+        const int rr0 = tid / TJ;  // pair p holds rows rr0 + p TPC and rr0 + p TPC + TK/2 of column jj
         // check steps with a residual: |u| of the previous level at this
-        // thread's two nodes of the next tile, loaded one tile ahead (every
+        // thread's nodes of the next tile, loaded one tile ahead (every
         // atlas position is valid memory; idle nodes ignore the value)
-        R sp_next[2] = {R(0), R(0)};
+        R sp_next[2 * NP];
+#pragma unroll
+        for (int m = 0; m < 2 * NP; ++m) sp_next[m] = R(0);
         auto prefetch_speed = [&](int i) {
             if (CHK && i < ntiles && A.residual) {
                 const int2 kj = *reinterpret_cast<const int2*>(A.tiles + batch_tile_at<PAR>(i, ntiles));
 #pragma unroll
-                for (int m = 0; m < 2; ++m)
-                    sp_next[m] = A.speed[(long long)(kj.x + rr0 + m * (TK / 2)) * A.pitch + kj.y + jj];
+                for (int m = 0; m < 2 * NP; ++m)
+                    sp_next[m] = A.speed[(long long)(kj.x + rr0 + (m / 2) * TPC + (m % 2) * (TK / 2)) * A.pitch + kj.y + jj];
             }
         };
         prefetch_speed(blockIdx.x);
@@ -517,7 +527,9 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
         for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++it) {
             const int s = it % NS;
             const int tile = batch_tile_at<PAR>(i, ntiles);
-            const R sp_old[2] = {sp_next[0], sp_next[1]};
+            R sp_old[2 * NP];
+#pragma unroll
+            for (int m = 0; m < 2 * NP; ++m) sp_old[m] = sp_next[m];
             prefetch_speed(i + gridDim.x);
             // a lane whose wait gave up skips the tile; the warp leaves the loop
             // together below (its lanes meet in warp-wide operations)
@@ -546,13 +558,16 @@ k_bulk_batch(const __grid_constant__ CUtensorMap map, const BatchArgs<S, R> A) {
                 const bool side_lane = PAR == 1 && D.side && (jl == 0 || jl == D.nr - 1);
                 // (a vote among the lanes that reached here: a lane whose wait gave up is not one of them)
                 const bool eg = PAR == 1 && __any_sync(__activemask(), side_lane);
-                // one node pair per thread: rows rr0 and rr0 + TK/2 of column jj
-                if (dth)
-                    batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old, red,
-                                                                          eg);
-                else
-                    batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0, inv_r, az, sp_old,
-                                                                             red, eg);
+                // node pairs of column jj: rows rr0 + p TPC and rr0 + p TPC + TK/2
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    if (dth)
+                        batch_nodes<S, R, RC, SW, TH, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0 + p * TPC, inv_r,
+                                                                              az, sp_old + 2 * p, red, eg);
+                    else
+                        batch_nodes<S, R, RC, SW, false, PAR, CHK, TK, TJ, WET>(A, D, st, k0, j0, jj, rr0 + p * TPC,
+                                                                                 inv_r, az, sp_old + 2 * p, red, eg);
+                }
                 if (CHK)
                     warp_slot_store(red, q, slots + s * kSlots, A.tile_part + 4ll * kSlots * kBatchMaxWarps * tile);
             }
@@ -657,6 +672,19 @@ __device__ __forceinline__ int batch_domain_of(const long long* nodes, int ndom,
     return lo;
 }
 
+// Node ranges of the all-domain field kernels: block b takes the packed nodes
+// [b per, (b + 1) per) with its threads side by side, so that a thread finds
+// its domain by one search and then moves to the next domain only where its
+// range crosses into it (a grid-wide stride would search for every node).
+struct NodeRange {
+    long long i, end;
+};
+__device__ __forceinline__ NodeRange block_node_range(long long total) {
+    const long long per = (total + gridDim.x - 1) / gridDim.x;
+    const long long beg = (long long)blockIdx.x * per;
+    return {beg + threadIdx.x, beg + per < total ? beg + per : total};
+}
+
 // The argument block of domain d alone, as the per-domain field calls build it.
 template <class S>
 __device__ __forceinline__ KArgs<S, float> batch_domain_kargs(const BatchArgs<S, float>& A, int d) {
@@ -700,14 +728,21 @@ __device__ __forceinline__ void batch_node_moments(const KArgs<S, float>& K, int
 template <class S, class O>
 __global__ void __launch_bounds__(kThreads)
     k_moments_batch(const BatchArgs<S, float> A, const long long* nodes, int parity, unsigned mask, int nf, O* out) {
-    const long long total = nodes[A.ndom];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int d = batch_domain_of(nodes, A.ndom, i);
+    const NodeRange rng = block_node_range(nodes[A.ndom]);
+    int d = -1;
+    long long dbeg = 0, dend = 0;
+    for (long long i = rng.i; i < rng.end; i += blockDim.x) {
+        if (i >= dend) {
+            d = d < 0 ? batch_domain_of(nodes, A.ndom, i) : d + 1;
+            while (nodes[d + 1] <= i) ++d;
+            dbeg = nodes[d];
+            dend = nodes[d + 1];
+        }
         const KArgs<S, float> K = batch_domain_kargs(A, d);
         // a batch domain holds at most 2^28 nodes: 32-bit index arithmetic
-        const int lid = int(i - nodes[d]), k = lid / K.G.nr, j = lid - k * K.G.nr;
+        const int lid = int(i - dbeg), k = lid / K.G.nr, j = lid - k * K.G.nr;
         const long long n = (long long)K.G.nr * K.G.nz, li = lid;
-        O* o = out + (long long)nf * nodes[d];
+        O* o = out + (long long)nf * dbeg;
         if (A.doms[d].temperature) batch_node_moments<S, true>(K, j, k, n, li, parity, mask, o);
         else batch_node_moments<S, false>(K, j, k, n, li, parity, mask, o);
     }
@@ -718,15 +753,22 @@ __global__ void __launch_bounds__(kThreads)
 template <class S, class I>
 __global__ void __launch_bounds__(kThreads) k_init_batch(const BatchArgs<S, float> A, const long long* nodes, const I* fields) {
     using R = float;
-    const long long total = nodes[A.ndom];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int d = batch_domain_of(nodes, A.ndom, i);
+    const NodeRange rng = block_node_range(nodes[A.ndom]);
+    int d = -1;
+    long long dbeg = 0, dend = 0;
+    for (long long i = rng.i; i < rng.end; i += blockDim.x) {
+        if (i >= dend) {
+            d = d < 0 ? batch_domain_of(nodes, A.ndom, i) : d + 1;
+            while (nodes[d + 1] <= i) ++d;
+            dbeg = nodes[d];
+            dend = nodes[d + 1];
+        }
         const KArgs<S, float> K = batch_domain_kargs(A, d);
         const Geom& G = K.G;
         // a batch domain holds at most 2^28 nodes: 32-bit index arithmetic
-        const int lid = int(i - nodes[d]), k = lid / G.nr, j = lid - k * G.nr;
+        const int lid = int(i - dbeg), k = lid / G.nr, j = lid - k * G.nr;
         const long long n = (long long)G.nr * G.nz, li = lid;
-        const I* fd = fields + 5 * nodes[d];
+        const I* fd = fields + 5 * dbeg;
         const R rho = R(fd[li]), ur = R(fd[n + li]), uz = R(fd[2 * n + li]);
         const R uth = R(fd[3 * n + li]), temp = R(fd[4 * n + li]);
         // rho - rho0 rounded once to FP32: for FP32 inputs the FP32 subtraction does that directly
@@ -794,7 +836,7 @@ k_batch_fold(const int* tile_start, const int* tile_index, const TileRec* tiles,
              const int* ring_start, const double* ring_part, int with_ring, double* result) {
     const int d = blockIdx.x;
     Red v{0.0, 0.0, 0.0, 0.0};
-    const int groups = tj / 32, nwarps = tk * tj / 64;
+    const int groups = tj / 32, nwarps = batch_nwarps_of(tk, tj);  // computing warps of the tile's CTA
     for (int i = tile_start[d] + threadIdx.x; i < tile_start[d + 1]; i += blockDim.x) {
         const int e = tile_index[i];
         const int tile = e / kSlots, q = e % kSlots;

@@ -8,12 +8,16 @@
 
 namespace axl {
 
-// Candidate bulk tile shapes (rows x nodes) of both parities: 512-node tiles
-// for CTAs of eight computing warps and the producer warp, two CTAs per SM.
-// Each parity's shape is timed at creation (axlbm_batch_create).
-constexpr int kBatchShapes = 2;
-constexpr int kShapeTK[kBatchShapes] = {4, 8};
-constexpr int kShapeTJ[kBatchShapes] = {128, 64};
+// Candidate bulk tile shapes (rows x nodes) of both parities, run by CTAs of
+// eight computing warps and the producer warp, two CTAs per SM: 512-node
+// tiles (one node pair per thread) for every storage, and with 16-bit
+// storage also 1024-node tiles (two pairs per thread; with FP32 storage their
+// stages would not leave room for two CTAs per SM).  Each parity's shape is
+// timed at creation (axlbm_batch_create).
+constexpr int kBatchShapes = 3;
+constexpr int kShapeTK[kBatchShapes] = {4, 8, 8};
+constexpr int kShapeTJ[kBatchShapes] = {128, 64, 128};
+inline int batch_shape_count(size_t elem) { return elem == 2 ? 3 : 2; }
 
 struct BatchTiles {
     int ntiles;

@@ -96,6 +96,9 @@ cudaError_t launch_bulk_batch(axlbm_batch* b, const BatchArgs<S, R>& A) {
 
 template <class S, class R, bool TH, int PAR, bool CHK, bool WET>
 cudaError_t launch_bulk_batch_wet(axlbm_batch* b, const BatchArgs<S, R>& A) {
+    if constexpr (sizeof(S) == 2) {
+        if (b->shape[PAR] == 2) return launch_bulk_batch<S, R, TH, PAR, CHK, 2, WET>(b, A);
+    }
     return b->shape[PAR] == 0 ? launch_bulk_batch<S, R, TH, PAR, CHK, 0, WET>(b, A)
                               : launch_bulk_batch<S, R, TH, PAR, CHK, 1, WET>(b, A);
 }

@@ -337,6 +337,36 @@ def test_results_do_not_depend_on_the_tile_shape(B):
                 assert (x is None and y is None) or np.array_equal(x, y), d
 
 
+def test_fp16_tile_shapes_give_the_same_state(B):
+    """With 16-bit storage the bulk kernel also runs 8 x 128 tiles (each
+    computing thread updates two node pairs of its column): the populations
+    and residuals equal those of the 512-node tiles bit for bit, in every
+    combination of even- and odd-step shapes."""
+    doms = mixed_batch()
+    runs = []
+    for shapes in (((4, 128), (4, 128)), ((8, 128), (8, 128)), ((8, 128), (4, 128)), ((8, 64), (8, 128))):
+        batch = B.Batch(doms, "fp16")
+        for d, pb in enumerate(doms):
+            st = seeded_state(pb, seed=170 + d)
+            batch.set_populations(d, st.f, st.g, st.h if pb.temperature else None)
+        batch.tile_shapes = shapes
+        assert batch.tile_shapes == shapes
+        batch.step(7)
+        runs.append(([batch.get_populations(d) for d in range(len(doms))], batch.residuals()))
+        batch.close()
+    pops0, res0 = runs[0]
+    for pops, res in runs[1:]:
+        assert np.array_equal(res[:, 0], res0[:, 0])
+        assert np.all(np.abs(res[:, 1:] - res0[:, 1:]) <= 1e-9 * res0[:, 1:2])  # mass and budget: summation order
+        for d in range(len(doms)):
+            for x, y in zip(pops[d], pops0[d]):
+                assert (x is None and y is None) or np.array_equal(x, y), d
+    fp32 = B.Batch(doms, "fp32")
+    with pytest.raises(B.AxlbmError):
+        fp32.tile_shape = (8, 128)  # its stages would not fit two CTAs per SM with FP32 storage
+    fp32.close()
+
+
 def test_graph_replay_matches_direct_launches(B):
     """Runs of plain steps replayed from captured CUDA graphs give the same
     populations and check values bit for bit as launching every kernel, from
