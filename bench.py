@@ -40,11 +40,11 @@ sys.path.insert(0, ROOT)
 # at capture time.  Reported as null once the source has changed.
 NCU_TRAFFIC = {
     # profiles/k_bulk_batch_fp32_sweep320_launches.md: one even and one odd launch (4 x 128 tiles)
-    "batch fp32": {"src_sha": "bb850171a9ef0d27", "dram_per_alg_byte": 0.9867},
-    # profiles/k_bulk_batch_fp16_sweep_half_full.md: full-size DRAM capture, one even and one odd launch (4 x 128)
-    "batch fp16": {"src_sha": "bb850171a9ef0d27", "dram_per_alg_byte": 0.9621},
+    "batch fp32": {"src_sha": "f7b72f9a80ea9d10", "dram_per_alg_byte": 0.9899},
+    # profiles/k_bulk_batch_fp16_sweep_half_full.md: full-size DRAM capture, one even (8 x 128) and one odd launch
+    "batch fp16": {"src_sha": "f7b72f9a80ea9d10", "dram_per_alg_byte": 0.9657},
     # profiles/k_bulk_fp32_pipe4096x8192_launches.md: one even and one odd launch (4 x 128 tiles)
-    "pipe fp32": {"src_sha": "bb850171a9ef0d27", "dram_per_alg_byte": 1.0349},
+    "pipe fp32": {"src_sha": "f7b72f9a80ea9d10", "dram_per_alg_byte": 1.0577},
 }
 
 
@@ -60,7 +60,7 @@ def parse():
     p.add_argument("--scale", type=float, default=1.0, help="batch: shrink every domain (small profiling cases)")
     p.add_argument("--tile", default=None,
                    help="batch: bulk tile shape RxN for both steps, or RxN,RxN for even and odd steps, instead "
-                        "of the timed ones (4x128 or 8x64)")
+                        "of the timed ones (4x128 or 8x64; also 8x128 with FP16 storage)")
     p.add_argument("--nr", type=int, default=4096)
     p.add_argument("--nz", type=int, default=8192)
     p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
