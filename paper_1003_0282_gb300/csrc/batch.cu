@@ -8,11 +8,11 @@
 // shelf (up to kSlots: every domain is given at least kMinCols columns), so
 // only the shelves' ragged ends are loaded without being updated.  Tiles are
 // listed row-major, so concurrently running CTAs sweep neighbouring rows
-// together (shared rows of the TMA boxes then hit L2).  Tile shapes: each
-// parity has two candidates (512-node tiles for CTAs of eight computing
-// warps; 256-node tiles in CTAs of four for FP32 odd steps); the four pairs
-// are timed on the batch at creation and the fastest kept (cached per GPU,
-// precision, mix).
+// together (shared rows of the TMA boxes then hit L2).  Tile shapes: every
+// parity has the candidates 4 x 128 and 8 x 64 (512-node tiles for CTAs of
+// eight computing warps), and with 16-bit storage also 8 x 128 (two node
+// pairs per thread); every pair of an even and an odd candidate is timed on
+// the batch at creation and the fastest kept (cached per GPU, precision, mix).
 #include <math.h>
 #include <string.h>
 
