@@ -40,11 +40,11 @@ sys.path.insert(0, ROOT)
 # at capture time.  Reported as null once the source has changed.
 NCU_TRAFFIC = {
     # profiles/k_bulk_batch_fp32_sweep320_launches.md: one even and one odd launch (4 x 128 tiles)
-    "batch fp32": {"src_sha": "22774f0639e27225", "dram_per_alg_byte": 0.9899},
+    "batch fp32": {"src_sha": "9953980fb660c4fe", "dram_per_alg_byte": 0.9899},
     # profiles/k_bulk_batch_fp16_sweep_half_full.md: full-size DRAM capture, one even (8 x 128) and one odd launch
-    "batch fp16": {"src_sha": "22774f0639e27225", "dram_per_alg_byte": 0.9657},
+    "batch fp16": {"src_sha": "9953980fb660c4fe", "dram_per_alg_byte": 0.9657},
     # profiles/k_bulk_fp32_pipe4096x8192_launches.md: one even and one odd launch (4 x 128 tiles)
-    "pipe fp32": {"src_sha": "22774f0639e27225", "dram_per_alg_byte": 1.0577},
+    "pipe fp32": {"src_sha": "9953980fb660c4fe", "dram_per_alg_byte": 1.0577},
 }
 
 

@@ -428,7 +428,8 @@ __device__ __forceinline__ void batch_nodes(const BatchArgs<S, R>& A, const Slot
 }
 
 // Persistent bulk update of every domain of the batch (even step: every
-// node; odd step: interior nodes), warp-specialised.  A lane of the producer
+// node; odd step: interior nodes and the side columns of domains with the
+// half-spacing axis and the bounce-back outer wall), warp-specialised.  A lane of the producer
 // warp stages, per tile, the population boxes (TMA), the tile record, each
 // slot's domain descriptor and its a(t) (bulk copies), all completing on the
 // stage's full barrier, and refills a stage with the tile NS ahead once every

@@ -755,8 +755,10 @@ __device__ __forceinline__ void issue_tile(const CUtensorMap* map, S* dst, uint6
     }
 }
 
-// Bulk update (persistent, warp-specialised): every node in even steps,
-// interior nodes in odd steps.  Even: plane a of a node is its own population
+// Bulk update (persistent, warp-specialised): every node in even steps; in
+// odd steps the interior nodes and, on grids with the half-spacing axis and
+// the bounce-back outer wall, the side columns below the first and above the
+// last row (the boundary ring takes the rest).  Even: plane a of a node is its own population
 // a, written back to plane opp(a) of the node.  Odd: population a comes from
 // plane opp(a) of the node x - e_a and goes to plane a of x + e_a.
 //
