@@ -77,3 +77,23 @@ def test_our_arm_has_no_cpu_path():
     assert out.returncode != 0
     assert "no CUDA device" in out.stderr
     assert not _json_lines(out.stdout)
+
+
+def test_dram_traffic_entries_describe_the_current_kernels():
+    """Each DRAM-traffic factor bench.py reports (from a committed ncu capture)
+    is tagged with the hash of the kernel sources it was measured on; a stale
+    tag would silently drop `roofline.traffic`, so every tag must match the
+    sources as they stand, and each entry must name a committed profile."""
+    sys.path.insert(0, ROOT)
+    try:
+        import bench
+    finally:
+        sys.path.remove(ROOT)
+    sha = bench.kernel_source_sha()
+    src = open(BENCH).read()
+    for key, entry in bench.NCU_TRAFFIC.items():
+        assert entry["src_sha"] == sha, (key, entry["src_sha"], sha)
+        assert 0.8 < entry["dram_per_alg_byte"] < 1.2, key
+    for name in ("k_bulk_batch_fp32_sweep320_launches.md", "k_bulk_batch_fp16_sweep_half_full.md",
+                 "k_bulk_fp32_pipe4096x8192_launches.md"):
+        assert name in src and os.path.exists(os.path.join(ROOT, "profiles", name)), name
